@@ -1,0 +1,139 @@
+"""Deterministic closed triangle meshes (vertices in metres, wavelength 1).
+
+Every generator returns ``(xyz, tri)``: ``xyz`` float64 (n_vert, 3) and
+``tri`` int32 (n_tri, 3) with counter-clockwise vertex order seen from the
+outside (outward normals), which is what an RWG discretisation of a closed
+PEC body expects.
+"""
+
+import numpy as np
+
+
+def icosphere(subdivisions: int, radius: float):
+    """Icosahedron refined ``subdivisions`` times (each triangle into four),
+    vertices projected onto the sphere of the given radius.
+
+    subdivisions=3 gives 1,280 triangles / 1,920 edges; 5 gives 20,480 / 30,720.
+    Midpoints are created in a fixed order, so the output is bit-reproducible.
+    """
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    verts = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0),
+             (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+             (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11),
+             (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6), (7, 1, 8),
+             (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9),
+             (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    v = [np.array(p, dtype=np.float64) / np.linalg.norm(p) for p in verts]
+    for _ in range(subdivisions):
+        cache = {}
+
+        def mid(a, b):
+            key = (a, b) if a < b else (b, a)
+            if key not in cache:
+                p = v[a] + v[b]
+                v.append(p / np.linalg.norm(p))
+                cache[key] = len(v) - 1
+            return cache[key]
+
+        nf = []
+        for (a, b, c) in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    xyz = np.array(v, dtype=np.float64) * radius
+    tri = np.array(faces, dtype=np.int32)
+    _orient_outward(xyz, tri)
+    return xyz, tri
+
+
+def _orient_outward(xyz, tri):
+    """Flip triangles whose normal points towards the body centroid (in place).
+    Valid for star-shaped bodies about their vertex centroid."""
+    c = xyz.mean(axis=0)
+    p0, p1, p2 = xyz[tri[:, 0]], xyz[tri[:, 1]], xyz[tri[:, 2]]
+    n = np.cross(p1 - p0, p2 - p0)
+    inward = np.einsum('ij,ij->i', n, (p0 + p1 + p2) / 3.0 - c) < 0
+    tri[inward, 1], tri[inward, 2] = tri[inward, 2].copy(), tri[inward, 1].copy()
+
+
+def box_surface(size, n):
+    """Closed surface of an axis-aligned box ``size = (sx, sy, sz)`` centred at
+    the origin, each face split into an ``n[i] x n[j]`` grid of squares, each
+    square into two triangles along a fixed diagonal."""
+    sx, sy, sz = size
+    nx, ny, nz = n
+    xs = np.linspace(-sx / 2, sx / 2, nx + 1)
+    ys = np.linspace(-sy / 2, sy / 2, ny + 1)
+    zs = np.linspace(-sz / 2, sz / 2, nz + 1)
+    index = {}
+    verts = []
+
+    def vid(p):
+        key = tuple(np.round(np.asarray(p) * 1e9).astype(np.int64))
+        if key not in index:
+            index[key] = len(verts)
+            verts.append(p)
+        return index[key]
+
+    tris = []
+
+    def face(u, w, fixed_axis, fixed_val):
+        for i in range(len(u) - 1):
+            for j in range(len(w) - 1):
+                quad = []
+                for (a, b) in ((i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)):
+                    p = [0.0, 0.0, 0.0]
+                    axes = [ax for ax in range(3) if ax != fixed_axis]
+                    p[axes[0]], p[axes[1]], p[fixed_axis] = u[a], w[b], fixed_val
+                    quad.append(vid(tuple(p)))
+                tris.append((quad[0], quad[1], quad[2]))
+                tris.append((quad[0], quad[2], quad[3]))
+
+    face(ys, zs, 0, -sx / 2), face(ys, zs, 0, sx / 2)
+    face(xs, zs, 1, -sy / 2), face(xs, zs, 1, sy / 2)
+    face(xs, ys, 2, -sz / 2), face(xs, ys, 2, sz / 2)
+    xyz = np.array(verts, dtype=np.float64)
+    tri = np.array(tris, dtype=np.int32)
+    _orient_outward(xyz, tri)
+    return xyz, tri
+
+
+def closed_cylinder(radius, height, n_around, n_along, n_rings):
+    """Closed circular cylinder along z (side wall plus two flat caps made of
+    concentric rings), centred at the origin."""
+    verts = []
+    tris = []
+    ang = 2 * np.pi * np.arange(n_around) / n_around
+    zs = np.linspace(-height / 2, height / 2, n_along + 1)
+    side = np.zeros((n_along + 1, n_around), dtype=np.int64)
+    for i, z in enumerate(zs):
+        for j, a in enumerate(ang):
+            side[i, j] = len(verts)
+            verts.append((radius * np.cos(a), radius * np.sin(a), z))
+    for i in range(n_along):
+        for j in range(n_around):
+            j1 = (j + 1) % n_around
+            tris.append((side[i, j], side[i, j1], side[i + 1, j1]))
+            tris.append((side[i, j], side[i + 1, j1], side[i + 1, j]))
+    for ring_row, z in ((0, zs[0]), (n_along, zs[-1])):
+        outer = side[ring_row]
+        for r in range(n_rings - 1, 0, -1):
+            rr = radius * r / n_rings
+            inner = []
+            for a in ang:
+                inner.append(len(verts))
+                verts.append((rr * np.cos(a), rr * np.sin(a), z))
+            for j in range(n_around):
+                j1 = (j + 1) % n_around
+                tris.append((outer[j], outer[j1], inner[j1]))
+                tris.append((outer[j], inner[j1], inner[j]))
+            outer = inner
+        centre = len(verts)
+        verts.append((0.0, 0.0, z))
+        for j in range(n_around):
+            tris.append((outer[j], outer[(j + 1) % n_around], centre))
+    xyz = np.array(verts, dtype=np.float64)
+    tri = np.array(tris, dtype=np.int32)
+    _orient_outward(xyz, tri)
+    return xyz, tri
