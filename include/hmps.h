@@ -1,0 +1,234 @@
+/*
+ * hmps.h — C ABI of the GB300 (sm_103a) multi-level power-series solver for
+ * surface EFIE H-Matrices (arxiv 2307.03968, "Multi-Level Power Series
+ * Solution for Large Surface and Volume Electric Field Integral Equation").
+ *
+ * Problem (paper §II eq. 5, §III eq. 6): Z x = b with Z = Z_N + Z_F, the
+ * Galerkin RWG discretisation of the S-EFIE (eq. 3) of a closed PEC surface,
+ * Z_N dense near-field leaf blocks and Z_F low-rank far-field blocks U V
+ * grouped by tree level (eq. 8).  The solve (§IV eqs. 12-22) applies the leaf
+ * self-block inverses D^{-1} and a fixed number K of power-series terms of
+ * the H-Matrix product, level by level from the leaf level.
+ *
+ * Conventions used by every call
+ *  - Unknowns are RWG functions numbered in the ORIGINAL order: interior edges
+ *    of the triangle mesh sorted by (smaller vertex id, larger vertex id); T+ is
+ *    the triangle with the lower index.  The tree permutation is internal.
+ *  - Vectors are column-major N x nrhs arrays of interleaved complex numbers:
+ *    complex64 (float re, float im) unless a call says otherwise; leading
+ *    dimension ld >= N counted in complex elements.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work is
+ *    stream ordered; calls return after enqueueing unless they say they
+ *    synchronise.
+ *  - Ownership: an hm_matrix owns all device memory of one operator and its
+ *    workspaces; caller buffers are never retained after a call returns.
+ *  - Errors: every call returns an hm_status.  Argument and state errors are
+ *    detected on the host and returned before any work is enqueued.  Errors
+ *    found on the device (singular leaf block, non-finite values, wait
+ *    time-outs) are recorded in the handle's device status word and returned
+ *    by hm_sync_status() (which synchronises the stream) and by the next call
+ *    that synchronises.  hm_last_error() gives a message for the last failing
+ *    call of the calling thread.
+ *  - One handle must not be used concurrently from several host threads.
+ */
+#ifndef HMPS_H
+#define HMPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_matrix_s *hm_matrix;
+
+typedef enum {
+    HM_OK = 0,
+    HM_ERR_ARG = 1,       /* invalid argument (null pointer, size, option) */
+    HM_ERR_OOM = 2,       /* device or pinned host allocation failed */
+    HM_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    HM_ERR_STATE = 4,     /* call out of order (e.g. solve before hm_factor_leaf) */
+    HM_ERR_SINGULAR = 5,  /* a leaf self block has a zero pivot (hm_factor_leaf) */
+    HM_ERR_DIVERGED = 6,  /* non-finite values in a solve result */
+    HM_ERR_TIMEOUT = 7    /* a bounded device wait gave up */
+} hm_status;
+
+/* ---------------------------------------------------------------- build --- */
+
+/* Triangle mesh of a closed PEC surface (paper §II: RWG basis, S-EFIE). */
+typedef struct {
+    int64_t n_vert;
+    const double *xyz;      /* host, 3*n_vert, metres */
+    int64_t n_tri;
+    const int32_t *tri;     /* host, 3*n_tri vertex ids, outward normals (CCW) */
+    double wavelength;      /* metres; k = 2 pi / wavelength, eta = 376.73 ohm */
+} hm_mesh;
+
+/* Tree, admissibility (eq. 7) and compression (§III) options. */
+typedef struct {
+    int leaf_size;     /* split clusters until every leaf holds <= leaf_size unknowns */
+    int arity;         /* 2 = binary tree (the paper's runs), 4, or 8 = octree */
+    double adm;        /* c in dist(t,s) >= c * min(diam t, diam s); the paper's
+                          eta = 1 is c = 1, the 2-diameter rule is c = 2 */
+    double aca_tol;    /* relative Frobenius tolerance of ACA and of re-compression */
+    int levels;        /* far-field levels to compute: 1 = leaf level only (the
+                          paper's runs skip the coarser levels), -1 = all */
+    int keep_fp64;     /* also keep a complex128 copy of every block (for the
+                          plain FP64 solve path) */
+} hm_build_opts;
+
+/*
+ * Build the H-Matrix of `mesh` on the GPU: RWG basis, cluster tree, eq. 7
+ * partition, near-field fill and ACA + re-compression of the far blocks, all
+ * on the device (§III).  Synchronises `stream` before returning.
+ */
+hm_status hm_build(const hm_mesh *mesh, const hm_build_opts *opts, void *stream, hm_matrix *out);
+
+/*
+ * Import an H-Matrix given as explicit blocks (complex128, host memory), e.g.
+ * one assembled by another program, so that solves of the same operator can be
+ * compared.  Layout (all host pointers, read during the call only):
+ *   perm[N]                    tree position p -> original unknown perm[p]
+ *   leaf_off[n_leaves+1]       leaf i covers tree positions [leaf_off[i], leaf_off[i+1])
+ *   self[]                     leaf self blocks D_i, row-major n_i x n_i, concatenated
+ *   near: n_near pairs         rows [near_row0[b], +near_m[b]), cols [near_col0[b], +near_n[b]),
+ *                              values near_vals (row-major m x n, concatenated);
+ *                              the row block must lie before the column block (half storage:
+ *                              the mirrored block is the transpose)
+ *   far:  n_far blocks         level far_level[b] (1 = leaf level, counted upward), rows/cols as
+ *                              for near, rank far_rank[b]; far_u = U (m x k, row-major),
+ *                              far_v = V (k x n, row-major), concatenated; block ~ U V
+ * Blocks of any level are accepted; hm_build_opts is not used.
+ */
+typedef struct {
+    int64_t n;
+    const int64_t *perm;
+    int64_t n_leaves;
+    const int64_t *leaf_off;
+    const double *self;             /* complex128 interleaved */
+    int64_t n_near;
+    const int64_t *near_row0, *near_col0;
+    const int32_t *near_m, *near_n;
+    const double *near_vals;        /* complex128 interleaved */
+    int64_t n_far;
+    const int32_t *far_level;
+    const int64_t *far_row0, *far_col0;
+    const int32_t *far_m, *far_n, *far_rank;
+    const double *far_u, *far_v;    /* complex128 interleaved */
+    int keep_fp64;
+} hm_blocks;
+
+hm_status hm_build_from_blocks(const hm_blocks *blocks, void *stream, hm_matrix *out);
+
+/* --------------------------------------------------------------- factor --- */
+
+/*
+ * Factor the leaf self blocks (paper eq. 12, [Z~_N]^{-1}): FP64 Gauss-Jordan
+ * with partial pivoting on the device, one block per CTA; the explicit inverse
+ * is kept in complex64 (and complex128 with keep_fp64).  Synchronises; returns
+ * HM_ERR_SINGULAR if a pivot is exactly zero.
+ */
+hm_status hm_factor_leaf(hm_matrix h, void *stream);
+
+/* ---------------------------------------------------------------- solve --- */
+
+typedef struct {
+    int n_terms;   /* K: power-series terms (applications of the level operator),
+                      the paper's "two fixed iterations" is 2 */
+    int n_levels;  /* m: 1 = leaf level only (the paper's runs), -1 = all levels */
+    int nested;    /* 1 = literal nested form of eq. 19 (each level's operator is
+                      preconditioned by the full lower-level series),
+                      0 = flat form S_K(D^{-1}(A_m - D)) D^{-1} (identical for m = 1) */
+    int refine;    /* 1 = one refinement step: r = b - A_m x with FP64 accumulation,
+                      x += (same series)(r) */
+    int fp64;      /* 1 = plain FP64 path: b, x are complex128 and the operator's
+                      complex128 copy is used (needs keep_fp64) */
+} hm_solve_opts;
+
+typedef struct {
+    double rel_residual;     /* |b - A_m x| / |b| (max over columns), FP64; only if refine */
+    int levels_used;         /* m after clamping to the levels present */
+    int64_t bytes_streamed;  /* algorithmic operator + vector bytes of this solve */
+    int64_t kernel_launches; /* kernels enqueued by this call */
+} hm_solve_info;
+
+/*
+ * x = power-series solution of A_m x = b (paper eq. 19 with the fixed-term
+ * series of §IV).  b, x: DEVICE pointers, nrhs columns.  b is not modified;
+ * b and x must not overlap.  `info` may be NULL; when given, the call
+ * synchronises and fills it.
+ */
+hm_status hm_powerseries_solve(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx,
+                               int nrhs, const hm_solve_opts *opts, void *stream, hm_solve_info *info);
+
+/*
+ * Same as hm_powerseries_solve with HOST buffers b and x (any host memory):
+ * copies b to the device through pinned staging, solves, copies x back, and
+ * synchronises before returning.
+ */
+hm_status hm_powerseries_solve_host(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx,
+                                    int nrhs, const hm_solve_opts *opts, void *stream);
+
+/*
+ * y = A_m x (the H-Matrix product of §IV, "the solution process only depends
+ * on the matrix-vector product"), x, y DEVICE complex64, original order.
+ * n_levels as in hm_solve_opts.  fp64_accumulate = 1 accumulates in FP64.
+ */
+hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy, int nrhs,
+                   int n_levels, int fp64_accumulate, void *stream);
+
+/* ---------------------------------------------------------- inspection --- */
+
+typedef struct {
+    int64_t n;               /* unknowns */
+    int64_t n_leaves;
+    int depth;               /* tree depth L (root = 0) */
+    int n_levels;            /* far-field levels present (1 = leaf level only) */
+    int64_t n_near;          /* stored (half) near blocks */
+    int64_t n_far[16];       /* stored far blocks per level (index 0 = level 1) */
+    int64_t near_elems;      /* complex elements of the near blocks */
+    int64_t far_elems[16];   /* complex elements k (m + n) per level */
+    int64_t self_elems;      /* sum n_i^2 */
+    int max_rank;
+    int factored;
+    int has_fp64;
+    int64_t device_bytes;    /* device memory held by the handle */
+} hm_info;
+
+hm_status hm_get_info(hm_matrix h, hm_info *info);
+
+/* Tree permutation (tree position -> original unknown), host int64[n]. */
+hm_status hm_get_perm(hm_matrix h, int64_t *perm);
+
+/* Leaf offsets, host int64[n_leaves + 1]. */
+hm_status hm_get_leaves(hm_matrix h, int64_t *leaf_off);
+
+/*
+ * Block list of level `level` (1 = leaf level; level 1 lists the near blocks
+ * first, rank 0), host arrays of length count (query count with NULL arrays):
+ * row0, col0 (tree positions), m, n, rank.
+ */
+hm_status hm_get_blocks(hm_matrix h, int level, int64_t *count, int64_t *row0, int64_t *col0,
+                        int32_t *m, int32_t *n, int32_t *rank);
+
+/*
+ * Copy one stored block to host complex128 memory: dense blocks as row-major
+ * m x n into `a` (b unused); low-rank blocks as U (m x k row-major) into `a`
+ * and V (k x n row-major) into `b`.  index as in hm_get_blocks.
+ */
+hm_status hm_get_block(hm_matrix h, int level, int64_t index, double *a, double *b);
+
+/* Device status word: synchronises `stream`, returns and clears the first
+ * device-side error recorded since the last call. */
+hm_status hm_sync_status(hm_matrix h, void *stream);
+
+int64_t hm_size(hm_matrix h);
+void hm_destroy(hm_matrix h);
+const char *hm_last_error(void);
+const char *hm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMPS_H */

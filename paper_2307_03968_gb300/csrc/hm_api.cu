@@ -1,0 +1,768 @@
+// C ABI of the hmps library: handle management, block import, leaf
+// factorisation, the multi-level power-series solve (arxiv 2307.03968 §IV,
+// eqs. 12-22) and the H-Matrix product.  The numerical work runs in the
+// kernels of k_solve.cu / k_factor.cu / k_build.cu; this file only checks
+// arguments, lays out device memory and enqueues kernels.
+#include "hm_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+namespace hm {
+
+static thread_local std::string g_last_error;
+
+hm_status fail(hm_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+hm_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? HM_ERR_OOM : HM_ERR_CUDA;
+}
+
+hm_status dev_alloc(hm_matrix h, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    h->device_bytes += (int64_t)bytes;
+    return HM_OK;
+}
+
+template <class T> static hm_status upload(hm_matrix h, T **dst, const std::vector<T> &src, cudaStream_t s)
+{
+    hm_status st = dev_alloc(h, (void **)dst, src.size() * sizeof(T));
+    if (st != HM_OK) return st;
+    if (!src.empty()) HM_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return HM_OK;
+}
+
+static void free_handle(hm_matrix h)
+{
+    if (!h) return;
+    void *ptrs[] = {h->d_pperm, h->d_pleaf_off, h->d_dinv_off, h->d_leaf_n, h->d_self_off, h->d_bad_leaf,
+                    h->d_self64, h->d_self32, h->d_dinv32, h->d_dinv64, h->d_pool32, h->d_pool64, h->d_status,
+                    h->ws.d_acc64, h->ws.d_io};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &kv : h->levels)
+        if (kv.second.d_items) cudaFree(kv.second.d_items);
+    for (void *p : h->ws.vec32) if (p) cudaFree(p);
+    for (void *p : h->ws.vec64) if (p) cudaFree(p);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->ws.h_pinned) cudaFreeHost(h->ws.h_pinned);
+    delete h;
+}
+
+// Padded layout from perm / leaf_off; allocates the per-leaf arrays and the
+// status word.  Called by every constructor once perm and leaf_off are set.
+hm_status finalize_layout(hm_matrix h, cudaStream_t s)
+{
+    const int64_t L = h->n_leaves;
+    h->pleaf_off.assign(L + 1, 0);
+    for (int64_t i = 0; i < L; ++i) h->pleaf_off[i + 1] = h->pleaf_off[i] + even(h->leaf_off[i + 1] - h->leaf_off[i]);
+    h->pN = h->pleaf_off[L];
+    h->h_pperm.assign(h->pN, -1);
+    for (int64_t i = 0; i < L; ++i)
+        for (int64_t p = h->leaf_off[i]; p < h->leaf_off[i + 1]; ++p)
+            h->h_pperm[h->pleaf_off[i] + (p - h->leaf_off[i])] = (int32_t)h->perm[p];
+    h->dinv_off.assign(L, 0);
+    h->self_off.assign(L, 0);
+    int64_t doff = 0, soff = 0;
+    std::vector<int64_t> leaf_n(L);
+    for (int64_t i = 0; i < L; ++i) {
+        const int64_t n = h->leaf_off[i + 1] - h->leaf_off[i], np = even(n);
+        leaf_n[i] = n;
+        h->dinv_off[i] = doff;
+        h->self_off[i] = soff;
+        doff += np * np;
+        soff += n * n;
+    }
+    h->dinv_elems = doff;
+    h->self_elems = soff;
+    std::vector<int32_t> pl(h->pleaf_off.begin(), h->pleaf_off.end());
+    hm_status st;
+    if ((st = upload(h, &h->d_pperm, h->h_pperm, s)) != HM_OK) return st;
+    if ((st = upload(h, &h->d_pleaf_off, pl, s)) != HM_OK) return st;
+    if ((st = upload(h, &h->d_dinv_off, h->dinv_off, s)) != HM_OK) return st;
+    if ((st = upload(h, &h->d_self_off, h->self_off, s)) != HM_OK) return st;
+    if ((st = upload(h, &h->d_leaf_n, leaf_n, s)) != HM_OK) return st;
+    if ((st = dev_alloc(h, (void **)&h->d_bad_leaf, sizeof(int))) != HM_OK) return st;
+    if ((st = dev_alloc(h, (void **)&h->d_status, sizeof(int))) != HM_OK) return st;
+    HM_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
+    HM_CUDA(cudaMemsetAsync(h->d_bad_leaf, 0xff, sizeof(int), s));
+    HM_CUDA(cudaMallocHost((void **)&h->h_status, sizeof(int)));
+    if ((st = dev_alloc(h, (void **)&h->d_dinv32, sizeof(float2) * h->dinv_elems)) != HM_OK) return st;
+    if ((st = dev_alloc(h, (void **)&h->d_self32, sizeof(float2) * h->dinv_elems)) != HM_OK) return st;
+    if (h->has_fp64)
+        if ((st = dev_alloc(h, (void **)&h->d_dinv64, sizeof(double2) * h->dinv_elems)) != HM_OK) return st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    return HM_OK;
+}
+
+// ---- solve orchestration ----------------------------------------------------------
+
+struct SolveCtx {
+    hm_matrix h;
+    int nrhs, K, m;
+    bool fp64;
+    cudaStream_t s;
+    int64_t launches = 0;
+    int64_t bytes = 0;
+    size_t vbytes;   // bytes of one [nrhs][pN] vector
+    std::vector<void *> Y, X, Z, W;  // per level 0..m
+};
+
+static size_t elem_size(bool fp64) { return fp64 ? sizeof(double2) : sizeof(float2); }
+
+static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
+{
+    hm::Workspace &ws = h->ws;
+    const size_t need_vecs = 4 * (size_t)(m + 1) + 8;
+    if (ws.nrhs >= nrhs && ws.vec32.size() >= need_vecs && (!h->has_fp64 || ws.vec64.size() >= need_vecs))
+        return HM_OK;
+    for (void *p : ws.vec32) if (p) cudaFree(p);
+    for (void *p : ws.vec64) if (p) cudaFree(p);
+    if (ws.d_acc64) cudaFree(ws.d_acc64);
+    ws.vec32.clear(); ws.vec64.clear(); ws.d_acc64 = nullptr;
+    const int r = std::max(nrhs, ws.nrhs);
+    const size_t n32 = sizeof(float2) * h->pN * r, n64 = sizeof(double2) * h->pN * r;
+    for (size_t i = 0; i < need_vecs; ++i) {
+        void *p = nullptr;
+        HM_CUDA(cudaMalloc(&p, n32));
+        HM_CUDA(cudaMemset(p, 0, n32));
+        ws.vec32.push_back(p);
+        if (h->has_fp64) {
+            HM_CUDA(cudaMalloc(&p, n64));
+            HM_CUDA(cudaMemset(p, 0, n64));
+            ws.vec64.push_back(p);
+        }
+    }
+    HM_CUDA(cudaMalloc((void **)&ws.d_acc64, n64 + 2 * sizeof(double) * r));
+    ws.nrhs = r;
+    return HM_OK;
+}
+
+static int64_t level_bytes(hm_matrix h, int lev, bool fp64)
+{
+    auto it = h->levels.find(lev);
+    return it == h->levels.end() ? 0 : it->second.elems * (int64_t)elem_size(fp64);
+}
+
+// z (zeroed) += M_lev x
+static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
+{
+    auto it = c.h->levels.find(lev);
+    if (it == c.h->levels.end() || it->second.items.empty()) return;
+    launch_apply_items(c.h, it->second, x, z, c.nrhs, c.fp64, c.s);
+    c.launches++;
+    c.bytes += level_bytes(c.h, lev, c.fp64) * c.nrhs;
+}
+
+static void leaf_update(SolveCtx &c, const void *y, void *zin, void *out, bool zero_in)
+{
+    launch_leaf_update(c.h, y, zin, out, c.nrhs, zero_in, c.fp64, c.s);
+    c.launches++;
+    c.bytes += c.h->dinv_elems * (int64_t)elem_size(c.fp64) + 3 * (int64_t)c.vbytes;
+}
+
+static void copy_vec(SolveCtx &c, void *dst, const void *src)
+{
+    cudaMemcpyAsync(dst, src, c.vbytes, cudaMemcpyDeviceToDevice, c.s);
+}
+
+// P_level(r) -> out (eq. 19 nested recursion); out must not alias r.
+// Invariant: Z[1] is all zero on entry and on exit.
+static void P(SolveCtx &c, int level, const void *r, void *out)
+{
+    if (level == 0) {
+        leaf_update(c, nullptr, const_cast<void *>(r), out, false);
+        return;
+    }
+    if (level == 1) {
+        void *Y = c.Y[1], *X = c.X[1], *Z = c.Z[1];
+        leaf_update(c, nullptr, const_cast<void *>(r), Y, false);     // y = D^{-1} r
+        const void *cur = Y;
+        for (int j = 1; j <= c.K; ++j) {
+            apply_level(c, 1, cur, Z);                                 // z = M_1 x_{j-1}
+            void *dst = (j == c.K) ? out : X;
+            leaf_update(c, Y, Z, dst, true);                           // x_j = y - D^{-1} z
+            cur = dst;
+        }
+        if (c.K == 0) copy_vec(c, out, Y);
+        return;
+    }
+    void *Y = c.Y[level], *X = c.X[level], *Z = c.Z[level], *W = c.W[level];
+    P(c, level - 1, r, Y);                                              // y = P_{m-1}(r)
+    const void *cur = Y;
+    for (int j = 1; j <= c.K; ++j) {
+        cudaMemsetAsync(Z, 0, c.vbytes, c.s);
+        apply_level(c, level, cur, Z);                                  // z = M_m x
+        P(c, level - 1, Z, W);                                          // w = P_{m-1}(z)
+        void *dst = (j == c.K) ? out : X;
+        launch_sub(Y, W, dst, c.h->pN * c.nrhs, c.fp64, c.s);           // x = y - w
+        c.launches++;
+        cur = dst;
+    }
+    if (c.K == 0) copy_vec(c, out, Y);
+}
+
+// Flat form: x = S_K(D^{-1}(A_m - D)) D^{-1} r
+static void Pflat(SolveCtx &c, const void *r, void *out)
+{
+    void *Y = c.Y[1], *X = c.X[1], *Z = c.Z[1];
+    leaf_update(c, nullptr, const_cast<void *>(r), Y, false);
+    const void *cur = Y;
+    for (int j = 1; j <= c.K; ++j) {
+        for (int lev = 1; lev <= c.m; ++lev) apply_level(c, lev, cur, Z);
+        void *dst = (j == c.K) ? out : X;
+        leaf_update(c, Y, Z, dst, true);
+        cur = dst;
+    }
+    if (c.K == 0) copy_vec(c, out, Y);
+}
+
+static int clamp_levels(hm_matrix h, int n_levels)
+{
+    int m = (n_levels < 0 || n_levels > h->n_levels) ? h->n_levels : n_levels;
+    return std::max(m, 1);
+}
+
+// acc (double2, zeroed here) = A_m x over complex64 blocks with FP64 accumulation
+static void apply_acc64(SolveCtx &c, const float2 *xt, double2 *acc)
+{
+    cudaMemsetAsync(acc, 0, sizeof(double2) * c.h->pN * c.nrhs, c.s);
+    launch_apply_self_acc64(c.h, xt, acc, c.nrhs, c.s);
+    c.launches++;
+    for (int lev = 1; lev <= c.m; ++lev) {
+        auto it = c.h->levels.find(lev);
+        if (it == c.h->levels.end() || it->second.items.empty()) continue;
+        launch_apply_items_acc64(c.h, it->second, xt, acc, c.nrhs, c.s);
+        c.launches++;
+    }
+}
+
+static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx, int nrhs,
+                              const hm_solve_opts *o, cudaStream_t s, hm_solve_info *info)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    if (!o) return fail(HM_ERR_ARG, "null opts");
+    if (nrhs < 0) return fail(HM_ERR_ARG, "nrhs < 0");
+    if (nrhs == 0) {
+        if (info) { memset(info, 0, sizeof(*info)); info->levels_used = clamp_levels(h, o->n_levels); }
+        return HM_OK;
+    }
+    if (!b || !x) return fail(HM_ERR_ARG, "null b or x");
+    if (ldb < h->N || ldx < h->N) return fail(HM_ERR_ARG, "leading dimension < N");
+    if (o->n_terms < 0 || o->n_terms > 64) return fail(HM_ERR_ARG, "n_terms out of range [0, 64]");
+    if (!h->factored) return fail(HM_ERR_STATE, "hm_factor_leaf has not completed on this handle");
+    if (o->fp64 && !h->has_fp64) return fail(HM_ERR_STATE, "fp64 solve needs an operator built with keep_fp64");
+    if (o->fp64 && o->refine) return fail(HM_ERR_ARG, "refine applies to the complex64 path only");
+    const size_t es = elem_size(o->fp64);
+    {
+        const char *bb = (const char *)b, *xx = (const char *)x;
+        const size_t bl = es * (size_t)ldb * nrhs, xl = es * (size_t)ldx * nrhs;
+        if (nrhs > 0 && bb < xx + xl && xx < bb + bl) return fail(HM_ERR_ARG, "b and x overlap");
+    }
+    SolveCtx c;
+    c.h = h; c.nrhs = nrhs; c.K = o->n_terms; c.fp64 = o->fp64 != 0; c.s = s;
+    c.m = clamp_levels(h, o->n_levels);
+    c.vbytes = es * h->pN * nrhs;
+    hm_status st = ensure_workspace(h, nrhs, c.m);
+    if (st != HM_OK) return st;
+    std::vector<void *> &V = c.fp64 ? h->ws.vec64 : h->ws.vec32;
+    size_t vi = 0;
+    c.Y.assign(c.m + 1, nullptr); c.X = c.Y; c.Z = c.Y; c.W = c.Y;
+    for (int l = 1; l <= c.m; ++l) { c.Y[l] = V[vi++]; c.X[l] = V[vi++]; c.Z[l] = V[vi++]; c.W[l] = V[vi++]; }
+    void *bt = V[vi++], *xt = V[vi++], *rt = V[vi++], *dx = V[vi++];
+    launch_permute_in(b, ldb, bt, h->pN, h->d_pperm, nrhs, c.fp64, s);
+    c.launches++;
+    if (o->nested) P(c, c.m, bt, xt);
+    else Pflat(c, bt, xt);
+    double *norms = nullptr;
+    if (o->refine) {
+        double2 *acc = (double2 *)h->ws.d_acc64;
+        norms = (double *)(acc + h->pN * nrhs);
+        apply_acc64(c, (const float2 *)xt, acc);
+        cudaMemsetAsync(norms, 0, 2 * sizeof(double) * nrhs, s);
+        launch_residual((const float2 *)bt, acc, (float2 *)rt, norms, h->pN, nrhs, s);
+        c.launches++;
+        if (o->nested) P(c, c.m, rt, dx);
+        else Pflat(c, rt, dx);
+        launch_add_inplace(xt, dx, h->pN * nrhs, false, s);
+        c.launches++;
+        if (info) {   // residual of the refined solution
+            apply_acc64(c, (const float2 *)xt, acc);
+            cudaMemsetAsync(norms, 0, 2 * sizeof(double) * nrhs, s);
+            launch_residual((const float2 *)bt, acc, (float2 *)rt, norms, h->pN, nrhs, s);
+            c.launches++;
+        }
+    }
+    launch_check_finite(xt, h->pN * nrhs, c.fp64, h->d_status, s);
+    c.launches++;
+    launch_permute_out(xt, h->pN, x, ldx, h->d_pperm, nrhs, c.fp64, s);
+    c.launches++;
+    HM_CUDA(cudaGetLastError());
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->levels_used = c.m;
+        info->kernel_launches = c.launches;
+        info->bytes_streamed = c.bytes;
+        HM_CUDA(cudaStreamSynchronize(s));
+        if (norms) {
+            std::vector<double> hn(2 * nrhs);
+            HM_CUDA(cudaMemcpy(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            double worst = 0.0;
+            for (int r = 0; r < nrhs; ++r)
+                worst = std::max(worst, hn[2 * r + 1] > 0 ? std::sqrt(hn[2 * r] / hn[2 * r + 1]) : 0.0);
+            info->rel_residual = worst;
+        }
+        int stv = 0;
+        HM_CUDA(cudaMemcpy(&stv, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (stv != 0) {
+            cudaMemset(h->d_status, 0, sizeof(int));
+            return fail((hm_status)stv, "device reported non-finite values in the solution");
+        }
+    }
+    return HM_OK;
+}
+
+} // namespace hm
+
+using namespace hm;
+
+// ---- import of explicit blocks ---------------------------------------------------------
+
+static hm_status import_blocks(const hm_blocks *B, cudaStream_t s, hm_matrix h)
+{
+    const int64_t N = B->n;
+    h->N = N;
+    h->perm.assign(B->perm, B->perm + N);
+    {
+        std::vector<char> seen(N, 0);
+        for (int64_t p = 0; p < N; ++p) {
+            const int64_t v = h->perm[p];
+            if (v < 0 || v >= N || seen[v]) return fail(HM_ERR_ARG, "perm is not a permutation of 0..n-1");
+            seen[v] = 1;
+        }
+    }
+    if (B->n_leaves < 1) return fail(HM_ERR_ARG, "n_leaves < 1");
+    h->n_leaves = B->n_leaves;
+    h->leaf_off.assign(B->leaf_off, B->leaf_off + B->n_leaves + 1);
+    if (h->leaf_off[0] != 0 || h->leaf_off[h->n_leaves] != N) return fail(HM_ERR_ARG, "leaf_off must run from 0 to n");
+    for (int64_t i = 0; i < h->n_leaves; ++i) {
+        const int64_t n = h->leaf_off[i + 1] - h->leaf_off[i];
+        if (n < 1) return fail(HM_ERR_ARG, "empty leaf");
+        if (n > factor_max_leaf()) return fail(HM_ERR_ARG, "leaf larger than the device factorisation supports (112)");
+    }
+    h->has_fp64 = B->keep_fp64 != 0;
+    hm_status st = finalize_layout(h, s);
+    if (st != HM_OK) return st;
+    // leaf index of each tree position, and leaf start lookup
+    std::vector<int64_t> leaf_of(N);
+    std::map<int64_t, int64_t> leaf_start, leaf_end;
+    for (int64_t i = 0; i < h->n_leaves; ++i) {
+        for (int64_t p = h->leaf_off[i]; p < h->leaf_off[i + 1]; ++p) leaf_of[p] = i;
+        leaf_start[h->leaf_off[i]] = i;
+        leaf_end[h->leaf_off[i + 1]] = i;
+    }
+    auto cluster = [&](int64_t r0, int64_t m, int64_t &pr0, int64_t &pm) -> bool {
+        if (m < 1 || r0 < 0 || r0 + m > N) return false;
+        auto a = leaf_start.find(r0);
+        auto b = leaf_end.find(r0 + m);
+        if (a == leaf_start.end() || b == leaf_end.end()) return false;
+        pr0 = h->pleaf_off[a->second];
+        pm = h->pleaf_off[b->second + 1] - pr0;
+        return true;
+    };
+    auto ppos = [&](int64_t p) { const int64_t l = leaf_of[p]; return h->pleaf_off[l] + (p - h->leaf_off[l]); };
+
+    // self blocks
+    std::vector<double2> self64(h->self_elems);
+    std::memcpy(self64.data(), B->self, sizeof(double2) * h->self_elems);
+    if ((st = upload(h, &h->d_self64, self64, s)) != HM_OK) return st;
+
+    // items and pool layout
+    struct Pending { int level; Item it; int64_t src; int32_t tm, tn; int64_t trow0, tcol0; };
+    std::vector<Pending> pend;
+    int64_t pool = 0;
+    int64_t nsrc = 0;
+    for (int64_t b = 0; b < B->n_near; ++b) {
+        const int64_t r0 = B->near_row0[b], c0 = B->near_col0[b];
+        const int64_t m = B->near_m[b], n = B->near_n[b];
+        if (r0 < 0 || c0 < 0 || r0 + m > N || c0 + n > N || m < 1 || n < 1)
+            return fail(HM_ERR_ARG, "near block out of range");
+        if (leaf_start.count(r0) == 0 || leaf_of[r0 + m - 1] != leaf_of[r0] || leaf_end.count(r0 + m) == 0 ||
+            leaf_start.count(c0) == 0 || leaf_end.count(c0 + n) == 0 || leaf_of[c0 + n - 1] != leaf_of[c0])
+            return fail(HM_ERR_ARG, "near blocks must couple two whole leaves");
+        if (r0 + m > c0) return fail(HM_ERR_ARG, "near block rows must lie before its columns (half storage)");
+        Item it{};
+        it.off = pool; it.row0 = (int32_t)ppos(r0); it.col0 = (int32_t)ppos(c0);
+        it.m = (int32_t)m; it.n = (int32_t)n; it.k = 0;
+        pool += item_elems(it);
+        pend.push_back({1, it, nsrc, (int32_t)m, (int32_t)n, r0, c0});
+        nsrc += m * n;
+    }
+    int64_t usrc = 0;
+    int max_level = 1, max_rank = 0;
+    std::vector<int64_t> far_src(B->n_far);
+    for (int64_t b = 0; b < B->n_far; ++b) {
+        const int lev = B->far_level[b];
+        const int64_t r0 = B->far_row0[b], c0 = B->far_col0[b];
+        const int64_t m = B->far_m[b], n = B->far_n[b], k = B->far_rank[b];
+        if (lev < 1 || lev > 16) return fail(HM_ERR_ARG, "far level out of range [1, 16]");
+        if (k < 1 || k > 4096) return fail(HM_ERR_ARG, "far rank out of range");
+        int64_t pr0, pm, pc0, pn;
+        if (!cluster(r0, m, pr0, pm) || !cluster(c0, n, pc0, pn))
+            return fail(HM_ERR_ARG, "far block rows/cols must be unions of whole leaves");
+        if (r0 + m > c0) return fail(HM_ERR_ARG, "far block rows must lie before its columns (half storage)");
+        Item it{};
+        it.off = pool; it.row0 = (int32_t)pr0; it.col0 = (int32_t)pc0;
+        it.m = (int32_t)pm; it.n = (int32_t)pn; it.k = (int32_t)k;
+        pool += item_elems(it);
+        far_src[b] = usrc;
+        pend.push_back({lev, it, b, (int32_t)m, (int32_t)n, r0, c0});
+        usrc += k * (m + n);
+        max_level = std::max(max_level, lev);
+        max_rank = std::max<int>(max_rank, (int)k);
+    }
+    h->pool_elems = pool;
+    h->n_levels = max_level;
+    h->max_rank = max_rank;
+    // fill host pools
+    std::vector<float2> p32(pool, make_float2(0.f, 0.f));
+    std::vector<double2> p64;
+    if (h->has_fp64) p64.assign(pool, make_double2(0.0, 0.0));
+    const double2 *nv = reinterpret_cast<const double2 *>(B->near_vals);
+    const double2 *fu = reinterpret_cast<const double2 *>(B->far_u);
+    const double2 *fv = reinterpret_cast<const double2 *>(B->far_v);
+    int64_t uo = 0, vo = 0;   // running offsets into far_u / far_v
+    std::vector<int64_t> uoff(B->n_far), voff(B->n_far);
+    for (int64_t b = 0; b < B->n_far; ++b) {
+        uoff[b] = uo; voff[b] = vo;
+        uo += (int64_t)B->far_m[b] * B->far_rank[b];
+        vo += (int64_t)B->far_rank[b] * B->far_n[b];
+    }
+    auto put = [&](int64_t dst, double2 v) {
+        p32[dst] = make_float2((float)v.x, (float)v.y);
+        if (h->has_fp64) p64[dst] = v;
+    };
+    for (const Pending &pd : pend) {
+        const Item &it = pd.it;
+        if (it.k == 0) {
+            const int64_t ld = even(it.n);
+            for (int64_t i = 0; i < it.m; ++i)
+                for (int64_t j = 0; j < it.n; ++j) put(it.off + i * ld + j, nv[pd.src + i * it.n + j]);
+        } else {
+            const int64_t b = pd.src, k = it.k;
+            const int64_t m = pd.tm, n = pd.tn;
+            const double2 *U = fu + uoff[b];     // m x k row-major
+            const double2 *Vv = fv + voff[b];    // k x n row-major
+            const int64_t vbase = it.off + k * it.m;
+            for (int64_t i = 0; i < m; ++i) {
+                const int64_t pi = ppos(pd.trow0 + i) - it.row0;
+                for (int64_t l = 0; l < k; ++l) put(it.off + l * it.m + pi, U[i * k + l]);
+            }
+            for (int64_t j = 0; j < n; ++j) {
+                const int64_t pj = ppos(pd.tcol0 + j) - it.col0;
+                for (int64_t l = 0; l < k; ++l) put(vbase + l * it.n + pj, Vv[l * n + j]);
+            }
+        }
+        LevelList &L = h->levels[pd.level];
+        L.items.push_back(it);
+        L.true_m.push_back(pd.tm);
+        L.true_n.push_back(pd.tn);
+        L.elems += item_elems(it);
+        if (it.k == 0) L.n_dense++; else L.n_lowrank++;
+    }
+    (void)usrc;
+    if ((st = upload(h, &h->d_pool32, p32, s)) != HM_OK) return st;
+    if (h->has_fp64 && (st = upload(h, &h->d_pool64, p64, s)) != HM_OK) return st;
+    for (auto &kv : h->levels)
+        if ((st = upload(h, &kv.second.d_items, kv.second.items, s)) != HM_OK) return st;
+    // tree depth is not given by the import; report the number of levels instead
+    h->depth = max_level;
+    HM_CUDA(cudaStreamSynchronize(s));
+    return HM_OK;
+}
+
+extern "C" {
+
+hm_status hm_build_from_blocks(const hm_blocks *blocks, void *stream, hm_matrix *out)
+{
+    if (!blocks || !out) return fail(HM_ERR_ARG, "null argument");
+    *out = nullptr;
+    const hm_blocks *B = blocks;
+    if (B->n < 1 || !B->perm || !B->leaf_off || !B->self) return fail(HM_ERR_ARG, "missing n, perm, leaf_off or self");
+    if (B->n > (int64_t)1 << 30) return fail(HM_ERR_ARG, "n too large");
+    if (B->n_near < 0 || B->n_far < 0) return fail(HM_ERR_ARG, "negative block count");
+    if (B->n_near > 0 && (!B->near_row0 || !B->near_col0 || !B->near_m || !B->near_n || !B->near_vals))
+        return fail(HM_ERR_ARG, "missing near block arrays");
+    if (B->n_far > 0 && (!B->far_level || !B->far_row0 || !B->far_col0 || !B->far_m || !B->far_n ||
+                         !B->far_rank || !B->far_u || !B->far_v))
+        return fail(HM_ERR_ARG, "missing far block arrays");
+    hm_matrix h = new hm_matrix_s();
+    hm_status st = import_blocks(B, (cudaStream_t)stream, h);
+    if (st != HM_OK) {
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return HM_OK;
+}
+
+hm_status hm_build(const hm_mesh *mesh, const hm_build_opts *opts, void *stream, hm_matrix *out)
+{
+    if (!mesh || !opts || !out) return fail(HM_ERR_ARG, "null argument");
+    *out = nullptr;
+    return build_from_mesh(mesh, opts, (cudaStream_t)stream, out);
+}
+
+hm_status hm_factor_leaf(hm_matrix h, void *stream)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    HM_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
+    launch_factor(h, s);
+    HM_CUDA(cudaGetLastError());
+    HM_CUDA(cudaStreamSynchronize(s));
+    int stv = 0, bad = -1;
+    HM_CUDA(cudaMemcpy(&stv, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    HM_CUDA(cudaMemcpy(&bad, h->d_bad_leaf, sizeof(int), cudaMemcpyDeviceToHost));
+    if (stv != 0) {
+        cudaMemset(h->d_status, 0, sizeof(int));
+        h->factored = 0;
+        return fail((hm_status)stv, "zero pivot in leaf self block " + std::to_string(bad));
+    }
+    h->factored = 1;
+    return HM_OK;
+}
+
+hm_status hm_powerseries_solve(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx, int nrhs,
+                               const hm_solve_opts *opts, void *stream, hm_solve_info *info)
+{
+    return solve_device(h, b, ldb, x, ldx, nrhs, opts, (cudaStream_t)stream, info);
+}
+
+hm_status hm_powerseries_solve_host(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx, int nrhs,
+                                    const hm_solve_opts *opts, void *stream)
+{
+    if (!h || !b || !x || !opts) return fail(HM_ERR_ARG, "null argument");
+    if (nrhs < 0 || ldb < h->N || ldx < h->N) return fail(HM_ERR_ARG, "bad nrhs or leading dimension");
+    if (nrhs == 0) return HM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t es = opts->fp64 ? sizeof(double2) : sizeof(float2);
+    const size_t bytes = es * (size_t)h->N * nrhs;
+    hm::Workspace &ws = h->ws;
+    if (ws.h_pinned_bytes < 2 * bytes) {
+        if (ws.h_pinned) cudaFreeHost(ws.h_pinned);
+        ws.h_pinned = nullptr;
+        ws.h_pinned_bytes = 0;
+        HM_CUDA(cudaMallocHost(&ws.h_pinned, 2 * bytes));
+        ws.h_pinned_bytes = 2 * bytes;
+    }
+    if (ws.d_io_bytes < 2 * bytes) {
+        if (ws.d_io) cudaFree(ws.d_io);
+        ws.d_io = nullptr;
+        ws.d_io_bytes = 0;
+        HM_CUDA(cudaMalloc(&ws.d_io, 2 * bytes));
+        ws.d_io_bytes = 2 * bytes;
+    }
+    char *hb = (char *)ws.h_pinned, *hx = hb + bytes;
+    char *db = (char *)ws.d_io, *dxp = db + bytes;
+    for (int r = 0; r < nrhs; ++r)
+        std::memcpy(hb + es * h->N * r, (const char *)b + es * (size_t)ldb * r, es * h->N);
+    HM_CUDA(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, s));
+    hm_status st = solve_device(h, db, h->N, dxp, h->N, nrhs, opts, s, nullptr);
+    if (st != HM_OK) return st;
+    HM_CUDA(cudaMemcpyAsync(hx, dxp, bytes, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < nrhs; ++r)
+        std::memcpy((char *)x + es * (size_t)ldx * r, hx + es * h->N * r, es * h->N);
+    return HM_OK;
+}
+
+hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy, int nrhs, int n_levels,
+                   int fp64_accumulate, void *stream)
+{
+    if (!h || !x || !y) return fail(HM_ERR_ARG, "null argument");
+    if (nrhs < 0 || ldx < h->N || ldy < h->N) return fail(HM_ERR_ARG, "bad nrhs or leading dimension");
+    if (!h->factored) return fail(HM_ERR_STATE, "hm_factor_leaf has not completed (it also prepares D)");
+    if (nrhs == 0) return HM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveCtx c;
+    c.h = h; c.nrhs = nrhs; c.K = 0; c.fp64 = false; c.s = s;
+    c.m = clamp_levels(h, n_levels);
+    c.vbytes = sizeof(float2) * h->pN * nrhs;
+    hm_status st = ensure_workspace(h, nrhs, c.m);
+    if (st != HM_OK) return st;
+    void *xt = h->ws.vec32[0], *yt = h->ws.vec32[1];
+    double2 *acc = (double2 *)h->ws.d_acc64;
+    launch_permute_in(x, ldx, xt, h->pN, h->d_pperm, nrhs, false, s);
+    if (fp64_accumulate) {
+        apply_acc64(c, (const float2 *)xt, acc);
+        launch_convert_f64_to_f32(acc, (float2 *)yt, h->pN * nrhs, s);
+    } else {
+        HM_CUDA(cudaMemsetAsync(yt, 0, c.vbytes, s));
+        launch_apply_self_f32(h, (const float2 *)xt, (float2 *)yt, nrhs, s);
+        for (int lev = 1; lev <= c.m; ++lev) apply_level(c, lev, xt, yt);
+    }
+    launch_permute_out(yt, h->pN, y, ldy, h->d_pperm, nrhs, false, s);
+    HM_CUDA(cudaGetLastError());
+    return HM_OK;
+}
+
+hm_status hm_get_info(hm_matrix h, hm_info *info)
+{
+    if (!h || !info) return fail(HM_ERR_ARG, "null argument");
+    memset(info, 0, sizeof(*info));
+    info->n = h->N;
+    info->n_leaves = h->n_leaves;
+    info->depth = h->depth;
+    info->n_levels = h->n_levels;
+    for (auto &kv : h->levels) {
+        const int lev = kv.first;
+        const LevelList &L = kv.second;
+        if (lev == 1) {
+            info->n_near = L.n_dense;
+            for (size_t i = 0; i < L.items.size(); ++i)
+                if (L.items[i].k == 0) info->near_elems += (int64_t)L.true_m[i] * L.true_n[i];
+        }
+        if (lev >= 1 && lev <= 16) {
+            info->n_far[lev - 1] = L.n_lowrank;
+            for (size_t i = 0; i < L.items.size(); ++i)
+                if (L.items[i].k > 0) info->far_elems[lev - 1] += (int64_t)L.items[i].k * (L.true_m[i] + L.true_n[i]);
+        }
+    }
+    for (int64_t i = 0; i < h->n_leaves; ++i) {
+        const int64_t n = h->leaf_off[i + 1] - h->leaf_off[i];
+        info->self_elems += n * n;
+    }
+    info->max_rank = h->max_rank;
+    info->factored = h->factored;
+    info->has_fp64 = h->has_fp64 ? 1 : 0;
+    info->device_bytes = h->device_bytes;
+    return HM_OK;
+}
+
+hm_status hm_get_perm(hm_matrix h, int64_t *perm)
+{
+    if (!h || !perm) return fail(HM_ERR_ARG, "null argument");
+    std::copy(h->perm.begin(), h->perm.end(), perm);
+    return HM_OK;
+}
+
+hm_status hm_get_leaves(hm_matrix h, int64_t *leaf_off)
+{
+    if (!h || !leaf_off) return fail(HM_ERR_ARG, "null argument");
+    std::copy(h->leaf_off.begin(), h->leaf_off.end(), leaf_off);
+    return HM_OK;
+}
+
+static int64_t tree_of_padded(hm_matrix h, int64_t pp)
+{
+    // padded position -> tree position (pp must not be a pad slot)
+    auto it = std::upper_bound(h->pleaf_off.begin(), h->pleaf_off.end(), pp);
+    const int64_t l = (it - h->pleaf_off.begin()) - 1;
+    return h->leaf_off[l] + (pp - h->pleaf_off[l]);
+}
+
+hm_status hm_get_blocks(hm_matrix h, int level, int64_t *count, int64_t *row0, int64_t *col0, int32_t *m,
+                        int32_t *n, int32_t *rank)
+{
+    if (!h || !count) return fail(HM_ERR_ARG, "null argument");
+    auto f = h->levels.find(level);
+    if (f == h->levels.end()) { *count = 0; return HM_OK; }
+    const LevelList &L = f->second;
+    *count = (int64_t)L.items.size();
+    for (size_t i = 0; i < L.items.size(); ++i) {
+        const Item &it = L.items[i];
+        if (row0) row0[i] = tree_of_padded(h, it.row0);
+        if (col0) col0[i] = tree_of_padded(h, it.col0);
+        if (m) m[i] = L.true_m[i];
+        if (n) n[i] = L.true_n[i];
+        if (rank) rank[i] = it.k;
+    }
+    return HM_OK;
+}
+
+hm_status hm_get_block(hm_matrix h, int level, int64_t index, double *a, double *b)
+{
+    if (!h || !a) return fail(HM_ERR_ARG, "null argument");
+    auto f = h->levels.find(level);
+    if (f == h->levels.end() || index < 0 || index >= (int64_t)f->second.items.size())
+        return fail(HM_ERR_ARG, "no such block");
+    const LevelList &L = f->second;
+    const Item it = L.items[index];
+    const int64_t elems = item_elems(it);
+    std::vector<double2> buf(elems);
+    if (h->has_fp64) {
+        HM_CUDA(cudaMemcpy(buf.data(), h->d_pool64 + it.off, elems * sizeof(double2), cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float2> t(elems);
+        HM_CUDA(cudaMemcpy(t.data(), h->d_pool32 + it.off, elems * sizeof(float2), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < elems; ++i) buf[i] = make_double2(t[i].x, t[i].y);
+    }
+    double2 *A = reinterpret_cast<double2 *>(a);
+    const int64_t tm = L.true_m[index], tn = L.true_n[index];
+    if (it.k == 0) {
+        const int64_t ld = even(it.n);
+        for (int64_t i = 0; i < tm; ++i)
+            for (int64_t j = 0; j < tn; ++j) A[i * tn + j] = buf[i * ld + j];
+        return HM_OK;
+    }
+    if (!b) return fail(HM_ERR_ARG, "low-rank block needs both a (U) and b (V)");
+    double2 *Bv = reinterpret_cast<double2 *>(b);
+    const int64_t k = it.k;
+    int64_t ti = 0;
+    for (int64_t pi = 0; pi < it.m; ++pi) {
+        if (h->h_pperm[it.row0 + pi] < 0) continue;
+        for (int64_t l = 0; l < k; ++l) A[ti * k + l] = buf[l * it.m + pi];
+        ++ti;
+    }
+    int64_t tj = 0;
+    for (int64_t pj = 0; pj < it.n; ++pj) {
+        if (h->h_pperm[it.col0 + pj] < 0) continue;
+        for (int64_t l = 0; l < k; ++l) Bv[l * tn + tj] = buf[k * it.m + l * it.n + pj];
+        ++tj;
+    }
+    return HM_OK;
+}
+
+hm_status hm_sync_status(hm_matrix h, void *stream)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    HM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int stv = 0;
+    HM_CUDA(cudaMemcpy(&stv, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (stv != 0) {
+        HM_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
+        return fail((hm_status)stv, "device-side error recorded");
+    }
+    return HM_OK;
+}
+
+int64_t hm_size(hm_matrix h) { return h ? h->N : 0; }
+
+void hm_destroy(hm_matrix h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_handle(h);
+}
+
+const char *hm_last_error(void) { return g_last_error.c_str(); }
+
+const char *hm_version(void) { return "hmps 0.1 (sm_103a)"; }
+
+} // extern "C"

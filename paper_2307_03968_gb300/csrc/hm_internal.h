@@ -1,0 +1,156 @@
+// Internal declarations of the hmps library (not part of the C ABI).
+//
+// Data layout in HBM (one hm_matrix):
+//  - "padded tree order": unknowns are permuted into tree order (leaves
+//    contiguous, depth-first) and every leaf is padded to an even length, so
+//    every leaf and every coarser cluster starts on a 16-byte boundary for
+//    complex64 vectors.  pad slots hold zeros.  pN = padded length.
+//  - vectors: column-major [nrhs][pN] complex.
+//  - stored blocks (half storage, row cluster before column cluster) are
+//    packed into one pool per precision, each block starting on an even
+//    complex index:
+//      dense  m x n   row-major, row stride ld = even(n)
+//      low-rank       U^T (k x m', stride even(m')) then V (k x n', stride even(n')),
+//                     m', n' = padded cluster lengths; the block is U V.
+//  - leaf inverses D_i^{-1}: column-major n_i x n_i, column stride even(n_i).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <map>
+
+#include "../../include/hmps.h"
+
+namespace hm {
+
+// One stored block = one work item of the product kernels (32 bytes).
+struct Item {
+    int64_t off;    // complex-element offset into the pool
+    int32_t row0;   // padded-tree offset of the row cluster
+    int32_t col0;   // padded-tree offset of the column cluster
+    int32_t m, n;   // padded cluster lengths (dense: m = true rows, n = true cols)
+    int32_t k;      // rank; 0 = dense block
+    int32_t pad;
+};
+static_assert(sizeof(Item) == 32, "Item layout");
+
+inline int64_t even(int64_t v) { return (v + 1) & ~int64_t(1); }
+
+inline int64_t item_elems(const Item &it)
+{
+    if (it.k == 0) return int64_t(it.m) * even(it.n);
+    return int64_t(it.k) * (even(it.m) + even(it.n));
+}
+
+struct LevelList {
+    std::vector<Item> items;      // host copy
+    std::vector<int32_t> true_m, true_n;  // unpadded sizes (for export)
+    Item *d_items = nullptr;      // device copy
+    int64_t n_dense = 0, n_lowrank = 0;
+    int64_t elems = 0;            // stored complex elements
+};
+
+struct Workspace {
+    int nrhs = 0;
+    // complex vectors [nrhs][pN], allocated for the current nrhs, per precision
+    std::vector<void *> vec32, vec64;
+    double *d_acc64 = nullptr;    // FP64 accumulator for residuals [nrhs][pN] complex
+    void *h_pinned = nullptr;     // pinned staging for host-buffer solves
+    size_t h_pinned_bytes = 0;
+    void *d_io = nullptr;         // device b / x for host-buffer solves
+    size_t d_io_bytes = 0;
+};
+
+} // namespace hm
+
+struct hm_matrix_s {
+    int64_t N = 0, pN = 0, n_leaves = 0;
+    int depth = 0, n_levels = 0, max_rank = 0;
+    std::vector<int64_t> perm;        // tree position -> original index
+    std::vector<int64_t> leaf_off;    // tree positions
+    std::vector<int64_t> pleaf_off;   // padded positions
+    std::vector<int32_t> h_pperm;     // padded position -> original index or -1
+    int32_t *d_pperm = nullptr;
+    int32_t *d_pleaf_off = nullptr;   // [n_leaves+1]
+    int64_t *d_dinv_off = nullptr;    // [n_leaves] complex offset of D_i^{-1} (and of the complex64 D_i)
+    int64_t *d_leaf_n = nullptr;      // [n_leaves] true leaf sizes
+    int64_t *d_self_off = nullptr;    // [n_leaves] complex offset of D_i in d_self64
+    int *d_bad_leaf = nullptr;        // leaf index of the first zero pivot
+    std::vector<int64_t> dinv_off;
+    int64_t dinv_elems = 0;
+
+    // leaf self blocks, complex128 row-major n_i x n_i (input of the factorisation)
+    double2 *d_self64 = nullptr;
+    float2 *d_self32 = nullptr;       // complex64 copy, column-major like D^{-1} (residual)
+    std::vector<int64_t> self_off;    // complex offsets into d_self64 / d_self32
+    int64_t self_elems = 0;
+    float2 *d_dinv32 = nullptr;
+    double2 *d_dinv64 = nullptr;
+    int factored = 0;
+
+    // block pools and per-level lists; level index 1 = leaf level
+    float2 *d_pool32 = nullptr;
+    double2 *d_pool64 = nullptr;
+    int64_t pool_elems = 0;
+    bool has_fp64 = false;
+    std::map<int, hm::LevelList> levels;
+
+    int *d_status = nullptr;          // device status word (hm_status code, first error wins)
+    int *h_status = nullptr;          // pinned mirror
+    hm::Workspace ws;
+    int64_t device_bytes = 0;
+    int num_sms = 0;
+};
+
+namespace hm {
+
+// error helpers (hm_api.cu)
+hm_status fail(hm_status s, const std::string &msg);
+hm_status cuda_fail(cudaError_t e, const char *what);
+#define HM_CUDA(call)                                                         \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ::hm::cuda_fail(e_, #call);             \
+    } while (0)
+
+hm_status dev_alloc(hm_matrix h, void **p, size_t bytes);
+
+// kernels launchers (k_solve.cu)
+void launch_permute_in(const void *b, int64_t ldb, void *xt, int64_t pN, const int32_t *pperm,
+                       int nrhs, bool fp64, cudaStream_t s);
+void launch_permute_out(const void *xt, int64_t pN, void *x, int64_t ldx, const int32_t *pperm,
+                        int nrhs, bool fp64, cudaStream_t s);
+void launch_zero(void *p, size_t bytes, cudaStream_t s);
+// z (+)= M_level x  for one item list; z must be pre-zeroed by the caller
+void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
+                        cudaStream_t s);
+// FP64-accumulating apply: acc (double2) += A x over complex64 blocks
+void launch_apply_items_acc64(hm_matrix h, const LevelList &L, const float2 *x, double2 *acc, int nrhs,
+                              cudaStream_t s);
+void launch_apply_self_acc64(hm_matrix h, const float2 *x, double2 *acc, int nrhs, cudaStream_t s);
+void launch_apply_self_f32(hm_matrix h, const float2 *x, float2 *acc, int nrhs, cudaStream_t s);
+// per leaf: out = (y ? y - Dinv zin : Dinv zin); if zero_in, zin is cleared afterwards
+void launch_leaf_update(hm_matrix h, const void *y, void *zin, void *out, int nrhs, bool zero_in, bool fp64,
+                        cudaStream_t s);
+// out = y - w
+void launch_sub(const void *y, const void *w, void *out, int64_t n, bool fp64, cudaStream_t s);
+// r32 = b32 - acc, with acc = A x in FP64; also writes per-column |r|^2, |b|^2 into norms[2*nrhs]
+void launch_residual(const float2 *b, const double2 *acc, float2 *r, double *norms, int64_t pN, int nrhs,
+                     cudaStream_t s);
+void launch_add_inplace(void *x, const void *dx, int64_t n, bool fp64, cudaStream_t s);
+void launch_check_finite(const void *x, int64_t n, bool fp64, int *status, cudaStream_t s);
+void launch_convert_f64_to_f32(const double2 *a, float2 *b, int64_t n, cudaStream_t s);
+
+// factorisation (k_factor.cu)
+int factor_max_leaf();
+void launch_factor(hm_matrix h, cudaStream_t s);
+
+// GPU build from a mesh (k_build.cu)
+hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *opts, cudaStream_t s, hm_matrix *out);
+
+// shared construction helpers (hm_api.cu)
+hm_status finalize_layout(hm_matrix h, cudaStream_t s);
+
+} // namespace hm

@@ -1,0 +1,295 @@
+"""ctypes binding of the hmps C ABI (include/hmps.h).
+
+Argument marshalling only: every step of the build, factorisation and solve
+runs in the CUDA library.  Device buffers are torch CUDA tensors (PyTorch is
+used for device memory and streams); host buffers are numpy arrays.  The
+library must be present: importing this module on a machine without the
+built ``libhmps.so`` raises, there is no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhmps.so")
+
+HM_OK, HM_ERR_ARG, HM_ERR_OOM, HM_ERR_CUDA, HM_ERR_STATE, HM_ERR_SINGULAR, HM_ERR_DIVERGED, HM_ERR_TIMEOUT = range(8)
+STATUS_NAMES = ["HM_OK", "HM_ERR_ARG", "HM_ERR_OOM", "HM_ERR_CUDA", "HM_ERR_STATE", "HM_ERR_SINGULAR",
+                "HM_ERR_DIVERGED", "HM_ERR_TIMEOUT"]
+
+P = ctypes.c_void_p
+I64 = ctypes.c_int64
+I32 = ctypes.c_int32
+PI64 = ctypes.POINTER(ctypes.c_int64)
+PI32 = ctypes.POINTER(ctypes.c_int32)
+PD = ctypes.POINTER(ctypes.c_double)
+
+
+class HmMesh(ctypes.Structure):
+    _fields_ = [("n_vert", I64), ("xyz", PD), ("n_tri", I64), ("tri", PI32), ("wavelength", ctypes.c_double)]
+
+
+class HmBuildOpts(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("arity", ctypes.c_int), ("adm", ctypes.c_double),
+                ("aca_tol", ctypes.c_double), ("levels", ctypes.c_int), ("keep_fp64", ctypes.c_int)]
+
+
+class HmBlocks(ctypes.Structure):
+    _fields_ = [("n", I64), ("perm", PI64), ("n_leaves", I64), ("leaf_off", PI64), ("self", PD),
+                ("n_near", I64), ("near_row0", PI64), ("near_col0", PI64), ("near_m", PI32), ("near_n", PI32),
+                ("near_vals", PD),
+                ("n_far", I64), ("far_level", PI32), ("far_row0", PI64), ("far_col0", PI64), ("far_m", PI32),
+                ("far_n", PI32), ("far_rank", PI32), ("far_u", PD), ("far_v", PD), ("keep_fp64", ctypes.c_int)]
+
+
+class HmSolveOpts(ctypes.Structure):
+    _fields_ = [("n_terms", ctypes.c_int), ("n_levels", ctypes.c_int), ("nested", ctypes.c_int),
+                ("refine", ctypes.c_int), ("fp64", ctypes.c_int)]
+
+
+class HmSolveInfo(ctypes.Structure):
+    _fields_ = [("rel_residual", ctypes.c_double), ("levels_used", ctypes.c_int),
+                ("bytes_streamed", I64), ("kernel_launches", I64)]
+
+
+class HmInfo(ctypes.Structure):
+    _fields_ = [("n", I64), ("n_leaves", I64), ("depth", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("n_near", I64), ("n_far", I64 * 16), ("near_elems", I64), ("far_elems", I64 * 16),
+                ("self_elems", I64), ("max_rank", ctypes.c_int), ("factored", ctypes.c_int),
+                ("has_fp64", ctypes.c_int), ("device_bytes", I64)]
+
+
+EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_powerseries_solve",
+           "hm_powerseries_solve_host", "hm_apply", "hm_get_info", "hm_get_perm", "hm_get_leaves",
+           "hm_get_blocks", "hm_get_block", "hm_sync_status", "hm_size", "hm_destroy", "hm_last_error",
+           "hm_version"]
+
+_lib = None
+
+
+def load():
+    """Load libhmps.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError("hmps CUDA library not built: %s is missing (run __graft_entry__.build())" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    L.hm_build.argtypes = [ctypes.POINTER(HmMesh), ctypes.POINTER(HmBuildOpts), P, ctypes.POINTER(P)]
+    L.hm_build_from_blocks.argtypes = [ctypes.POINTER(HmBlocks), P, ctypes.POINTER(P)]
+    L.hm_factor_leaf.argtypes = [P, P]
+    L.hm_powerseries_solve.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.POINTER(HmSolveOpts), P,
+                                       ctypes.POINTER(HmSolveInfo)]
+    L.hm_powerseries_solve_host.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.POINTER(HmSolveOpts), P]
+    L.hm_apply.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    L.hm_get_info.argtypes = [P, ctypes.POINTER(HmInfo)]
+    L.hm_get_perm.argtypes = [P, PI64]
+    L.hm_get_leaves.argtypes = [P, PI64]
+    L.hm_get_blocks.argtypes = [P, ctypes.c_int, PI64, PI64, PI64, PI32, PI32, PI32]
+    L.hm_get_block.argtypes = [P, ctypes.c_int, I64, PD, PD]
+    L.hm_sync_status.argtypes = [P, P]
+    L.hm_size.argtypes = [P]
+    L.hm_size.restype = I64
+    L.hm_destroy.argtypes = [P]
+    L.hm_destroy.restype = None
+    L.hm_last_error.restype = ctypes.c_char_p
+    L.hm_version.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name.startswith("hm_") and name not in ("hm_size", "hm_destroy", "hm_last_error", "hm_version"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class HmError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+
+
+def _check(st):
+    if st != HM_OK:
+        raise HmError(st, load().hm_last_error().decode())
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return P(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return P(stream)
+    return P(stream.cuda_stream)
+
+
+class HMatrix:
+    """An H-Matrix operator held on the GPU (owns a hm_matrix handle)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    # ---- construction ------------------------------------------------------------------
+    @classmethod
+    def build(cls, xyz, tri, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1, keep_fp64=False,
+              wavelength=1.0, stream=None):
+        """hm_build: GPU fill and ACA of the S-EFIE H-Matrix of a closed triangle mesh."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        mesh = HmMesh(len(xyz), _ptr(xyz, ctypes.c_double), len(tri), _ptr(tri, ctypes.c_int32), wavelength)
+        opts = HmBuildOpts(leaf_size, arity, adm, aca_tol, levels, 1 if keep_fp64 else 0)
+        h = P()
+        _check(load().hm_build(ctypes.byref(mesh), ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def from_blocks(cls, perm, leaf_off, self_blocks, near, far, keep_fp64=False, stream=None):
+        """hm_build_from_blocks.
+
+        perm: tree position -> original index; leaf_off: leaf offsets (n_leaves+1);
+        self_blocks: list of (n_i, n_i) complex arrays; near: list of
+        (row0, col0, B); far: list of (level, row0, col0, U, V)."""
+        n = len(perm)
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a
+
+        perm_a = arr(perm, np.int64)
+        lo = arr(leaf_off, np.int64)
+        selfv = arr(np.concatenate([np.asarray(S, np.complex128).ravel() for S in self_blocks]), np.complex128)
+        nr0 = arr([b[0] for b in near], np.int64)
+        nc0 = arr([b[1] for b in near], np.int64)
+        nm = arr([b[2].shape[0] for b in near], np.int32)
+        nn = arr([b[2].shape[1] for b in near], np.int32)
+        nv = arr(np.concatenate([np.asarray(b[2], np.complex128).ravel() for b in near])
+                 if near else np.zeros(1, np.complex128), np.complex128)
+        fl = arr([b[0] for b in far], np.int32)
+        fr0 = arr([b[1] for b in far], np.int64)
+        fc0 = arr([b[2] for b in far], np.int64)
+        fm = arr([b[3].shape[0] for b in far], np.int32)
+        fn = arr([b[4].shape[1] for b in far], np.int32)
+        fk = arr([b[3].shape[1] for b in far], np.int32)
+        fu = arr(np.concatenate([np.asarray(b[3], np.complex128).ravel() for b in far])
+                 if far else np.zeros(1, np.complex128), np.complex128)
+        fv = arr(np.concatenate([np.asarray(b[4], np.complex128).ravel() for b in far])
+                 if far else np.zeros(1, np.complex128), np.complex128)
+        B = HmBlocks(n, _ptr(perm_a, I64), len(lo) - 1, _ptr(lo, I64), _ptr(selfv.view(np.float64), ctypes.c_double),
+                     len(near), _ptr(nr0, I64), _ptr(nc0, I64), _ptr(nm, I32), _ptr(nn, I32),
+                     _ptr(nv.view(np.float64), ctypes.c_double),
+                     len(far), _ptr(fl, I32), _ptr(fr0, I64), _ptr(fc0, I64), _ptr(fm, I32), _ptr(fn, I32),
+                     _ptr(fk, I32), _ptr(fu.view(np.float64), ctypes.c_double),
+                     _ptr(fv.view(np.float64), ctypes.c_double), 1 if keep_fp64 else 0)
+        h = P()
+        _check(load().hm_build_from_blocks(ctypes.byref(B), _stream(stream), ctypes.byref(h)))
+        return cls(h)
+
+    def factor_leaf(self, stream=None):
+        _check(load().hm_factor_leaf(self._h, _stream(stream)))
+
+    # ---- solve / apply -------------------------------------------------------------------
+    def solve(self, b, x, n_terms=2, n_levels=1, nested=True, refine=False, fp64=False, stream=None,
+              info=False):
+        """hm_powerseries_solve on torch CUDA tensors b, x of shape (N,) or (nrhs, N)
+        (each row one right-hand side, contiguous), complex64 (complex128 if fp64)."""
+        nrhs, ldb = self._cols(b)
+        _, ldx = self._cols(x)
+        o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0)
+        si = HmSolveInfo()
+        _check(load().hm_powerseries_solve(self._h, P(b.data_ptr()), ldb, P(x.data_ptr()), ldx, nrhs,
+                                           ctypes.byref(o), _stream(stream), ctypes.byref(si) if info else None))
+        return si if info else None
+
+    def solve_host(self, b, n_terms=2, n_levels=1, nested=True, refine=False, fp64=False, stream=None):
+        """hm_powerseries_solve_host on numpy arrays: b (N,) or (nrhs, N); returns x."""
+        dt = np.complex128 if fp64 else np.complex64
+        b = np.ascontiguousarray(b, dtype=dt)
+        x = np.empty_like(b)
+        nrhs = 1 if b.ndim == 1 else b.shape[0]
+        n = b.shape[-1]
+        o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0)
+        _check(load().hm_powerseries_solve_host(self._h, P(b.ctypes.data), n, P(x.ctypes.data), n, nrhs,
+                                                ctypes.byref(o), _stream(stream)))
+        return x
+
+    def apply(self, x, y, n_levels=-1, fp64_accumulate=True, stream=None):
+        nrhs, ldx = self._cols(x)
+        _, ldy = self._cols(y)
+        _check(load().hm_apply(self._h, P(x.data_ptr()), ldx, P(y.data_ptr()), ldy, nrhs, n_levels,
+                               1 if fp64_accumulate else 0, _stream(stream)))
+
+    def sync_status(self, stream=None):
+        _check(load().hm_sync_status(self._h, _stream(stream)))
+
+    @staticmethod
+    def _cols(t):
+        if t.dim() == 1:
+            return 1, t.shape[0]
+        if not t.is_contiguous():
+            raise ValueError("right-hand sides must be contiguous rows")
+        return t.shape[0], t.shape[1]
+
+    # ---- inspection ------------------------------------------------------------------------
+    def info(self):
+        i = HmInfo()
+        _check(load().hm_get_info(self._h, ctypes.byref(i)))
+        return i
+
+    @property
+    def n(self):
+        return int(load().hm_size(self._h))
+
+    def perm(self):
+        p = np.zeros(self.n, dtype=np.int64)
+        _check(load().hm_get_perm(self._h, _ptr(p, I64)))
+        return p
+
+    def leaves(self):
+        lo = np.zeros(self.info().n_leaves + 1, dtype=np.int64)
+        _check(load().hm_get_leaves(self._h, _ptr(lo, I64)))
+        return lo
+
+    def blocks(self, level):
+        c = I64(0)
+        L = load()
+        _check(L.hm_get_blocks(self._h, level, ctypes.byref(c), None, None, None, None, None))
+        n = c.value
+        r0, c0 = np.zeros(n, np.int64), np.zeros(n, np.int64)
+        m, nn, k = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32)
+        _check(L.hm_get_blocks(self._h, level, ctypes.byref(c), _ptr(r0, I64), _ptr(c0, I64), _ptr(m, I32),
+                               _ptr(nn, I32), _ptr(k, I32)))
+        return r0, c0, m, nn, k
+
+    def block(self, level, index):
+        r0, c0, m, n, k = self.blocks(level)
+        mi, ni, ki = int(m[index]), int(n[index]), int(k[index])
+        if ki == 0:
+            a = np.zeros((mi, ni), np.complex128)
+            _check(load().hm_get_block(self._h, level, index, _ptr(a.view(np.float64), ctypes.c_double), None))
+            return a
+        U = np.zeros((mi, ki), np.complex128)
+        V = np.zeros((ki, ni), np.complex128)
+        _check(load().hm_get_block(self._h, level, index, _ptr(U.view(np.float64), ctypes.c_double),
+                                   _ptr(V.view(np.float64), ctypes.c_double)))
+        return U, V
+
+    def close(self):
+        if self._h:
+            load().hm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version():
+    return load().hm_version().decode()
