@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the multi-level power-series solve (arxiv 2307.03968 §IV).
+
+Workload (default): S-EFIE PEC sphere of radius 2 wavelengths, icosphere with
+20,480 triangles -> 30,720 RWG unknowns, octree with leaves of <= 64 unknowns,
+admissibility dist >= 2 * min(diam), ACA tolerance 1e-4, complex64 on the GPU,
+one plane-wave right-hand side (+z incidence, x polarised).  The operator is
+built on the GPU (hm_build) and its leaf blocks factored (hm_factor_leaf)
+before timing; it stays resident in HBM (about 1.5 GB of blocks, larger than
+L2, so no L2 flush is needed between steps).
+
+One step = one hm_powerseries_solve with the paper's settings: leaf level only,
+K = 2 terms, plus the FP64-accumulated residual and one refinement step — the
+whole hot path (permute, D^{-1}, K x (near/far product + series accumulate),
+residual, correction solve, un-permute).
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead
+(a bounded sample of the same workload, scaled to the whole operator).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="sefie_pec_sphere_r2lambda_30720rwg", subdivisions=5, radius=2.0, leaf_size=64, arity=8,
+                adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True)
+METRIC = "power-series solves RHS/s at <=1e-4 rel err vs FP64 oracle; p50/p99 latency"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="hm", choices=["hm", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU time budget of the oracle sample")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle sample --
+def oracle_sample_rate(cpu_seconds, warmup=1, steps=None):
+    """Time the CPU oracle's power-series solve (series.solve, leaf level, K=2,
+    refine) on a sample of the workload's operator: the leaf self blocks of
+    S evenly spaced leaves plus every stored near / leaf-level far block whose
+    row cluster is one of them.  The time is scaled to the whole operator by
+    the ratio of stored complex elements.  Returns a dict for the JSON line."""
+    import numpy as np
+    from synth import icosphere, plane_wave_z
+    from oracle.rwg import RWGMesh
+    from oracle.hmatrix import ClusterTree, HMatrix, partition, recompress
+    from oracle import series
+
+    w = WORKLOAD
+    xyz, tri = icosphere(w["subdivisions"], w["radius"])
+    mesh = RWGMesh(xyz, tri)
+    tree = ClusterTree(mesh.centres(), *mesh.support_boxes(), w["leaf_size"], w["arity"])
+    near_pairs, far_pairs = partition(tree, w["adm"])
+    L = tree.depth
+    leaves = tree.leaves()
+    S = 8
+    sample = set(int(i) for i in np.linspace(0, len(leaves) - 1, S).round())
+    P = tree.perm
+    Hs = HMatrix.__new__(HMatrix)
+    Hs.mesh, Hs.tree, Hs.N, Hs.perm, Hs.depth, Hs.n_levels = mesh, tree, tree.N, tree.perm, L, 1
+    Hs.leaves = [leaves[i] for i in sorted(sample)]
+    Hs.D = []
+    for (off, n) in Hs.leaves:
+        B = mesh.fill(P[off:off + n], P[off:off + n])
+        iu = np.triu_indices(n, 1)
+        B[(iu[1], iu[0])] = B[iu]
+        Hs.D.append(B)
+    Hs.near = []
+    for (a, b) in near_pairs:
+        if a in sample:
+            (io, m), (jo, n) = leaves[a], leaves[b]
+            Hs.near.append((io, m, jo, n, mesh.fill(P[io:io + m], P[jo:jo + n])))
+    fl = [(a, b) for (a, b) in far_pairs.get(L, []) if a in sample]
+    facs = mesh.aca_many([(P[leaves[a][0]:leaves[a][0] + leaves[a][1]], P[leaves[b][0]:leaves[b][0] + leaves[b][1]])
+                          for (a, b) in fl], w["aca_tol"])
+    Hs.far = {1: []}
+    for (a, b), (U, V) in zip(fl, facs):
+        U, V = recompress(U, V, w["aca_tol"])
+        Hs.far[1].append((leaves[a][0], leaves[a][1], leaves[b][0], leaves[b][1], U, V))
+    # element counts of the sample and of the whole leaf-level operator
+    samp = sum(n * n for (_, n) in Hs.leaves) + sum(m * n for (_, m, _, n, _) in Hs.near) + \
+        sum(U.shape[1] * (m + n) for (_, m, _, n, U, _) in Hs.far[1])
+    n_far_total = len(far_pairs.get(L, []))
+    mean_far = np.mean([U.shape[1] * (m + n) for (_, m, _, n, U, _) in Hs.far[1]]) if Hs.far[1] else 0.0
+    full = sum(n * n for (_, n) in leaves) + sum(leaves[a][1] * leaves[b][1] for (a, b) in near_pairs) + \
+        n_far_total * mean_far
+    scale = full / samp
+    b = mesh.rhs(*plane_wave_z())[:, 0]
+    for _ in range(warmup):
+        series.solve(Hs, b, K=w["n_terms"], levels=1, refine=True)
+    times, cpu = [], []
+    t_end = time.perf_counter() + cpu_seconds
+    n = 0
+    while (steps is None and (time.perf_counter() < t_end or n < 3)) or (steps is not None and n < steps):
+        c0, t0 = time.process_time(), time.perf_counter()
+        series.solve(Hs, b, K=w["n_terms"], levels=1, refine=True)
+        times.append(time.perf_counter() - t0)
+        cpu.append(time.process_time() - c0)
+        n += 1
+    t = statistics.median(times) * scale
+    cores = max(1, round(sum(cpu) / max(sum(times), 1e-9)))
+    return dict(value=1.0 / t, unit="RHS/s", cores=cores, kind="oracle",
+                sample="oracle series.solve (K=2, leaf level, refine) on %d of %d leaves with their %d near and "
+                       "%d leaf-level far block rows (%.1f%% of the stored elements, far elements of unsampled "
+                       "rows estimated from the sample's mean rank); median of %d solves scaled by %.1f"
+                       % (S, len(leaves), len(Hs.near), len(Hs.far[1]), 100.0 / scale, n, scale),
+                solve_s_scaled=t, n_timed=n)
+
+
+# ---------------------------------------------------------------- clocks --------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- traffic -------
+def committed_traffic():
+    """Per-launch DRAM traffic of the product kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2307_03968_gb300", "csrc", "k_solve.cu")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("k_solve_sha256_16") == h and d.get("workload") == WORKLOAD["name"]:
+            return d.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- main ----------
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOAD
+    config = {"workload": w["name"], "unknowns": 30720, "triangles": 20480, "radius_lambda": w["radius"],
+              "leaf_size": w["leaf_size"], "tree": "octree (median splits)", "admissibility": "dist>=2*min(diam)",
+              "aca_tol": w["aca_tol"], "n_terms": w["n_terms"], "levels": "leaf level only",
+              "refine": "one FP64-residual refinement step", "nrhs": 1, "rhs": "plane wave +z, x-pol",
+              "l2": "operator resident in HBM is larger than L2; no flush", "parallelism": "replicas"}
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        r = oracle_sample_rate(a.cpu_seconds, warmup=min(a.warmup, 1), steps=max(a.steps, 1) if a.steps < 50 else None)
+        line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": "RHS/s", "n_gpus": a.gpus,
+                "steps": r["n_timed"], "warmup": min(a.warmup, 1), "ms_per_step": 1e3 / r["value"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": r["value"], "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import numpy as np
+    import torch
+    from synth import icosphere
+    from paper_2307_03968_gb300.hm import HMatrix
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    xyz, tri = icosphere(w["subdivisions"], w["radius"])
+    t0 = time.perf_counter()
+    A = HMatrix.build(xyz, tri, leaf_size=w["leaf_size"], arity=w["arity"], adm=w["adm"], aca_tol=w["aca_tol"],
+                      levels=-1)
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    A.factor_leaf()
+    factor_s = time.perf_counter() - t0
+    info = A.info()
+    N = A.n
+    kh, ph = np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]])
+    b = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    A.rhs_plane_wave(kh, ph, b)
+    x = torch.empty_like(b)
+    opts = dict(n_terms=w["n_terms"], n_levels=w["n_levels"], refine=w["refine"])
+    si = A.solve(b, x, info=True, **opts)
+    launches_per_step = si.kernel_launches
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        A.solve(b, x, **opts)
+    K = a.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    A.profile(True)
+    for i in range(K):
+        starts[i].record(stream)
+        A.solve(b, x, **opts)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof_ms, prof_n, prof_bytes = A.profile_read()
+    A.profile(False)
+    total_ms = starts[0].elapsed_time(ends[-1])
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    lat = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+    value = K * world / (total_ms / 1e3)
+
+    # extras: unrefined solve and full-level solve (nested, all levels)
+    def time_solves(n, **kw):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            A.solve(b, x, **kw)
+        s0.record(stream)
+        for _ in range(n):
+            A.solve(b, x, **kw)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / n
+    no_refine_ms = time_solves(200, n_terms=2, n_levels=1, refine=False)
+    full_nested_ms = time_solves(20, n_terms=2, n_levels=-1, nested=True, refine=False)
+    full_flat_ms = time_solves(100, n_terms=2, n_levels=-1, nested=False, refine=False)
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not a.no_e2e:
+        bh = b.cpu().numpy()
+        for _ in range(3):
+            A.solve_host(bh, **opts)
+        Ke = max(10, min(K, 500))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            xh = A.solve_host(bh, **opts)
+            _ = float(np.abs(xh[0, 0]))
+        dt = time.perf_counter() - t0
+        e2e = {"value": Ke * world / dt, "unit": "RHS/s", "h2d_bytes_per_step": int(bh.nbytes),
+               "d2h_bytes_per_step": int(xh.nbytes), "steps": Ke}
+
+    peak, peak_kind = peaks()
+    per_launch_bytes = prof_bytes / max(prof_n, 1)
+    per_launch_ms = prof_ms / max(prof_n, 1)
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if prof_n else None
+    roof = {"bound": "hbm", "kernel": "k_apply_items<float,float> (near + leaf far block product)",
+            "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": committed_traffic(),
+            "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms, "launches": prof_n,
+            "share_of_step": (prof_ms / total_ms) if total_ms else None}
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        try:
+            r = oracle_sample_rate(a.cpu_seconds)
+            cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": "RHS/s", "cores": None, "kind": "oracle", "sample": "failed: %r" % ex}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": K, "warmup": a.warmup,
+                "ms_per_step": total_ms / K, "p50_ms": p50, "p99_ms": p99, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic", "config": config,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches_per_step) * K,
+                "extras": {"build_s": build_s, "factor_s": factor_s, "no_refine_ms": no_refine_ms,
+                           "full_level_nested_ms": full_nested_ms, "full_level_flat_ms": full_flat_ms,
+                           "n_levels": info.n_levels, "near_blocks": info.n_near,
+                           "far_blocks": [info.n_far[i] for i in range(info.n_levels)],
+                           "max_rank": info.max_rank, "device_bytes": info.device_bytes,
+                           "launches_per_step": int(launches_per_step)}}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

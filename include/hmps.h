@@ -178,6 +178,37 @@ hm_status hm_powerseries_solve_host(hm_matrix h, const void *b, int64_t ldb, voi
 hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy, int nrhs,
                    int n_levels, int fp64_accumulate, void *stream);
 
+/* ------------------------------------------------------------ excitation --- */
+
+/*
+ * Right-hand sides of eq. 5 for incident plane waves (paper §II: "b is a known
+ * incident plane wave"): b_m = Int f_m . p_hat exp(-jk k_hat . r) dS for the RWG
+ * function f_m (same 7-point rule as the fill), unit amplitude.  khat, phat:
+ * HOST arrays of 3*nrhs doubles (unit propagation direction, unit polarisation).
+ * b: DEVICE complex64, column-major N x nrhs in the original order, leading
+ * dimension ldb.  Only for operators made by hm_build (the mesh is kept).
+ */
+hm_status hm_rhs_plane_wave(hm_matrix h, const double *khat, const double *phat, int nrhs, void *b, int64_t ldb,
+                            void *stream);
+
+/* ------------------------------------------------------------- profiling --- */
+
+/*
+ * Opt-in timing of the block-product kernel (the near/far-field H-Matrix product
+ * of every series term): while enabled, every launch of that kernel made by
+ * hm_powerseries_solve is bracketed by CUDA events recorded on the launching
+ * stream.  enable = 1 starts a new measurement (counters reset), 0 stops.
+ */
+hm_status hm_profile(hm_matrix h, int enable);
+
+/*
+ * Synchronises the recorded events and returns the summed kernel time (ms), the
+ * number of timed launches, and the algorithmic bytes those launches had to move
+ * (complex64 block elements at their unpadded sizes, plus one read of x and one
+ * write of z per right-hand side).
+ */
+hm_status hm_profile_read(hm_matrix h, double *product_ms, int64_t *launches, int64_t *bytes);
+
 /* ---------------------------------------------------------- inspection --- */
 
 typedef struct {

@@ -48,6 +48,10 @@ template <class T> static hm_status upload(hm_matrix h, T **dst, const std::vect
 static void free_handle(hm_matrix h)
 {
     if (!h) return;
+    for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+    void *geo[] = {h->d_qpd, h->d_vtx, h->d_etri, h->d_efree, h->d_elen};
+    for (void *p : geo)
+        if (p) cudaFree(p);
     void *ptrs[] = {h->d_pperm, h->d_pleaf_off, h->d_dinv_off, h->d_leaf_n, h->d_self_off, h->d_bad_leaf,
                     h->d_self64, h->d_self32, h->d_dinv32, h->d_dinv64, h->d_pool32, h->d_pool64, h->d_status,
                     h->ws.d_acc64, h->ws.d_io};
@@ -164,7 +168,25 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
 {
     auto it = c.h->levels.find(lev);
     if (it == c.h->levels.end() || it->second.items.empty()) return;
+    hm_matrix h = c.h;
+    const bool timed = h->prof && !c.fp64;
+    if (timed) {
+        if (h->prof_used + 2 > h->prof_ev.size() && h->prof_ev.size() < 8192) {
+            for (int q = 0; q < 256; ++q) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) break;
+                h->prof_ev.push_back(e);
+            }
+        }
+        if (h->prof_used + 2 <= h->prof_ev.size()) cudaEventRecord(h->prof_ev[h->prof_used], c.s);
+    }
     launch_apply_items(c.h, it->second, x, z, c.nrhs, c.fp64, c.s);
+    if (timed && h->prof_used + 2 <= h->prof_ev.size()) {
+        cudaEventRecord(h->prof_ev[h->prof_used + 1], c.s);
+        h->prof_used += 2;
+        h->prof_launches++;
+        h->prof_bytes += (it->second.alg_elems * 8 + 2 * 8 * h->N) * (int64_t)c.nrhs;
+    }
     c.launches++;
     c.bytes += level_bytes(c.h, lev, c.fp64) * c.nrhs;
 }
@@ -483,6 +505,7 @@ static hm_status import_blocks(const hm_blocks *B, cudaStream_t s, hm_matrix h)
         L.true_m.push_back(pd.tm);
         L.true_n.push_back(pd.tn);
         L.elems += item_elems(it);
+        L.alg_elems += it.k == 0 ? (int64_t)pd.tm * pd.tn : (int64_t)it.k * (pd.tm + pd.tn);
         if (it.k == 0) L.n_dense++; else L.n_lowrank++;
     }
     (void)usrc;
@@ -619,6 +642,58 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
     }
     launch_permute_out(yt, h->pN, y, ldy, h->d_pperm, nrhs, false, s);
     HM_CUDA(cudaGetLastError());
+    return HM_OK;
+}
+
+hm_status hm_rhs_plane_wave(hm_matrix h, const double *khat, const double *phat, int nrhs, void *b, int64_t ldb,
+                            void *stream)
+{
+    if (!h || !khat || !phat || !b) return fail(HM_ERR_ARG, "null argument");
+    if (!h->has_mesh) return fail(HM_ERR_STATE, "operator has no mesh (built from blocks)");
+    if (nrhs < 0 || ldb < h->N) return fail(HM_ERR_ARG, "bad nrhs or leading dimension");
+    if (nrhs == 0) return HM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> kp(6 * (size_t)nrhs);
+    std::memcpy(kp.data(), khat, 3 * sizeof(double) * nrhs);
+    std::memcpy(kp.data() + 3 * nrhs, phat, 3 * sizeof(double) * nrhs);
+    double *d_kp = nullptr;
+    HM_CUDA(cudaMalloc(&d_kp, kp.size() * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(d_kp, kp.data(), kp.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        launch_rhs_plane_wave(h, d_kp, d_kp + 3 * nrhs, nrhs, (float2 *)b, ldb, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_kp);
+    if (e != cudaSuccess) return cuda_fail(e, "hm_rhs_plane_wave");
+    return HM_OK;
+}
+
+hm_status hm_profile(hm_matrix h, int enable)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    h->prof = enable != 0;
+    if (enable) {
+        h->prof_used = 0;
+        h->prof_launches = 0;
+        h->prof_bytes = 0;
+    }
+    return HM_OK;
+}
+
+hm_status hm_profile_read(hm_matrix h, double *product_ms, int64_t *launches, int64_t *bytes)
+{
+    if (!h || !product_ms || !launches || !bytes) return fail(HM_ERR_ARG, "null argument");
+    double tot = 0.0;
+    for (size_t q = 0; q + 1 < h->prof_used; q += 2) {
+        HM_CUDA(cudaEventSynchronize(h->prof_ev[q + 1]));
+        float ms = 0.f;
+        HM_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[q], h->prof_ev[q + 1]));
+        tot += ms;
+    }
+    *product_ms = tot;
+    *launches = h->prof_launches;
+    *bytes = h->prof_bytes;
     return HM_OK;
 }
 

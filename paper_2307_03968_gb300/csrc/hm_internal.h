@@ -45,6 +45,7 @@ inline int64_t item_elems(const Item &it)
 }
 
 struct LevelList {
+    int64_t alg_elems = 0;        // complex elements at unpadded sizes (algorithmic bytes / 8)
     std::vector<Item> items;      // host copy
     std::vector<int32_t> true_m, true_n;  // unpadded sizes (for export)
     Item *d_items = nullptr;      // device copy
@@ -102,6 +103,20 @@ struct hm_matrix_s {
     hm::Workspace ws;
     int64_t device_bytes = 0;
     int num_sms = 0;
+
+    // mesh geometry kept for excitation (operators made by hm_build)
+    bool has_mesh = false;
+    double *d_qpd = nullptr;      // nt x 7 x 3 quadrature points
+    double *d_vtx = nullptr;      // nv x 3
+    int32_t *d_etri = nullptr, *d_efree = nullptr;
+    double *d_elen = nullptr;
+    double wavenumber = 0.0;
+
+    // opt-in event timing of the product kernel
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;     // pairs (start, end)
+    size_t prof_used = 0;
+    int64_t prof_launches = 0, prof_bytes = 0;
 };
 
 namespace hm {
@@ -142,10 +157,15 @@ void launch_residual(const float2 *b, const double2 *acc, float2 *r, double *nor
 void launch_add_inplace(void *x, const void *dx, int64_t n, bool fp64, cudaStream_t s);
 void launch_check_finite(const void *x, int64_t n, bool fp64, int *status, cudaStream_t s);
 void launch_convert_f64_to_f32(const double2 *a, float2 *b, int64_t n, cudaStream_t s);
+void launch_convert_f32_to_f64(const float2 *a, double2 *b, int64_t n, cudaStream_t s);
 
 // factorisation (k_factor.cu)
 int factor_max_leaf();
 void launch_factor(hm_matrix h, cudaStream_t s);
+
+// plane-wave right-hand sides (k_build.cu)
+void launch_rhs_plane_wave(hm_matrix h, const double *d_k, const double *d_p, int nrhs, float2 *b, int64_t ldb,
+                           cudaStream_t s);
 
 // GPU build from a mesh (k_build.cu)
 hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *opts, cudaStream_t s, hm_matrix *out);

@@ -642,6 +642,34 @@ __global__ void k_pack_far(const PackJob *__restrict__ jobs, const float2 *__res
     }
 }
 
+// b[r*ldb + m] = Int f_m . p_hat exp(-jk k_hat . r) dS  (7-point rule on T+ and T-)
+__global__ void k_rhs_plane_wave(const double *__restrict__ qpd, const double *__restrict__ vtx,
+                                 const int32_t *__restrict__ etri, const int32_t *__restrict__ efree,
+                                 const double *__restrict__ elen, int64_t N, double k, const double *__restrict__ kh,
+                                 const double *__restrict__ ph, int nrhs, float2 *b, int64_t ldb)
+{
+    const int64_t total = N * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / N, m = t - r * N;
+        const double *kk = kh + 3 * r, *pp = ph + 3 * r;
+        double re = 0.0, im = 0.0;
+        for (int p = 0; p < 2; ++p) {
+            const int tt = etri[2 * m + p];
+            const double *v = vtx + 3 * efree[2 * m + p];
+            const double sg = p == 0 ? 1.0 : -1.0;
+            for (int q = 0; q < NQ; ++q) {
+                const double *rq = qpd + (tt * NQ + q) * 3;
+                const double proj = (rq[0] - v[0]) * pp[0] + (rq[1] - v[1]) * pp[1] + (rq[2] - v[2]) * pp[2];
+                double sn, cs;
+                sincos(k * (kk[0] * rq[0] + kk[1] * rq[1] + kk[2] * rq[2]), &sn, &cs);
+                re += sg * c_qw[q] * proj * cs;
+                im -= sg * c_qw[q] * proj * sn;
+            }
+        }
+        b[r * ldb + m] = make_float2((float)(0.5 * elen[m] * re), (float)(0.5 * elen[m] * im));
+    }
+}
+
 // ------------------------------------------------------------ host side ---------
 struct HostTree {
     std::vector<std::vector<std::pair<int64_t, int64_t>>> levels;   // (offset, size) per depth
@@ -806,6 +834,15 @@ struct TmpBuffers {
 
 } // namespace
 
+void launch_rhs_plane_wave(hm_matrix h, const double *d_k, const double *d_p, int nrhs, float2 *b, int64_t ldb,
+                           cudaStream_t s)
+{
+    const int64_t total = h->N * nrhs;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    k_rhs_plane_wave<<<grid, 256, 0, s>>>(h->d_qpd, h->d_vtx, h->d_etri, h->d_efree, h->d_elen, h->N, h->wavenumber,
+                                          d_k, d_p, nrhs, b, ldb);
+}
+
 hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *o, cudaStream_t s, hm_matrix *out)
 {
     if (mesh->n_vert < 3 || mesh->n_tri < 2 || !mesh->xyz || !mesh->tri) return fail(HM_ERR_ARG, "empty mesh");
@@ -877,7 +914,6 @@ hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *o, cudaStrea
     for (int64_t i = 0; i < h->n_leaves; ++i) h->leaf_off[i] = T.levels[T.depth][i].first;
     h->leaf_off[h->n_leaves] = N;
     h->has_fp64 = o->keep_fp64 != 0;
-    if (h->has_fp64) return fail(HM_ERR_ARG, "keep_fp64 is available for imported operators only");
     if ((st = finalize_layout(h, s)) != HM_OK) return st;
     h->depth = T.depth;
 
@@ -1019,6 +1055,7 @@ hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *o, cudaStrea
         LevelList &L = h->levels[1];
         L.items.push_back(it); L.true_m.push_back(it.m); L.true_n.push_back(it.n);
         L.elems += item_elems(it); L.n_dense++;
+        L.alg_elems += (int64_t)it.m * it.n;
     }
     std::vector<PackJob> pj;
     int max_level = 1, max_rank = 0;
@@ -1037,6 +1074,7 @@ hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *o, cudaStrea
         LevelList &L = h->levels[f.level];
         L.items.push_back(it); L.true_m.push_back((int32_t)f.m); L.true_n.push_back((int32_t)f.n);
         L.elems += item_elems(it); L.n_lowrank++;
+        L.alg_elems += (int64_t)it.k * (f.m + f.n);
         max_level = std::max(max_level, f.level);
         max_rank = std::max(max_rank, it.k);
     }
@@ -1072,8 +1110,20 @@ hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *o, cudaStrea
         k_pack_far<<<(unsigned)pj.size(), 256, 0, s>>>(d_pj, d_scr, d_ptree, h->d_pool32);
         HM_CUDA(cudaGetLastError());
     }
+    if (h->has_fp64) {   // complex128 copy of the same (complex64-filled) blocks for the FP64 path
+        if ((st = dev_alloc(h, (void **)&h->d_pool64, sizeof(double2) * std::max<int64_t>(pool, 1))) != HM_OK)
+            return st;
+        launch_convert_f32_to_f64(h->d_pool32, h->d_pool64, std::max<int64_t>(pool, 1), s);
+    }
     for (auto &kv : h->levels)
         if ((st = up(h, &kv.second.d_items, kv.second.items, s)) != HM_OK) return st;
+    // geometry kept for the plane-wave excitation
+    if ((st = up(h, &h->d_qpd, qpd, s)) != HM_OK || (st = up(h, &h->d_vtx, vtx, s)) != HM_OK ||
+        (st = up(h, &h->d_etri, etri, s)) != HM_OK || (st = up(h, &h->d_efree, efree, s)) != HM_OK ||
+        (st = up(h, &h->d_elen, elen, s)) != HM_OK)
+        return st;
+    h->has_mesh = true;
+    h->wavenumber = g.k;
     HM_CUDA(cudaStreamSynchronize(s));
     guard.keep = true;
     *out = h;

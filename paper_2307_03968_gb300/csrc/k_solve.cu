@@ -492,6 +492,12 @@ __global__ void k_check_finite(const C *x, int64_t n, int *status)
     }
 }
 
+__global__ void k_f32_to_f64(const float2 *a, double2 *b, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = make_double2(a[t].x, a[t].y);
+}
+
 __global__ void k_f64_to_f32(const double2 *a, float2 *b, int64_t n)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -632,6 +638,11 @@ void launch_check_finite(const void *x, int64_t n, bool fp64, int *status, cudaS
     const int g = grid_for(n);
     if (fp64) k_check_finite<double2><<<g, 256, 0, s>>>((const double2 *)x, n, status);
     else k_check_finite<float2><<<g, 256, 0, s>>>((const float2 *)x, n, status);
+}
+
+void launch_convert_f32_to_f64(const float2 *a, double2 *b, int64_t n, cudaStream_t s)
+{
+    k_f32_to_f64<<<grid_for(n), 256, 0, s>>>(a, b, n);
 }
 
 void launch_convert_f64_to_f32(const double2 *a, float2 *b, int64_t n, cudaStream_t s)

@@ -62,9 +62,9 @@ class HmInfo(ctypes.Structure):
 
 
 EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_powerseries_solve",
-           "hm_powerseries_solve_host", "hm_apply", "hm_get_info", "hm_get_perm", "hm_get_leaves",
-           "hm_get_blocks", "hm_get_block", "hm_sync_status", "hm_size", "hm_destroy", "hm_last_error",
-           "hm_version"]
+           "hm_powerseries_solve_host", "hm_apply", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
+           "hm_get_info", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
+           "hm_size", "hm_destroy", "hm_last_error", "hm_version"]
 
 _lib = None
 
@@ -84,6 +84,9 @@ def load():
                                        ctypes.POINTER(HmSolveInfo)]
     L.hm_powerseries_solve_host.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.POINTER(HmSolveOpts), P]
     L.hm_apply.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    L.hm_rhs_plane_wave.argtypes = [P, PD, PD, ctypes.c_int, P, I64, P]
+    L.hm_profile.argtypes = [P, ctypes.c_int]
+    L.hm_profile_read.argtypes = [P, PD, PI64, PI64]
     L.hm_get_info.argtypes = [P, ctypes.POINTER(HmInfo)]
     L.hm_get_perm.argtypes = [P, PI64]
     L.hm_get_leaves.argtypes = [P, PI64]
@@ -223,6 +226,26 @@ class HMatrix:
         _, ldy = self._cols(y)
         _check(load().hm_apply(self._h, P(x.data_ptr()), ldx, P(y.data_ptr()), ldy, nrhs, n_levels,
                                1 if fp64_accumulate else 0, _stream(stream)))
+
+    def rhs_plane_wave(self, khat, phat, b, stream=None):
+        """hm_rhs_plane_wave into the torch CUDA tensor b (nrhs, N) complex64."""
+        k = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+        p = np.ascontiguousarray(np.atleast_2d(phat), dtype=np.float64)
+        nrhs, ldb = self._cols(b)
+        assert len(k) == nrhs and len(p) == nrhs
+        _check(load().hm_rhs_plane_wave(self._h, _ptr(k, ctypes.c_double), _ptr(p, ctypes.c_double), nrhs,
+                                        P(b.data_ptr()), ldb, _stream(stream)))
+
+    def profile(self, enable):
+        _check(load().hm_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(product kernel ms summed, launches, algorithmic bytes) since profile(True)."""
+        ms = ctypes.c_double(0.0)
+        n = I64(0)
+        by = I64(0)
+        _check(load().hm_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
+        return ms.value, n.value, by.value
 
     def sync_status(self, stream=None):
         _check(load().hm_sync_status(self._h, _stream(stream)))
