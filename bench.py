@@ -31,8 +31,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="sefie_pec_sphere_r2lambda_30720rwg", subdivisions=5, radius=2.0, leaf_size=64, arity=8,
-                adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True)
+WORKLOADS = {
+    # the metric's workload: 30,720 RWG unknowns
+    "sphere2": dict(name="sefie_pec_sphere_r2lambda_30720rwg", subdivisions=5, radius=2.0, leaf_size=64, arity=8,
+                    adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, unknowns=30720, triangles=20480),
+    # a smaller sphere of the same family (7,680 unknowns), for profiler captures
+    "sphere1": dict(name="sefie_pec_sphere_r1lambda_7680rwg", subdivisions=4, radius=1.0, leaf_size=64, arity=8,
+                    adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, unknowns=7680, triangles=5120),
+}
+WORKLOAD = WORKLOADS["sphere2"]
 METRIC = "power-series solves RHS/s at <=1e-4 rel err vs FP64 oracle; p50/p99 latency"
 
 
@@ -44,6 +51,8 @@ def parse():
     p.add_argument("--impl", default="hm", choices=["hm", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the unrefined / full-level timings")
+    p.add_argument("--workload", default="sphere2", choices=sorted(WORKLOADS))
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU time budget of the oracle sample")
     return p.parse_args()
 
@@ -196,11 +205,13 @@ def committed_traffic():
 # ---------------------------------------------------------------- main ----------
 def main():
     a = parse()
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[a.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     w = WORKLOAD
-    config = {"workload": w["name"], "unknowns": 30720, "triangles": 20480, "radius_lambda": w["radius"],
+    config = {"workload": w["name"], "unknowns": w["unknowns"], "triangles": w["triangles"], "radius_lambda": w["radius"],
               "leaf_size": w["leaf_size"], "tree": "octree (median splits)", "admissibility": "dist>=2*min(diam)",
               "aca_tol": w["aca_tol"], "n_terms": w["n_terms"], "levels": "leaf level only",
               "refine": "one FP64-residual refinement step", "nrhs": 1, "rhs": "plane wave +z, x-pol",
@@ -261,17 +272,27 @@ def main():
     clocks = ClockSampler(local)
     time.sleep(0.3)
     barrier()
-    A.profile(True)
-    for i in range(K):
+    for i in range(K):                       # timed region: CUDA-graph replays of the whole solve
         starts[i].record(stream)
         A.solve(b, x, **opts)
         ends[i].record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
+    total_ms = starts[0].elapsed_time(ends[-1])
+    # the same solves launched kernel by kernel, with CUDA events around every
+    # launch of the block-product kernel on its stream (graph replay hides them)
+    Kp = min(K, 1000)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    A.profile(True)
+    p0.record(stream)
+    for i in range(Kp):
+        A.solve(b, x, graph=False, **opts)
+    p1.record(stream)
+    torch.cuda.synchronize()
     prof_ms, prof_n, prof_bytes = A.profile_read()
     A.profile(False)
-    total_ms = starts[0].elapsed_time(ends[-1])
+    eager_ms = p0.elapsed_time(p1) / Kp
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -292,9 +313,11 @@ def main():
         s1.record(stream)
         torch.cuda.synchronize()
         return s0.elapsed_time(s1) / n
-    no_refine_ms = time_solves(200, n_terms=2, n_levels=1, refine=False)
-    full_nested_ms = time_solves(20, n_terms=2, n_levels=-1, nested=True, refine=False)
-    full_flat_ms = time_solves(100, n_terms=2, n_levels=-1, nested=False, refine=False)
+    no_refine_ms = full_nested_ms = full_flat_ms = None
+    if not a.no_extras:
+        no_refine_ms = time_solves(200, n_terms=2, n_levels=1, refine=False)
+        full_nested_ms = time_solves(20, n_terms=2, n_levels=-1, nested=True, refine=False)
+        full_flat_ms = time_solves(100, n_terms=2, n_levels=-1, nested=False, refine=False)
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -320,7 +343,8 @@ def main():
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": committed_traffic(),
             "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms, "launches": prof_n,
-            "share_of_step": (prof_ms / total_ms) if total_ms else None}
+            "share_of_step": (prof_ms / Kp / eager_ms) if eager_ms else None,
+            "measured_on": "the timed solve launched kernel by kernel (%d steps, %.4f ms/step)" % (Kp, eager_ms)}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
@@ -334,7 +358,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic", "config": config,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches_per_step) * K,
-                "extras": {"build_s": build_s, "factor_s": factor_s, "no_refine_ms": no_refine_ms,
+                "extras": {"eager_ms_per_step": eager_ms, "build_s": build_s, "factor_s": factor_s, "no_refine_ms": no_refine_ms,
                            "full_level_nested_ms": full_nested_ms, "full_level_flat_ms": full_flat_ms,
                            "n_levels": info.n_levels, "near_blocks": info.n_near,
                            "far_blocks": [info.n_far[i] for i in range(info.n_levels)],

@@ -144,6 +144,11 @@ typedef struct {
                       x += (same series)(r) */
     int fp64;      /* 1 = plain FP64 path: b, x are complex128 and the operator's
                       complex128 copy is used (needs keep_fp64) */
+    int graph;     /* 1 = capture the whole solve (every kernel of every term and
+                      level) into a CUDA graph on first use and replay it on later
+                      calls with the same pointers, sizes and options; 0 = launch
+                      kernels one by one.  Ignored while hm_profile is enabled or
+                      when info is requested. */
 } hm_solve_opts;
 
 typedef struct {
@@ -177,6 +182,19 @@ hm_status hm_powerseries_solve_host(hm_matrix h, const void *b, int64_t ldb, voi
  */
 hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy, int nrhs,
                    int n_levels, int fp64_accumulate, void *stream);
+
+/*
+ * r = b - A_m x, the residual of the refinement step, accumulated to FP64-class
+ * accuracy: complex64 blocks and vectors, every product formed exactly (FP32
+ * product plus its rounding error from an FMA), sums inside each block
+ * compensated (Dot2 of Ogita, Rump & Oishi 2005), sums across blocks in FP64,
+ * in a fixed order (no atomics on the sums).  b, x, r: DEVICE complex64,
+ * original order; r must not overlap b or x.  norms: NULL, or HOST array of
+ * 2*nrhs doubles receiving |r_j|^2 and |b_j|^2 (the call then synchronises).
+ * Needs hm_factor_leaf (it prepares the complex64 copy of D).
+ */
+hm_status hm_residual(hm_matrix h, const void *b, int64_t ldb, const void *x, int64_t ldx, void *r, int64_t ldr,
+                      int nrhs, int n_levels, double *norms, void *stream);
 
 /* ------------------------------------------------------------ excitation --- */
 

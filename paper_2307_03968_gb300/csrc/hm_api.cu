@@ -45,16 +45,24 @@ template <class T> static hm_status upload(hm_matrix h, T **dst, const std::vect
     return HM_OK;
 }
 
+static void clear_graphs(hm_matrix h)
+{
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
 static void free_handle(hm_matrix h)
 {
     if (!h) return;
+    clear_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     void *geo[] = {h->d_qpd, h->d_vtx, h->d_etri, h->d_efree, h->d_elen};
     for (void *p : geo)
         if (p) cudaFree(p);
     void *ptrs[] = {h->d_pperm, h->d_pleaf_off, h->d_dinv_off, h->d_leaf_n, h->d_self_off, h->d_bad_leaf,
                     h->d_self64, h->d_self32, h->d_dinv32, h->d_dinv64, h->d_pool32, h->d_pool64, h->d_status,
-                    h->ws.d_acc64, h->ws.d_io};
+                    h->ws.d_acc64, h->ws.d_io, h->ws.d_part, h->d_csr_off, h->d_csr_idx};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &kv : h->levels)
@@ -114,6 +122,44 @@ hm_status finalize_layout(hm_matrix h, cudaStream_t s)
     return HM_OK;
 }
 
+hm_status prepare_partials(hm_matrix h, cudaStream_t s)
+{
+    const int nl = std::max(h->n_levels, 1);
+    std::vector<std::vector<int64_t>> lists((size_t)h->n_leaves * nl);
+    auto leaf_of = [&](int64_t pp) {
+        return (int64_t)(std::upper_bound(h->pleaf_off.begin(), h->pleaf_off.end(), pp) - h->pleaf_off.begin()) - 1;
+    };
+    int64_t off = 0;
+    for (int lev = 1; lev <= nl; ++lev) {
+        auto f = h->levels.find(lev);
+        if (f == h->levels.end()) continue;
+        for (Item &it : f->second.items) {
+            const int64_t rl = even(it.m), cl = even(it.n);
+            if (off > INT32_MAX - rl - cl) return fail(HM_ERR_ARG, "operator too large for the partial-slot index");
+            it.pad = (int32_t)off;
+            for (int64_t l = leaf_of(it.row0); l < h->n_leaves && h->pleaf_off[l] < it.row0 + rl; ++l)
+                lists[l * nl + lev - 1].push_back(off + (h->pleaf_off[l] - it.row0));
+            for (int64_t l = leaf_of(it.col0); l < h->n_leaves && h->pleaf_off[l] < it.col0 + cl; ++l)
+                lists[l * nl + lev - 1].push_back(off + rl + (h->pleaf_off[l] - it.col0));
+            off += rl + cl;
+        }
+    }
+    h->partial_elems = off;
+    std::vector<int64_t> csr_off((size_t)h->n_leaves * (nl + 1)), csr_idx;
+    for (int64_t l = 0; l < h->n_leaves; ++l) {
+        csr_off[l * (nl + 1)] = (int64_t)csr_idx.size();
+        for (int lev = 1; lev <= nl; ++lev) {
+            const auto &v = lists[l * nl + lev - 1];
+            csr_idx.insert(csr_idx.end(), v.begin(), v.end());
+            csr_off[l * (nl + 1) + lev] = (int64_t)csr_idx.size();
+        }
+    }
+    hm_status st;
+    if ((st = upload(h, &h->d_csr_off, csr_off, s)) != HM_OK) return st;
+    if ((st = upload(h, &h->d_csr_idx, csr_idx, s)) != HM_OK) return st;
+    return HM_OK;
+}
+
 // ---- solve orchestration ----------------------------------------------------------
 
 struct SolveCtx {
@@ -135,10 +181,12 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
     const size_t need_vecs = 4 * (size_t)(m + 1) + 8;
     if (ws.nrhs >= nrhs && ws.vec32.size() >= need_vecs && (!h->has_fp64 || ws.vec64.size() >= need_vecs))
         return HM_OK;
+    clear_graphs(h);   // graphs hold the old workspace pointers
     for (void *p : ws.vec32) if (p) cudaFree(p);
     for (void *p : ws.vec64) if (p) cudaFree(p);
     if (ws.d_acc64) cudaFree(ws.d_acc64);
-    ws.vec32.clear(); ws.vec64.clear(); ws.d_acc64 = nullptr;
+    if (ws.d_part) cudaFree(ws.d_part);
+    ws.vec32.clear(); ws.vec64.clear(); ws.d_acc64 = nullptr; ws.d_part = nullptr;
     const int r = std::max(nrhs, ws.nrhs);
     const size_t n32 = sizeof(float2) * h->pN * r, n64 = sizeof(double2) * h->pN * r;
     for (size_t i = 0; i < need_vecs; ++i) {
@@ -152,7 +200,9 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
             ws.vec64.push_back(p);
         }
     }
-    HM_CUDA(cudaMalloc((void **)&ws.d_acc64, n64 + 2 * sizeof(double) * r));
+    HM_CUDA(cudaMalloc((void **)&ws.d_acc64, 2 * sizeof(double) * r));
+    ws.part_rhs = std::min(r, 4);
+    HM_CUDA(cudaMalloc((void **)&ws.d_part, sizeof(double2) * std::max<int64_t>(h->partial_elems, 1) * ws.part_rhs));
     ws.nrhs = r;
     return HM_OK;
 }
@@ -260,16 +310,24 @@ static int clamp_levels(hm_matrix h, int n_levels)
     return std::max(m, 1);
 }
 
-// acc (double2, zeroed here) = A_m x over complex64 blocks with FP64 accumulation
-static void apply_acc64(SolveCtx &c, const float2 *xt, double2 *acc)
+// out = b - A_m x (with |r|^2, |b|^2 per column into norms) when b is given, else
+// out = A_m x; complex64 blocks, FP64 products and sums, deterministic order:
+// every block writes its FP64 partial slots, then each leaf gathers its slots.
+static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *out, double *norms)
 {
-    cudaMemsetAsync(acc, 0, sizeof(double2) * c.h->pN * c.nrhs, c.s);
-    launch_apply_self_acc64(c.h, xt, acc, c.nrhs, c.s);
-    c.launches++;
-    for (int lev = 1; lev <= c.m; ++lev) {
-        auto it = c.h->levels.find(lev);
-        if (it == c.h->levels.end() || it->second.items.empty()) continue;
-        launch_apply_items_acc64(c.h, it->second, xt, acc, c.nrhs, c.s);
+    hm_matrix h = c.h;
+    const int chunk = std::max(1, h->ws.part_rhs);
+    for (int r0 = 0; r0 < c.nrhs; r0 += chunk) {
+        const int nr = std::min(chunk, c.nrhs - r0);
+        const float2 *x = xt + (int64_t)r0 * h->pN;
+        for (int lev = 1; lev <= c.m; ++lev) {
+            auto it = h->levels.find(lev);
+            if (it == h->levels.end() || it->second.items.empty()) continue;
+            launch_apply_items_partials(h, it->second, x, h->ws.d_part, h->partial_elems, nr, c.s);
+            c.launches++;
+        }
+        launch_gather_acc64(h, x, c.m, h->ws.d_part, h->partial_elems, bt ? bt + (int64_t)r0 * h->pN : nullptr,
+                            out + (int64_t)r0 * h->pN, norms ? norms + 2 * r0 : nullptr, nr, c.s);
         c.launches++;
     }
 }
@@ -277,6 +335,7 @@ static void apply_acc64(SolveCtx &c, const float2 *xt, double2 *acc)
 static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx, int nrhs,
                               const hm_solve_opts *o, cudaStream_t s, hm_solve_info *info)
 {
+    void *caller_stream = (void *)s;
     if (!h) return fail(HM_ERR_ARG, "null handle");
     if (!o) return fail(HM_ERR_ARG, "null opts");
     if (nrhs < 0) return fail(HM_ERR_ARG, "nrhs < 0");
@@ -302,6 +361,19 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
     c.vbytes = es * h->pN * nrhs;
     hm_status st = ensure_workspace(h, nrhs, c.m);
     if (st != HM_OK) return st;
+    const bool use_graph = o->graph && !info && !h->prof;
+    hm_matrix_s::GraphKey key{b, x, ldb, ldx, nrhs, c.K, c.m, o->nested, o->refine, o->fp64};
+    if (use_graph) {
+        auto g = h->graphs.find(key);
+        if (g != h->graphs.end()) {
+            HM_CUDA(cudaGraphLaunch(g->second, s));
+            return HM_OK;
+        }
+        if (!h->cap_stream) HM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        HM_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        c.s = h->cap_stream;
+        s = h->cap_stream;
+    }
     std::vector<void *> &V = c.fp64 ? h->ws.vec64 : h->ws.vec32;
     size_t vi = 0;
     c.Y.assign(c.m + 1, nullptr); c.X = c.Y; c.Z = c.Y; c.W = c.Y;
@@ -313,27 +385,34 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
     else Pflat(c, bt, xt);
     double *norms = nullptr;
     if (o->refine) {
-        double2 *acc = (double2 *)h->ws.d_acc64;
-        norms = (double *)(acc + h->pN * nrhs);
-        apply_acc64(c, (const float2 *)xt, acc);
+        norms = h->ws.d_acc64;
         cudaMemsetAsync(norms, 0, 2 * sizeof(double) * nrhs, s);
-        launch_residual((const float2 *)bt, acc, (float2 *)rt, norms, h->pN, nrhs, s);
-        c.launches++;
+        residual64(c, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
         if (o->nested) P(c, c.m, rt, dx);
         else Pflat(c, rt, dx);
         launch_add_inplace(xt, dx, h->pN * nrhs, false, s);
         c.launches++;
         if (info) {   // residual of the refined solution
-            apply_acc64(c, (const float2 *)xt, acc);
             cudaMemsetAsync(norms, 0, 2 * sizeof(double) * nrhs, s);
-            launch_residual((const float2 *)bt, acc, (float2 *)rt, norms, h->pN, nrhs, s);
-            c.launches++;
+            residual64(c, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
         }
     }
     launch_check_finite(xt, h->pN * nrhs, c.fp64, h->d_status, s);
     c.launches++;
     launch_permute_out(xt, h->pN, x, ldx, h->d_pperm, nrhs, c.fp64, s);
     c.launches++;
+    if (use_graph) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        h->graphs[key] = exec;
+        HM_CUDA(cudaGraphLaunch(exec, (cudaStream_t)caller_stream));
+        return HM_OK;
+    }
     HM_CUDA(cudaGetLastError());
     if (info) {
         memset(info, 0, sizeof(*info));
@@ -511,6 +590,7 @@ static hm_status import_blocks(const hm_blocks *B, cudaStream_t s, hm_matrix h)
     (void)usrc;
     if ((st = upload(h, &h->d_pool32, p32, s)) != HM_OK) return st;
     if (h->has_fp64 && (st = upload(h, &h->d_pool64, p64, s)) != HM_OK) return st;
+    if ((st = prepare_partials(h, s)) != HM_OK) return st;
     for (auto &kv : h->levels)
         if ((st = upload(h, &kv.second.d_items, kv.second.items, s)) != HM_OK) return st;
     // tree depth is not given by the import; report the number of levels instead
@@ -630,11 +710,9 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
     hm_status st = ensure_workspace(h, nrhs, c.m);
     if (st != HM_OK) return st;
     void *xt = h->ws.vec32[0], *yt = h->ws.vec32[1];
-    double2 *acc = (double2 *)h->ws.d_acc64;
     launch_permute_in(x, ldx, xt, h->pN, h->d_pperm, nrhs, false, s);
     if (fp64_accumulate) {
-        apply_acc64(c, (const float2 *)xt, acc);
-        launch_convert_f64_to_f32(acc, (float2 *)yt, h->pN * nrhs, s);
+        residual64(c, (const float2 *)xt, nullptr, (float2 *)yt, nullptr);
     } else {
         HM_CUDA(cudaMemsetAsync(yt, 0, c.vbytes, s));
         launch_apply_self_f32(h, (const float2 *)xt, (float2 *)yt, nrhs, s);
@@ -642,6 +720,36 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
     }
     launch_permute_out(yt, h->pN, y, ldy, h->d_pperm, nrhs, false, s);
     HM_CUDA(cudaGetLastError());
+    return HM_OK;
+}
+
+hm_status hm_residual(hm_matrix h, const void *b, int64_t ldb, const void *x, int64_t ldx, void *r, int64_t ldr,
+                      int nrhs, int n_levels, double *norms, void *stream)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    if (nrhs < 0 || ldb < h->N || ldx < h->N || ldr < h->N) return fail(HM_ERR_ARG, "bad nrhs or leading dimension");
+    if (nrhs == 0) return HM_OK;
+    if (!b || !x || !r) return fail(HM_ERR_ARG, "null b, x or r");
+    if (!h->factored) return fail(HM_ERR_STATE, "hm_factor_leaf has not completed (it also prepares D)");
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveCtx c;
+    c.h = h; c.nrhs = nrhs; c.K = 0; c.fp64 = false; c.s = s;
+    c.m = clamp_levels(h, n_levels);
+    c.vbytes = sizeof(float2) * h->pN * nrhs;
+    hm_status st = ensure_workspace(h, nrhs, c.m);
+    if (st != HM_OK) return st;
+    void *bt = h->ws.vec32[0], *xt = h->ws.vec32[1], *rt = h->ws.vec32[3];
+    launch_permute_in(b, ldb, bt, h->pN, h->d_pperm, nrhs, false, s);
+    launch_permute_in(x, ldx, xt, h->pN, h->d_pperm, nrhs, false, s);
+    double *dn = h->ws.d_acc64;
+    HM_CUDA(cudaMemsetAsync(dn, 0, 2 * sizeof(double) * nrhs, s));
+    residual64(c, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, dn);
+    launch_permute_out(rt, h->pN, r, ldr, h->d_pperm, nrhs, false, s);
+    HM_CUDA(cudaGetLastError());
+    if (norms) {
+        HM_CUDA(cudaMemcpyAsync(norms, dn, 2 * sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+    }
     return HM_OK;
 }
 

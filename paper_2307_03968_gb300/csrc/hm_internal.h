@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 #include <map>
+#include <tuple>
 
 #include "../../include/hmps.h"
 
@@ -32,7 +33,7 @@ struct Item {
     int32_t col0;   // padded-tree offset of the column cluster
     int32_t m, n;   // padded cluster lengths (dense: m = true rows, n = true cols)
     int32_t k;      // rank; 0 = dense block
-    int32_t pad;
+    int32_t pad;    // offset of the block's FP64 partial slot (row side, then column side)
 };
 static_assert(sizeof(Item) == 32, "Item layout");
 
@@ -57,7 +58,9 @@ struct Workspace {
     int nrhs = 0;
     // complex vectors [nrhs][pN], allocated for the current nrhs, per precision
     std::vector<void *> vec32, vec64;
-    double *d_acc64 = nullptr;    // FP64 accumulator for residuals [nrhs][pN] complex
+    double *d_acc64 = nullptr;    // norms of the residual (2 doubles per right-hand side)
+    double2 *d_part = nullptr;    // FP64 partial slots for PART_RHS right-hand sides
+    int part_rhs = 0;
     void *h_pinned = nullptr;     // pinned staging for host-buffer solves
     size_t h_pinned_bytes = 0;
     void *d_io = nullptr;         // device b / x for host-buffer solves
@@ -98,6 +101,12 @@ struct hm_matrix_s {
     bool has_fp64 = false;
     std::map<int, hm::LevelList> levels;
 
+    // partial slots of the deterministic FP64 products: per leaf and level, the
+    // list of slot positions holding contributions to that leaf's rows
+    int64_t partial_elems = 0;
+    int64_t *d_csr_off = nullptr;     // [n_leaves * (n_levels + 1)]
+    int64_t *d_csr_idx = nullptr;
+
     int *d_status = nullptr;          // device status word (hm_status code, first error wins)
     int *h_status = nullptr;          // pinned mirror
     hm::Workspace ws;
@@ -111,6 +120,18 @@ struct hm_matrix_s {
     int32_t *d_etri = nullptr, *d_efree = nullptr;
     double *d_elen = nullptr;
     double wavenumber = 0.0;
+
+    // CUDA graphs of whole solves, keyed by pointers, sizes and options
+    struct GraphKey {
+        const void *b; void *x; int64_t ldb, ldx; int nrhs, K, m, nested, refine, fp64;
+        bool operator<(const GraphKey &o) const
+        {
+            return std::tie(b, x, ldb, ldx, nrhs, K, m, nested, refine, fp64) <
+                   std::tie(o.b, o.x, o.ldb, o.ldx, o.nrhs, o.K, o.m, o.nested, o.refine, o.fp64);
+        }
+    };
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;
 
     // opt-in event timing of the product kernel
     bool prof = false;
@@ -141,19 +162,19 @@ void launch_zero(void *p, size_t bytes, cudaStream_t s);
 // z (+)= M_level x  for one item list; z must be pre-zeroed by the caller
 void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
                         cudaStream_t s);
-// FP64-accumulating apply: acc (double2) += A x over complex64 blocks
-void launch_apply_items_acc64(hm_matrix h, const LevelList &L, const float2 *x, double2 *acc, int nrhs,
-                              cudaStream_t s);
-void launch_apply_self_acc64(hm_matrix h, const float2 *x, double2 *acc, int nrhs, cudaStream_t s);
+// FP64 products of every block of a level into its partial slots (no atomics)
+void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride,
+                                 int nrhs, cudaStream_t s);
+// per leaf: acc = D x + sum of the leaf's partial slots of levels 1..m (FP64, fixed order);
+// out = b - acc (+ norms) when b is given, else out = acc (rounded to complex64)
+void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const double2 *part, int64_t pstride,
+                         const float2 *b, float2 *out, double *norms, int nrhs, cudaStream_t s);
 void launch_apply_self_f32(hm_matrix h, const float2 *x, float2 *acc, int nrhs, cudaStream_t s);
 // per leaf: out = (y ? y - Dinv zin : Dinv zin); if zero_in, zin is cleared afterwards
 void launch_leaf_update(hm_matrix h, const void *y, void *zin, void *out, int nrhs, bool zero_in, bool fp64,
                         cudaStream_t s);
 // out = y - w
 void launch_sub(const void *y, const void *w, void *out, int64_t n, bool fp64, cudaStream_t s);
-// r32 = b32 - acc, with acc = A x in FP64; also writes per-column |r|^2, |b|^2 into norms[2*nrhs]
-void launch_residual(const float2 *b, const double2 *acc, float2 *r, double *norms, int64_t pN, int nrhs,
-                     cudaStream_t s);
 void launch_add_inplace(void *x, const void *dx, int64_t n, bool fp64, cudaStream_t s);
 void launch_check_finite(const void *x, int64_t n, bool fp64, int *status, cudaStream_t s);
 void launch_convert_f64_to_f32(const double2 *a, float2 *b, int64_t n, cudaStream_t s);
@@ -172,5 +193,8 @@ hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *opts, cudaSt
 
 // shared construction helpers (hm_api.cu)
 hm_status finalize_layout(hm_matrix h, cudaStream_t s);
+// assigns the FP64 partial slots (Item::pad) and uploads the per-leaf slot lists;
+// call after every level list is complete and before the items are uploaded
+hm_status prepare_partials(hm_matrix h, cudaStream_t s);
 
 } // namespace hm

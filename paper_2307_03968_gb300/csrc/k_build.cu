@@ -1115,6 +1115,7 @@ hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *o, cudaStrea
             return st;
         launch_convert_f32_to_f64(h->d_pool32, h->d_pool64, std::max<int64_t>(pool, 1), s);
     }
+    if ((st = prepare_partials(h, s)) != HM_OK) return st;
     for (auto &kv : h->levels)
         if ((st = up(h, &kv.second.d_items, kv.second.items, s)) != HM_OK) return st;
     // geometry kept for the plane-wave excitation

@@ -46,7 +46,7 @@ class HmBlocks(ctypes.Structure):
 
 class HmSolveOpts(ctypes.Structure):
     _fields_ = [("n_terms", ctypes.c_int), ("n_levels", ctypes.c_int), ("nested", ctypes.c_int),
-                ("refine", ctypes.c_int), ("fp64", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("fp64", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class HmSolveInfo(ctypes.Structure):
@@ -62,7 +62,7 @@ class HmInfo(ctypes.Structure):
 
 
 EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_powerseries_solve",
-           "hm_powerseries_solve_host", "hm_apply", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
+           "hm_powerseries_solve_host", "hm_apply", "hm_residual", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
            "hm_get_info", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
            "hm_size", "hm_destroy", "hm_last_error", "hm_version"]
 
@@ -84,6 +84,7 @@ def load():
                                        ctypes.POINTER(HmSolveInfo)]
     L.hm_powerseries_solve_host.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.POINTER(HmSolveOpts), P]
     L.hm_apply.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    L.hm_residual.argtypes = [P, P, I64, P, I64, P, I64, ctypes.c_int, ctypes.c_int, PD, P]
     L.hm_rhs_plane_wave.argtypes = [P, PD, PD, ctypes.c_int, P, I64, P]
     L.hm_profile.argtypes = [P, ctypes.c_int]
     L.hm_profile_read.argtypes = [P, PD, PI64, PI64]
@@ -198,12 +199,13 @@ class HMatrix:
 
     # ---- solve / apply -------------------------------------------------------------------
     def solve(self, b, x, n_terms=2, n_levels=1, nested=True, refine=False, fp64=False, stream=None,
-              info=False):
+              info=False, graph=True):
         """hm_powerseries_solve on torch CUDA tensors b, x of shape (N,) or (nrhs, N)
         (each row one right-hand side, contiguous), complex64 (complex128 if fp64)."""
         nrhs, ldb = self._cols(b)
         _, ldx = self._cols(x)
-        o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0)
+        o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0,
+                        1 if graph else 0)
         si = HmSolveInfo()
         _check(load().hm_powerseries_solve(self._h, P(b.data_ptr()), ldb, P(x.data_ptr()), ldx, nrhs,
                                            ctypes.byref(o), _stream(stream), ctypes.byref(si) if info else None))
@@ -216,7 +218,7 @@ class HMatrix:
         x = np.empty_like(b)
         nrhs = 1 if b.ndim == 1 else b.shape[0]
         n = b.shape[-1]
-        o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0)
+        o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0, 1)
         _check(load().hm_powerseries_solve_host(self._h, P(b.ctypes.data), n, P(x.ctypes.data), n, nrhs,
                                                 ctypes.byref(o), _stream(stream)))
         return x
@@ -226,6 +228,16 @@ class HMatrix:
         _, ldy = self._cols(y)
         _check(load().hm_apply(self._h, P(x.data_ptr()), ldx, P(y.data_ptr()), ldy, nrhs, n_levels,
                                1 if fp64_accumulate else 0, _stream(stream)))
+
+    def residual(self, b, x, r, n_levels=-1, stream=None):
+        """hm_residual: r = b - A_m x (torch CUDA complex64); returns (|r|^2, |b|^2) per column."""
+        nrhs, ldb = self._cols(b)
+        _, ldx = self._cols(x)
+        _, ldr = self._cols(r)
+        norms = np.zeros(2 * max(nrhs, 1))
+        _check(load().hm_residual(self._h, P(b.data_ptr()), ldb, P(x.data_ptr()), ldx, P(r.data_ptr()), ldr, nrhs,
+                                  n_levels, _ptr(norms, ctypes.c_double), _stream(stream)))
+        return norms[0::2], norms[1::2]
 
     def rhs_plane_wave(self, khat, phat, b, stream=None):
         """hm_rhs_plane_wave into the torch CUDA tensor b (nrhs, N) complex64."""

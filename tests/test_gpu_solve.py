@@ -184,3 +184,37 @@ def test_layout_round_trip(torch_cuda, odd):
     U, V = A.block(lev, 0)
     Uo, Vo = odd.far[lev][0][4], odd.far[lev][0][5]
     assert np.array_equal(U, Uo.astype(np.complex64)) and np.array_equal(V, Vo.astype(np.complex64))
+
+
+def _rounded_operator(H):
+    """The oracle's operator with every stored block rounded to complex64, as the
+    library keeps it (complex128 copy so the oracle's products are FP64)."""
+    import copy
+    G = copy.copy(H)
+    c64 = lambda a: a.astype(np.complex64).astype(np.complex128)
+    G.D = [c64(d) for d in H.D]
+    G.near = [(a, b, c, d, c64(B)) for (a, b, c, d, B) in H.near]
+    G.far = {lev: [(a, b, c, d, c64(U), c64(V)) for (a, b, c, d, U, V) in lst] for lev, lst in H.far.items()}
+    return G
+
+
+@pytest.mark.parametrize("levels", [1, -1])
+def test_residual_is_fp64_class(torch_cuda, ml2, levels):
+    """b = A x rounded to complex64, so the true residual is ~1e-8 |A x|: an
+    FP32-accumulated residual would be wrong by more than its own size; the
+    FP64-class one must match the FP64 oracle residual to 1e-3 of |r|."""
+    G = _rounded_operator(ml2)
+    rng = np.random.default_rng(12)
+    x = (rng.normal(size=(2, G.N)) + 1j * rng.normal(size=(2, G.N))).astype(np.complex64)
+    y = np.ascontiguousarray(G.from_tree(G.apply(G.to_tree(x.T.astype(np.complex128)), levels)).T)  # FP64 A x
+    b = np.ascontiguousarray(y.astype(np.complex64))
+    r_ref = b.astype(np.complex128) - y
+    A = gpu_operator(ml2)
+    bt = torch_cuda.from_numpy(b).cuda()
+    xt = torch_cuda.from_numpy(x).cuda()
+    rt = torch_cuda.empty_like(bt)
+    rr, bb = A.residual(bt, xt, rt, n_levels=levels)
+    r = rt.cpu().numpy()
+    assert rel_err(r, r_ref) < 1e-3
+    assert np.allclose(rr, np.sum(np.abs(r_ref) ** 2, axis=1), rtol=1e-3)
+    assert np.allclose(bb, np.sum(np.abs(b.astype(np.complex128)) ** 2, axis=1), rtol=1e-6)
