@@ -196,6 +196,28 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
 hm_status hm_residual(hm_matrix h, const void *b, int64_t ldb, const void *x, int64_t ldx, void *r, int64_t ldr,
                       int nrhs, int n_levels, double *norms, void *stream);
 
+/*
+ * hm_residual_noalloc: the same residual as hm_residual (same arguments, same
+ * result), for callers that must not allocate device memory after start-up.
+ * One example is a serving process whose memory is reserved up front by a
+ * framework's caching allocator, where a late cudaMalloc may fail or stall the
+ * device mid-request.  Real-time loops are another.  hm_residual may grow the
+ * handle's workspace; this call never allocates (no cudaMalloc, cudaFree or
+ * allocating library routine).  It keeps all temporary data in one fixed
+ * 32 MiB array in device memory that every GPU loading the library holds until
+ * the process exits.  Calls whose operator and nrhs need more than that
+ * (3 complex64 vectors of padded length x nrhs, 2 doubles per right-hand side,
+ * and the FP64 partial slots of one right-hand side) return HM_ERR_ARG before
+ * any device work.
+ * The first call on each device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the previous call's contents: calls that may overlap on the GPU (other
+ * streams, other threads, other handles) race and must be serialised by the
+ * caller.  The paper has no counterpart; this is an interface of this library.
+ */
+hm_status hm_residual_noalloc(hm_matrix h, const void *b, int64_t ldb, const void *x, int64_t ldx, void *r,
+                              int64_t ldr, int nrhs, int n_levels, double *norms, void *stream);
+
 /* ------------------------------------------------------------ excitation --- */
 
 /*

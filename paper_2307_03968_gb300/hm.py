@@ -62,7 +62,7 @@ class HmInfo(ctypes.Structure):
 
 
 EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_powerseries_solve",
-           "hm_powerseries_solve_host", "hm_apply", "hm_residual", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
+           "hm_powerseries_solve_host", "hm_apply", "hm_residual", "hm_residual_noalloc", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
            "hm_get_info", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
            "hm_size", "hm_destroy", "hm_last_error", "hm_version"]
 
@@ -85,6 +85,7 @@ def load():
     L.hm_powerseries_solve_host.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.POINTER(HmSolveOpts), P]
     L.hm_apply.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
     L.hm_residual.argtypes = [P, P, I64, P, I64, P, I64, ctypes.c_int, ctypes.c_int, PD, P]
+    L.hm_residual_noalloc.argtypes = [P, P, I64, P, I64, P, I64, ctypes.c_int, ctypes.c_int, PD, P]
     L.hm_rhs_plane_wave.argtypes = [P, PD, PD, ctypes.c_int, P, I64, P]
     L.hm_profile.argtypes = [P, ctypes.c_int]
     L.hm_profile_read.argtypes = [P, PD, PI64, PI64]
