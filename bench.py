@@ -190,12 +190,12 @@ def committed_traffic():
     summary, if it was taken on the current kernel source; else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2307_03968_gb300", "csrc", "k_solve.cu")
+    src = os.path.join(ROOT, "paper_2307_03968_gb300", "csrc", "k_product.cu")
     try:
         with open(path) as f:
             d = json.load(f)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if d.get("k_solve_sha256_16") == h and d.get("workload") == WORKLOAD["name"]:
+        if d.get("k_product_sha256_16") == h and d.get("workload") == WORKLOAD["name"]:
             return d.get("bytes_per_launch")
     except Exception:
         pass
@@ -339,7 +339,7 @@ def main():
     per_launch_bytes = prof_bytes / max(prof_n, 1)
     per_launch_ms = prof_ms / max(prof_n, 1)
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if prof_n else None
-    roof = {"bound": "hbm", "kernel": "k_apply_items<float,float> (near + leaf far block product)",
+    roof = {"bound": "hbm", "kernel": "k_apply_items<float,float,2> (near + leaf-level far block product, k_product.cu)",
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": committed_traffic(),
             "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms, "launches": prof_n,

@@ -37,9 +37,9 @@ struct Item {
 };
 static_assert(sizeof(Item) == 32, "Item layout");
 
-inline int64_t even(int64_t v) { return (v + 1) & ~int64_t(1); }
+__host__ __device__ inline int64_t even(int64_t v) { return (v + 1) & ~int64_t(1); }
 
-inline int64_t item_elems(const Item &it)
+__host__ __device__ inline int64_t item_elems(const Item &it)
 {
     if (it.k == 0) return int64_t(it.m) * even(it.n);
     return int64_t(it.k) * (even(it.m) + even(it.n));

@@ -1,0 +1,402 @@
+// FP64-class residual of the refinement step, r = b - A_m x, over complex64
+// blocks (the precision rule of the solve: the final residual check runs at
+// FP64-class accuracy).  k_residual_items writes every block's products into
+// its FP64 partial slots (no atomics); k_gather_acc64 sums each leaf's slots in a
+// fixed order in FP64, adds D_I x_I and forms b - A x.
+#include "k_common.cuh"
+
+namespace hm {
+namespace {
+
+using namespace kc;
+constexpr int APPLY_WARPS = 8;
+
+// ---------------------------------------------------------------------------
+// FP64-class products for the refinement residual (complex64 data).
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so a full-operator pass
+// in FP64 arithmetic costs many times its HBM time.  The residual products
+// therefore use error-free transformations in FP32 (Ogita, Rump & Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2):
+// every product a*b is split exactly into p + e with e = fma(a, b, -p), and
+// every sum is compensated (Knuth's TwoSum), so each block's sums are as
+// accurate as if computed in twice the working precision.  The per-block
+// results are stored as FP64 partial slots and summed across blocks in FP64.
+struct df { float hi, lo; };
+struct cdf { df re, im; };
+
+// The error-free transformations below must not be contracted into FMAs or
+// reassociated, so every operation is an explicitly rounded intrinsic.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// acc += a * b  (Dot2 step): p + ep == a * b exactly
+__device__ __forceinline__ void dot2(df &acc, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float ep = __fmaf_rn(a, b, -p);
+    float s, q;
+    two_sum(acc.hi, p, s, q);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(q, ep));
+}
+// acc += a * b for complex a (FP32) and b (FP32)
+__device__ __forceinline__ void cdot2(cdf &acc, float2 a, float2 b)
+{
+    dot2(acc.re, a.x, b.x);
+    dot2(acc.re, -a.y, b.y);
+    dot2(acc.im, a.x, b.y);
+    dot2(acc.im, a.y, b.x);
+}
+// acc += a * (bh + bl) for complex a and a double-float complex b
+__device__ __forceinline__ void cdot2_df(cdf &acc, float2 a, const cdf &b)
+{
+    cdot2(acc, a, make_float2(b.re.hi, b.im.hi));
+    acc.re.lo += a.x * b.re.lo - a.y * b.im.lo;
+    acc.im.lo += a.x * b.im.lo + a.y * b.re.lo;
+}
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ cdf cdf_add(const cdf &a, const cdf &b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ cdf shfl_xor(const cdf &v, int s)
+{
+    return {{__shfl_xor_sync(FULL, v.re.hi, s), __shfl_xor_sync(FULL, v.re.lo, s)},
+            {__shfl_xor_sync(FULL, v.im.hi, s), __shfl_xor_sync(FULL, v.im.lo, s)}};
+}
+__device__ __forceinline__ cdf shfl_idx(const cdf &v, int l)
+{
+    return {{__shfl_sync(FULL, v.re.hi, l), __shfl_sync(FULL, v.re.lo, l)},
+            {__shfl_sync(FULL, v.im.hi, l), __shfl_sync(FULL, v.im.lo, l)}};
+}
+__device__ __forceinline__ double2 to_d2(const cdf &v)
+{
+    return make_double2((double)v.re.hi + (double)v.re.lo, (double)v.im.hi + (double)v.im.lo);
+}
+// lane l ends with the sum over all lanes of v[l & (S-1)] in v[0] (S = 8 or 4)
+template <int S>
+__device__ __forceinline__ void reduce_cdf(cdf (&v)[S], int lane)
+{
+#pragma unroll
+    for (int s = S / 2; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+            const cdf send = up ? v[j] : v[j + s];
+            const cdf keep = up ? v[j + s] : v[j];
+            v[j] = cdf_add(keep, shfl_xor(send, s));
+        }
+    }
+#pragma unroll
+    for (int s = S; s < 32; s <<= 1) v[0] = cdf_add(v[0], shfl_xor(v[0], s));
+}
+
+// Dense block: slot rows (even(m)) = B x_J, slot columns (even(n)) = B^T x_I.
+__device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__restrict__ pool,
+                                             const float2 *__restrict__ x, double2 *__restrict__ part, float2 *xs,
+                                             int lane)
+{
+    const float2 *B = pool + it.off;
+    const int m = it.m, n = it.n, ld = even_d(n), em = even_d(m);
+    for (int c0 = 0; c0 < n; c0 += 64) {
+        const int j = c0 + 2 * lane;
+        const bool jv = j < n;
+        float2 xj0 = make_float2(0.f, 0.f), xj1 = xj0;
+        if (jv) {
+            xj0 = x[it.col0 + j];
+            if (j + 1 < n) xj1 = x[it.col0 + j + 1];
+        }
+        cdf cs0 = cdf_zero(), cs1 = cdf_zero();
+        for (int r0 = 0; r0 < m; r0 += 32) {
+            __syncwarp();
+            xs[lane] = (r0 + lane < m) ? x[it.row0 + r0 + lane] : make_float2(0.f, 0.f);
+            __syncwarp();
+            for (int q = 0; q < 4; ++q) {
+                const int rb = r0 + 8 * q;
+                if (rb >= m) break;
+                cdf rp[8];
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) {
+                    const int i = rb + rr;
+                    Pair<float> b{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    if (jv && i < m) b = ld_stream(B + (int64_t)i * ld + j);
+                    const float2 xi = xs[8 * q + rr];
+                    cdot2(cs0, b.a, xi);
+                    cdot2(cs1, b.b, xi);
+                    rp[rr] = cdf_zero();
+                    cdot2(rp[rr], b.a, xj0);
+                    cdot2(rp[rr], b.b, xj1);
+                }
+                reduce_cdf<8>(rp, lane);
+                const int row = rb + lane;
+                if (lane < 8 && row < em) part[it.pad + row] = to_d2(rp[0]);
+            }
+        }
+        if (jv) {
+            part[it.pad + em + j] = to_d2(cs0);
+            part[it.pad + em + j + 1] = to_d2(cs1);
+        }
+    }
+}
+
+// Low-rank block U V: slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I);
+// the rank-k intermediates stay in double-float.
+__device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__restrict__ pool,
+                                               const float2 *__restrict__ x, double2 *__restrict__ part, int lane)
+{
+    const int m = it.m, n = it.n, k = it.k;
+    const float2 *UT = pool + it.off;
+    const float2 *V = UT + (int64_t)k * m;
+    if (m <= 64 && n <= 64) {
+        // registers hold a chunk of 4 rank rows of both panels; outputs stay in
+        // registers across chunks and are stored once
+        const int i = 2 * lane;
+        const bool iv = i < m, jv = i < n;
+        Pair<float> xi{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, xj = xi;
+        if (iv) xi = ld_vec(x + it.row0 + i);
+        if (jv) xj = ld_vec(x + it.col0 + i);
+        cdf oi0 = cdf_zero(), oi1 = cdf_zero(), oj0 = cdf_zero(), oj1 = cdf_zero();
+        for (int l0 = 0; l0 < k; l0 += 4) {
+            Pair<float> u[4], v[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                u[l] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                v[l] = u[l];
+                if (l0 + l < k) {
+                    if (iv) u[l] = ld_stream(UT + (int64_t)(l0 + l) * m + i);
+                    if (jv) v[l] = ld_stream(V + (int64_t)(l0 + l) * n + i);
+                }
+            }
+            cdf tp[4], t[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                tp[l] = cdf_zero();
+                cdot2(tp[l], u[l].a, xi.a);
+                cdot2(tp[l], u[l].b, xi.b);
+                t[l] = cdf_zero();
+                cdot2(t[l], v[l].a, xj.a);
+                cdot2(t[l], v[l].b, xj.b);
+            }
+            reduce_cdf<4>(tp, lane);
+            reduce_cdf<4>(t, lane);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                if (l0 + l >= k) break;
+                const cdf tl = shfl_idx(t[0], l), tpl = shfl_idx(tp[0], l);
+                cdot2_df(oi0, u[l].a, tl);
+                cdot2_df(oi1, u[l].b, tl);
+                cdot2_df(oj0, v[l].a, tpl);
+                cdot2_df(oj1, v[l].b, tpl);
+            }
+        }
+        if (iv) { part[it.pad + i] = to_d2(oi0); part[it.pad + i + 1] = to_d2(oi1); }
+        if (jv) { part[it.pad + m + i] = to_d2(oj0); part[it.pad + m + i + 1] = to_d2(oj1); }
+        return;
+    }
+    for (int l0 = 0; l0 < k; l0 += 4) {
+        cdf tp[4], t[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) { tp[l] = cdf_zero(); t[l] = cdf_zero(); }
+        for (int c0 = 0; c0 < m; c0 += 64) {
+            const int i = c0 + 2 * lane;
+            if (i >= m) continue;
+            const Pair<float> xp = ld_vec(x + it.row0 + i);
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                if (l0 + l < k) {
+                    const Pair<float> u = ld_cached(UT + (int64_t)(l0 + l) * m + i);
+                    cdot2(tp[l], u.a, xp.a);
+                    cdot2(tp[l], u.b, xp.b);
+                }
+        }
+        for (int c0 = 0; c0 < n; c0 += 64) {
+            const int j = c0 + 2 * lane;
+            if (j >= n) continue;
+            const Pair<float> xp = ld_vec(x + it.col0 + j);
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                if (l0 + l < k) {
+                    const Pair<float> v = ld_cached(V + (int64_t)(l0 + l) * n + j);
+                    cdot2(t[l], v.a, xp.a);
+                    cdot2(t[l], v.b, xp.b);
+                }
+        }
+        reduce_cdf<4>(tp, lane);
+        reduce_cdf<4>(t, lane);
+        cdf tb[4], tpb[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) { tb[l] = shfl_idx(t[0], l); tpb[l] = shfl_idx(tp[0], l); }
+        for (int c0 = 0; c0 < m; c0 += 64) {
+            const int i = c0 + 2 * lane;
+            if (i >= m) continue;
+            cdf o0 = cdf_zero(), o1 = cdf_zero();
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                if (l0 + l < k) {
+                    const Pair<float> u = ld_cached(UT + (int64_t)(l0 + l) * m + i);
+                    cdot2_df(o0, u.a, tb[l]);
+                    cdot2_df(o1, u.b, tb[l]);
+                }
+            double2 *q = part + it.pad + i;
+            const double2 a0 = to_d2(o0), a1 = to_d2(o1);
+            if (l0 == 0) { q[0] = a0; q[1] = a1; }
+            else { q[0] = cadd(q[0], a0); q[1] = cadd(q[1], a1); }
+        }
+        for (int c0 = 0; c0 < n; c0 += 64) {
+            const int j = c0 + 2 * lane;
+            if (j >= n) continue;
+            cdf o0 = cdf_zero(), o1 = cdf_zero();
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                if (l0 + l < k) {
+                    const Pair<float> v = ld_cached(V + (int64_t)(l0 + l) * n + j);
+                    cdot2_df(o0, v.a, tpb[l]);
+                    cdot2_df(o1, v.b, tpb[l]);
+                }
+            double2 *q = part + it.pad + m + j;
+            const double2 a0 = to_d2(o0), a1 = to_d2(o1);
+            if (l0 == 0) { q[0] = a0; q[1] = a1; }
+            else { q[0] = cadd(q[0], a0); q[1] = cadd(q[1], a1); }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(APPLY_WARPS * 32, 2)
+k_residual_items(const Item *__restrict__ items, int64_t n_items, const float2 *__restrict__ pool,
+                 const float2 *__restrict__ x, int64_t ldx, double2 *__restrict__ part, int64_t pstride, int nrhs)
+{
+    __shared__ float2 xs_all[APPLY_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * APPLY_WARPS;
+    for (int64_t t = (int64_t)blockIdx.x * APPLY_WARPS + w; t < n_items; t += nw) {
+        const Item it = items[t];
+        for (int r = 0; r < nrhs; ++r) {
+            if (it.k == 0) dense_item_c(it, pool, x + r * ldx, part + r * pstride, xs_all[w], lane);
+            else lowrank_item_c(it, pool, x + r * ldx, part + r * pstride, lane);
+        }
+    }
+}
+
+// Per leaf (blockIdx.x) and right-hand side (blockIdx.y): acc = D_I x_I +
+// sum of the leaf's partial slots of levels 1..m, in FP64 and in a fixed order
+// (each of the 4 warps sums every 4th slot, lanes own row pairs; the warps are
+// then added in warp order).  If b is given, out = b - acc (complex64) and
+// |r|^2, |b|^2 go to norms; else out = acc (complex64).  No atomics on sums.
+__global__ void __launch_bounds__(128)
+k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
+               const float2 *__restrict__ self32, const float2 *__restrict__ x, int64_t ld,
+               const int64_t *__restrict__ csr_off, int csr_stride, int m, const int64_t *__restrict__ csr_idx,
+               const double2 *__restrict__ part, int64_t pstride, const float2 *__restrict__ b,
+               float2 *__restrict__ out, double *norms)
+{
+    constexpr int MAXR = 128;
+    __shared__ double2 acc_s[4][MAXR];
+    __shared__ double2 xs[MAXR];
+    const int leaf = blockIdx.x, r = blockIdx.y;
+    const int o = pleaf_off[leaf], np = pleaf_off[leaf + 1] - o;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int j = tid; j < np; j += blockDim.x) xs[j] = conv<double2>(x[r * ld + o + j]);
+    __syncthreads();
+    const double2 *P = part + r * pstride;
+    const int64_t e0 = csr_off[(int64_t)leaf * csr_stride], e1 = csr_off[(int64_t)leaf * csr_stride + m];
+    for (int rc = 0; rc < np; rc += 64) {
+        const int i = rc + 2 * lane;
+        double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
+        if (i < np) {
+            int64_t e = e0 + w;
+            for (; e + 12 < e1; e += 16) {      // four slots in flight per warp
+                const int64_t q0 = csr_idx[e], q1 = csr_idx[e + 4], q2 = csr_idx[e + 8], q3 = csr_idx[e + 12];
+                const double2 v00 = P[q0 + i], v01 = P[q0 + i + 1], v10 = P[q1 + i], v11 = P[q1 + i + 1];
+                const double2 v20 = P[q2 + i], v21 = P[q2 + i + 1], v30 = P[q3 + i], v31 = P[q3 + i + 1];
+                a0 = cadd(a0, cadd(cadd(v00, v10), cadd(v20, v30)));
+                a1 = cadd(a1, cadd(cadd(v01, v11), cadd(v21, v31)));
+            }
+            for (; e < e1; e += 4) {
+                const int64_t q = csr_idx[e];
+                a0 = cadd(a0, P[q + i]);
+                a1 = cadd(a1, P[q + i + 1]);
+            }
+            if (w == 0) {   // the self block, FP64
+                const float2 *S = self32 + dinv_off[leaf];   // column-major
+                for (int j = 0; j < np; ++j) {
+                    const Pair<float> d = ld_vec(S + (int64_t)j * np + i);
+                    cfma(a0, conv<double2>(d.a), xs[j]);
+                    cfma(a1, conv<double2>(d.b), xs[j]);
+                }
+            }
+        }
+        acc_s[w][2 * lane] = a0;
+        acc_s[w][2 * lane + 1] = a1;
+        __syncthreads();
+        double rr = 0.0, bb = 0.0;
+        if (tid < 64 && rc + tid < np) {
+            double2 acc = acc_s[0][tid];
+            for (int q = 1; q < 4; ++q) acc = cadd(acc, acc_s[q][tid]);
+            const int64_t g = r * ld + o + rc + tid;
+            if (b) {
+                const double2 bv = conv<double2>(b[g]);
+                const double2 rv = csub(bv, acc);
+                out[g] = make_float2((float)rv.x, (float)rv.y);
+                rr = rv.x * rv.x + rv.y * rv.y;
+                bb = bv.x * bv.x + bv.y * bv.y;
+            } else {
+                out[g] = make_float2((float)acc.x, (float)acc.y);
+            }
+        }
+        if (norms && tid < 64) {
+            for (int s = 16; s >= 1; s >>= 1) {
+                rr += __shfl_xor_sync(FULL, rr, s);
+                bb += __shfl_xor_sync(FULL, bb, s);
+            }
+            if (lane == 0) {
+                atomicAdd(&norms[2 * r], rr);
+                atomicAdd(&norms[2 * r + 1], bb);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+} // namespace
+
+void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride,
+                                 int nrhs, cudaStream_t s)
+{
+    const int64_t n = (int64_t)L.items.size();
+    if (n == 0) return;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_residual_items, APPLY_WARPS * 32, 0);
+        per_sm = v > 0 ? v : 1;
+    }
+    int g = per_sm * (h->num_sms > 0 ? h->num_sms : 1);
+    if ((int64_t)g * APPLY_WARPS > n) g = (int)((n + APPLY_WARPS - 1) / APPLY_WARPS);
+    k_residual_items<<<g, APPLY_WARPS * 32, 0, s>>>(L.d_items, n, h->d_pool32, x, h->pN, part, pstride, nrhs);
+}
+
+void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const double2 *part, int64_t pstride,
+                         const float2 *b, float2 *out, double *norms, int nrhs, cudaStream_t s)
+{
+    dim3 grid((unsigned)h->n_leaves, (unsigned)nrhs);
+    const int64_t maxnp = [&] {
+        int64_t v = 0;
+        for (int64_t i = 0; i < h->n_leaves; ++i) v = std::max<int64_t>(v, h->pleaf_off[i + 1] - h->pleaf_off[i]);
+        return v;
+    }();
+    (void)maxnp;
+    k_gather_acc64<<<grid, 128, 0, s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_self32, x, h->pN,
+                                                              h->d_csr_off, h->n_levels + 1, m, h->d_csr_idx, part,
+                                                              pstride, b, out, norms);
+}
+
+} // namespace hm
