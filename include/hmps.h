@@ -249,6 +249,41 @@ hm_status hm_profile(hm_matrix h, int enable);
  */
 hm_status hm_profile_read(hm_matrix h, double *product_ms, int64_t *launches, int64_t *bytes);
 
+/* --------------------------------------------------------------- serving --- */
+
+/*
+ * Continuous-batching solve server.  Operators are registered as meshes (with
+ * build and solve options) and built on the GPU on first use.  Requests carry
+ * nrhs right-hand sides in host memory and are queued per operator.  A
+ * scheduler thread merges the queued requests of one operator, in arrival
+ * order, into one multi-RHS solve of at most max_batch_rhs columns.  It runs
+ * batches of different operators concurrently on n_slots CUDA streams (their
+ * kernels overlap on the device).  Before building an operator it evicts idle
+ * least-recently-used operators until the resident device bytes fit
+ * hbm_budget_bytes (a target: an operator larger than the budget is still
+ * admitted when nothing else is resident).  Requests that arrive while
+ * others run join the next batch of their operator.  Complex64 only.
+ * The server owns its operators; all calls are thread safe.
+ */
+typedef struct hm_server_s *hm_server;
+typedef struct {
+    int64_t batches, solved_rhs, builds, evictions, resident_bytes, peak_resident_bytes;
+} hm_server_info;
+
+hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_rhs, hm_server *out);
+/* Registers a mesh; *n_unknowns receives its RWG count N (the length of every
+ * right-hand side of this operator). */
+hm_status hm_server_add_mesh(hm_server s, const hm_mesh *mesh, const hm_build_opts *bo, const hm_solve_opts *so,
+                             int *op_id, int64_t *n_unknowns);
+/* Queues nrhs right-hand sides b (host, complex64, N x nrhs column-major, copied
+ * during the call); n must equal the operator's N. */
+hm_status hm_server_submit(hm_server s, int op_id, const void *b, int64_t n, int nrhs, int64_t *req_id);
+/* Blocks until the request is solved (at most 600 s), copies its solution to x
+ * (host, N x nrhs) and gives the submit-to-completion latency in ms. */
+hm_status hm_server_wait(hm_server s, int64_t req_id, void *x, double *latency_ms);
+hm_status hm_server_get_info(hm_server s, hm_server_info *info);
+void hm_server_destroy(hm_server s);
+
 /* ---------------------------------------------------------- inspection --- */
 
 typedef struct {

@@ -1,0 +1,418 @@
+// Continuous-batching solve server (host runtime around the solve kernels).
+//
+// Requests (operator id, right-hand sides in host memory) are queued per
+// operator.  A scheduler thread repeatedly
+//   1. retires finished batches (event query on each slot's stream), copies the
+//      solutions out of the slot's pinned buffer into each request's result and
+//      records its latency (submit -> completion);
+//   2. for every operator with queued requests and no batch in flight, takes
+//      requests in arrival order until max_batch_rhs right-hand sides, makes the
+//      operator resident (building it on the GPU on first use, after evicting
+//      idle least-recently-used operators until the HBM budget admits it), and
+//      launches one multi-RHS solve on a free slot: H2D copy, the power-series
+//      solve, D2H copy, event record, all on the slot's stream.
+// Batches of different operators run on different streams and overlap on the
+// device; requests that arrive while others run join the next batch of their
+// operator as soon as its previous batch retires.  One handle never has two
+// batches in flight (its workspace is per handle).
+#include "hm_internal.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Request {
+    int64_t id;
+    int op;
+    int nrhs;
+    std::vector<float2> b;    // N x nrhs, column-major
+    std::vector<float2> x;
+    clk::time_point t_submit, t_done;
+    bool done = false;
+    hm_status status = HM_OK;
+};
+
+struct Operator {
+    std::vector<double> xyz;
+    std::vector<int32_t> tri;
+    double wavelength;
+    hm_build_opts bo;
+    hm_solve_opts so;
+    hm_matrix h = nullptr;
+    int64_t n = 0;
+    int64_t bytes = 0;         // device bytes when resident (estimate before the first build)
+    bool busy = false;
+    clk::time_point last_use;
+    std::deque<int64_t> queue;
+    int builds = 0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    float2 *h_buf = nullptr;   // pinned: b then x
+    float2 *d_b = nullptr, *d_x = nullptr;
+    size_t cap = 0;            // complex elements per half
+    bool busy = false;
+    int op = -1;
+    std::vector<int64_t> reqs;
+    int nrhs = 0;
+};
+
+} // namespace
+
+struct hm_server_s {
+    int max_batch_rhs;
+    int64_t budget;
+    std::vector<Slot> slots;
+    std::vector<Operator> ops;
+    std::map<int64_t, Request> reqs;
+    int64_t next_id = 1;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    std::atomic<bool> stop{false};
+    hm_status fatal = HM_OK;
+    std::string fatal_msg;
+    int device = 0;
+    // statistics
+    int64_t batches = 0, solved_rhs = 0, evictions = 0, builds = 0;
+    int64_t resident_bytes = 0, peak_resident = 0;
+};
+
+namespace {
+
+hm_status slot_reserve(Slot &s, size_t elems)
+{
+    if (s.cap >= elems) return HM_OK;
+    if (s.h_buf) cudaFreeHost(s.h_buf);
+    if (s.d_b) cudaFree(s.d_b);
+    if (s.d_x) cudaFree(s.d_x);
+    s.h_buf = nullptr; s.d_b = s.d_x = nullptr; s.cap = 0;
+    HM_CUDA(cudaMallocHost((void **)&s.h_buf, 2 * elems * sizeof(float2)));
+    HM_CUDA(cudaMalloc((void **)&s.d_b, elems * sizeof(float2)));
+    HM_CUDA(cudaMalloc((void **)&s.d_x, elems * sizeof(float2)));
+    s.cap = elems;
+    return HM_OK;
+}
+
+// make operator op resident, evicting idle LRU operators to respect the budget
+hm_status make_resident(hm_server_s *S, int op)
+{
+    Operator &o = S->ops[op];
+    if (o.h) return HM_OK;
+    const int64_t need = o.bytes;
+    while (S->resident_bytes + need > S->budget) {
+        int victim = -1;
+        for (int i = 0; i < (int)S->ops.size(); ++i) {
+            const Operator &c = S->ops[i];
+            if (c.h && !c.busy && (victim < 0 || c.last_use < S->ops[victim].last_use)) victim = i;
+        }
+        if (victim < 0) break;   // everything resident is in use: admit anyway, the budget is a target
+        hm_destroy(S->ops[victim].h);
+        S->ops[victim].h = nullptr;
+        S->resident_bytes -= S->ops[victim].bytes;
+        S->evictions++;
+    }
+    hm_mesh mesh{(int64_t)o.xyz.size() / 3, o.xyz.data(), (int64_t)o.tri.size() / 3, o.tri.data(), o.wavelength};
+    hm_matrix h = nullptr;
+    hm_status st = hm_build(&mesh, &o.bo, nullptr, &h);
+    if (st != HM_OK) return st;
+    st = hm_factor_leaf(h, nullptr);
+    if (st != HM_OK) {
+        hm_destroy(h);
+        return st;
+    }
+    hm_info info;
+    hm_get_info(h, &info);
+    o.h = h;
+    o.n = info.n;
+    o.bytes = info.device_bytes;
+    o.builds++;
+    S->builds++;
+    S->resident_bytes += o.bytes;
+    S->peak_resident = std::max(S->peak_resident, S->resident_bytes);
+    return HM_OK;
+}
+
+void retire(hm_server_s *S, Slot &s)
+{
+    const int64_t N = S->ops[s.op].n;
+    const float2 *hx = s.h_buf + s.cap;
+    int col = 0;
+    const auto now = clk::now();
+    for (int64_t id : s.reqs) {
+        Request &r = S->reqs[id];
+        r.x.assign(hx + (size_t)col * N, hx + (size_t)(col + r.nrhs) * N);
+        col += r.nrhs;
+        r.t_done = now;
+        r.done = true;
+    }
+    S->ops[s.op].busy = false;
+    S->ops[s.op].last_use = now;
+    S->solved_rhs += s.nrhs;
+    s.busy = false;
+    s.reqs.clear();
+    s.op = -1;
+}
+
+void fail_requests(hm_server_s *S, int op, hm_status st)
+{
+    Operator &o = S->ops[op];
+    for (int64_t id : o.queue) {
+        Request &r = S->reqs[id];
+        r.status = st;
+        r.done = true;
+        r.t_done = clk::now();
+    }
+    o.queue.clear();
+}
+
+void loop(hm_server_s *S)
+{
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        bool progressed = false;
+        // 1. retire finished batches
+        for (Slot &s : S->slots) {
+            if (!s.busy) continue;
+            const cudaError_t e = cudaEventQuery(s.done);
+            if (e == cudaSuccess) {
+                retire(S, s);
+                progressed = true;
+            } else if (e != cudaErrorNotReady) {
+                S->fatal = HM_ERR_CUDA;
+                S->fatal_msg = cudaGetErrorString(e);
+                S->stop = true;
+            }
+        }
+        if (progressed) S->cv_done.notify_all();
+        // 2. launch new batches
+        for (int op = 0; op < (int)S->ops.size(); ++op) {
+            Operator &o = S->ops[op];
+            if (o.busy || o.queue.empty()) continue;
+            Slot *slot = nullptr;
+            for (Slot &s : S->slots)
+                if (!s.busy) { slot = &s; break; }
+            if (!slot) break;
+            hm_status st = make_resident(S, op);
+            if (st != HM_OK) {
+                fail_requests(S, op, st);
+                S->cv_done.notify_all();
+                continue;
+            }
+            // take requests in arrival order up to max_batch_rhs right-hand sides
+            std::vector<int64_t> take;
+            int nrhs = 0;
+            while (!o.queue.empty()) {
+                const Request &r = S->reqs[o.queue.front()];
+                if (!take.empty() && nrhs + r.nrhs > S->max_batch_rhs) break;
+                take.push_back(o.queue.front());
+                nrhs += r.nrhs;
+                o.queue.pop_front();
+            }
+            const int64_t N = o.n;
+            st = slot_reserve(*slot, (size_t)N * nrhs);
+            if (st != HM_OK) {
+                for (int64_t id : take) { S->reqs[id].status = st; S->reqs[id].done = true; }
+                S->cv_done.notify_all();
+                continue;
+            }
+            int col = 0;
+            for (int64_t id : take) {
+                const Request &r = S->reqs[id];
+                std::memcpy(slot->h_buf + (size_t)col * N, r.b.data(), sizeof(float2) * N * r.nrhs);
+                col += r.nrhs;
+            }
+            cudaMemcpyAsync(slot->d_b, slot->h_buf, sizeof(float2) * N * nrhs, cudaMemcpyHostToDevice, slot->stream);
+            st = hm_powerseries_solve(o.h, slot->d_b, N, slot->d_x, N, nrhs, &o.so, slot->stream, nullptr);
+            if (st != HM_OK) {
+                for (int64_t id : take) { S->reqs[id].status = st; S->reqs[id].done = true; }
+                S->cv_done.notify_all();
+                continue;
+            }
+            cudaMemcpyAsync(slot->h_buf + slot->cap, slot->d_x, sizeof(float2) * N * nrhs, cudaMemcpyDeviceToHost,
+                            slot->stream);
+            cudaEventRecord(slot->done, slot->stream);
+            slot->busy = true;
+            slot->op = op;
+            slot->reqs = take;
+            slot->nrhs = nrhs;
+            o.busy = true;
+            o.last_use = clk::now();
+            S->batches++;
+            progressed = true;
+        }
+        if (!progressed) {
+            bool any_busy = false;
+            for (Slot &s : S->slots) any_busy |= s.busy;
+            if (any_busy) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                lk.lock();
+            } else {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            }
+        }
+    }
+}
+
+} // namespace
+
+using namespace hm;
+
+extern "C" {
+
+hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_rhs, hm_server *out)
+{
+    if (!out || n_slots < 1 || n_slots > 64 || hbm_budget_bytes <= 0 || max_batch_rhs < 1)
+        return fail(HM_ERR_ARG, "bad server arguments");
+    *out = nullptr;
+    hm_server S = new hm_server_s();
+    S->max_batch_rhs = max_batch_rhs;
+    S->budget = hbm_budget_bytes;
+    cudaGetDevice(&S->device);
+    S->slots.resize(n_slots);
+    for (Slot &s : S->slots) {
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            hm_server_destroy(S);
+            return fail(HM_ERR_CUDA, "stream or event creation failed");
+        }
+    }
+    S->worker = std::thread(loop, S);
+    *out = S;
+    return HM_OK;
+}
+
+hm_status hm_server_add_mesh(hm_server S, const hm_mesh *mesh, const hm_build_opts *bo, const hm_solve_opts *so,
+                             int *op_id, int64_t *n_unknowns)
+{
+    if (!S || !mesh || !bo || !so || !op_id || !mesh->xyz || !mesh->tri || mesh->n_vert < 3 || mesh->n_tri < 2)
+        return fail(HM_ERR_ARG, "bad operator arguments");
+    // RWG unknowns = edges shared by exactly two triangles
+    std::vector<int64_t> keys;
+    keys.reserve(3 * mesh->n_tri);
+    for (int64_t t = 0; t < mesh->n_tri; ++t)
+        for (int e = 0; e < 3; ++e) {
+            const int64_t a = mesh->tri[3 * t + e], b = mesh->tri[3 * t + (e + 1) % 3];
+            if (a < 0 || b < 0 || a >= mesh->n_vert || b >= mesh->n_vert) return fail(HM_ERR_ARG, "bad vertex id");
+            keys.push_back(std::min(a, b) * mesh->n_vert + std::max(a, b));
+        }
+    std::sort(keys.begin(), keys.end());
+    int64_t nrwg = 0;
+    for (size_t i = 0; i < keys.size();) {
+        size_t j = i;
+        while (j < keys.size() && keys[j] == keys[i]) ++j;
+        if (j - i == 2) ++nrwg;
+        i = j;
+    }
+    if (so->fp64) return fail(HM_ERR_ARG, "the server runs the complex64 path");
+    Operator o;
+    o.xyz.assign(mesh->xyz, mesh->xyz + 3 * mesh->n_vert);
+    o.tri.assign(mesh->tri, mesh->tri + 3 * mesh->n_tri);
+    o.wavelength = mesh->wavelength;
+    o.bo = *bo;
+    o.bo.keep_fp64 = 0;
+    o.so = *so;
+    o.n = nrwg;
+    // size estimate before the first build: ~60 KB per unknown
+    o.bytes = nrwg * 60 * 1024;
+    o.last_use = clk::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->ops.push_back(std::move(o));
+    *op_id = (int)S->ops.size() - 1;
+    if (n_unknowns) *n_unknowns = nrwg;
+    return HM_OK;
+}
+
+hm_status hm_server_submit(hm_server S, int op_id, const void *b, int64_t n, int nrhs, int64_t *req_id)
+{
+    if (!S || !b || !req_id || nrhs < 1) return fail(HM_ERR_ARG, "bad request");
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (op_id < 0 || op_id >= (int)S->ops.size()) return fail(HM_ERR_ARG, "unknown operator");
+    if (n != S->ops[op_id].n) return fail(HM_ERR_ARG, "right-hand side length differs from the operator's N");
+    if (nrhs > S->max_batch_rhs) return fail(HM_ERR_ARG, "request has more right-hand sides than max_batch_rhs");
+    if (S->fatal != HM_OK) return fail(S->fatal, S->fatal_msg);
+    Request r;
+    r.id = S->next_id++;
+    r.op = op_id;
+    r.nrhs = nrhs;
+    r.b.assign((const float2 *)b, (const float2 *)b + (size_t)n * nrhs);
+    r.t_submit = clk::now();
+    const int64_t id = r.id;
+    S->reqs.emplace(id, std::move(r));
+    S->ops[op_id].queue.push_back(id);
+    *req_id = id;
+    lk.unlock();
+    S->cv_work.notify_one();
+    return HM_OK;
+}
+
+hm_status hm_server_wait(hm_server S, int64_t req_id, void *x, double *latency_ms)
+{
+    if (!S || !x) return fail(HM_ERR_ARG, "null argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end()) return fail(HM_ERR_ARG, "unknown request id");
+    const auto deadline = clk::now() + std::chrono::seconds(600);
+    while (!it->second.done && S->fatal == HM_OK) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout)
+            return fail(HM_ERR_TIMEOUT, "request did not complete within 600 s");
+    }
+    if (!it->second.done) return fail(S->fatal, S->fatal_msg);
+    Request r = std::move(it->second);
+    S->reqs.erase(it);
+    if (r.status != HM_OK) return fail(r.status, "request failed");
+    std::memcpy(x, r.x.data(), r.x.size() * sizeof(float2));
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+    return HM_OK;
+}
+
+hm_status hm_server_get_info(hm_server S, hm_server_info *st)
+{
+    if (!S || !st) return fail(HM_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    st->batches = S->batches;
+    st->solved_rhs = S->solved_rhs;
+    st->builds = S->builds;
+    st->evictions = S->evictions;
+    st->resident_bytes = S->resident_bytes;
+    st->peak_resident_bytes = S->peak_resident;
+    return HM_OK;
+}
+
+void hm_server_destroy(hm_server S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (Slot &s : S->slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.h_buf) cudaFreeHost(s.h_buf);
+        if (s.d_b) cudaFree(s.d_b);
+        if (s.d_x) cudaFree(s.d_x);
+    }
+    for (Operator &o : S->ops)
+        if (o.h) hm_destroy(o.h);
+    delete S;
+}
+
+} // extern "C"

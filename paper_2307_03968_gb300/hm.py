@@ -61,8 +61,15 @@ class HmInfo(ctypes.Structure):
                 ("has_fp64", ctypes.c_int), ("device_bytes", I64)]
 
 
+class HmServerInfo(ctypes.Structure):
+    _fields_ = [("batches", I64), ("solved_rhs", I64), ("builds", I64), ("evictions", I64),
+                ("resident_bytes", I64), ("peak_resident_bytes", I64)]
+
+
 EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_powerseries_solve",
            "hm_powerseries_solve_host", "hm_apply", "hm_residual", "hm_residual_noalloc", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
+           "hm_server_create", "hm_server_add_mesh", "hm_server_submit", "hm_server_wait", "hm_server_get_info",
+           "hm_server_destroy",
            "hm_get_info", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
            "hm_size", "hm_destroy", "hm_last_error", "hm_version"]
 
@@ -89,6 +96,14 @@ def load():
     L.hm_rhs_plane_wave.argtypes = [P, PD, PD, ctypes.c_int, P, I64, P]
     L.hm_profile.argtypes = [P, ctypes.c_int]
     L.hm_profile_read.argtypes = [P, PD, PI64, PI64]
+    L.hm_server_create.argtypes = [ctypes.c_int, I64, ctypes.c_int, ctypes.POINTER(P)]
+    L.hm_server_add_mesh.argtypes = [P, ctypes.POINTER(HmMesh), ctypes.POINTER(HmBuildOpts),
+                                     ctypes.POINTER(HmSolveOpts), ctypes.POINTER(ctypes.c_int), PI64]
+    L.hm_server_submit.argtypes = [P, ctypes.c_int, P, I64, ctypes.c_int, PI64]
+    L.hm_server_wait.argtypes = [P, I64, P, PD]
+    L.hm_server_get_info.argtypes = [P, ctypes.POINTER(HmServerInfo)]
+    L.hm_server_destroy.argtypes = [P]
+    L.hm_server_destroy.restype = None
     L.hm_get_info.argtypes = [P, ctypes.POINTER(HmInfo)]
     L.hm_get_perm.argtypes = [P, PI64]
     L.hm_get_leaves.argtypes = [P, PI64]
@@ -102,7 +117,8 @@ def load():
     L.hm_last_error.restype = ctypes.c_char_p
     L.hm_version.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name.startswith("hm_") and name not in ("hm_size", "hm_destroy", "hm_last_error", "hm_version"):
+        if name.startswith("hm_") and name not in ("hm_size", "hm_destroy", "hm_last_error", "hm_version",
+                                                    "hm_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -319,6 +335,59 @@ class HMatrix:
         if self._h:
             load().hm_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """hm_server: continuous-batching solves of several operators (complex64)."""
+
+    def __init__(self, n_slots=4, hbm_budget_bytes=8 << 30, max_batch_rhs=64):
+        self._s = P()
+        self.max_batch_rhs = max_batch_rhs
+        _check(load().hm_server_create(n_slots, hbm_budget_bytes, max_batch_rhs, ctypes.byref(self._s)))
+        self._keep = []
+
+    def add_mesh(self, xyz, tri, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1, wavelength=1.0,
+                 n_terms=2, n_levels=1, nested=True, refine=False):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        mesh = HmMesh(len(xyz), _ptr(xyz, ctypes.c_double), len(tri), _ptr(tri, ctypes.c_int32), wavelength)
+        bo = HmBuildOpts(leaf_size, arity, adm, aca_tol, levels, 0)
+        so = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 0, 1)
+        op = ctypes.c_int(0)
+        n = I64(0)
+        _check(load().hm_server_add_mesh(self._s, ctypes.byref(mesh), ctypes.byref(bo), ctypes.byref(so),
+                                         ctypes.byref(op), ctypes.byref(n)))
+        return op.value, n.value
+
+    def submit(self, op, b):
+        """b: numpy (nrhs, N) or (N,); returns a request id."""
+        b = np.ascontiguousarray(np.atleast_2d(b), dtype=np.complex64)
+        rid = I64(0)
+        _check(load().hm_server_submit(self._s, op, P(b.ctypes.data), b.shape[1], b.shape[0], ctypes.byref(rid)))
+        return rid.value, b.shape
+
+    def wait(self, req):
+        rid, shape = req
+        x = np.empty(shape, dtype=np.complex64)
+        lat = ctypes.c_double(0.0)
+        _check(load().hm_server_wait(self._s, rid, P(x.ctypes.data), ctypes.byref(lat)))
+        return x, lat.value
+
+    def info(self):
+        i = HmServerInfo()
+        _check(load().hm_server_get_info(self._s, ctypes.byref(i)))
+        return i
+
+    def close(self):
+        if self._s:
+            load().hm_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:
