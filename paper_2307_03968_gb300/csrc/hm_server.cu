@@ -14,7 +14,10 @@
 // Batches of different operators run on different streams and overlap on the
 // device; requests that arrive while others run join the next batch of their
 // operator as soon as its previous batch retires.  One handle never has two
-// batches in flight (its workspace is per handle).
+// batches in flight (its workspace is per handle).  When the resident operators
+// exceed the HBM budget (every operator was busy at admission), idle operators
+// with no queued requests are evicted, least recently used first, as soon as
+// batches retire.
 #include "hm_internal.h"
 
 #include <algorithm>
@@ -197,7 +200,24 @@ void loop(hm_server_s *S)
                 S->stop = true;
             }
         }
-        if (progressed) S->cv_done.notify_all();
+        if (progressed) {
+            S->cv_done.notify_all();
+            // shrink to the budget: evict idle operators without queued requests, LRU first
+            while (S->resident_bytes > S->budget) {
+                int victim = -1;
+                for (int i = 0; i < (int)S->ops.size(); ++i) {
+                    const Operator &c = S->ops[i];
+                    if (c.h && !c.busy && c.queue.empty() &&
+                        (victim < 0 || c.last_use < S->ops[victim].last_use))
+                        victim = i;
+                }
+                if (victim < 0) break;
+                hm_destroy(S->ops[victim].h);
+                S->ops[victim].h = nullptr;
+                S->resident_bytes -= S->ops[victim].bytes;
+                S->evictions++;
+            }
+        }
         // 2. launch new batches
         for (int op = 0; op < (int)S->ops.size(); ++op) {
             Operator &o = S->ops[op];

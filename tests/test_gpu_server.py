@@ -67,8 +67,21 @@ def test_server_mix_equals_alone(torch_cuda):
     info = srv.info()
     assert info.solved_rhs == sum(b.shape[0] for _, b, _ in reqs)
     assert info.batches < len(reqs)          # requests were merged
-    assert info.evictions >= 1 and info.builds > len(meshes) - 1
     assert all(v > 0 for v in lat)
+    # one request at a time, cycling through the operators: each one is idle when
+    # the next is built, so the budget must evict it (and rebuild it later)
+    for rnd in range(2):
+        for k, (op, n) in enumerate(ops):
+            b = (rng.normal(size=(1, n)) + 1j * rng.normal(size=(1, n))).astype(np.complex64)
+            x, _ = srv.wait(srv.submit(op, b))
+            bt = torch_cuda.from_numpy(b).cuda()
+            xt = torch_cuda.empty_like(bt)
+            alone[k].solve(bt, xt, **sopts)
+            torch_cuda.cuda.synchronize()
+            assert rel_err(x, xt.cpu().numpy()) < 1e-5
+    info = srv.info()
+    assert info.evictions >= len(meshes) and info.builds >= 2 * len(meshes)
+    assert info.peak_resident_bytes <= 2 * max(sizes) * 1.3
     srv.close()
 
 

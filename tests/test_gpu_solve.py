@@ -218,3 +218,4 @@ def test_residual_is_fp64_class(torch_cuda, ml2, levels):
     assert rel_err(r, r_ref) < 1e-3
     assert np.allclose(rr, np.sum(np.abs(r_ref) ** 2, axis=1), rtol=1e-3)
     assert np.allclose(bb, np.sum(np.abs(b.astype(np.complex128)) ** 2, axis=1), rtol=1e-6)
+
