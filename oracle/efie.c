@@ -123,15 +123,19 @@ void hmo_ctx_free(hmo_ctx *c)
  * 1984, eqs. for a uniform and a linear source on a polygon):
  *   s0      = Int_T 1/|r - r'| dS'
  *   s1v     = Int_T (rho' - rho)/|r - r'| dS'     (in-plane vector)
- * where rho is the projection of r onto the triangle's plane.
+ *   sR      = Int_T |r - r'| dS'                  (if sR_out is not NULL)
+ * where rho is the projection of r onto the triangle's plane.  sR follows from
+ * the in-plane divergence of (rho' - rho) R, which is 3R - d^2/R:
+ *   sR = ( d^2 s0 + sum_edges t * Int_edge R dl ) / 3,
+ *   Int_edge R dl = ( l+ R+ - l- R- + R0^2 f ) / 2.
  * Edges are taken counter-clockwise about the unit normal n; for each edge,
  * l_hat is its direction, u_hat = l_hat x n the outward in-plane normal,
  * t = signed distance from rho to the edge line (positive inside),
  * l+- the coordinates of the edge end points along l_hat relative to rho,
  * R0^2 = t^2 + d^2 and R+- = sqrt(R0^2 + l+-^2).
  */
-void hmo_potential_integrals(const double *p0, const double *p1, const double *p2,
-                             const double *r, double *s0_out, double *s1v_out)
+void hmo_potential_integrals3(const double *p0, const double *p1, const double *p2,
+                              const double *r, double *s0_out, double *s1v_out, double *sR_out)
 {
     const double *P[3] = {p0, p1, p2};
     double e1[3], e2[3], n[3];
@@ -143,7 +147,7 @@ void hmo_potential_integrals(const double *p0, const double *p1, const double *p
     double d = dot3(n, rp0);
     double ad = fabs(d);
     double rho[3] = {r[0] - d * n[0], r[1] - d * n[1], r[2] - d * n[2]};
-    double s0 = 0.0, s1[3] = {0, 0, 0};
+    double s0 = 0.0, s1[3] = {0, 0, 0}, edgeR = 0.0;
     for (int i = 0; i < 3; ++i) {
         const double *a = P[i], *b = P[(i + 1) % 3];
         double lv[3];
@@ -172,9 +176,17 @@ void hmo_potential_integrals(const double *p0, const double *p1, const double *p
         double g = 0.5 * ((R02 > 0.0 ? R02 * f : 0.0) + lp * Rp - lm * Rm);
         /* u_hat points outward; the vector integral uses the outward normal */
         s1[0] += g * uh[0]; s1[1] += g * uh[1]; s1[2] += g * uh[2];
+        edgeR += t * g;   /* g is also Int_edge R dl */
     }
     *s0_out = s0;
     s1v_out[0] = s1[0]; s1v_out[1] = s1[1]; s1v_out[2] = s1[2];
+    if (sR_out) *sR_out = (d * d * s0 + edgeR) / 3.0;
+}
+
+void hmo_potential_integrals(const double *p0, const double *p1, const double *p2,
+                             const double *r, double *s0_out, double *s1v_out)
+{
+    hmo_potential_integrals3(p0, p1, p2, r, s0_out, s1v_out, NULL);
 }
 
 /* (1/(A_m A_n)) Int_Tm Int_Tn [ 1/4 (r - vm).(r' - vn) - 1/k^2 ] G dS' dS */
@@ -316,8 +328,10 @@ void hmo_radiation(const hmo_ctx *c, const zc *x, int ndir, const double *rhat, 
  * with |S_k|_F^2 updated incrementally.  U is stored column-major (U[l*m + i]),
  * V row-major (V[l*n + j]).  Returns the rank k (<= kmax).
  */
-int hmo_aca(const hmo_ctx *c, const int32_t *rows, int m, const int32_t *cols, int n,
-            double tol, int kmax, zc *U, zc *V)
+typedef zc (*hmo_entry_fn)(const void *ctx, int m, int n);
+
+int hmo_aca_generic(hmo_entry_fn entry, const void *c, const int32_t *rows, int m, const int32_t *cols, int n,
+                    double tol, int kmax, zc *U, zc *V)
 {
     char *used = (char *)calloc(m, 1);
     zc *row = (zc *)malloc(sizeof(zc) * n);
@@ -327,7 +341,7 @@ int hmo_aca(const hmo_ctx *c, const int32_t *rows, int m, const int32_t *cols, i
     if (kmax > n) kmax = n;
     while (k < kmax) {
         for (int j = 0; j < n; ++j) {
-            zc v = hmo_entry(c, rows[istar], cols[j]);
+            zc v = entry(c, rows[istar], cols[j]);
             for (int l = 0; l < k; ++l) v -= U[(int64_t)l * m + istar] * V[(int64_t)l * n + j];
             row[j] = v;
         }
@@ -349,7 +363,7 @@ int hmo_aca(const hmo_ctx *c, const int32_t *rows, int m, const int32_t *cols, i
         zc *v = V + (int64_t)k * n, *u = U + (int64_t)k * m;
         for (int j = 0; j < n; ++j) v[j] = row[j] / piv;
         for (int i = 0; i < m; ++i) {
-            zc w = hmo_entry(c, rows[i], cols[jstar]);
+            zc w = entry(c, rows[i], cols[jstar]);
             for (int l = 0; l < k; ++l) w -= V[(int64_t)l * n + jstar] * U[(int64_t)l * m + i];
             u[i] = w;
         }
@@ -381,6 +395,24 @@ int hmo_aca(const hmo_ctx *c, const int32_t *rows, int m, const int32_t *cols, i
     return k;
 }
 
+static zc rwg_entry_cb(const void *c, int m, int n) { return hmo_entry((const hmo_ctx *)c, m, n); }
+
+int hmo_aca(const hmo_ctx *c, const int32_t *rows, int m, const int32_t *cols, int n,
+            double tol, int kmax, zc *U, zc *V)
+{
+    return hmo_aca_generic(rwg_entry_cb, c, rows, m, cols, n, tol, kmax, U, V);
+}
+
+void hmo_aca_many_generic(hmo_entry_fn entry, const void *c, int nb, const int32_t *idx, const int64_t *roff,
+                          const int32_t *m, const int64_t *coff, const int32_t *n, double tol, const int32_t *kmax,
+                          const int64_t *uoff, const int64_t *voff, zc *U, zc *V, int32_t *rank)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < nb; ++b)
+        rank[b] = hmo_aca_generic(entry, c, idx + roff[b], m[b], idx + coff[b], n[b], tol, kmax[b], U + uoff[b],
+                                  V + voff[b]);
+}
+
 /* ACA of many blocks in parallel; block b covers rows[roff[b] .. roff[b]+m[b]),
  * cols[coff[b] .. coff[b]+n[b]); U/V written at uoff[b]/voff[b] with room for
  * kmax[b] terms.  rank[b] receives the rank. */
@@ -388,7 +420,5 @@ void hmo_aca_many(const hmo_ctx *c, int nb, const int32_t *idx, const int64_t *r
                   const int64_t *coff, const int32_t *n, double tol, const int32_t *kmax,
                   const int64_t *uoff, const int64_t *voff, zc *U, zc *V, int32_t *rank)
 {
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int b = 0; b < nb; ++b)
-        rank[b] = hmo_aca(c, idx + roff[b], m[b], idx + coff[b], n[b], tol, kmax[b], U + uoff[b], V + voff[b]);
+    hmo_aca_many_generic(rwg_entry_cb, c, nb, idx, roff, m, coff, n, tol, kmax, uoff, voff, U, V, rank);
 }

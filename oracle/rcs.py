@@ -6,6 +6,10 @@ Far field of a surface current J (e^{jwt}):
   F(r_hat) = Int J(r') exp(+jk r_hat . r') dS'
 so  sigma = 4 pi r^2 |E_s . p|^2 / |E_inc|^2 = (k eta)^2 / (4 pi) |p . F|^2
 for a unit incident field and receive polarisation p (perpendicular to r_hat).
+A volume polarisation current J = jw kappa D radiates the same way with
+F = jw eps0 P, P = Int kappa (D/eps0) exp(+jk r_hat . r') dV', which gives
+sigma = k^4 / (4 pi) |p . P|^2.  Each mesh class carries its factor as
+``rcs_scale`` and its radiation vector as ``radiation``.
 """
 
 import numpy as np
@@ -18,7 +22,7 @@ def bistatic_theta_pol(mesh, x, theta, phi=0.0):
     that = np.stack([np.cos(th) * np.cos(phi), np.cos(th) * np.sin(phi), -np.sin(th)], axis=1)
     F = mesh.radiation(x, rhat)
     Ft = np.einsum('ij,ij->i', F, that)
-    return (mesh.k * mesh.eta) ** 2 / (4.0 * np.pi) * np.abs(Ft) ** 2
+    return mesh.rcs_scale * np.abs(Ft) ** 2
 
 
 def monostatic(mesh, X, khat, phat):
@@ -27,7 +31,7 @@ def monostatic(mesh, X, khat, phat):
     out = np.empty(X.shape[1])
     for r in range(X.shape[1]):
         F = mesh.radiation(X[:, r], -khat[r:r + 1])[0]
-        out[r] = (mesh.k * mesh.eta) ** 2 / (4.0 * np.pi) * abs(np.dot(F, phat[r])) ** 2
+        out[r] = mesh.rcs_scale * abs(np.dot(F, phat[r])) ** 2
     return out
 
 

@@ -17,19 +17,19 @@ ETA0 = 376.730313461770655   # free-space impedance (ohm) = mu0 * c0
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_DIR = os.path.join(_HERE, "_lib")
 _LIB_PATH = os.path.join(_LIB_DIR, "libhmoracle.so")
-_SRC = os.path.join(_HERE, "efie.c")
+_SRCS = [os.path.join(_HERE, "efie.c"), os.path.join(_HERE, "vefie.c")]
 _lib = None
 
 
 def build_lib(force=False):
-    """Compile efie.c into oracle/_lib/libhmoracle.so (gcc, OpenMP)."""
+    """Compile efie.c and vefie.c into oracle/_lib/libhmoracle.so (gcc, OpenMP)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
     subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
-                           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+                           "-ffp-contract=off", *_SRCS, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -94,6 +94,8 @@ class RWGMesh:
             np.linalg.norm(self.xyz[self.ev[:, 0]] - self.xyz[self.ev[:, 1]], axis=1))
         self.k = 2.0 * np.pi / wavelength
         self.eta = ETA0
+        # sigma = rcs_scale |p . F|^2 for the radiation vector F below
+        self.rcs_scale = (self.k * self.eta) ** 2 / (4.0 * np.pi)
         self._ctx = lib().hmo_ctx_new(len(self.xyz), _p(self.xyz), len(self.tri), _p(self.tri),
                                       self.ne, _p(self.etri), _p(self.efree), _p(self.elen),
                                       self.k, self.eta)

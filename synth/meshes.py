@@ -137,3 +137,58 @@ def closed_cylinder(radius, height, n_around, n_along, n_rings):
     tri = np.array(tris, dtype=np.int32)
     _orient_outward(xyz, tri)
     return xyz, tri
+
+
+def cube_tets(n, size=1.0):
+    """Cube [-size/2, size/2]^3 split into n^3 voxels, each voxel into the 6
+    tetrahedra around its main diagonal (Freudenthal subdivision; conforming
+    across voxels).  Returns (xyz float64 (nv,3), tet int32 (nt,4)) with
+    positive orientation."""
+    g = np.linspace(-size / 2, size / 2, n + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+    def vid(i, j, k):
+        return (i * (n + 1) + j) * (n + 1) + k
+
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                for p in perms:
+                    c = [0, 0, 0]
+                    path = [vid(i, j, k)]
+                    for ax in p:
+                        c[ax] = 1
+                        path.append(vid(i + c[0], j + c[1], k + c[2]))
+                    tets.append(path)
+    tet = np.array(tets, dtype=np.int32)
+    _orient_tets(xyz, tet)
+    return xyz, tet
+
+
+def ball_tets(n, radius):
+    """Tetrahedral mesh of a ball: the cube mesh of cube_tets(n, 2) mapped
+    radially, p -> radius * p * |p|_inf / |p|_2, so that the cube surface lands
+    on the sphere."""
+    xyz, tet = cube_tets(n, 2.0)
+    ninf = np.abs(xyz).max(axis=1)
+    n2 = np.linalg.norm(xyz, axis=1)
+    s = np.where(n2 > 0, ninf / np.where(n2 > 0, n2, 1.0), 0.0)
+    xyz = radius * xyz * s[:, None]
+    _orient_tets(xyz, tet)
+    return xyz, tet
+
+
+def _orient_tets(xyz, tet):
+    """Swap two vertices of negatively oriented tetrahedra (in place)."""
+    p = xyz[tet]
+    vol = np.einsum('ij,ij->i', np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0])
+    neg = vol < 0
+    tet[neg, 2], tet[neg, 3] = tet[neg, 3].copy(), tet[neg, 2].copy()
+
+
+def random_permittivity(n_tet, lo, hi, seed):
+    """Relative permittivity per tetrahedron, iid uniform in [lo, hi]."""
+    return np.random.default_rng(seed).uniform(lo, hi, n_tet)
