@@ -56,13 +56,34 @@ typedef enum {
 
 /* ---------------------------------------------------------------- build --- */
 
-/* Triangle mesh of a closed PEC surface (paper §II: RWG basis, S-EFIE). */
+/* Basis and integral equation of a mesh (paper §II). */
+typedef enum {
+    HM_RWG = 0,   /* closed PEC surface, triangles, RWG basis, S-EFIE (eq. 3) */
+    HM_SWG = 1    /* inhomogeneous dielectric volume, tetrahedra, SWG basis, V-EFIE (eq. 4) */
+} hm_basis;
+
+/*
+ * Mesh of the scatterer, in metres.
+ *   HM_RWG: cells are triangles (3 vertex ids each, counter-clockwise seen from
+ *           outside); one unknown per edge shared by exactly two triangles,
+ *           ordered by (lower vertex id, higher vertex id).
+ *   HM_SWG: cells are tetrahedra (4 vertex ids each, either orientation) with a
+ *           real relative permittivity eps_r > 0 per tetrahedron; one unknown
+ *           per face (interior and boundary), ordered by the ascending vertex
+ *           triple.  The unknowns x give the electric flux density
+ *           D = eps0 sum_n x_n f_n, and the equation is tested with
+ *           kappa f_m, kappa = 1 - 1/eps_r, so that the matrix is complex
+ *           symmetric (the half storage of §III).
+ * All pointers are host memory, read during the call only.
+ */
 typedef struct {
+    int basis;              /* hm_basis */
     int64_t n_vert;
-    const double *xyz;      /* host, 3*n_vert, metres */
-    int64_t n_tri;
-    const int32_t *tri;     /* host, 3*n_tri vertex ids, outward normals (CCW) */
-    double wavelength;      /* metres; k = 2 pi / wavelength, eta = 376.73 ohm */
+    const double *xyz;      /* 3*n_vert */
+    int64_t n_cell;
+    const int32_t *cells;   /* 3*n_cell (HM_RWG) or 4*n_cell (HM_SWG) vertex ids */
+    const double *eps_r;    /* HM_SWG: n_cell relative permittivities; HM_RWG: ignored (NULL) */
+    double wavelength;      /* free-space wavelength; k = 2 pi / wavelength, eta = 376.73 ohm */
 } hm_mesh;
 
 /* Tree, admissibility (eq. 7) and compression (§III) options. */
@@ -79,9 +100,12 @@ typedef struct {
 } hm_build_opts;
 
 /*
- * Build the H-Matrix of `mesh` on the GPU: RWG basis, cluster tree, eq. 7
- * partition, near-field fill and ACA + re-compression of the far blocks, all
- * on the device (§III).  Synchronises `stream` before returning.
+ * Build the H-Matrix of `mesh` on the GPU: RWG or SWG basis, cluster tree,
+ * eq. 7 partition, near-field fill and ACA + re-compression of the far blocks,
+ * all on the device (§III).  Synchronises `stream` before returning.
+ * HM_ERR_ARG for an empty or malformed mesh (vertex id out of range, a
+ * degenerate cell, eps_r missing or not > 0 for HM_SWG, a face shared by more
+ * than two tetrahedra).
  */
 hm_status hm_build(const hm_mesh *mesh, const hm_build_opts *opts, void *stream, hm_matrix *out);
 
@@ -222,8 +246,11 @@ hm_status hm_residual_noalloc(hm_matrix h, const void *b, int64_t ldb, const voi
 
 /*
  * Right-hand sides of eq. 5 for incident plane waves (paper §II: "b is a known
- * incident plane wave"): b_m = Int f_m . p_hat exp(-jk k_hat . r) dS for the RWG
- * function f_m (same 7-point rule as the fill), unit amplitude.  khat, phat:
+ * incident plane wave"), unit amplitude: for HM_RWG
+ *   b_m = Int f_m . p_hat exp(-jk k_hat . r) dS     (7-point triangle rule),
+ * for HM_SWG
+ *   b_m = Int kappa f_m . p_hat exp(-jk k_hat . r) dV (4-point tetrahedron rule),
+ * the same rules as the fill.  khat, phat:
  * HOST arrays of 3*nrhs doubles (unit propagation direction, unit polarisation).
  * b: DEVICE complex64, column-major N x nrhs in the original order, leading
  * dimension ldb.  Only for operators made by hm_build (the mesh is kept).
@@ -271,7 +298,7 @@ typedef struct {
 } hm_server_info;
 
 hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_rhs, hm_server *out);
-/* Registers a mesh; *n_unknowns receives its RWG count N (the length of every
+/* Registers a mesh (either basis); *n_unknowns receives its unknown count N (the length of every
  * right-hand side of this operator). */
 hm_status hm_server_add_mesh(hm_server s, const hm_mesh *mesh, const hm_build_opts *bo, const hm_solve_opts *so,
                              int *op_id, int64_t *n_unknowns);

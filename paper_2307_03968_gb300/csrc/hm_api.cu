@@ -57,7 +57,7 @@ static void free_handle(hm_matrix h)
     clear_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
-    void *geo[] = {h->d_qpd, h->d_vtx, h->d_etri, h->d_efree, h->d_elen};
+    void *geo[] = {h->d_qpd, h->d_vtx, h->d_ucell, h->d_ufree, h->d_ucoef, h->d_rhs_w};
     for (void *p : geo)
         if (p) cudaFree(p);
     void *ptrs[] = {h->d_pperm, h->d_pleaf_off, h->d_dinv_off, h->d_leaf_n, h->d_self_off, h->d_bad_leaf,

@@ -113,12 +113,17 @@ struct hm_matrix_s {
     int64_t device_bytes = 0;
     int num_sms = 0;
 
-    // mesh geometry kept for excitation (operators made by hm_build)
+    // mesh geometry kept for excitation (operators made by hm_build):
+    // b_m = sum over the two sides s of ucoef[m][s] * sum_q w_q (r_q - v) . p exp(-jk k . r_q)
+    // on the side's cell (triangle or tetrahedron), v = the side's free vertex
     bool has_mesh = false;
-    double *d_qpd = nullptr;      // nt x 7 x 3 quadrature points
+    int basis = HM_RWG;
+    int rhs_nq = 0;               // quadrature points per cell
+    double *d_qpd = nullptr;      // n_cell x rhs_nq x 3 quadrature points
+    double *d_rhs_w = nullptr;    // rhs_nq weights
     double *d_vtx = nullptr;      // nv x 3
-    int32_t *d_etri = nullptr, *d_efree = nullptr;
-    double *d_elen = nullptr;
+    int32_t *d_ucell = nullptr, *d_ufree = nullptr;   // N x 2 (cell -1: no side)
+    double *d_ucoef = nullptr;    // N x 2
     double wavenumber = 0.0;
 
     // CUDA graphs of whole solves, keyed by pointers, sizes and options
@@ -184,12 +189,20 @@ void launch_convert_f32_to_f64(const float2 *a, double2 *b, int64_t n, cudaStrea
 int factor_max_leaf();
 void launch_factor(hm_matrix h, cudaStream_t s);
 
+// unknown count of a mesh (RWG edges or SWG faces) with the checks of hm_build (k_build.cu)
+hm_status count_unknowns(const hm_mesh *mesh, int64_t *n);
+
 // plane-wave right-hand sides (k_build.cu)
 void launch_rhs_plane_wave(hm_matrix h, const double *d_k, const double *d_p, int nrhs, float2 *b, int64_t ldb,
                            cudaStream_t s);
 
-// GPU build from a mesh (k_build.cu)
+// GPU build from a mesh (k_build.cu dispatches; the SWG volume build is in k_build_swg.cu)
 hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *opts, cudaStream_t s, hm_matrix *out);
+hm_status build_from_tets(const hm_mesh *mesh, const hm_build_opts *opts, cudaStream_t s, hm_matrix *out);
+// SWG faces of a tetrahedral mesh (sorted vertex triples; T+ = lower tetrahedron,
+// T- = -1 on the boundary); HM_ERR_ARG for a face of more than two tetrahedra
+hm_status swg_faces(int64_t nv, int64_t nt, const int32_t *tet, std::vector<int32_t> &fv, std::vector<int32_t> &ftet,
+                    std::vector<int32_t> &ffree);
 
 // shared construction helpers (hm_api.cu)
 hm_status finalize_layout(hm_matrix h, cudaStream_t s);

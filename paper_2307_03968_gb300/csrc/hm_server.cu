@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -46,8 +47,10 @@ struct Request {
 };
 
 struct Operator {
+    int basis = HM_RWG;
     std::vector<double> xyz;
-    std::vector<int32_t> tri;
+    std::vector<int32_t> cells;
+    std::vector<double> eps_r;
     double wavelength;
     hm_build_opts bo;
     hm_solve_opts so;
@@ -127,7 +130,9 @@ hm_status make_resident(hm_server_s *S, int op)
         S->resident_bytes -= S->ops[victim].bytes;
         S->evictions++;
     }
-    hm_mesh mesh{(int64_t)o.xyz.size() / 3, o.xyz.data(), (int64_t)o.tri.size() / 3, o.tri.data(), o.wavelength};
+    const int per = o.basis == HM_SWG ? 4 : 3;
+    hm_mesh mesh{o.basis, (int64_t)o.xyz.size() / 3, o.xyz.data(), (int64_t)o.cells.size() / per, o.cells.data(),
+                 o.eps_r.empty() ? nullptr : o.eps_r.data(), o.wavelength};
     hm_matrix h = nullptr;
     hm_status st = hm_build(&mesh, &o.bo, nullptr, &h);
     if (st != HM_OK) return st;
@@ -319,41 +324,35 @@ hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_
 hm_status hm_server_add_mesh(hm_server S, const hm_mesh *mesh, const hm_build_opts *bo, const hm_solve_opts *so,
                              int *op_id, int64_t *n_unknowns)
 {
-    if (!S || !mesh || !bo || !so || !op_id || !mesh->xyz || !mesh->tri || mesh->n_vert < 3 || mesh->n_tri < 2)
-        return fail(HM_ERR_ARG, "bad operator arguments");
-    // RWG unknowns = edges shared by exactly two triangles
-    std::vector<int64_t> keys;
-    keys.reserve(3 * mesh->n_tri);
-    for (int64_t t = 0; t < mesh->n_tri; ++t)
-        for (int e = 0; e < 3; ++e) {
-            const int64_t a = mesh->tri[3 * t + e], b = mesh->tri[3 * t + (e + 1) % 3];
-            if (a < 0 || b < 0 || a >= mesh->n_vert || b >= mesh->n_vert) return fail(HM_ERR_ARG, "bad vertex id");
-            keys.push_back(std::min(a, b) * mesh->n_vert + std::max(a, b));
-        }
-    std::sort(keys.begin(), keys.end());
-    int64_t nrwg = 0;
-    for (size_t i = 0; i < keys.size();) {
-        size_t j = i;
-        while (j < keys.size() && keys[j] == keys[i]) ++j;
-        if (j - i == 2) ++nrwg;
-        i = j;
+    if (!S || !mesh || !bo || !so || !op_id) return fail(HM_ERR_ARG, "bad operator arguments");
+    int64_t nunk = 0;
+    hm_status st = count_unknowns(mesh, &nunk);
+    if (st != HM_OK) return st;
+    if (mesh->basis == HM_SWG) {
+        if (!mesh->eps_r) return fail(HM_ERR_ARG, "eps_r is required for an SWG mesh");
+        for (int64_t t = 0; t < mesh->n_cell; ++t)
+            if (!(mesh->eps_r[t] > 0) || !std::isfinite(mesh->eps_r[t]))
+                return fail(HM_ERR_ARG, "eps_r must be finite and > 0");
     }
     if (so->fp64) return fail(HM_ERR_ARG, "the server runs the complex64 path");
     Operator o;
+    const int per = mesh->basis == HM_SWG ? 4 : 3;
+    o.basis = mesh->basis;
     o.xyz.assign(mesh->xyz, mesh->xyz + 3 * mesh->n_vert);
-    o.tri.assign(mesh->tri, mesh->tri + 3 * mesh->n_tri);
+    o.cells.assign(mesh->cells, mesh->cells + per * mesh->n_cell);
+    if (mesh->basis == HM_SWG) o.eps_r.assign(mesh->eps_r, mesh->eps_r + mesh->n_cell);
     o.wavelength = mesh->wavelength;
     o.bo = *bo;
     o.bo.keep_fp64 = 0;
     o.so = *so;
-    o.n = nrwg;
+    o.n = nunk;
     // size estimate before the first build: ~60 KB per unknown
-    o.bytes = nrwg * 60 * 1024;
+    o.bytes = nunk * 60 * 1024;
     o.last_use = clk::now();
     std::lock_guard<std::mutex> lk(S->mu);
     S->ops.push_back(std::move(o));
     *op_id = (int)S->ops.size() - 1;
-    if (n_unknowns) *n_unknowns = nrwg;
+    if (n_unknowns) *n_unknowns = nunk;
     return HM_OK;
 }
 

@@ -27,8 +27,32 @@ PI32 = ctypes.POINTER(ctypes.c_int32)
 PD = ctypes.POINTER(ctypes.c_double)
 
 
+HM_RWG, HM_SWG = 0, 1
+
+
 class HmMesh(ctypes.Structure):
-    _fields_ = [("n_vert", I64), ("xyz", PD), ("n_tri", I64), ("tri", PI32), ("wavelength", ctypes.c_double)]
+    _fields_ = [("basis", ctypes.c_int), ("n_vert", I64), ("xyz", PD), ("n_cell", I64), ("cells", PI32),
+                ("eps_r", PD), ("wavelength", ctypes.c_double)]
+
+
+def _mesh(xyz, cells, eps_r, wavelength):
+    """hm_mesh for triangles (RWG, S-EFIE) or tetrahedra with eps_r (SWG, V-EFIE);
+    returns the struct and the arrays it points into (keep them alive)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    if cells.ndim != 2 or cells.shape[1] not in (3, 4):
+        raise ValueError("cells must be (n, 3) triangles or (n, 4) tetrahedra")
+    basis = HM_RWG if cells.shape[1] == 3 else HM_SWG
+    keep = [xyz, cells]
+    ep = None
+    if basis == HM_SWG:
+        if eps_r is None:
+            raise ValueError("a tetrahedral mesh needs eps_r")
+        e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps_r, dtype=np.float64), (len(cells),)))
+        keep.append(e)
+        ep = _ptr(e, ctypes.c_double)
+    m = HmMesh(basis, len(xyz), _ptr(xyz, ctypes.c_double), len(cells), _ptr(cells, ctypes.c_int32), ep, wavelength)
+    return m, keep
 
 
 class HmBuildOpts(ctypes.Structure):
@@ -156,12 +180,11 @@ class HMatrix:
 
     # ---- construction ------------------------------------------------------------------
     @classmethod
-    def build(cls, xyz, tri, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1, keep_fp64=False,
-              wavelength=1.0, stream=None):
-        """hm_build: GPU fill and ACA of the S-EFIE H-Matrix of a closed triangle mesh."""
-        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
-        tri = np.ascontiguousarray(tri, dtype=np.int32)
-        mesh = HmMesh(len(xyz), _ptr(xyz, ctypes.c_double), len(tri), _ptr(tri, ctypes.c_int32), wavelength)
+    def build(cls, xyz, cells, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1, keep_fp64=False,
+              wavelength=1.0, eps_r=None, stream=None):
+        """hm_build: GPU fill and ACA of the H-Matrix of a closed triangle mesh
+        (RWG, S-EFIE) or of a tetrahedral mesh with per-cell eps_r (SWG, V-EFIE)."""
+        mesh, _keep = _mesh(xyz, cells, eps_r, wavelength)
         opts = HmBuildOpts(leaf_size, arity, adm, aca_tol, levels, 1 if keep_fp64 else 0)
         h = P()
         _check(load().hm_build(ctypes.byref(mesh), ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
@@ -352,11 +375,9 @@ class Server:
         _check(load().hm_server_create(n_slots, hbm_budget_bytes, max_batch_rhs, ctypes.byref(self._s)))
         self._keep = []
 
-    def add_mesh(self, xyz, tri, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1, wavelength=1.0,
-                 n_terms=2, n_levels=1, nested=True, refine=False):
-        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
-        tri = np.ascontiguousarray(tri, dtype=np.int32)
-        mesh = HmMesh(len(xyz), _ptr(xyz, ctypes.c_double), len(tri), _ptr(tri, ctypes.c_int32), wavelength)
+    def add_mesh(self, xyz, cells, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1, wavelength=1.0,
+                 n_terms=2, n_levels=1, nested=True, refine=False, eps_r=None):
+        mesh, _keep = _mesh(xyz, cells, eps_r, wavelength)
         bo = HmBuildOpts(leaf_size, arity, adm, aca_tol, levels, 0)
         so = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 0, 1)
         op = ctypes.c_int(0)

@@ -62,3 +62,38 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(hm, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(OSError):
         hm.load()
+
+
+def test_build_rejects_bad_meshes_on_the_host(lib):
+    """hm_build validates the mesh before any device work."""
+    import synth
+    from paper_2307_03968_gb300 import hm
+    xyz, tet = synth.cube_tets(1, 1.0)
+    opts = hm.HmBuildOpts(16, 2, 1.0, 1e-4, -1, 0)
+    out = ctypes.c_void_p()
+
+    def status(xyz, cells, eps):
+        m, keep = hm._mesh(xyz, cells, eps, 1.0)
+        return lib.hm_build(ctypes.byref(m), ctypes.byref(opts), None, ctypes.byref(out))
+
+    bad = tet.copy()
+    bad[0, 0] = len(xyz) + 3
+    assert status(xyz, bad, 2.0) == hm.HM_ERR_ARG                      # vertex id out of range
+    assert status(xyz, tet, -1.0) == hm.HM_ERR_ARG                     # eps_r must be > 0
+    assert status(xyz, tet, np.nan) == hm.HM_ERR_ARG
+    rep = tet.copy()
+    rep[0, 1] = rep[0, 0]
+    assert status(xyz, rep, 2.0) == hm.HM_ERR_ARG                      # repeated vertex
+    three = np.concatenate([tet, tet[:1]])                             # a face of three tetrahedra
+    assert status(xyz, three, 2.0) == hm.HM_ERR_ARG
+    flat = xyz.copy()
+    flat[:, 2] = 0.0                                                   # zero-volume tetrahedra
+    assert status(flat, tet, 2.0) == hm.HM_ERR_ARG
+    m, keep = hm._mesh(xyz, tet, 2.0, 1.0)
+    m.eps_r = None
+    assert lib.hm_build(ctypes.byref(m), ctypes.byref(opts), None, ctypes.byref(out)) == hm.HM_ERR_ARG
+    assert b"eps_r" in lib.hm_last_error()
+    tri_bad = np.array([[0, 1, 99], [1, 2, 3]], dtype=np.int32)
+    assert status(xyz, tri_bad, None) == hm.HM_ERR_ARG                 # triangle id out of range
+    with pytest.raises(ValueError):
+        hm._mesh(xyz, tet, None, 1.0)                                  # tetrahedra need eps_r
