@@ -33,14 +33,58 @@ if ROOT not in sys.path:
 
 WORKLOADS = {
     # the metric's workload: 30,720 RWG unknowns
-    "sphere2": dict(name="sefie_pec_sphere_r2lambda_30720rwg", subdivisions=5, radius=2.0, leaf_size=64, arity=8,
-                    adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, unknowns=30720, triangles=20480),
+    "sphere2": dict(name="sefie_pec_sphere_r2lambda_30720rwg", kind="rwg", subdivisions=5, radius=2.0, leaf_size=64,
+                    arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=30720,
+                    triangles=20480),
     # a smaller sphere of the same family (7,680 unknowns), for profiler captures
-    "sphere1": dict(name="sefie_pec_sphere_r1lambda_7680rwg", subdivisions=4, radius=1.0, leaf_size=64, arity=8,
-                    adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, unknowns=7680, triangles=5120),
+    "sphere1": dict(name="sefie_pec_sphere_r1lambda_7680rwg", kind="rwg", subdivisions=4, radius=1.0, leaf_size=64,
+                    arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=7680,
+                    triangles=5120),
+    # V-EFIE: inhomogeneous dielectric cube, side 1 wavelength, 15^3 voxels of 6 tetrahedra
+    # (41,850 SWG unknowns), eps_r iid uniform [2, 6], binary tree, eq. 7 with eta = 1, 16 random incidences
+    "vefie_cube": dict(name="vefie_dielectric_cube_1lambda_41850swg", kind="swg", voxels=15, side=1.0, eps_lo=2.0,
+                       eps_hi=6.0, seed=4, leaf_size=64, arity=2, adm=1.0, aca_tol=1e-4, n_terms=2, n_levels=1,
+                       refine=True, nrhs=16, unknowns=41850, tetrahedra=20250),
+    # the same element size on a 2/3-wavelength cube (12,600 SWG unknowns), for profiler captures
+    "vefie_cube_small": dict(name="vefie_dielectric_cube_0.667lambda_12600swg", kind="swg", voxels=10, side=2.0 / 3.0,
+                             eps_lo=2.0, eps_hi=6.0, seed=4, leaf_size=64, arity=2, adm=1.0, aca_tol=1e-4, n_terms=2,
+                             n_levels=1, refine=True, nrhs=16, unknowns=12600, tetrahedra=6000),
 }
 WORKLOAD = WORKLOADS["sphere2"]
 METRIC = "power-series solves RHS/s at <=1e-4 rel err vs FP64 oracle; p50/p99 latency"
+
+
+def workload_mesh(w):
+    """(xyz, cells, eps_r or None) of a workload, from the seeded generators."""
+    import synth
+    if w["kind"] == "rwg":
+        xyz, tri = synth.icosphere(w["subdivisions"], w["radius"])
+        return xyz, tri, None
+    xyz, tet = synth.cube_tets(w["voxels"], w["side"])
+    return xyz, tet, synth.random_permittivity(len(tet), w["eps_lo"], w["eps_hi"], seed=w["seed"])
+
+
+def workload_incidences(w):
+    import synth
+    if w["kind"] == "rwg":
+        return synth.plane_wave_z()
+    return synth.random_incidences(w["nrhs"], seed=w["seed"])
+
+
+def workload_config(w):
+    c = {"workload": w["name"], "unknowns": w["unknowns"]}
+    if w["kind"] == "rwg":
+        c.update({"triangles": w["triangles"], "radius_lambda": w["radius"], "tree": "octree (median splits)",
+                  "admissibility": "dist>=2*min(diam)", "rhs": "plane wave +z, x-pol"})
+    else:
+        c.update({"tetrahedra": w["tetrahedra"], "side_lambda": w["side"],
+                  "eps_r": "iid uniform [%g, %g], seed %d" % (w["eps_lo"], w["eps_hi"], w["seed"]),
+                  "tree": "binary (median splits)", "admissibility": "dist>=min(diam) (eq. 7, eta=1)",
+                  "rhs": "%d plane waves, random incidence and polarisation, seed %d" % (w["nrhs"], w["seed"])})
+    c.update({"leaf_size": w["leaf_size"], "aca_tol": w["aca_tol"], "n_terms": w["n_terms"],
+              "levels": "leaf level only", "refine": "one FP64-residual refinement step", "nrhs": w["nrhs"],
+              "l2": "operator resident in HBM is larger than L2; no flush", "parallelism": "replicas"})
+    return c
 
 
 def parse():
@@ -75,14 +119,14 @@ def oracle_sample_rate(cpu_seconds, warmup=1, steps=None):
     row cluster is one of them.  The time is scaled to the whole operator by
     the ratio of stored complex elements.  Returns a dict for the JSON line."""
     import numpy as np
-    from synth import icosphere, plane_wave_z
     from oracle.rwg import RWGMesh
+    from oracle.swg import SWGMesh
     from oracle.hmatrix import ClusterTree, HMatrix, partition, recompress
     from oracle import series
 
     w = WORKLOAD
-    xyz, tri = icosphere(w["subdivisions"], w["radius"])
-    mesh = RWGMesh(xyz, tri)
+    xyz, cells, eps = workload_mesh(w)
+    mesh = RWGMesh(xyz, cells) if w["kind"] == "rwg" else SWGMesh(xyz, cells, eps)
     tree = ClusterTree(mesh.centres(), *mesh.support_boxes(), w["leaf_size"], w["arity"])
     near_pairs, far_pairs = partition(tree, w["adm"])
     L = tree.depth
@@ -119,7 +163,9 @@ def oracle_sample_rate(cpu_seconds, warmup=1, steps=None):
     full = sum(n * n for (_, n) in leaves) + sum(leaves[a][1] * leaves[b][1] for (a, b) in near_pairs) + \
         n_far_total * mean_far
     scale = full / samp
-    b = mesh.rhs(*plane_wave_z())[:, 0]
+    b = mesh.rhs(*workload_incidences(w))
+    if b.shape[1] == 1:
+        b = b[:, 0]
     for _ in range(warmup):
         series.solve(Hs, b, K=w["n_terms"], levels=1, refine=True)
     times, cpu = [], []
@@ -133,11 +179,12 @@ def oracle_sample_rate(cpu_seconds, warmup=1, steps=None):
         n += 1
     t = statistics.median(times) * scale
     cores = max(1, round(sum(cpu) / max(sum(times), 1e-9)))
-    return dict(value=1.0 / t, unit="RHS/s", cores=cores, kind="oracle",
-                sample="oracle series.solve (K=2, leaf level, refine) on %d of %d leaves with their %d near and "
-                       "%d leaf-level far block rows (%.1f%% of the stored elements, far elements of unsampled "
+    nrhs = w["nrhs"]
+    return dict(value=nrhs / t, unit="RHS/s", cores=cores, kind="oracle",
+                sample="oracle series.solve (K=2, leaf level, refine, %d RHS) on %d of %d leaves with their %d near "
+                       "and %d leaf-level far block rows (%.1f%% of the stored elements, far elements of unsampled "
                        "rows estimated from the sample's mean rank); median of %d solves scaled by %.1f"
-                       % (S, len(leaves), len(Hs.near), len(Hs.far[1]), 100.0 / scale, n, scale),
+                       % (nrhs, S, len(leaves), len(Hs.near), len(Hs.far[1]), 100.0 / scale, n, scale),
                 solve_s_scaled=t, n_timed=n)
 
 
@@ -211,18 +258,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     w = WORKLOAD
-    config = {"workload": w["name"], "unknowns": w["unknowns"], "triangles": w["triangles"], "radius_lambda": w["radius"],
-              "leaf_size": w["leaf_size"], "tree": "octree (median splits)", "admissibility": "dist>=2*min(diam)",
-              "aca_tol": w["aca_tol"], "n_terms": w["n_terms"], "levels": "leaf level only",
-              "refine": "one FP64-residual refinement step", "nrhs": 1, "rhs": "plane wave +z, x-pol",
-              "l2": "operator resident in HBM is larger than L2; no flush", "parallelism": "replicas"}
+    config = workload_config(w)
 
     if a.impl == "reference":
         if rank != 0:
             return
         r = oracle_sample_rate(a.cpu_seconds, warmup=min(a.warmup, 1), steps=max(a.steps, 1) if a.steps < 50 else None)
         line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": "RHS/s", "n_gpus": a.gpus,
-                "steps": r["n_timed"], "warmup": min(a.warmup, 1), "ms_per_step": 1e3 / r["value"],
+                "steps": r["n_timed"], "warmup": min(a.warmup, 1), "ms_per_step": 1e3 * w["nrhs"] / r["value"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                 "data": "synthetic", "config": config,
                 "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
@@ -232,7 +275,6 @@ def main():
 
     import numpy as np
     import torch
-    from synth import icosphere
     from paper_2307_03968_gb300.hm import HMatrix
 
     torch.cuda.set_device(local)
@@ -246,18 +288,19 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    xyz, tri = icosphere(w["subdivisions"], w["radius"])
+    xyz, cells, eps = workload_mesh(w)
     t0 = time.perf_counter()
-    A = HMatrix.build(xyz, tri, leaf_size=w["leaf_size"], arity=w["arity"], adm=w["adm"], aca_tol=w["aca_tol"],
-                      levels=-1)
+    A = HMatrix.build(xyz, cells, eps_r=eps, leaf_size=w["leaf_size"], arity=w["arity"], adm=w["adm"],
+                      aca_tol=w["aca_tol"], levels=-1)
     build_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     A.factor_leaf()
     factor_s = time.perf_counter() - t0
     info = A.info()
     N = A.n
-    kh, ph = np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]])
-    b = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    kh, ph = workload_incidences(w)
+    nrhs = len(kh)
+    b = torch.empty((nrhs, N), dtype=torch.complex64, device="cuda")
     A.rhs_plane_wave(kh, ph, b)
     x = torch.empty_like(b)
     opts = dict(n_terms=w["n_terms"], n_levels=w["n_levels"], refine=w["refine"])
@@ -300,7 +343,7 @@ def main():
     lat = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
-    value = K * world / (total_ms / 1e3)
+    value = K * nrhs * world / (total_ms / 1e3)
 
     # extras: unrefined solve and full-level solve (nested, all levels)
     def time_solves(n, **kw):
@@ -316,7 +359,9 @@ def main():
     no_refine_ms = full_nested_ms = full_flat_ms = None
     if not a.no_extras:
         no_refine_ms = time_solves(200, n_terms=2, n_levels=1, refine=False)
-        full_nested_ms = time_solves(20, n_terms=2, n_levels=-1, nested=True, refine=False)
+        # the nested form costs ~(K+1)^levels leaf-level products: few repetitions on deep trees
+        full_nested_ms = time_solves(20 if info.n_levels <= 3 else 2, n_terms=2, n_levels=-1, nested=True,
+                                     refine=False)
         full_flat_ms = time_solves(100, n_terms=2, n_levels=-1, nested=False, refine=False)
 
     # end to end through the host-buffer entry point
@@ -332,17 +377,34 @@ def main():
             xh = A.solve_host(bh, **opts)
             _ = float(np.abs(xh[0, 0]))
         dt = time.perf_counter() - t0
-        e2e = {"value": Ke * world / dt, "unit": "RHS/s", "h2d_bytes_per_step": int(bh.nbytes),
+        e2e = {"value": Ke * nrhs * world / dt, "unit": "RHS/s", "h2d_bytes_per_step": int(bh.nbytes),
                "d2h_bytes_per_step": int(xh.nbytes), "steps": Ke}
 
     peak, peak_kind = peaks()
     per_launch_bytes = prof_bytes / max(prof_n, 1)
     per_launch_ms = prof_ms / max(prof_n, 1)
-    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if prof_n else None
-    roof = {"bound": "hbm", "kernel": "k_apply_items<float,float,2> (near + leaf-level far block product, k_product.cu)",
-            "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": committed_traffic(),
-            "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms, "launches": prof_n,
+    # every stored complex element is used twice per right-hand side (the block and its
+    # half-storage mirror): 2 complex multiply-adds = 16 real flops per 8 bytes per RHS
+    flops_per_launch = 2.0 * per_launch_bytes * nrhs
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
+    alu_bound = flops_per_launch / (alu_peak * 1e12) > per_launch_bytes / (peak * 1e9)
+    if not prof_n:
+        achieved = None
+    elif alu_bound:
+        achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+    else:
+        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    roof = {"bound": "alu" if alu_bound else "hbm",
+            "kernel": "k_apply_items<float,float,2> (near + leaf-level far block product, k_product.cu)",
+            "achieved": achieved, "peak": alu_peak if alu_bound else peak,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock" if alu_bound else peak_kind,
+            "unit": "TFLOP/s" if alu_bound else "GB/s",
+            "frac": (achieved / (alu_peak if alu_bound else peak)) if achieved else None,
+            "traffic": committed_traffic(),
+            "bytes_per_launch": per_launch_bytes, "flops_per_launch": flops_per_launch, "nrhs": nrhs,
+            "ms_per_launch": per_launch_ms, "launches": prof_n,
+            "hbm_gbs": per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if prof_n else None,
             "share_of_step": (prof_ms / Kp / eager_ms) if eager_ms else None,
             "measured_on": "the timed solve launched kernel by kernel (%d steps, %.4f ms/step)" % (Kp, eager_ms)}
     cpu = None

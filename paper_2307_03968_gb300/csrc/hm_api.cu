@@ -45,6 +45,31 @@ template <class T> static hm_status upload(hm_matrix h, T **dst, const std::vect
     return HM_OK;
 }
 
+hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
+{
+    hm_status st;
+    for (auto &kv : h->levels) {
+        LevelList &L = kv.second;
+        std::vector<Item> small, big;
+        L.small_dim = 2;
+        L.small_rank = 0;
+        for (const Item &it : L.items) {
+            const bool fits = it.m <= MRHS_MAX_DIM && it.n <= MRHS_MAX_DIM && it.k <= MRHS_MAX_RANK;
+            (fits ? small : big).push_back(it);
+            if (fits) {
+                L.small_dim = std::max<int>(L.small_dim, (int)std::max(even(it.m), even(it.n)));
+                L.small_rank = std::max(L.small_rank, it.k);
+            }
+        }
+        L.n_small = (int64_t)small.size();
+        L.n_big = (int64_t)big.size();
+        if ((st = upload(h, &L.d_items, L.items, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_small, small, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_big, big, s)) != HM_OK) return st;
+    }
+    return HM_OK;
+}
+
 static void clear_graphs(hm_matrix h)
 {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
@@ -65,8 +90,11 @@ static void free_handle(hm_matrix h)
                     h->ws.d_acc64, h->ws.d_io, h->ws.d_part, h->d_csr_off, h->d_csr_idx};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    for (auto &kv : h->levels)
+    for (auto &kv : h->levels) {
         if (kv.second.d_items) cudaFree(kv.second.d_items);
+        if (kv.second.d_small) cudaFree(kv.second.d_small);
+        if (kv.second.d_big) cudaFree(kv.second.d_big);
+    }
     for (void *p : h->ws.vec32) if (p) cudaFree(p);
     for (void *p : h->ws.vec64) if (p) cudaFree(p);
     if (h->h_status) cudaFreeHost(h->h_status);
@@ -235,7 +263,8 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
         cudaEventRecord(h->prof_ev[h->prof_used + 1], c.s);
         h->prof_used += 2;
         h->prof_launches++;
-        h->prof_bytes += (it->second.alg_elems * 8 + 2 * 8 * h->N) * (int64_t)c.nrhs;
+        // algorithmic bytes: every stored block once, x read and z written once per right-hand side
+        h->prof_bytes += it->second.alg_elems * 8 + 2 * 8 * h->N * (int64_t)c.nrhs;
     }
     c.launches++;
     c.bytes += level_bytes(c.h, lev, c.fp64) * c.nrhs;
@@ -591,8 +620,7 @@ static hm_status import_blocks(const hm_blocks *B, cudaStream_t s, hm_matrix h)
     if ((st = upload(h, &h->d_pool32, p32, s)) != HM_OK) return st;
     if (h->has_fp64 && (st = upload(h, &h->d_pool64, p64, s)) != HM_OK) return st;
     if ((st = prepare_partials(h, s)) != HM_OK) return st;
-    for (auto &kv : h->levels)
-        if ((st = upload(h, &kv.second.d_items, kv.second.items, s)) != HM_OK) return st;
+    if ((st = upload_item_lists(h, s)) != HM_OK) return st;
     // tree depth is not given by the import; report the number of levels instead
     h->depth = max_level;
     HM_CUDA(cudaStreamSynchronize(s));

@@ -26,6 +26,9 @@
 
 namespace hm {
 
+constexpr int MRHS_MAX_DIM = 64;    // largest block side of the multi-RHS product kernel
+constexpr int MRHS_MAX_RANK = 32;   // largest rank of a low-rank block it takes
+
 // One stored block = one work item of the product kernels (32 bytes).
 struct Item {
     int64_t off;    // complex-element offset into the pool
@@ -50,6 +53,12 @@ struct LevelList {
     std::vector<Item> items;      // host copy
     std::vector<int32_t> true_m, true_n;  // unpadded sizes (for export)
     Item *d_items = nullptr;      // device copy
+    // the same items split for the multi-right-hand-side product: blocks of at
+    // most MRHS_MAX_DIM x MRHS_MAX_DIM (and rank <= MRHS_MAX_RANK) staged whole
+    // in shared memory, and the rest
+    Item *d_small = nullptr, *d_big = nullptr;
+    int64_t n_small = 0, n_big = 0;
+    int small_dim = 0, small_rank = 0;   // largest (even) side and rank among the small items
     int64_t n_dense = 0, n_lowrank = 0;
     int64_t elems = 0;            // stored complex elements
 };
@@ -209,5 +218,11 @@ hm_status finalize_layout(hm_matrix h, cudaStream_t s);
 // assigns the FP64 partial slots (Item::pad) and uploads the per-leaf slot lists;
 // call after every level list is complete and before the items are uploaded
 hm_status prepare_partials(hm_matrix h, cudaStream_t s);
+// uploads every level's item list and its multi-RHS split (small / big)
+hm_status upload_item_lists(hm_matrix h, cudaStream_t s);
+// multi-right-hand-side product of the small items of a level (k_mrhs.cu):
+// z (+)= M_level x for right-hand sides [0, nrhs), blocks read once per chunk of rb
+void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, int rb,
+                             cudaStream_t s);
 
 } // namespace hm

@@ -848,8 +848,7 @@ hm_status assemble(BasisData &B, G g, const hm_build_opts *o, TmpBuffers &tmp, c
         launch_convert_f32_to_f64(h->d_pool32, h->d_pool64, std::max<int64_t>(pool, 1), s);
     }
     if ((st = prepare_partials(h, s)) != HM_OK) return st;
-    for (auto &kv : h->levels)
-        if ((st = up(h, &kv.second.d_items, kv.second.items, s)) != HM_OK) return st;
+    if ((st = upload_item_lists(h, s)) != HM_OK) return st;
     // geometry kept for the plane-wave excitation
     if ((st = up(h, &h->d_qpd, B.qpd, s)) != HM_OK || (st = up(h, &h->d_vtx, B.vtx, s)) != HM_OK ||
         (st = up(h, &h->d_ucell, B.ucell, s)) != HM_OK || (st = up(h, &h->d_ufree, B.ufree, s)) != HM_OK ||

@@ -1,0 +1,231 @@
+// Block product z += M x for many right-hand sides (arxiv 2307.03968 eqs. 6
+// and 8 with the half storage of §III), reading every stored block once per
+// chunk of RB right-hand sides instead of once per right-hand side:
+//     dense  B (I,J):  Z_I += B X_J,            Z_J += B^T X_I
+//     low rank U V:    Z_I += U (V X_J),        Z_J += V^T (U^T X_I)
+// with X_I, X_J the row / column cluster panels of the RB right-hand sides.
+//
+// One CTA of 128 threads per block, persistent over the item list.  The block
+// (or both low-rank panels) and the two RHS panels are copied to shared memory
+// with cp.async; each small product is then a SIMT GEMM in which a thread owns
+// 2 rows x RB/4 right-hand sides of the output, so every shared-memory load of
+// the block feeds RB/4 complex FMAs.  Shared rows have an odd stride (complex
+// elements) so that the row pairs a warp touches fall in distinct banks, and
+// the shared buffers are sized for the largest block and rank of the level, so
+// that several CTAs per SM overlap one block's copy with another's arithmetic.
+// Results go to z with vector atomics, as in the single-RHS kernel.  Blocks
+// larger than MRHS_MAX_DIM or of rank above MRHS_MAX_RANK stay on the
+// single-RHS kernel.
+#include "k_common.cuh"
+
+namespace hm {
+namespace {
+
+using namespace kc;
+constexpr int MT = 128;   // threads per CTA
+
+struct Geom {             // shared-memory geometry of one launch (complex-element units)
+    int sld;              // block row stride: dim + 1 (odd)
+    int xld;              // RHS panel row stride: RB + 1 (odd)
+    int kmax;             // rows reserved for U^T (V follows)
+    int srows;            // rows of the block area
+    int dim;              // rows of each RHS panel
+};
+
+__device__ __forceinline__ void cma(float2 &acc, float2 a, float2 b)   // acc += a b
+{
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+__device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Y[r][q] = sum_c S[r][c] X[c][q] for rows r < R.  Thread t owns rows 2(t/4),
+// 2(t/4)+1 and right-hand sides (t%4)*TC .. +TC-1.  z given: add into z
+// (column-major, z[q*ldz + base + r]); else store into Y (row stride xld).
+template <int RB>
+__device__ __forceinline__ void mm_rows(const float2 *S, int sld, int R, int C, const float2 *X, int xld, float2 *Y,
+                                        float2 *z, int64_t ldz, int base, int nr)
+{
+    constexpr int TC = RB / 4;
+    const int t = threadIdx.x, q0 = (t & 3) * TC;
+    const int r = 2 * (t >> 2);
+    if (r >= R) return;
+    float2 a0[TC], a1[TC];
+#pragma unroll
+    for (int q = 0; q < TC; ++q) { a0[q] = make_float2(0.f, 0.f); a1[q] = a0[q]; }
+    const float2 *s0 = S + r * sld, *s1 = s0 + sld;
+    const float2 *xc = X + q0;
+    for (int c = 0; c < C; ++c, xc += xld) {
+        const float2 b0 = s0[c], b1 = s1[c];
+#pragma unroll
+        for (int q = 0; q < TC; ++q) {
+            const float2 xv = xc[q];
+            cma(a0[q], b0, xv);
+            cma(a1[q], b1, xv);
+        }
+    }
+    const bool two = r + 1 < R;
+    if (z) {
+#pragma unroll
+        for (int q = 0; q < TC; ++q) {
+            if (q0 + q >= nr) break;
+            float2 *zz = z + (int64_t)(q0 + q) * ldz + base + r;
+            if (two) red2(zz, a0[q], a1[q]);
+            else red1(zz, a0[q]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < TC; ++q) {
+            Y[r * xld + q0 + q] = a0[q];
+            if (two) Y[(r + 1) * xld + q0 + q] = a1[q];
+        }
+    }
+}
+
+// z[q*ldz + base + c] += sum_r S[r][c] X[r][q] for columns c < C, rows r < R.
+// Thread t owns columns 2(t/4), 2(t/4)+1 and right-hand sides (t%4)*TC .. +TC-1.
+template <int RB>
+__device__ __forceinline__ void mm_cols(const float2 *S, int sld, int R, int C, const float2 *X, int xld, float2 *z,
+                                        int64_t ldz, int base, int nr)
+{
+    constexpr int TC = RB / 4;
+    const int t = threadIdx.x, q0 = (t & 3) * TC;
+    const int c = 2 * (t >> 2);
+    if (c >= C) return;
+    float2 a0[TC], a1[TC];
+#pragma unroll
+    for (int q = 0; q < TC; ++q) { a0[q] = make_float2(0.f, 0.f); a1[q] = a0[q]; }
+    const float2 *sc = S + c;
+    const float2 *xr = X + q0;
+    for (int r = 0; r < R; ++r, sc += sld, xr += xld) {
+        const float2 b0 = sc[0], b1 = sc[1];
+#pragma unroll
+        for (int q = 0; q < TC; ++q) {
+            const float2 xv = xr[q];
+            cma(a0[q], b0, xv);
+            cma(a1[q], b1, xv);
+        }
+    }
+    const bool two = c + 1 < C;
+#pragma unroll
+    for (int q = 0; q < TC; ++q) {
+        if (q0 + q >= nr) break;
+        float2 *zz = z + (int64_t)(q0 + q) * ldz + base + c;
+        if (two) red2(zz, a0[q], a1[q]);
+        else red1(zz, a0[q]);
+    }
+}
+
+// rows x cols complex matrix (row stride ld in global memory) -> S (row stride sld);
+// warp w copies rows w, w+4, ..., lanes the columns
+__device__ __forceinline__ void stage(const float2 *__restrict__ g, int rows, int cols, int ld, float2 *S, int sld)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int r = w; r < rows; r += MT / 32)
+        for (int c = lane; c < cols; c += 32) cp_async8(S + r * sld + c, g + (int64_t)r * ld + c);
+}
+
+// RHS panel X[i][q] = x[q * ldx + base + i] for i < len, q < RB (zero for q >= nr)
+template <int RB>
+__device__ __forceinline__ void stage_x(const float2 *__restrict__ x, int64_t ldx, int base, int len, int nr,
+                                        float2 *X, int xld)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = w; q < RB; q += MT / 32)
+        for (int i = lane; i < len; i += 32) {
+            if (q < nr) cp_async8(X + i * xld + q, x + (int64_t)q * ldx + base + i);
+            else X[i * xld + q] = make_float2(0.f, 0.f);
+        }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(MT)
+k_apply_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *__restrict__ pool,
+             const float2 *__restrict__ x, int64_t ldx, float2 *__restrict__ z, int64_t ldz, int nr, Geom gm)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    float2 *S = sm;                                   // srows x sld: the block, or U^T then V
+    float2 *SV = S + gm.kmax * gm.sld;
+    float2 *XI = S + gm.srows * gm.sld;               // dim x xld
+    float2 *XJ = XI + gm.dim * gm.xld;                // dim x xld
+    float2 *T = XJ + gm.dim * gm.xld;                 // kmax x xld : V X_J
+    float2 *TP = T + gm.kmax * gm.xld;                // kmax x xld : U^T X_I
+    for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
+        const Item it = items[b];
+        __syncthreads();                              // the previous item is done with shared memory
+        stage_x<RB>(x, ldx, it.row0, it.m, nr, XI, gm.xld);
+        stage_x<RB>(x, ldx, it.col0, it.n, nr, XJ, gm.xld);
+        if (it.k == 0) {
+            stage(pool + it.off, it.m, it.n, (int)even(it.n), S, gm.sld);
+            cp_async_wait_all();
+            __syncthreads();
+            mm_rows<RB>(S, gm.sld, it.m, it.n, XJ, gm.xld, nullptr, z, ldz, it.row0, nr);   // Z_I += B X_J
+            mm_cols<RB>(S, gm.sld, it.m, it.n, XI, gm.xld, z, ldz, it.col0, nr);            // Z_J += B^T X_I
+        } else {
+            const float2 *UT = pool + it.off;
+            const float2 *V = UT + (int64_t)it.k * it.m;
+            stage(UT, it.k, it.m, it.m, S, gm.sld);
+            stage(V, it.k, it.n, it.n, SV, gm.sld);
+            cp_async_wait_all();
+            __syncthreads();
+            mm_rows<RB>(SV, gm.sld, it.k, it.n, XJ, gm.xld, T, nullptr, 0, 0, nr);          // T  = V X_J
+            mm_rows<RB>(S, gm.sld, it.k, it.m, XI, gm.xld, TP, nullptr, 0, 0, nr);          // T' = U^T X_I
+            __syncthreads();
+            mm_cols<RB>(S, gm.sld, it.k, it.m, T, gm.xld, z, ldz, it.row0, nr);             // Z_I += U T
+            mm_cols<RB>(SV, gm.sld, it.k, it.n, TP, gm.xld, z, ldz, it.col0, nr);           // Z_J += V^T T'
+        }
+    }
+}
+
+template <int RB>
+void launch_rb(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
+{
+    Geom gm;
+    gm.dim = L.small_dim;                              // even, <= MRHS_MAX_DIM
+    gm.sld = gm.dim + 1;
+    gm.xld = RB + 1;
+    gm.kmax = L.small_rank;
+    gm.srows = std::max(gm.dim, 2 * gm.kmax) + 1;     // one spare row: a thread's second row may be read past the end
+    const size_t sm = sizeof(float2) * ((size_t)gm.srows * gm.sld + 2 * (size_t)gm.dim * gm.xld +
+                                        2 * (size_t)std::max(gm.kmax, 1) * gm.xld);
+    static size_t attr = 0;                            // largest dynamic size enabled so far
+    if (sm > attr) {
+        cudaFuncSetAttribute(k_apply_mrhs<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = sm;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_mrhs<RB>, MT, sm);
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
+    if (g > L.n_small) g = L.n_small;
+    for (int r0 = 0; r0 < nrhs; r0 += RB) {
+        const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
+        k_apply_mrhs<RB><<<(unsigned)g, MT, sm, s>>>(L.d_small, L.n_small, h->d_pool32, x + (int64_t)r0 * h->pN,
+                                                     h->pN, z + (int64_t)r0 * h->pN, h->pN, nr, gm);
+    }
+}
+
+} // namespace
+
+void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, int rb,
+                             cudaStream_t s)
+{
+    if (L.n_small == 0 || nrhs <= 0) return;
+    if (rb <= 8) launch_rb<8>(h, L, x, z, nrhs, s);
+    else if (rb <= 16) launch_rb<16>(h, L, x, z, nrhs, s);
+    else launch_rb<32>(h, L, x, z, nrhs, s);
+}
+
+} // namespace hm

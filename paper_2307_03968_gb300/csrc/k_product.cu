@@ -17,6 +17,7 @@ namespace {
 
 using namespace kc;
 constexpr int APPLY_WARPS = 8;   // warps per CTA of the product kernel
+constexpr int MRHS_MIN_RHS = 4;  // from this many right-hand sides on, the multi-RHS kernel takes the small blocks
 
 // Dense near block B (m x n, row-major, stride even(n)) between leaves I (rows)
 // and J (columns):  z_I += B x_J,  z_J += B^T x_I.
@@ -251,10 +252,20 @@ void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z,
         k_apply_items<double, double, 1><<<g, APPLY_WARPS * 32, 0, s>>>(
             L.d_items, n, h->d_pool64, (const double2 *)x, h->pN, (double2 *)z, h->pN, nrhs);
     } else {
+        const Item *list = L.d_items;
+        int64_t cnt = n;
+        if (nrhs >= MRHS_MIN_RHS && L.n_small > 0) {
+            // many right-hand sides: blocks that fit shared memory are read once per RHS chunk
+            const int rb = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : 32;
+            launch_apply_items_mrhs(h, L, (const float2 *)x, (float2 *)z, nrhs, rb, s);
+            list = L.d_big;
+            cnt = L.n_big;
+            if (cnt == 0) return;
+        }
         int g = apply_grid<float, float, 2>(h);
-        if ((int64_t)g * APPLY_WARPS > n) g = (int)((n + APPLY_WARPS - 1) / APPLY_WARPS);
+        if ((int64_t)g * APPLY_WARPS > cnt) g = (int)((cnt + APPLY_WARPS - 1) / APPLY_WARPS);
         k_apply_items<float, float, 2><<<g, APPLY_WARPS * 32, 0, s>>>(
-            L.d_items, n, h->d_pool32, (const float2 *)x, h->pN, (float2 *)z, h->pN, nrhs);
+            list, cnt, h->d_pool32, (const float2 *)x, h->pN, (float2 *)z, h->pN, nrhs);
     }
 }
 

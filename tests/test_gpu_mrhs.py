@@ -1,0 +1,72 @@
+"""Many right-hand sides: the block product that reads each block once per
+chunk of right-hand sides (shared-memory staged, k_mrhs.cu) against the same
+product taken one right-hand side at a time (the single-RHS kernel), on the
+same operator, in FP32 arithmetic.  Both accumulate with atomics in an
+unspecified order, so they agree to FP32 rounding: relative 2-norm per column
+<= 1e-5.  RHS counts cover every chunk width (8, 16, 32), ragged last chunks,
+and the switch-over point; the operators mix dense blocks, low-rank blocks
+that fit shared memory, and blocks that do not (leaves of 108 unknowns)."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_03968_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def operators(torch_cuda):
+    import synth
+    from paper_2307_03968_gb300.hm import HMatrix
+    ops = {}
+    xyz, tri = synth.icosphere(3, 0.3)
+    ops["rwg_binary15"] = HMatrix.build(xyz, tri, leaf_size=15, arity=2, adm=1.0, aca_tol=1e-4, levels=-1)
+    xyz, tet = synth.cube_tets(4, 1.0)
+    xyz = xyz * np.array([2.0, 0.25, 0.125])
+    eps = synth.random_permittivity(len(tet), 2.0, 6.0, seed=4)
+    ops["swg_slab"] = HMatrix.build(xyz, tet, eps_r=eps, leaf_size=16, arity=2, adm=1.0, aca_tol=1e-4, levels=-1)
+    # 864 unknowns halved three times: leaves of 108, dense blocks too large for shared memory
+    ops["swg_slab_leaf112"] = HMatrix.build(xyz, tet, eps_r=eps, leaf_size=112, arity=2, adm=1.0, aca_tol=1e-6,
+                                            levels=-1)
+    for A in ops.values():
+        A.factor_leaf()
+    return ops
+
+
+@pytest.mark.parametrize("name", ["rwg_binary15", "swg_slab", "swg_slab_leaf112"])
+@pytest.mark.parametrize("nrhs", [3, 4, 7, 8, 13, 16, 33, 70])
+def test_many_rhs_product_equals_column_products(torch_cuda, operators, name, nrhs):
+    A = operators[name]
+    N = A.n
+    rng = np.random.default_rng(nrhs)
+    x = (rng.normal(size=(nrhs, N)) + 1j * rng.normal(size=(nrhs, N))).astype(np.complex64)
+    xt = torch_cuda.from_numpy(x).cuda()
+    yt = torch_cuda.empty_like(xt)
+    A.apply(xt, yt, n_levels=-1, fp64_accumulate=False)
+    got = yt.cpu().numpy()
+    for r in range(nrhs):
+        y1 = torch_cuda.empty((1, N), dtype=torch_cuda.complex64, device="cuda")
+        A.apply(xt[r:r + 1].contiguous(), y1, n_levels=-1, fp64_accumulate=False)
+        ref = y1.cpu().numpy()[0]
+        assert np.linalg.norm(got[r] - ref) / np.linalg.norm(ref) < 1e-5, r
+
+
+def test_operators_exercise_both_kernels(operators):
+    big = 0
+    small = 0
+    for A in operators.values():
+        for lev in range(1, A.info().n_levels + 1):
+            r0, c0, m, n, k = A.blocks(lev)
+            fits = (m <= 64) & (n <= 64) & (k <= 32)
+            small += int(fits.sum())
+            big += int((~fits).sum())
+    assert small > 100 and big > 10
