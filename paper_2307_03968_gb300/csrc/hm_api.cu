@@ -229,7 +229,7 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
         }
     }
     HM_CUDA(cudaMalloc((void **)&ws.d_acc64, 2 * sizeof(double) * r));
-    ws.part_rhs = std::min(r, 4);
+    ws.part_rhs = std::min(r, RESID_CHUNK);
     HM_CUDA(cudaMalloc((void **)&ws.d_part, sizeof(double2) * std::max<int64_t>(h->partial_elems, 1) * ws.part_rhs));
     ws.nrhs = r;
     return HM_OK;

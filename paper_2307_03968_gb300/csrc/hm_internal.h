@@ -28,6 +28,8 @@ namespace hm {
 
 constexpr int MRHS_MAX_DIM = 64;    // largest block side of the multi-RHS product kernel
 constexpr int MRHS_MAX_RANK = 32;   // largest rank of a low-rank block it takes
+constexpr int MRHS_MIN_RHS = 4;     // from this many right-hand sides on, the multi-RHS kernels take the small blocks
+constexpr int RESID_CHUNK = 16;     // right-hand sides per chunk of the FP64-class residual (partial slots held)
 
 // One stored block = one work item of the product kernels (32 bytes).
 struct Item {
@@ -224,5 +226,8 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s);
 // z (+)= M_level x for right-hand sides [0, nrhs), blocks read once per chunk of rb
 void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, int rb,
                              cudaStream_t s);
+// the FP64-class partial-slot products of the small items for many right-hand sides (k_mrhs.cu)
+void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, double2 *part,
+                                      int64_t pstride, int nrhs, cudaStream_t s);
 
 } // namespace hm

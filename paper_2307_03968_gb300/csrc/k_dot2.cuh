@@ -1,0 +1,102 @@
+// Error-free FP32 arithmetic for the FP64-class residual products
+// (shared by the single- and multi-right-hand-side residual kernels).
+#pragma once
+
+#include "k_common.cuh"
+
+namespace hm {
+namespace dot2 {
+
+using kc::FULL;
+
+// ---------------------------------------------------------------------------
+// FP64-class products for the refinement residual (complex64 data).
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so a full-operator pass
+// in FP64 arithmetic costs many times its HBM time.  The residual products
+// therefore use error-free transformations in FP32 (Ogita, Rump & Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2):
+// every product a*b is split exactly into p + e with e = fma(a, b, -p), and
+// every sum is compensated (Knuth's TwoSum), so each block's sums are as
+// accurate as if computed in twice the working precision.  The per-block
+// results are stored as FP64 partial slots and summed across blocks in FP64.
+struct df { float hi, lo; };
+struct cdf { df re, im; };
+
+// The error-free transformations below must not be contracted into FMAs or
+// reassociated, so every operation is an explicitly rounded intrinsic.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// acc += a * b  (Dot2 step): p + ep == a * b exactly
+__device__ __forceinline__ void dot2(df &acc, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float ep = __fmaf_rn(a, b, -p);
+    float s, q;
+    two_sum(acc.hi, p, s, q);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(q, ep));
+}
+// acc += a * b for complex a (FP32) and b (FP32)
+__device__ __forceinline__ void cdot2(cdf &acc, float2 a, float2 b)
+{
+    dot2(acc.re, a.x, b.x);
+    dot2(acc.re, -a.y, b.y);
+    dot2(acc.im, a.x, b.y);
+    dot2(acc.im, a.y, b.x);
+}
+// acc += a * (bh + bl) for complex a and a double-float complex b
+__device__ __forceinline__ void cdot2_df(cdf &acc, float2 a, const cdf &b)
+{
+    cdot2(acc, a, make_float2(b.re.hi, b.im.hi));
+    acc.re.lo += a.x * b.re.lo - a.y * b.im.lo;
+    acc.im.lo += a.x * b.im.lo + a.y * b.re.lo;
+}
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ cdf cdf_add(const cdf &a, const cdf &b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ cdf shfl_xor(const cdf &v, int s)
+{
+    return {{__shfl_xor_sync(FULL, v.re.hi, s), __shfl_xor_sync(FULL, v.re.lo, s)},
+            {__shfl_xor_sync(FULL, v.im.hi, s), __shfl_xor_sync(FULL, v.im.lo, s)}};
+}
+__device__ __forceinline__ cdf shfl_idx(const cdf &v, int l)
+{
+    return {{__shfl_sync(FULL, v.re.hi, l), __shfl_sync(FULL, v.re.lo, l)},
+            {__shfl_sync(FULL, v.im.hi, l), __shfl_sync(FULL, v.im.lo, l)}};
+}
+__device__ __forceinline__ double2 to_d2(const cdf &v)
+{
+    return make_double2((double)v.re.hi + (double)v.re.lo, (double)v.im.hi + (double)v.im.lo);
+}
+// lane l ends with the sum over all lanes of v[l & (S-1)] in v[0] (S = 8 or 4)
+template <int S>
+__device__ __forceinline__ void reduce_cdf(cdf (&v)[S], int lane)
+{
+#pragma unroll
+    for (int s = S / 2; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+            const cdf send = up ? v[j] : v[j + s];
+            const cdf keep = up ? v[j + s] : v[j];
+            v[j] = cdf_add(keep, shfl_xor(send, s));
+        }
+    }
+#pragma unroll
+    for (int s = S; s < 32; s <<= 1) v[0] = cdf_add(v[0], shfl_xor(v[0], s));
+}
+
+} // namespace dot2
+} // namespace hm

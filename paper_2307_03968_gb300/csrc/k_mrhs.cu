@@ -17,6 +17,7 @@
 // larger than MRHS_MAX_DIM or of rank above MRHS_MAX_RANK stay on the
 // single-RHS kernel.
 #include "k_common.cuh"
+#include "k_dot2.cuh"
 
 namespace hm {
 namespace {
@@ -189,17 +190,13 @@ k_apply_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *__re
     }
 }
 
+Geom level_geom(const LevelList &L, int rb, size_t t_elem, size_t &bytes);
+
 template <int RB>
 void launch_rb(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
 {
-    Geom gm;
-    gm.dim = L.small_dim;                              // even, <= MRHS_MAX_DIM
-    gm.sld = gm.dim + 1;
-    gm.xld = RB + 1;
-    gm.kmax = L.small_rank;
-    gm.srows = std::max(gm.dim, 2 * gm.kmax) + 1;     // one spare row: a thread's second row may be read past the end
-    const size_t sm = sizeof(float2) * ((size_t)gm.srows * gm.sld + 2 * (size_t)gm.dim * gm.xld +
-                                        2 * (size_t)std::max(gm.kmax, 1) * gm.xld);
+    size_t sm = 0;
+    const Geom gm = level_geom(L, RB, sizeof(float2), sm);
     static size_t attr = 0;                            // largest dynamic size enabled so far
     if (sm > attr) {
         cudaFuncSetAttribute(k_apply_mrhs<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -217,6 +214,181 @@ void launch_rb(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int 
     }
 }
 
+// ------------------------------------------------------------------------------
+// FP64-class residual products for many right-hand sides: the same staging, the
+// products accumulated by the error-free Dot2 steps, each block's results
+// stored in its FP64 partial slots (row side: even(m) slots from it.pad, column
+// side: even(n) slots after them; no atomics, so the per-leaf FP64 gather that
+// follows stays deterministic).  Right-hand side q of the chunk writes
+// part[q * pstride + slot].
+
+// slots[q*pstride + r] = sum_c S[r][c] X[c][q] for r < Rs (rows R .. Rs-1 are zero).
+// Y given (double-float staging, row stride xld) instead of slots: store there.
+template <int RB>
+__device__ __forceinline__ void mm_rows_c(const float2 *S, int sld, int R, int Rs, int C, const float2 *X, int xld,
+                                          dot2::cdf *Y, double2 *slots, int64_t pstride, int nr)
+{
+    using namespace dot2;
+    constexpr int TC = RB / 4;
+    const int t = threadIdx.x, q0 = (t & 3) * TC;
+    const int r = 2 * (t >> 2);
+    if (r >= Rs) return;
+    cdf a0[TC], a1[TC];
+#pragma unroll
+    for (int q = 0; q < TC; ++q) { a0[q] = cdf_zero(); a1[q] = cdf_zero(); }
+    if (r < R) {
+        const float2 *s0 = S + r * sld, *s1 = s0 + sld;
+        const float2 *xc = X + q0;
+        for (int c = 0; c < C; ++c, xc += xld) {
+            const float2 b0 = s0[c], b1 = s1[c];
+#pragma unroll
+            for (int q = 0; q < TC; ++q) {
+                const float2 xv = xc[q];
+                cdot2(a0[q], b0, xv);
+                cdot2(a1[q], b1, xv);
+            }
+        }
+    }
+    const bool two = r + 1 < R;   // else row r+1 (if < Rs) is a zero pad slot
+#pragma unroll
+    for (int q = 0; q < TC; ++q) {
+        if (Y) {
+            Y[r * xld + q0 + q] = a0[q];
+            if (r + 1 < Rs) Y[(r + 1) * xld + q0 + q] = two ? a1[q] : cdf_zero();
+        } else {
+            if (q0 + q >= nr) break;
+            double2 *o = slots + (int64_t)(q0 + q) * pstride + r;
+            o[0] = to_d2(a0[q]);
+            if (r + 1 < Rs) o[1] = two ? to_d2(a1[q]) : make_double2(0.0, 0.0);
+        }
+    }
+}
+
+// slots[q*pstride + c] = sum_r S[r][c] X[r][q] for c < Cs (columns C .. Cs-1 zero);
+// X in FP32 (XF) or double-float (XD).
+template <int RB>
+__device__ __forceinline__ void mm_cols_c(const float2 *S, int sld, int R, int C, int Cs, const float2 *XF,
+                                          const dot2::cdf *XD, int xld, double2 *slots, int64_t pstride, int nr)
+{
+    using namespace dot2;
+    constexpr int TC = RB / 4;
+    const int t = threadIdx.x, q0 = (t & 3) * TC;
+    const int c = 2 * (t >> 2);
+    if (c >= Cs) return;
+    cdf a0[TC], a1[TC];
+#pragma unroll
+    for (int q = 0; q < TC; ++q) { a0[q] = cdf_zero(); a1[q] = cdf_zero(); }
+    if (c < C) {
+        const float2 *sc = S + c;
+        for (int r = 0; r < R; ++r, sc += sld) {
+            const float2 b0 = sc[0], b1 = sc[1];
+            if (XD) {
+                const cdf *xr = XD + r * xld + q0;
+#pragma unroll
+                for (int q = 0; q < TC; ++q) {
+                    cdot2_df(a0[q], b0, xr[q]);
+                    cdot2_df(a1[q], b1, xr[q]);
+                }
+            } else {
+                const float2 *xr = XF + r * xld + q0;
+#pragma unroll
+                for (int q = 0; q < TC; ++q) {
+                    const float2 xv = xr[q];
+                    cdot2(a0[q], b0, xv);
+                    cdot2(a1[q], b1, xv);
+                }
+            }
+        }
+    }
+    const bool two = c + 1 < C;
+#pragma unroll
+    for (int q = 0; q < TC; ++q) {
+        if (q0 + q >= nr) break;
+        double2 *o = slots + (int64_t)(q0 + q) * pstride + c;
+        o[0] = to_d2(a0[q]);
+        if (c + 1 < Cs) o[1] = two ? to_d2(a1[q]) : make_double2(0.0, 0.0);
+    }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(MT)
+k_residual_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *__restrict__ pool,
+                const float2 *__restrict__ x, int64_t ldx, double2 *__restrict__ part, int64_t pstride, int nr,
+                Geom gm)
+{
+    using dot2::cdf;
+    extern __shared__ __align__(16) float2 sm[];
+    float2 *S = sm;
+    float2 *SV = S + gm.kmax * gm.sld;
+    float2 *XI = S + gm.srows * gm.sld;
+    float2 *XJ = XI + gm.dim * gm.xld;
+    cdf *T = reinterpret_cast<cdf *>(XJ + gm.dim * gm.xld);    // kmax x xld (double-float)
+    cdf *TP = T + gm.kmax * gm.xld;
+    for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
+        const Item it = items[b];
+        __syncthreads();
+        stage_x<RB>(x, ldx, it.row0, it.m, nr, XI, gm.xld);
+        stage_x<RB>(x, ldx, it.col0, it.n, nr, XJ, gm.xld);
+        double2 *rows = part + it.pad;
+        if (it.k == 0) {
+            const int em = (int)even(it.m), en = (int)even(it.n);
+            stage(pool + it.off, it.m, it.n, en, S, gm.sld);
+            cp_async_wait_all();
+            __syncthreads();
+            mm_rows_c<RB>(S, gm.sld, it.m, em, it.n, XJ, gm.xld, nullptr, rows, pstride, nr);          // B x_J
+            mm_cols_c<RB>(S, gm.sld, it.m, it.n, en, XI, nullptr, gm.xld, rows + em, pstride, nr);    // B^T x_I
+        } else {
+            const float2 *UT = pool + it.off;
+            const float2 *V = UT + (int64_t)it.k * it.m;
+            stage(UT, it.k, it.m, it.m, S, gm.sld);
+            stage(V, it.k, it.n, it.n, SV, gm.sld);
+            cp_async_wait_all();
+            __syncthreads();
+            mm_rows_c<RB>(SV, gm.sld, it.k, it.k, it.n, XJ, gm.xld, T, nullptr, 0, nr);               // T  = V x_J
+            mm_rows_c<RB>(S, gm.sld, it.k, it.k, it.m, XI, gm.xld, TP, nullptr, 0, nr);               // T' = U^T x_I
+            __syncthreads();
+            mm_cols_c<RB>(S, gm.sld, it.k, it.m, it.m, nullptr, T, gm.xld, rows, pstride, nr);        // U T
+            mm_cols_c<RB>(SV, gm.sld, it.k, it.n, it.n, nullptr, TP, gm.xld, rows + it.m, pstride, nr); // V^T T'
+        }
+    }
+}
+
+Geom level_geom(const LevelList &L, int rb, size_t t_elem, size_t &bytes)
+{
+    Geom gm;
+    gm.dim = L.small_dim;                              // even, <= MRHS_MAX_DIM
+    gm.sld = gm.dim + 1;
+    gm.xld = rb + 1;
+    gm.kmax = L.small_rank;
+    gm.srows = std::max(gm.dim, 2 * gm.kmax) + 1;     // one spare row: a thread's second row may be read past the end
+    bytes = sizeof(float2) * ((size_t)gm.srows * gm.sld + 2 * (size_t)gm.dim * gm.xld) +
+            t_elem * 2 * (size_t)std::max(gm.kmax, 1) * gm.xld;
+    return gm;
+}
+
+template <int RB>
+void launch_resid_rb(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride, int nrhs,
+                     cudaStream_t s)
+{
+    size_t sm = 0;
+    const Geom gm = level_geom(L, RB, sizeof(dot2::cdf), sm);
+    static size_t attr = 0;
+    if (sm > attr) {
+        cudaFuncSetAttribute(k_residual_mrhs<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = sm;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual_mrhs<RB>, MT, sm);
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
+    if (g > L.n_small) g = L.n_small;
+    for (int r0 = 0; r0 < nrhs; r0 += RB) {
+        const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
+        k_residual_mrhs<RB><<<(unsigned)g, MT, sm, s>>>(L.d_small, L.n_small, h->d_pool32, x + (int64_t)r0 * h->pN,
+                                                        h->pN, part + (int64_t)r0 * pstride, pstride, nr, gm);
+    }
+}
+
 } // namespace
 
 void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, int rb,
@@ -226,6 +398,18 @@ void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, f
     if (rb <= 8) launch_rb<8>(h, L, x, z, nrhs, s);
     else if (rb <= 16) launch_rb<16>(h, L, x, z, nrhs, s);
     else launch_rb<32>(h, L, x, z, nrhs, s);
+}
+
+} // namespace hm
+
+namespace hm {
+
+void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, double2 *part,
+                                      int64_t pstride, int nrhs, cudaStream_t s)
+{
+    if (L.n_small == 0 || nrhs <= 0) return;
+    if (nrhs <= 8) launch_resid_rb<8>(h, L, x, part, pstride, nrhs, s);
+    else launch_resid_rb<16>(h, L, x, part, pstride, nrhs, s);
 }
 
 } // namespace hm

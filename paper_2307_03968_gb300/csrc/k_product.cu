@@ -17,7 +17,6 @@ namespace {
 
 using namespace kc;
 constexpr int APPLY_WARPS = 8;   // warps per CTA of the product kernel
-constexpr int MRHS_MIN_RHS = 4;  // from this many right-hand sides on, the multi-RHS kernel takes the small blocks
 
 // Dense near block B (m x n, row-major, stride even(n)) between leaves I (rows)
 // and J (columns):  z_I += B x_J,  z_J += B^T x_I.

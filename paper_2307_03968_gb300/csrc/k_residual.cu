@@ -3,102 +3,14 @@
 // FP64-class accuracy).  k_residual_items writes every block's products into
 // its FP64 partial slots (no atomics); k_gather_acc64 sums each leaf's slots in a
 // fixed order in FP64, adds D_I x_I and forms b - A x.
-#include "k_common.cuh"
+#include "k_dot2.cuh"
 
 namespace hm {
 namespace {
 
 using namespace kc;
+using namespace dot2;
 constexpr int APPLY_WARPS = 8;
-
-// ---------------------------------------------------------------------------
-// FP64-class products for the refinement residual (complex64 data).
-//
-// GB300 runs FP64 at a small fraction of its FP32 rate, so a full-operator pass
-// in FP64 arithmetic costs many times its HBM time.  The residual products
-// therefore use error-free transformations in FP32 (Ogita, Rump & Oishi,
-// "Accurate sum and dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2):
-// every product a*b is split exactly into p + e with e = fma(a, b, -p), and
-// every sum is compensated (Knuth's TwoSum), so each block's sums are as
-// accurate as if computed in twice the working precision.  The per-block
-// results are stored as FP64 partial slots and summed across blocks in FP64.
-struct df { float hi, lo; };
-struct cdf { df re, im; };
-
-// The error-free transformations below must not be contracted into FMAs or
-// reassociated, so every operation is an explicitly rounded intrinsic.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-// acc += a * b  (Dot2 step): p + ep == a * b exactly
-__device__ __forceinline__ void dot2(df &acc, float a, float b)
-{
-    const float p = __fmul_rn(a, b);
-    const float ep = __fmaf_rn(a, b, -p);
-    float s, q;
-    two_sum(acc.hi, p, s, q);
-    acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(q, ep));
-}
-// acc += a * b for complex a (FP32) and b (FP32)
-__device__ __forceinline__ void cdot2(cdf &acc, float2 a, float2 b)
-{
-    dot2(acc.re, a.x, b.x);
-    dot2(acc.re, -a.y, b.y);
-    dot2(acc.im, a.x, b.y);
-    dot2(acc.im, a.y, b.x);
-}
-// acc += a * (bh + bl) for complex a and a double-float complex b
-__device__ __forceinline__ void cdot2_df(cdf &acc, float2 a, const cdf &b)
-{
-    cdot2(acc, a, make_float2(b.re.hi, b.im.hi));
-    acc.re.lo += a.x * b.re.lo - a.y * b.im.lo;
-    acc.im.lo += a.x * b.im.lo + a.y * b.re.lo;
-}
-__device__ __forceinline__ df df_add(df a, df b)
-{
-    float s, e;
-    two_sum(a.hi, b.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    const float h = __fadd_rn(s, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, s))};
-}
-__device__ __forceinline__ cdf cdf_add(const cdf &a, const cdf &b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
-__device__ __forceinline__ cdf cdf_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
-__device__ __forceinline__ cdf shfl_xor(const cdf &v, int s)
-{
-    return {{__shfl_xor_sync(FULL, v.re.hi, s), __shfl_xor_sync(FULL, v.re.lo, s)},
-            {__shfl_xor_sync(FULL, v.im.hi, s), __shfl_xor_sync(FULL, v.im.lo, s)}};
-}
-__device__ __forceinline__ cdf shfl_idx(const cdf &v, int l)
-{
-    return {{__shfl_sync(FULL, v.re.hi, l), __shfl_sync(FULL, v.re.lo, l)},
-            {__shfl_sync(FULL, v.im.hi, l), __shfl_sync(FULL, v.im.lo, l)}};
-}
-__device__ __forceinline__ double2 to_d2(const cdf &v)
-{
-    return make_double2((double)v.re.hi + (double)v.re.lo, (double)v.im.hi + (double)v.im.lo);
-}
-// lane l ends with the sum over all lanes of v[l & (S-1)] in v[0] (S = 8 or 4)
-template <int S>
-__device__ __forceinline__ void reduce_cdf(cdf (&v)[S], int lane)
-{
-#pragma unroll
-    for (int s = S / 2; s >= 1; s >>= 1) {
-        const bool up = (lane & s) != 0;
-#pragma unroll
-        for (int j = 0; j < s; ++j) {
-            const cdf send = up ? v[j] : v[j + s];
-            const cdf keep = up ? v[j + s] : v[j];
-            v[j] = cdf_add(keep, shfl_xor(send, s));
-        }
-    }
-#pragma unroll
-    for (int s = S; s < 32; s <<= 1) v[0] = cdf_add(v[0], shfl_xor(v[0], s));
-}
 
 // Dense block: slot rows (even(m)) = B x_J, slot columns (even(n)) = B^T x_I.
 __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__restrict__ pool,
@@ -371,7 +283,14 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
 void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride,
                                  int nrhs, cudaStream_t s)
 {
-    const int64_t n = (int64_t)L.items.size();
+    const Item *list = L.d_items;
+    int64_t n = (int64_t)L.items.size();
+    if (nrhs >= MRHS_MIN_RHS && L.n_small > 0) {
+        // many right-hand sides: blocks that fit shared memory are read once per chunk
+        launch_apply_items_partials_mrhs(h, L, x, part, pstride, nrhs, s);
+        list = L.d_big;
+        n = L.n_big;
+    }
     if (n == 0) return;
     static int per_sm = -1;
     if (per_sm < 0) {
@@ -381,7 +300,7 @@ void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *
     }
     int g = per_sm * (h->num_sms > 0 ? h->num_sms : 1);
     if ((int64_t)g * APPLY_WARPS > n) g = (int)((n + APPLY_WARPS - 1) / APPLY_WARPS);
-    k_residual_items<<<g, APPLY_WARPS * 32, 0, s>>>(L.d_items, n, h->d_pool32, x, h->pN, part, pstride, nrhs);
+    k_residual_items<<<g, APPLY_WARPS * 32, 0, s>>>(list, n, h->d_pool32, x, h->pN, part, pstride, nrhs);
 }
 
 void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const double2 *part, int64_t pstride,

@@ -70,3 +70,31 @@ def test_operators_exercise_both_kernels(operators):
             small += int(fits.sum())
             big += int((~fits).sum())
     assert small > 100 and big > 10
+
+
+@pytest.mark.parametrize("name", ["rwg_binary15", "swg_slab", "swg_slab_leaf112"])
+@pytest.mark.parametrize("nrhs", [4, 9, 16, 21])
+def test_many_rhs_residual_equals_column_residuals(torch_cuda, operators, name, nrhs):
+    # FP64-class residual r = b - A x: the multi-RHS kernel (chunks of up to 16,
+    # blocks staged once) against one right-hand side at a time; both sum each
+    # block in compensated FP32 and the blocks in FP64, in different orders
+    A = operators[name]
+    N = A.n
+    rng = np.random.default_rng(100 + nrhs)
+    x = (rng.normal(size=(nrhs, N)) + 1j * rng.normal(size=(nrhs, N))).astype(np.complex64)
+    xt = torch_cuda.from_numpy(x).cuda()
+    ax = torch_cuda.empty_like(xt)
+    A.apply(xt, ax, n_levels=-1, fp64_accumulate=True)
+    # b close to A x, so that the residual is small and its FP64-class accuracy matters
+    b = ax.cpu().numpy() + (1e-5 * (rng.normal(size=(nrhs, N)) + 1j * rng.normal(size=(nrhs, N)))).astype(np.complex64)
+    bt = torch_cuda.from_numpy(b).cuda()
+    rt = torch_cuda.empty_like(xt)
+    rr, bb = A.residual(bt, xt, rt, n_levels=-1)
+    got = rt.cpu().numpy()
+    for r in range(nrhs):
+        r1 = torch_cuda.empty((1, N), dtype=torch_cuda.complex64, device="cuda")
+        rr1, bb1 = A.residual(bt[r:r + 1].contiguous(), xt[r:r + 1].contiguous(), r1, n_levels=-1)
+        ref = r1.cpu().numpy()[0]
+        assert np.abs(got[r] - ref).max() <= 1e-6 * np.abs(ref).max(), r
+        assert rr[r] == pytest.approx(rr1[0], rel=1e-9)
+        assert bb[r] == pytest.approx(bb1[0], rel=1e-12)
