@@ -43,12 +43,12 @@ WORKLOADS = {
     # V-EFIE: inhomogeneous dielectric cube, side 1 wavelength, 15^3 voxels of 6 tetrahedra
     # (41,850 SWG unknowns), eps_r iid uniform [2, 6], binary tree, eq. 7 with eta = 1, 16 random incidences
     "vefie_cube": dict(name="vefie_dielectric_cube_1lambda_41850swg", kind="swg", voxels=15, side=1.0, eps_lo=2.0,
-                       eps_hi=6.0, seed=4, leaf_size=64, arity=2, adm=1.0, aca_tol=1e-4, n_terms=2, n_levels=1,
-                       refine=True, nrhs=16, unknowns=41850, tetrahedra=20250),
+                       eps_hi=6.0, seed=4, rhs_seed=44, leaf_size=64, arity=2, adm=1.0, aca_tol=1e-4, n_terms=2,
+                       n_levels=1, refine=True, nrhs=16, unknowns=41850, tetrahedra=20250),
     # the same element size on a 2/3-wavelength cube (12,600 SWG unknowns), for profiler captures
     "vefie_cube_small": dict(name="vefie_dielectric_cube_0.667lambda_12600swg", kind="swg", voxels=10, side=2.0 / 3.0,
-                             eps_lo=2.0, eps_hi=6.0, seed=4, leaf_size=64, arity=2, adm=1.0, aca_tol=1e-4, n_terms=2,
-                             n_levels=1, refine=True, nrhs=16, unknowns=12600, tetrahedra=6000),
+                             eps_lo=2.0, eps_hi=6.0, seed=4, rhs_seed=44, leaf_size=64, arity=2, adm=1.0, aca_tol=1e-4,
+                             n_terms=2, n_levels=1, refine=True, nrhs=16, unknowns=12600, tetrahedra=6000),
 }
 WORKLOAD = WORKLOADS["sphere2"]
 METRIC = "power-series solves RHS/s at <=1e-4 rel err vs FP64 oracle; p50/p99 latency"
@@ -68,7 +68,7 @@ def workload_incidences(w):
     import synth
     if w["kind"] == "rwg":
         return synth.plane_wave_z()
-    return synth.random_incidences(w["nrhs"], seed=w["seed"])
+    return synth.random_incidences(w["nrhs"], seed=w["rhs_seed"])
 
 
 def workload_config(w):
@@ -80,7 +80,7 @@ def workload_config(w):
         c.update({"tetrahedra": w["tetrahedra"], "side_lambda": w["side"],
                   "eps_r": "iid uniform [%g, %g], seed %d" % (w["eps_lo"], w["eps_hi"], w["seed"]),
                   "tree": "binary (median splits)", "admissibility": "dist>=min(diam) (eq. 7, eta=1)",
-                  "rhs": "%d plane waves, random incidence and polarisation, seed %d" % (w["nrhs"], w["seed"])})
+                  "rhs": "%d plane waves, random incidence and polarisation, seed %d" % (w["nrhs"], w["rhs_seed"])})
     c.update({"leaf_size": w["leaf_size"], "aca_tol": w["aca_tol"], "n_terms": w["n_terms"],
               "levels": "leaf level only", "refine": "one FP64-residual refinement step", "nrhs": w["nrhs"],
               "l2": "operator resident in HBM is larger than L2; no flush", "parallelism": "replicas"})
