@@ -36,6 +36,10 @@ WORKLOADS = {
     "sphere2": dict(name="sefie_pec_sphere_r2lambda_30720rwg", kind="rwg", subdivisions=5, radius=2.0, leaf_size=64,
                     arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=30720,
                     triangles=20480),
+    # the same operator, batched monostatic sweep: 181 RHS (theta 0..180 deg, phi = 0, theta-pol)
+    "sphere2_sweep181": dict(name="sefie_pec_sphere_r2lambda_30720rwg_sweep181", kind="rwg", subdivisions=5, radius=2.0,
+                             leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True,
+                             nrhs=181, sweep=True, unknowns=30720, triangles=20480),
     # a smaller sphere of the same family (7,680 unknowns), for profiler captures
     "sphere1": dict(name="sefie_pec_sphere_r1lambda_7680rwg", kind="rwg", subdivisions=4, radius=1.0, leaf_size=64,
                     arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=7680,
@@ -66,6 +70,8 @@ def workload_mesh(w):
 
 def workload_incidences(w):
     import synth
+    if w.get("sweep"):
+        return synth.monostatic_sweep(w["nrhs"])
     if w["kind"] == "rwg":
         return synth.plane_wave_z()
     return synth.random_incidences(w["nrhs"], seed=w["rhs_seed"])
@@ -75,7 +81,9 @@ def workload_config(w):
     c = {"workload": w["name"], "unknowns": w["unknowns"]}
     if w["kind"] == "rwg":
         c.update({"triangles": w["triangles"], "radius_lambda": w["radius"], "tree": "octree (median splits)",
-                  "admissibility": "dist>=2*min(diam)", "rhs": "plane wave +z, x-pol"})
+                  "admissibility": "dist>=2*min(diam)",
+                  "rhs": ("monostatic sweep, theta 0..180 deg step 1, phi 0, theta-pol" if w.get("sweep")
+                          else "plane wave +z, x-pol")})
     else:
         c.update({"tetrahedra": w["tetrahedra"], "side_lambda": w["side"],
                   "eps_r": "iid uniform [%g, %g], seed %d" % (w["eps_lo"], w["eps_hi"], w["seed"]),
@@ -425,6 +433,8 @@ def main():
                            "n_levels": info.n_levels, "near_blocks": info.n_near,
                            "far_blocks": [info.n_far[i] for i in range(info.n_levels)],
                            "max_rank": info.max_rank, "device_bytes": info.device_bytes,
+                           "tuning": (dict(zip(("product_rhs_chunk", "residual_rhs_chunk", "product_ms",
+                                                "residual_ms"), A.tuning(nrhs))) if nrhs >= 4 else None),
                            "launches_per_step": int(launches_per_step)}}
         print(json.dumps(line))
     if dist is not None:

@@ -194,6 +194,7 @@ struct SolveCtx {
     hm_matrix h;
     int nrhs, K, m;
     bool fp64;
+    int prod_rb = -1, res_rb = -1;   // kernel choices (autotune), -1 = default
     cudaStream_t s;
     int64_t launches = 0;
     int64_t bytes = 0;
@@ -258,7 +259,7 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
         }
         if (h->prof_used + 2 <= h->prof_ev.size()) cudaEventRecord(h->prof_ev[h->prof_used], c.s);
     }
-    launch_apply_items(c.h, it->second, x, z, c.nrhs, c.fp64, c.s);
+    launch_apply_items(c.h, it->second, x, z, c.nrhs, c.fp64, c.s, c.prod_rb);
     if (timed && h->prof_used + 2 <= h->prof_ev.size()) {
         cudaEventRecord(h->prof_ev[h->prof_used + 1], c.s);
         h->prof_used += 2;
@@ -352,12 +353,89 @@ static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *
         for (int lev = 1; lev <= c.m; ++lev) {
             auto it = h->levels.find(lev);
             if (it == h->levels.end() || it->second.items.empty()) continue;
-            launch_apply_items_partials(h, it->second, x, h->ws.d_part, h->partial_elems, nr, c.s);
+            launch_apply_items_partials(h, it->second, x, h->ws.d_part, h->partial_elems, nr, c.s, c.res_rb);
             c.launches++;
         }
         launch_gather_acc64(h, x, c.m, h->ws.d_part, h->partial_elems, bt ? bt + (int64_t)r0 * h->pN : nullptr,
                             out + (int64_t)r0 * h->pN, norms ? norms + 2 * r0 : nullptr, nr, c.s);
         c.launches++;
+    }
+}
+
+// Autotuner of the many-right-hand-side kernels.  On the first complex64 solve,
+// product or residual with a given right-hand-side count (>= MRHS_MIN_RHS), time
+// on this operator, with CUDA events on the caller's stream, the leaf-level
+// product with every candidate kernel (one right-hand side at a time; shared-
+// memory chunks of 8, 16, 32) and the FP64-class residual products likewise (one
+// at a time; chunks of 8, 16), and keep the fastest of each.  The candidates
+// compute the same sums (up to the order of FP32 atomics), so the choice changes
+// speed only.  It runs before any graph capture, so captured solves replay the
+// chosen kernels.
+static hm_status autotune(hm_matrix h, int nrhs, int m, cudaStream_t s)
+{
+    if (nrhs < MRHS_MIN_RHS || h->tune.count(nrhs)) return HM_OK;
+    auto it1 = h->levels.find(1);
+    hm_matrix_s::Tune t;
+    if (it1 == h->levels.end() || it1->second.items.empty() || it1->second.n_small == 0) {
+        t.prod_rb = 0;
+        t.res_rb = 0;
+        h->tune[nrhs] = t;
+        return HM_OK;
+    }
+    const LevelList &L = it1->second;
+    hm_status st = ensure_workspace(h, nrhs, m);
+    if (st != HM_OK) return st;
+    float2 *x = (float2 *)h->ws.vec32[0], *z = (float2 *)h->ws.vec32[1];
+    HM_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * h->pN * nrhs, s));
+    cudaEvent_t e0, e1;
+    HM_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(HM_ERR_CUDA, "cudaEventCreate"); }
+    auto time_it = [&](auto &&launch, double &ms) -> hm_status {
+        launch();                                       // warm-up (also sets kernel attributes)
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch();
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "autotune");
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        ms = f / 3.0;
+        return HM_OK;
+    };
+    double best = 1e30;
+    const int prod_c[] = {0, 8, 16, 32};
+    for (int rb : prod_c) {
+        if (rb > 8 && rb / 2 >= nrhs) continue;         // a chunk of twice the RHS count or more only adds idle work
+        double ms = 0;
+        if ((st = time_it([&] { launch_apply_items(h, L, x, z, nrhs, false, s, rb); }, ms)) != HM_OK) break;
+        if (ms < best) { best = ms; t.prod_rb = rb; t.prod_ms = ms; }
+    }
+    const int nr = std::min(nrhs, std::max(1, h->ws.part_rhs));
+    best = 1e30;
+    const int res_c[] = {0, 8, 16};
+    for (int rb : res_c) {
+        if (st != HM_OK) break;
+        if (rb > 8 && rb / 2 >= nr) continue;
+        double ms = 0;
+        if ((st = time_it([&] { launch_apply_items_partials(h, L, x, h->ws.d_part, h->partial_elems, nr, s, rb); },
+                          ms)) != HM_OK)
+            break;
+        if (ms < best) { best = ms; t.res_rb = rb; t.res_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HM_OK) return st;
+    h->tune[nrhs] = t;
+    return HM_OK;
+}
+
+static void use_tuning(SolveCtx &c)
+{
+    auto tn = c.h->tune.find(c.nrhs);
+    if (tn != c.h->tune.end()) {
+        c.prod_rb = tn->second.prod_rb;
+        c.res_rb = tn->second.res_rb;
     }
 }
 
@@ -390,6 +468,10 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
     c.vbytes = es * h->pN * nrhs;
     hm_status st = ensure_workspace(h, nrhs, c.m);
     if (st != HM_OK) return st;
+    if (!c.fp64) {
+        if ((st = autotune(h, nrhs, c.m, s)) != HM_OK) return st;
+        use_tuning(c);
+    }
     const bool use_graph = o->graph && !info && !h->prof;
     hm_matrix_s::GraphKey key{b, x, ldb, ldx, nrhs, c.K, c.m, o->nested, o->refine, o->fp64};
     if (use_graph) {
@@ -737,6 +819,8 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
     c.vbytes = sizeof(float2) * h->pN * nrhs;
     hm_status st = ensure_workspace(h, nrhs, c.m);
     if (st != HM_OK) return st;
+    if ((st = autotune(h, nrhs, c.m, s)) != HM_OK) return st;
+    use_tuning(c);
     void *xt = h->ws.vec32[0], *yt = h->ws.vec32[1];
     launch_permute_in(x, ldx, xt, h->pN, h->d_pperm, nrhs, false, s);
     if (fp64_accumulate) {
@@ -766,6 +850,8 @@ hm_status hm_residual(hm_matrix h, const void *b, int64_t ldb, const void *x, in
     c.vbytes = sizeof(float2) * h->pN * nrhs;
     hm_status st = ensure_workspace(h, nrhs, c.m);
     if (st != HM_OK) return st;
+    if ((st = autotune(h, nrhs, c.m, s)) != HM_OK) return st;
+    use_tuning(c);
     void *bt = h->ws.vec32[0], *xt = h->ws.vec32[1], *rt = h->ws.vec32[3];
     launch_permute_in(b, ldb, bt, h->pN, h->d_pperm, nrhs, false, s);
     launch_permute_in(x, ldx, xt, h->pN, h->d_pperm, nrhs, false, s);
@@ -830,6 +916,18 @@ hm_status hm_profile_read(hm_matrix h, double *product_ms, int64_t *launches, in
     *product_ms = tot;
     *launches = h->prof_launches;
     *bytes = h->prof_bytes;
+    return HM_OK;
+}
+
+hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double *prod_ms, double *res_ms)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    auto it = h->tune.find(nrhs);
+    if (it == h->tune.end()) return fail(HM_ERR_STATE, "no tuned kernel choice for this right-hand-side count");
+    if (prod_rb) *prod_rb = it->second.prod_rb;
+    if (res_rb) *res_rb = it->second.res_rb;
+    if (prod_ms) *prod_ms = it->second.prod_ms;
+    if (res_ms) *res_ms = it->second.res_ms;
     return HM_OK;
 }
 

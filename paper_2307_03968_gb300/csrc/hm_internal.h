@@ -149,6 +149,10 @@ struct hm_matrix_s {
     std::map<GraphKey, cudaGraphExec_t> graphs;
     cudaStream_t cap_stream = nullptr;
 
+    // kernel choices measured on this operator per right-hand-side count (hm_api.cu autotune)
+    struct Tune { int prod_rb = -1, res_rb = -1; double prod_ms = 0.0, res_ms = 0.0; };
+    std::map<int, Tune> tune;
+
     // opt-in event timing of the product kernel
     bool prof = false;
     std::vector<cudaEvent_t> prof_ev;     // pairs (start, end)
@@ -176,11 +180,13 @@ void launch_permute_out(const void *xt, int64_t pN, void *x, int64_t ldx, const 
                         int nrhs, bool fp64, cudaStream_t s);
 void launch_zero(void *p, size_t bytes, cudaStream_t s);
 // z (+)= M_level x  for one item list; z must be pre-zeroed by the caller
+// rb: -1 = default choice by nrhs, 0 = one right-hand side at a time for every block,
+// 8 / 16 / 32 = shared-memory multi-RHS kernel with that chunk for the blocks it takes
 void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
-                        cudaStream_t s);
+                        cudaStream_t s, int rb = -1);
 // FP64 products of every block of a level into its partial slots (no atomics)
 void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride,
-                                 int nrhs, cudaStream_t s);
+                                 int nrhs, cudaStream_t s, int rb = -1);
 // per leaf: acc = D x + sum of the leaf's partial slots of levels 1..m (FP64, fixed order);
 // out = b - acc (+ norms) when b is given, else out = acc (rounded to complex64)
 void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const double2 *part, int64_t pstride,
@@ -228,6 +234,6 @@ void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, f
                              cudaStream_t s);
 // the FP64-class partial-slot products of the small items for many right-hand sides (k_mrhs.cu)
 void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, double2 *part,
-                                      int64_t pstride, int nrhs, cudaStream_t s);
+                                      int64_t pstride, int nrhs, cudaStream_t s, int rb = -1);
 
 } // namespace hm

@@ -129,6 +129,112 @@ __device__ __forceinline__ void mm_cols(const float2 *S, int sld, int R, int C, 
     }
 }
 
+// Wider tiles for the FP32 product: 64 threads per product (tid in [0, 64)), each
+// owning 4 rows (or columns) x RB/4 right-hand sides.  Operands are addressed as
+// 32-bit offsets into the kernel's shared array (so that every access is a
+// shared-space load with an immediate offset), and the RHS panels have an even
+// row stride so that a thread's right-hand sides load as 128-bit pairs.
+extern __shared__ __align__(16) float2 smf2[];
+
+template <int RB>
+__device__ __forceinline__ void ld_x(int xi, float2 (&xv)[RB / 4])
+{
+#pragma unroll
+    for (int q = 0; q < RB / 4; q += 2) {
+        const float4 v = *reinterpret_cast<const float4 *>(&smf2[xi + q]);
+        xv[q] = make_float2(v.x, v.y);
+        xv[q + 1] = make_float2(v.z, v.w);
+    }
+}
+
+// Y[r][q] (yo >= 0: shared offset of Y, row stride xld) or z (yo < 0) = sum_c S[r][c] X[c][q], rows r < R
+template <int RB>
+__device__ __forceinline__ void mm4_rows(int tid, int so, int sld, int R, int C, int xo, int xld, int yo, float2 *z,
+                                         int64_t ldz, int base, int nr)
+{
+    constexpr int TQ = RB / 4;
+    const int q0 = (tid & 3) * TQ, r = 4 * (tid >> 2);
+    if (r >= R) return;
+    float2 a[4][TQ];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TQ; ++q) a[i][q] = make_float2(0.f, 0.f);
+    int si[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) si[i] = so + (r + i < R ? r + i : R - 1) * sld;
+    int xi = xo + q0;
+#pragma unroll 2
+    for (int c = 0; c < C; ++c, xi += xld) {
+        float2 xv[TQ];
+        ld_x<RB>(xi, xv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 b = smf2[si[i] + c];
+#pragma unroll
+            for (int q = 0; q < TQ; ++q) cma(a[i][q], b, xv[q]);
+        }
+    }
+    if (yo < 0) {
+#pragma unroll
+        for (int q = 0; q < TQ; ++q) {
+            if (q0 + q >= nr) break;
+            float2 *zz = z + (int64_t)(q0 + q) * ldz + base + r;
+#pragma unroll
+            for (int i = 0; i < 4; i += 2) {
+                if (r + i + 1 < R) red2(zz + i, a[i][q], a[i + 1][q]);
+                else if (r + i < R) red1(zz + i, a[i][q]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (r + i < R)
+#pragma unroll
+                for (int q = 0; q < TQ; ++q) smf2[yo + (r + i) * xld + q0 + q] = a[i][q];
+    }
+}
+
+// z[q*ldz + base + c] += sum_r S[r][c] X[r][q], columns c < C, rows r < R
+template <int RB>
+__device__ __forceinline__ void mm4_cols(int tid, int so, int sld, int R, int C, int xo, int xld, float2 *z,
+                                         int64_t ldz, int base, int nr)
+{
+    constexpr int TQ = RB / 4;
+    const int q0 = (tid & 3) * TQ, c = 4 * (tid >> 2);
+    if (c >= C) return;
+    float2 a[4][TQ];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TQ; ++q) a[i][q] = make_float2(0.f, 0.f);
+    int cc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cc[i] = so + (c + i < C ? c + i : C - 1);
+    int xi = xo + q0, srow = 0;
+#pragma unroll 2
+    for (int r = 0; r < R; ++r, xi += xld, srow += sld) {
+        float2 xv[TQ];
+        ld_x<RB>(xi, xv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 b = smf2[cc[i] + srow];
+#pragma unroll
+            for (int q = 0; q < TQ; ++q) cma(a[i][q], b, xv[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < TQ; ++q) {
+        if (q0 + q >= nr) break;
+        float2 *zz = z + (int64_t)(q0 + q) * ldz + base + c;
+#pragma unroll
+        for (int i = 0; i < 4; i += 2) {
+            if (c + i + 1 < C) red2(zz + i, a[i][q], a[i + 1][q]);
+            else if (c + i < C) red1(zz + i, a[i][q]);
+        }
+    }
+}
+
 // rows x cols complex matrix (row stride ld in global memory) -> S (row stride sld);
 // warp w copies rows w, w+4, ..., lanes the columns
 __device__ __forceinline__ void stage(const float2 *__restrict__ g, int rows, int cols, int ld, float2 *S, int sld)
@@ -156,61 +262,36 @@ __global__ void __launch_bounds__(MT)
 k_apply_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *__restrict__ pool,
              const float2 *__restrict__ x, int64_t ldx, float2 *__restrict__ z, int64_t ldz, int nr, Geom gm)
 {
-    extern __shared__ __align__(16) float2 sm[];
-    float2 *S = sm;                                   // srows x sld: the block, or U^T then V
-    float2 *SV = S + gm.kmax * gm.sld;
-    float2 *XI = S + gm.srows * gm.sld;               // dim x xld
-    float2 *XJ = XI + gm.dim * gm.xld;                // dim x xld
-    float2 *T = XJ + gm.dim * gm.xld;                 // kmax x xld : V X_J
-    float2 *TP = T + gm.kmax * gm.xld;                // kmax x xld : U^T X_I
+    // shared offsets (complex elements): the block, or U^T then V; the RHS panels; V X_J and U^T X_I
+    const int oS = 0, oSV = gm.kmax * gm.sld, oXI = gm.srows * gm.sld, oXJ = oXI + gm.dim * gm.xld;
+    const int oT = oXJ + gm.dim * gm.xld, oTP = oT + gm.kmax * gm.xld;
+    const int tid = threadIdx.x & 63;
+    const bool lo = threadIdx.x < 64;
     for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
         const Item it = items[b];
         __syncthreads();                              // the previous item is done with shared memory
-        stage_x<RB>(x, ldx, it.row0, it.m, nr, XI, gm.xld);
-        stage_x<RB>(x, ldx, it.col0, it.n, nr, XJ, gm.xld);
+        stage_x<RB>(x, ldx, it.row0, it.m, nr, smf2 + oXI, gm.xld);
+        stage_x<RB>(x, ldx, it.col0, it.n, nr, smf2 + oXJ, gm.xld);
         if (it.k == 0) {
-            stage(pool + it.off, it.m, it.n, (int)even(it.n), S, gm.sld);
+            stage(pool + it.off, it.m, it.n, (int)even(it.n), smf2 + oS, gm.sld);
             cp_async_wait_all();
             __syncthreads();
-            mm_rows<RB>(S, gm.sld, it.m, it.n, XJ, gm.xld, nullptr, z, ldz, it.row0, nr);   // Z_I += B X_J
-            mm_cols<RB>(S, gm.sld, it.m, it.n, XI, gm.xld, z, ldz, it.col0, nr);            // Z_J += B^T X_I
+            // the two mirrored products run side by side on the two halves of the CTA
+            if (lo) mm4_rows<RB>(tid, oS, gm.sld, it.m, it.n, oXJ, gm.xld, -1, z, ldz, it.row0, nr);   // Z_I += B X_J
+            else mm4_cols<RB>(tid, oS, gm.sld, it.m, it.n, oXI, gm.xld, z, ldz, it.col0, nr);         // Z_J += B^T X_I
         } else {
             const float2 *UT = pool + it.off;
             const float2 *V = UT + (int64_t)it.k * it.m;
-            stage(UT, it.k, it.m, it.m, S, gm.sld);
-            stage(V, it.k, it.n, it.n, SV, gm.sld);
+            stage(UT, it.k, it.m, it.m, smf2 + oS, gm.sld);
+            stage(V, it.k, it.n, it.n, smf2 + oSV, gm.sld);
             cp_async_wait_all();
             __syncthreads();
-            mm_rows<RB>(SV, gm.sld, it.k, it.n, XJ, gm.xld, T, nullptr, 0, 0, nr);          // T  = V X_J
-            mm_rows<RB>(S, gm.sld, it.k, it.m, XI, gm.xld, TP, nullptr, 0, 0, nr);          // T' = U^T X_I
+            if (lo) mm4_rows<RB>(tid, oSV, gm.sld, it.k, it.n, oXJ, gm.xld, oT, nullptr, 0, 0, nr);    // T  = V X_J
+            else mm4_rows<RB>(tid, oS, gm.sld, it.k, it.m, oXI, gm.xld, oTP, nullptr, 0, 0, nr);      // T' = U^T X_I
             __syncthreads();
-            mm_cols<RB>(S, gm.sld, it.k, it.m, T, gm.xld, z, ldz, it.row0, nr);             // Z_I += U T
-            mm_cols<RB>(SV, gm.sld, it.k, it.n, TP, gm.xld, z, ldz, it.col0, nr);           // Z_J += V^T T'
+            if (lo) mm4_cols<RB>(tid, oS, gm.sld, it.k, it.m, oT, gm.xld, z, ldz, it.row0, nr);        // Z_I += U T
+            else mm4_cols<RB>(tid, oSV, gm.sld, it.k, it.n, oTP, gm.xld, z, ldz, it.col0, nr);        // Z_J += V^T T'
         }
-    }
-}
-
-Geom level_geom(const LevelList &L, int rb, size_t t_elem, size_t &bytes);
-
-template <int RB>
-void launch_rb(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
-{
-    size_t sm = 0;
-    const Geom gm = level_geom(L, RB, sizeof(float2), sm);
-    static size_t attr = 0;                            // largest dynamic size enabled so far
-    if (sm > attr) {
-        cudaFuncSetAttribute(k_apply_mrhs<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = sm;
-    }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_mrhs<RB>, MT, sm);
-    if (per_sm < 1) per_sm = 1;
-    int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
-    if (g > L.n_small) g = L.n_small;
-    for (int r0 = 0; r0 < nrhs; r0 += RB) {
-        const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
-        k_apply_mrhs<RB><<<(unsigned)g, MT, sm, s>>>(L.d_small, L.n_small, h->d_pool32, x + (int64_t)r0 * h->pN,
-                                                     h->pN, z + (int64_t)r0 * h->pN, h->pN, nr, gm);
     }
 }
 
@@ -317,8 +398,7 @@ k_residual_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *_
                 Geom gm)
 {
     using dot2::cdf;
-    extern __shared__ __align__(16) float2 sm[];
-    float2 *S = sm;
+    float2 *S = smf2;
     float2 *SV = S + gm.kmax * gm.sld;
     float2 *XI = S + gm.srows * gm.sld;
     float2 *XJ = XI + gm.dim * gm.xld;
@@ -353,14 +433,15 @@ k_residual_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *_
     }
 }
 
-Geom level_geom(const LevelList &L, int rb, size_t t_elem, size_t &bytes)
+Geom level_geom(const LevelList &L, int xld, size_t t_elem, size_t &bytes)
 {
     Geom gm;
     gm.dim = L.small_dim;                              // even, <= MRHS_MAX_DIM
     gm.sld = gm.dim + 1;
-    gm.xld = rb + 1;
+    gm.xld = xld;
     gm.kmax = L.small_rank;
     gm.srows = std::max(gm.dim, 2 * gm.kmax) + 1;     // one spare row: a thread's second row may be read past the end
+    if ((gm.srows * gm.sld) & 1) ++gm.srows;           // keep the RHS panels that follow 16-byte aligned
     bytes = sizeof(float2) * ((size_t)gm.srows * gm.sld + 2 * (size_t)gm.dim * gm.xld) +
             t_elem * 2 * (size_t)std::max(gm.kmax, 1) * gm.xld;
     return gm;
@@ -371,7 +452,7 @@ void launch_resid_rb(hm_matrix h, const LevelList &L, const float2 *x, double2 *
                      cudaStream_t s)
 {
     size_t sm = 0;
-    const Geom gm = level_geom(L, RB, sizeof(dot2::cdf), sm);
+    const Geom gm = level_geom(L, RB + 1, sizeof(dot2::cdf), sm);
     static size_t attr = 0;
     if (sm > attr) {
         cudaFuncSetAttribute(k_residual_mrhs<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -386,6 +467,28 @@ void launch_resid_rb(hm_matrix h, const LevelList &L, const float2 *x, double2 *
         const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
         k_residual_mrhs<RB><<<(unsigned)g, MT, sm, s>>>(L.d_small, L.n_small, h->d_pool32, x + (int64_t)r0 * h->pN,
                                                         h->pN, part + (int64_t)r0 * pstride, pstride, nr, gm);
+    }
+}
+
+template <int RB>
+void launch_rb(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
+{
+    size_t sm = 0;
+    const Geom gm = level_geom(L, RB + 2, sizeof(float2), sm);   // even panel stride: 16-byte aligned rows
+    static size_t attr = 0;                                      // largest dynamic size enabled so far
+    if (sm > attr) {
+        cudaFuncSetAttribute(k_apply_mrhs<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = sm;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_mrhs<RB>, MT, sm);
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
+    if (g > L.n_small) g = L.n_small;
+    for (int r0 = 0; r0 < nrhs; r0 += RB) {
+        const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
+        k_apply_mrhs<RB><<<(unsigned)g, MT, sm, s>>>(L.d_small, L.n_small, h->d_pool32, x + (int64_t)r0 * h->pN,
+                                                     h->pN, z + (int64_t)r0 * h->pN, h->pN, nr, gm);
     }
 }
 
@@ -405,10 +508,11 @@ void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, f
 namespace hm {
 
 void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, double2 *part,
-                                      int64_t pstride, int nrhs, cudaStream_t s)
+                                      int64_t pstride, int nrhs, cudaStream_t s, int rb)
 {
     if (L.n_small == 0 || nrhs <= 0) return;
-    if (nrhs <= 8) launch_resid_rb<8>(h, L, x, part, pstride, nrhs, s);
+    if (rb < 0) rb = nrhs <= 8 ? 8 : 16;
+    if (rb <= 8) launch_resid_rb<8>(h, L, x, part, pstride, nrhs, s);
     else launch_resid_rb<16>(h, L, x, part, pstride, nrhs, s);
 }
 

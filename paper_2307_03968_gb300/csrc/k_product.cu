@@ -241,7 +241,7 @@ int apply_grid(hm_matrix h)
 } // namespace
 
 void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
-                        cudaStream_t s)
+                        cudaStream_t s, int rb)
 {
     const int64_t n = (int64_t)L.items.size();
     if (n == 0) return;
@@ -253,9 +253,9 @@ void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z,
     } else {
         const Item *list = L.d_items;
         int64_t cnt = n;
-        if (nrhs >= MRHS_MIN_RHS && L.n_small > 0) {
+        if (rb < 0) rb = nrhs < MRHS_MIN_RHS ? 0 : nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : 32;
+        if (rb > 0 && nrhs > 1 && L.n_small > 0) {
             // many right-hand sides: blocks that fit shared memory are read once per RHS chunk
-            const int rb = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : 32;
             launch_apply_items_mrhs(h, L, (const float2 *)x, (float2 *)z, nrhs, rb, s);
             list = L.d_big;
             cnt = L.n_big;

@@ -281,13 +281,14 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
 } // namespace
 
 void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride,
-                                 int nrhs, cudaStream_t s)
+                                 int nrhs, cudaStream_t s, int rb)
 {
     const Item *list = L.d_items;
     int64_t n = (int64_t)L.items.size();
-    if (nrhs >= MRHS_MIN_RHS && L.n_small > 0) {
+    if (rb < 0) rb = nrhs < MRHS_MIN_RHS ? 0 : nrhs <= 8 ? 8 : 16;
+    if (rb > 0 && nrhs > 1 && L.n_small > 0) {
         // many right-hand sides: blocks that fit shared memory are read once per chunk
-        launch_apply_items_partials_mrhs(h, L, x, part, pstride, nrhs, s);
+        launch_apply_items_partials_mrhs(h, L, x, part, pstride, nrhs, s, rb);
         list = L.d_big;
         n = L.n_big;
     }

@@ -98,3 +98,24 @@ def test_many_rhs_residual_equals_column_residuals(torch_cuda, operators, name, 
         assert np.abs(got[r] - ref).max() <= 1e-6 * np.abs(ref).max(), r
         assert rr[r] == pytest.approx(rr1[0], rel=1e-9)
         assert bb[r] == pytest.approx(bb1[0], rel=1e-12)
+
+
+def test_autotuner_records_a_choice(torch_cuda, operators):
+    from paper_2307_03968_gb300.hm import HmError, HM_ERR_STATE
+    A = operators["swg_slab"]
+    N = A.n
+    rng = np.random.default_rng(7)
+    x = (rng.normal(size=(24, N)) + 1j * rng.normal(size=(24, N))).astype(np.complex64)
+    xt = torch_cuda.from_numpy(x).cuda()
+    yt = torch_cuda.empty_like(xt)
+    A.apply(xt, yt, n_levels=-1, fp64_accumulate=False)      # first call with 24 RHS: tunes
+    prod_rb, res_rb, prod_ms, res_ms = A.tuning(24)
+    assert prod_rb in (0, 8, 16, 32) and res_rb in (0, 8, 16)
+    assert prod_ms > 0 and res_ms > 0
+    again = torch_cuda.empty_like(xt)
+    A.apply(xt, again, n_levels=-1, fp64_accumulate=False)   # tuned choice is kept
+    assert A.tuning(24) == (prod_rb, res_rb, prod_ms, res_ms)
+    assert np.allclose(again.cpu().numpy(), yt.cpu().numpy(), rtol=1e-5, atol=1e-6 * np.abs(yt.cpu().numpy()).max())
+    with pytest.raises(HmError) as e:
+        A.tuning(3)                                           # below the many-RHS threshold: nothing to tune
+    assert e.value.status == HM_ERR_STATE
