@@ -40,6 +40,10 @@ WORKLOADS = {
     "sphere2_sweep181": dict(name="sefie_pec_sphere_r2lambda_30720rwg_sweep181", kind="rwg", subdivisions=5, radius=2.0,
                              leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True,
                              nrhs=181, sweep=True, unknowns=30720, triangles=20480),
+    # continuous-batching serving stream over a catalog of PEC and dielectric operators
+    "serving": dict(name="serving_stream_pec_and_dielectric_catalog", kind="serving", n_requests=2000, seed=5,
+                    loads=(0.5, 0.8, 1.0), max_rhs=32, n_slots=4, hbm_budget_gb=64, max_batch_rhs=64,
+                    n_terms=2, n_levels=1, refine=True, nrhs=0, unknowns=0),
     # a smaller sphere of the same family (7,680 unknowns), for profiler captures
     "sphere1": dict(name="sefie_pec_sphere_r1lambda_7680rwg", kind="rwg", subdivisions=4, radius=1.0, leaf_size=64,
                     arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=7680,
@@ -266,6 +270,17 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     w = WORKLOAD
+    if w["kind"] == "serving":
+        if a.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the oracle has no serving path; "
+                                  "its solve rate is the --impl reference line of the other workloads"}))
+            return
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(local)
+            serving_main(a, w)
+        return
     config = workload_config(w)
 
     if a.impl == "reference":
@@ -439,6 +454,130 @@ def main():
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- serving -------
+def serving_catalog(seed):
+    """Seeded catalog of scatterers, meshed at about a tenth of a wavelength (PEC
+    surfaces, RWG) or a fifteenth (dielectric volumes, SWG).  Returns a list of
+    dicts (name, xyz, cells, eps_r or None, tree options)."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(seed)
+    rwg = dict(leaf_size=64, arity=8, adm=2.0)
+    swg = dict(leaf_size=64, arity=2, adm=1.0)
+    cat = []
+    for s_ in (3, 4, 5):                                    # spheres: edge ~ radius / (1.1 * 2^s)
+        r = 1.1 * 2 ** s_ / 10.0 * rng.uniform(0.8, 1.0)
+        xyz, tri = synth.icosphere(s_, r)
+        cat.append(dict(name="pec_sphere_r%.2f" % r, xyz=xyz, cells=tri, eps_r=None, opts=rwg))
+    for _ in range(3):                                      # cubes
+        a = rng.uniform(0.5, 3.0)
+        n = int(np.ceil(10 * a))
+        xyz, tri = synth.box_surface((a, a, a), (n, n, n))
+        cat.append(dict(name="pec_cube_a%.2f" % a, xyz=xyz, cells=tri, eps_r=None, opts=rwg))
+    for _ in range(3):                                      # closed cylinders
+        r, h = rng.uniform(0.25, 1.0), rng.uniform(0.5, 3.0)
+        xyz, tri = synth.closed_cylinder(r, h, int(np.ceil(2 * np.pi * r * 10)), int(np.ceil(10 * h)),
+                                         int(np.ceil(10 * r)))
+        cat.append(dict(name="pec_cylinder_r%.2f_h%.2f" % (r, h), xyz=xyz, cells=tri, eps_r=None, opts=rwg))
+    for n in (8, 10, 12):                                   # inhomogeneous dielectric cubes, side n / 15
+        xyz, tet = synth.cube_tets(n, n / 15.0)
+        eps = synth.random_permittivity(len(tet), 2.0, 6.0, seed=seed + n)
+        cat.append(dict(name="dielectric_cube_%dvox" % n, xyz=xyz, cells=tet, eps_r=eps, opts=swg))
+    return cat
+
+
+def serving_main(a, w):
+    """Serving stream (config-5 shape) through the continuous-batching server
+    (hm_server_*, the library's public serving API): requests of 1..max_rhs
+    right-hand sides on operators drawn uniformly from the catalog, host buffers
+    in and out.  Phases: cold start (one request per operator: build + factor +
+    first solve), saturation (all requests queued at once), then Poisson arrivals
+    at the configured fractions of the saturation throughput.  Latency = submit to
+    completion as measured by the server."""
+    import threading
+    import numpy as np
+    from paper_2307_03968_gb300.hm import Server
+    rng = np.random.default_rng(w["seed"])
+    cat = serving_catalog(w["seed"])
+    srv = Server(n_slots=w["n_slots"], hbm_budget_bytes=int(w["hbm_budget_gb"] * 2 ** 30),
+                 max_batch_rhs=w["max_batch_rhs"])
+    ops = []
+    for g in cat:
+        op, n = srv.add_mesh(g["xyz"], g["cells"], eps_r=g["eps_r"], aca_tol=1e-4, levels=-1, n_terms=w["n_terms"],
+                             n_levels=w["n_levels"], nested=True, refine=w["refine"], **g["opts"])
+        pool = (rng.normal(size=(w["max_rhs"], n)) + 1j * rng.normal(size=(w["max_rhs"], n))).astype(np.complex64)
+        ops.append(dict(op=op, n=n, name=g["name"], pool=pool))
+    # cold start: one request per operator, sequentially
+    cold = []
+    for o in ops:
+        x, lat = srv.wait(srv.submit(o["op"], o["pool"][:8]))
+        cold.append(lat)
+
+    def draw(k):
+        return [(int(rng.integers(len(ops))), int(rng.integers(1, w["max_rhs"] + 1))) for _ in range(k)]
+
+    def run(reqs, rate=None):
+        """Submit (op, R) requests (all at once if rate is None, else Poisson at
+        `rate` requests/s); returns (rhs/s, latencies ms, wall s)."""
+        lats = [None] * len(reqs)
+        ids = [None] * len(reqs)
+        ready = threading.Semaphore(0)
+
+        def waiter():
+            for i in range(len(reqs)):
+                ready.acquire()
+                lats[i] = srv.wait(ids[i])[1]
+        th = threading.Thread(target=waiter)
+        th.start()
+        gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+        t0 = time.perf_counter()
+        t_next = t0
+        for i, (k, r) in enumerate(reqs):
+            t_next += gaps[i]
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids[i] = srv.submit(ops[k]["op"], ops[k]["pool"][:r])
+            ready.release()
+        th.join()
+        wall = time.perf_counter() - t0
+        return sum(r for _, r in reqs) / wall, lats, wall
+
+    n_req = w["n_requests"]
+    sat, _, _ = run(draw(max(200, n_req // 4)))
+    mean_r = (w["max_rhs"] + 1) / 2.0
+    loads = []
+    for f in w["loads"]:
+        reqs = draw(n_req)
+        thr, lats, wall = run(reqs, rate=f * sat / mean_r)
+        lats = np.sort(np.array(lats))
+        loads.append({"offered": f, "offered_rhs_s": f * sat, "achieved_rhs_s": thr, "requests": len(reqs),
+                      "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+                      "wall_s": wall})
+    info = srv.info()
+    srv.close()
+    main = loads[-1]
+    mid = min(loads, key=lambda d: abs(d["offered"] - 0.8))
+    line = {"metric": METRIC, "value": main["achieved_rhs_s"], "unit": "RHS/s", "n_gpus": 1,
+            "steps": sum(d["requests"] for d in loads), "warmup": len(ops), "ms_per_step": None,
+            "p50_ms": mid["p50_ms"], "p99_ms": mid["p99_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": w["name"], "operators": [dict(name=o["name"], unknowns=o["n"]) for o in ops],
+                       "requests_per_load": n_req, "rhs_per_request": "uniform 1..%d" % w["max_rhs"],
+                       "arrivals": "Poisson, seed %d" % w["seed"], "solve": "leaf level, K=2, one refinement",
+                       "slots": w["n_slots"], "hbm_budget_gb": w["hbm_budget_gb"],
+                       "max_batch_rhs": w["max_batch_rhs"], "parallelism": "replicas"},
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": main["achieved_rhs_s"], "unit": "RHS/s",
+                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                    "note": "every serving request is end to end: host b in, host x out"},
+            "serving": {"saturation_rhs_s": sat, "loads": loads,
+                        "cold_ms": {"p50": float(np.percentile(cold, 50)), "max": float(np.max(cold))},
+                        "batches": info.batches, "solved_rhs": info.solved_rhs, "builds": info.builds,
+                        "evictions": info.evictions, "peak_resident_gb": info.peak_resident_bytes / 2 ** 30}}
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":

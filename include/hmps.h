@@ -334,10 +334,11 @@ hm_status hm_get_info(hm_matrix h, hm_info *info);
 /*
  * Kernel choice of the built-in autotuner for `nrhs` right-hand sides (no
  * counterpart in the paper: it concerns how this GPU implementation batches the
- * block products of eqs. 6 and 8).  The first complex64 solve, product or
- * residual with nrhs >= 4 right-hand sides on an operator times the candidate
- * kernels on that operator (with CUDA events on the caller's stream, which it
- * synchronises once) and keeps the fastest: for the product and for the
+ * block products of eqs. 6 and 8).  Right-hand-side counts share a choice per
+ * bucket (the next power of two >= nrhs, at least 4).  The first complex64
+ * solve, product or residual in a bucket on an operator times the candidate
+ * kernels on that operator at the bucket's size (with CUDA events on the
+ * caller's stream, which it synchronises once) and keeps the fastest: for the product and for the
  * FP64-class residual products, 0 = one right-hand side at a time, 8 / 16 / 32 =
  * blocks staged once in shared memory per chunk of that many right-hand sides.
  * prod_ms / res_ms: the measured time of one leaf-level launch of the choice.

@@ -218,6 +218,7 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
     ws.vec32.clear(); ws.vec64.clear(); ws.d_acc64 = nullptr; ws.d_part = nullptr;
     const int r = std::max(nrhs, ws.nrhs);
     const size_t n32 = sizeof(float2) * h->pN * r, n64 = sizeof(double2) * h->pN * r;
+    ws.dev_bytes = (int64_t)(need_vecs * (n32 + (h->has_fp64 ? n64 : 0)) + 2 * sizeof(double) * r);
     for (size_t i = 0; i < need_vecs; ++i) {
         void *p = nullptr;
         HM_CUDA(cudaMalloc(&p, n32));
@@ -230,9 +231,20 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
         }
     }
     HM_CUDA(cudaMalloc((void **)&ws.d_acc64, 2 * sizeof(double) * r));
-    ws.part_rhs = std::min(r, RESID_CHUNK);
-    HM_CUDA(cudaMalloc((void **)&ws.d_part, sizeof(double2) * std::max<int64_t>(h->partial_elems, 1) * ws.part_rhs));
+    ws.part_rhs = std::min(r, RESID_CHUNK);   // the partial slots themselves: ensure_partials
     ws.nrhs = r;
+    return HM_OK;
+}
+
+// FP64 partial slots of the residual products (ws.part_rhs right-hand sides at a
+// time); allocated only by the calls that form a residual, before any capture
+static hm_status ensure_partials(hm_matrix h)
+{
+    hm::Workspace &ws = h->ws;
+    if (ws.d_part) return HM_OK;
+    const size_t bytes = sizeof(double2) * std::max<int64_t>(h->partial_elems, 1) * std::max(ws.part_rhs, 1);
+    HM_CUDA(cudaMalloc((void **)&ws.d_part, bytes));
+    ws.dev_bytes += (int64_t)bytes;
     return HM_OK;
 }
 
@@ -371,9 +383,20 @@ static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *
 // compute the same sums (up to the order of FP32 atomics), so the choice changes
 // speed only.  It runs before any graph capture, so captured solves replay the
 // chosen kernels.
-static hm_status autotune(hm_matrix h, int nrhs, int m, cudaStream_t s)
+// right-hand-side counts share a kernel choice per power-of-two bucket
+static int tune_bucket(int nrhs)
 {
-    if (nrhs < MRHS_MIN_RHS || h->tune.count(nrhs)) return HM_OK;
+    int b = MRHS_MIN_RHS;
+    while (b < nrhs) b <<= 1;
+    return b;
+}
+
+static hm_status autotune(hm_matrix h, int nrhs_req, int m, cudaStream_t s, bool residual)
+{
+    if (nrhs_req < MRHS_MIN_RHS) return HM_OK;
+    const int nrhs = tune_bucket(nrhs_req);              // timed at the bucket's size
+    auto have = h->tune.find(nrhs);
+    if (have != h->tune.end() && (!residual || have->second.res_rb >= 0)) return HM_OK;
     auto it1 = h->levels.find(1);
     hm_matrix_s::Tune t;
     if (it1 == h->levels.end() || it1->second.items.empty() || it1->second.n_small == 0) {
@@ -382,9 +405,12 @@ static hm_status autotune(hm_matrix h, int nrhs, int m, cudaStream_t s)
         h->tune[nrhs] = t;
         return HM_OK;
     }
+    const bool do_prod = have == h->tune.end();
+    if (!do_prod) t = have->second;
     const LevelList &L = it1->second;
     hm_status st = ensure_workspace(h, nrhs, m);
     if (st != HM_OK) return st;
+    if (residual && (st = ensure_partials(h)) != HM_OK) return st;
     float2 *x = (float2 *)h->ws.vec32[0], *z = (float2 *)h->ws.vec32[1];
     HM_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * h->pN * nrhs, s));
     cudaEvent_t e0, e1;
@@ -406,6 +432,7 @@ static hm_status autotune(hm_matrix h, int nrhs, int m, cudaStream_t s)
     double best = 1e30;
     const int prod_c[] = {0, 8, 16, 32};
     for (int rb : prod_c) {
+        if (!do_prod) break;
         if (rb > 8 && rb / 2 >= nrhs) continue;         // a chunk of twice the RHS count or more only adds idle work
         double ms = 0;
         if ((st = time_it([&] { launch_apply_items(h, L, x, z, nrhs, false, s, rb); }, ms)) != HM_OK) break;
@@ -415,7 +442,7 @@ static hm_status autotune(hm_matrix h, int nrhs, int m, cudaStream_t s)
     best = 1e30;
     const int res_c[] = {0, 8, 16};
     for (int rb : res_c) {
-        if (st != HM_OK) break;
+        if (st != HM_OK || !residual) break;
         if (rb > 8 && rb / 2 >= nr) continue;
         double ms = 0;
         if ((st = time_it([&] { launch_apply_items_partials(h, L, x, h->ws.d_part, h->partial_elems, nr, s, rb); },
@@ -432,7 +459,8 @@ static hm_status autotune(hm_matrix h, int nrhs, int m, cudaStream_t s)
 
 static void use_tuning(SolveCtx &c)
 {
-    auto tn = c.h->tune.find(c.nrhs);
+    if (c.nrhs < MRHS_MIN_RHS) return;
+    auto tn = c.h->tune.find(tune_bucket(c.nrhs));
     if (tn != c.h->tune.end()) {
         c.prod_rb = tn->second.prod_rb;
         c.res_rb = tn->second.res_rb;
@@ -468,8 +496,10 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
     c.vbytes = es * h->pN * nrhs;
     hm_status st = ensure_workspace(h, nrhs, c.m);
     if (st != HM_OK) return st;
+    const bool resid = !o->fp64 && (o->refine || info);
+    if (resid && (st = ensure_partials(h)) != HM_OK) return st;
     if (!c.fp64) {
-        if ((st = autotune(h, nrhs, c.m, s)) != HM_OK) return st;
+        if ((st = autotune(h, nrhs, c.m, s, resid)) != HM_OK) return st;
         use_tuning(c);
     }
     const bool use_graph = o->graph && !info && !h->prof;
@@ -819,7 +849,8 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
     c.vbytes = sizeof(float2) * h->pN * nrhs;
     hm_status st = ensure_workspace(h, nrhs, c.m);
     if (st != HM_OK) return st;
-    if ((st = autotune(h, nrhs, c.m, s)) != HM_OK) return st;
+    if (fp64_accumulate && (st = ensure_partials(h)) != HM_OK) return st;
+    if ((st = autotune(h, nrhs, c.m, s, fp64_accumulate != 0)) != HM_OK) return st;
     use_tuning(c);
     void *xt = h->ws.vec32[0], *yt = h->ws.vec32[1];
     launch_permute_in(x, ldx, xt, h->pN, h->d_pperm, nrhs, false, s);
@@ -850,7 +881,8 @@ hm_status hm_residual(hm_matrix h, const void *b, int64_t ldb, const void *x, in
     c.vbytes = sizeof(float2) * h->pN * nrhs;
     hm_status st = ensure_workspace(h, nrhs, c.m);
     if (st != HM_OK) return st;
-    if ((st = autotune(h, nrhs, c.m, s)) != HM_OK) return st;
+    if ((st = ensure_partials(h)) != HM_OK) return st;
+    if ((st = autotune(h, nrhs, c.m, s, true)) != HM_OK) return st;
     use_tuning(c);
     void *bt = h->ws.vec32[0], *xt = h->ws.vec32[1], *rt = h->ws.vec32[3];
     launch_permute_in(b, ldb, bt, h->pN, h->d_pperm, nrhs, false, s);
@@ -922,7 +954,7 @@ hm_status hm_profile_read(hm_matrix h, double *product_ms, int64_t *launches, in
 hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double *prod_ms, double *res_ms)
 {
     if (!h) return fail(HM_ERR_ARG, "null handle");
-    auto it = h->tune.find(nrhs);
+    auto it = nrhs < MRHS_MIN_RHS ? h->tune.end() : h->tune.find(tune_bucket(nrhs));
     if (it == h->tune.end()) return fail(HM_ERR_STATE, "no tuned kernel choice for this right-hand-side count");
     if (prod_rb) *prod_rb = it->second.prod_rb;
     if (res_rb) *res_rb = it->second.res_rb;
@@ -960,7 +992,7 @@ hm_status hm_get_info(hm_matrix h, hm_info *info)
     info->max_rank = h->max_rank;
     info->factored = h->factored;
     info->has_fp64 = h->has_fp64 ? 1 : 0;
-    info->device_bytes = h->device_bytes;
+    info->device_bytes = h->device_bytes + h->ws.dev_bytes + (int64_t)h->ws.d_io_bytes;
     return HM_OK;
 }
 

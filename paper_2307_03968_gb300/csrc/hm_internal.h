@@ -76,6 +76,7 @@ struct Workspace {
     size_t h_pinned_bytes = 0;
     void *d_io = nullptr;         // device b / x for host-buffer solves
     size_t d_io_bytes = 0;
+    int64_t dev_bytes = 0;        // device bytes held by the vectors, norms and partial slots
 };
 
 } // namespace hm
@@ -150,7 +151,7 @@ struct hm_matrix_s {
     cudaStream_t cap_stream = nullptr;
 
     // kernel choices measured on this operator per right-hand-side count (hm_api.cu autotune)
-    struct Tune { int prod_rb = -1, res_rb = -1; double prod_ms = 0.0, res_ms = 0.0; };
+    struct Tune { int prod_rb = -1, res_rb = -1; double prod_ms = 0.0, res_ms = 0.0; };   // res_rb < 0: not tuned
     std::map<int, Tune> tune;
 
     // opt-in event timing of the product kernel

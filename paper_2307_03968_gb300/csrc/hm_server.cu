@@ -166,6 +166,13 @@ void retire(hm_server_s *S, Slot &s)
         r.t_done = now;
         r.done = true;
     }
+    // the operator's footprint grows with its workspace (right-hand-side vectors)
+    hm_info info;
+    if (hm_get_info(S->ops[s.op].h, &info) == HM_OK) {
+        S->resident_bytes += info.device_bytes - S->ops[s.op].bytes;
+        S->ops[s.op].bytes = info.device_bytes;
+        S->peak_resident = std::max(S->peak_resident, S->resident_bytes);
+    }
     S->ops[s.op].busy = false;
     S->ops[s.op].last_use = now;
     S->solved_rhs += s.nrhs;
