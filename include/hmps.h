@@ -340,12 +340,23 @@ hm_status hm_get_info(hm_matrix h, hm_info *info);
  * kernels on that operator at the bucket's size (with CUDA events on the
  * caller's stream, which it synchronises once) and keeps the fastest: for the product and for the
  * FP64-class residual products, 0 = one right-hand side at a time, 8 / 16 / 32 =
- * blocks staged once in shared memory per chunk of that many right-hand sides.
+ * blocks staged once in shared memory per chunk of that many right-hand sides,
+ * 1016 (product only) = dense blocks on the tensor cores in chunks of 16.
  * prod_ms / res_ms: the measured time of one leaf-level launch of the choice.
  * Any output pointer may be NULL.  HM_ERR_STATE if no call with that nrhs has
  * been made yet (or nrhs < 4, which needs no choice).
  */
 hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double *prod_ms, double *res_ms);
+
+/*
+ * Pin the kernel choice for the bucket of `nrhs` right-hand sides instead of
+ * letting the autotuner time it (e.g. for reproducible benchmarks or to test a
+ * kernel): prod_rb 0 (one right-hand side at a time), 8 / 16 / 32 (shared-memory
+ * SIMT chunks) or 1016 (tensor-core dense blocks, chunks of 16, tcgen05 3xTF32);
+ * res_rb 0, 8 or 16.  Drops captured solve graphs.  HM_ERR_ARG for nrhs < 4 or
+ * another value.
+ */
+hm_status hm_set_tuning(hm_matrix h, int nrhs, int prod_rb, int res_rb);
 
 /* Tree permutation (tree position -> original unknown), host int64[n]. */
 hm_status hm_get_perm(hm_matrix h, int64_t *perm);

@@ -63,9 +63,19 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         }
         L.n_small = (int64_t)small.size();
         L.n_big = (int64_t)big.size();
+        std::vector<Item> tc, lr;
+        L.tc_dim = 0;
+        for (const Item &it : small) {
+            (it.k == 0 ? tc : lr).push_back(it);
+            if (it.k == 0) L.tc_dim = std::max(L.tc_dim, std::max(it.m, it.n));
+        }
+        L.n_tc = (int64_t)tc.size();
+        L.n_lr = (int64_t)lr.size();
         if ((st = upload(h, &L.d_items, L.items, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_small, small, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_big, big, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_tc, tc, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_lr, lr, s)) != HM_OK) return st;
     }
     return HM_OK;
 }
@@ -94,6 +104,8 @@ static void free_handle(hm_matrix h)
         if (kv.second.d_items) cudaFree(kv.second.d_items);
         if (kv.second.d_small) cudaFree(kv.second.d_small);
         if (kv.second.d_big) cudaFree(kv.second.d_big);
+        if (kv.second.d_tc) cudaFree(kv.second.d_tc);
+        if (kv.second.d_lr) cudaFree(kv.second.d_lr);
     }
     for (void *p : h->ws.vec32) if (p) cudaFree(p);
     for (void *p : h->ws.vec64) if (p) cudaFree(p);
@@ -430,10 +442,12 @@ static hm_status autotune(hm_matrix h, int nrhs_req, int m, cudaStream_t s, bool
         return HM_OK;
     };
     double best = 1e30;
-    const int prod_c[] = {0, 8, 16, 32};
+    const int prod_c[] = {0, 8, 16, 32, RB_TC};
     for (int rb : prod_c) {
         if (!do_prod) break;
-        if (rb > 8 && rb / 2 >= nrhs) continue;         // a chunk of twice the RHS count or more only adds idle work
+        const int width = rb == RB_TC ? 16 : rb;
+        if (width > 8 && width / 2 >= nrhs) continue;   // a chunk of twice the RHS count or more only adds idle work
+        if (rb == RB_TC && L.n_tc == 0) continue;
         double ms = 0;
         if ((st = time_it([&] { launch_apply_items(h, L, x, z, nrhs, false, s, rb); }, ms)) != HM_OK) break;
         if (ms < best) { best = ms; t.prod_rb = rb; t.prod_ms = ms; }
@@ -948,6 +962,21 @@ hm_status hm_profile_read(hm_matrix h, double *product_ms, int64_t *launches, in
     *product_ms = tot;
     *launches = h->prof_launches;
     *bytes = h->prof_bytes;
+    return HM_OK;
+}
+
+hm_status hm_set_tuning(hm_matrix h, int nrhs, int prod_rb, int res_rb)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    if (nrhs < MRHS_MIN_RHS) return fail(HM_ERR_ARG, "kernel choices apply from 4 right-hand sides on");
+    const bool pok = prod_rb == 0 || prod_rb == 8 || prod_rb == 16 || prod_rb == 32 || prod_rb == RB_TC;
+    const bool rok = res_rb == 0 || res_rb == 8 || res_rb == 16;
+    if (!pok || !rok) return fail(HM_ERR_ARG, "prod_rb must be 0, 8, 16, 32 or 1016 and res_rb 0, 8 or 16");
+    hm_matrix_s::Tune t;
+    t.prod_rb = prod_rb;
+    t.res_rb = res_rb;
+    h->tune[tune_bucket(nrhs)] = t;
+    clear_graphs(h);   // captured solves hold the previous choice
     return HM_OK;
 }
 

@@ -30,6 +30,7 @@ constexpr int MRHS_MAX_DIM = 64;    // largest block side of the multi-RHS produ
 constexpr int MRHS_MAX_RANK = 32;   // largest rank of a low-rank block it takes
 constexpr int MRHS_MIN_RHS = 4;     // from this many right-hand sides on, the multi-RHS kernels take the small blocks
 constexpr int RESID_CHUNK = 16;     // right-hand sides per chunk of the FP64-class residual (partial slots held)
+constexpr int RB_TC = 1016;         // product choice: tensor-core dense blocks, 16 RHS per chunk
 
 // One stored block = one work item of the product kernels (32 bytes).
 struct Item {
@@ -61,6 +62,11 @@ struct LevelList {
     Item *d_small = nullptr, *d_big = nullptr;
     int64_t n_small = 0, n_big = 0;
     int small_dim = 0, small_rank = 0;   // largest (even) side and rank among the small items
+    // the small items split again for the tensor-core path: dense blocks (tcgen05
+    // products) and low-rank blocks (shared-memory SIMT products)
+    Item *d_tc = nullptr, *d_lr = nullptr;
+    int64_t n_tc = 0, n_lr = 0;
+    int tc_dim = 0;                       // largest side among the dense small items
     int64_t n_dense = 0, n_lowrank = 0;
     int64_t elems = 0;            // stored complex elements
 };
@@ -233,6 +239,12 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s);
 // z (+)= M_level x for right-hand sides [0, nrhs), blocks read once per chunk of rb
 void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, int rb,
                              cudaStream_t s);
+// the same for an explicit list of small items (k_mrhs.cu)
+void launch_apply_list_mrhs(hm_matrix h, const LevelList &L, const Item *items, int64_t n_items, const float2 *x,
+                            float2 *z, int nrhs, int rb, cudaStream_t s);
+// tensor-core products of dense items with sides <= dim <= 64 (k_mrhs_tc.cu)
+void launch_apply_dense_tc(hm_matrix h, const Item *items, int64_t n_items, int dim, const float2 *x, float2 *z,
+                           int nrhs, cudaStream_t s);
 // the FP64-class partial-slot products of the small items for many right-hand sides (k_mrhs.cu)
 void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, double2 *part,
                                       int64_t pstride, int nrhs, cudaStream_t s, int rb = -1);

@@ -471,7 +471,8 @@ void launch_resid_rb(hm_matrix h, const LevelList &L, const float2 *x, double2 *
 }
 
 template <int RB>
-void launch_rb(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
+void launch_rb(hm_matrix h, const LevelList &L, const Item *items, int64_t n_items, const float2 *x, float2 *z,
+               int nrhs, cudaStream_t s)
 {
     size_t sm = 0;
     const Geom gm = level_geom(L, RB + 2, sizeof(float2), sm);   // even panel stride: 16-byte aligned rows
@@ -484,10 +485,10 @@ void launch_rb(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_mrhs<RB>, MT, sm);
     if (per_sm < 1) per_sm = 1;
     int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
-    if (g > L.n_small) g = L.n_small;
+    if (g > n_items) g = n_items;
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
         const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
-        k_apply_mrhs<RB><<<(unsigned)g, MT, sm, s>>>(L.d_small, L.n_small, h->d_pool32, x + (int64_t)r0 * h->pN,
+        k_apply_mrhs<RB><<<(unsigned)g, MT, sm, s>>>(items, n_items, h->d_pool32, x + (int64_t)r0 * h->pN,
                                                      h->pN, z + (int64_t)r0 * h->pN, h->pN, nr, gm);
     }
 }
@@ -497,10 +498,16 @@ void launch_rb(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int 
 void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, int rb,
                              cudaStream_t s)
 {
-    if (L.n_small == 0 || nrhs <= 0) return;
-    if (rb <= 8) launch_rb<8>(h, L, x, z, nrhs, s);
-    else if (rb <= 16) launch_rb<16>(h, L, x, z, nrhs, s);
-    else launch_rb<32>(h, L, x, z, nrhs, s);
+    launch_apply_list_mrhs(h, L, L.d_small, L.n_small, x, z, nrhs, rb, s);
+}
+
+void launch_apply_list_mrhs(hm_matrix h, const LevelList &L, const Item *items, int64_t n_items, const float2 *x,
+                            float2 *z, int nrhs, int rb, cudaStream_t s)
+{
+    if (n_items == 0 || nrhs <= 0) return;
+    if (rb <= 8) launch_rb<8>(h, L, items, n_items, x, z, nrhs, s);
+    else if (rb <= 16) launch_rb<16>(h, L, items, n_items, x, z, nrhs, s);
+    else launch_rb<32>(h, L, items, n_items, x, z, nrhs, s);
 }
 
 } // namespace hm

@@ -94,7 +94,7 @@ EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_powerseries
            "hm_powerseries_solve_host", "hm_apply", "hm_residual", "hm_residual_noalloc", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
            "hm_server_create", "hm_server_add_mesh", "hm_server_submit", "hm_server_wait", "hm_server_get_info",
            "hm_server_destroy",
-           "hm_get_info", "hm_get_tuning", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
+           "hm_get_info", "hm_get_tuning", "hm_set_tuning", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
            "hm_size", "hm_destroy", "hm_last_error", "hm_version"]
 
 _lib = None
@@ -132,6 +132,7 @@ def load():
     L.hm_get_perm.argtypes = [P, PI64]
     L.hm_get_leaves.argtypes = [P, PI64]
     L.hm_get_tuning.argtypes = [P, ctypes.c_int, PI32, PI32, PD, PD]
+    L.hm_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.hm_get_blocks.argtypes = [P, ctypes.c_int, PI64, PI64, PI64, PI32, PI32, PI32]
     L.hm_get_block.argtypes = [P, ctypes.c_int, I64, PD, PD]
     L.hm_sync_status.argtypes = [P, P]
@@ -325,6 +326,10 @@ class HMatrix:
         _check(load().hm_get_tuning(self._h, nrhs, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                     ctypes.byref(d)))
         return a.value, b.value, c.value, d.value
+
+    def set_tuning(self, nrhs, prod_rb, res_rb):
+        """hm_set_tuning: pin the kernel choice for nrhs's bucket (1016 = tensor-core products)."""
+        _check(load().hm_set_tuning(self._h, nrhs, prod_rb, res_rb))
 
     @property
     def n(self):

@@ -42,6 +42,9 @@ def operators(torch_cuda):
     return ops
 
 
+PRODUCT_KERNELS = [0, 8, 16, 32, 1016]   # one RHS at a time, SIMT chunks, tensor-core dense blocks
+
+
 @pytest.mark.parametrize("name", ["rwg_binary15", "swg_slab", "swg_slab_leaf112"])
 @pytest.mark.parametrize("nrhs", [3, 4, 7, 8, 13, 16, 33, 70])
 def test_many_rhs_product_equals_column_products(torch_cuda, operators, name, nrhs):
@@ -50,14 +53,21 @@ def test_many_rhs_product_equals_column_products(torch_cuda, operators, name, nr
     rng = np.random.default_rng(nrhs)
     x = (rng.normal(size=(nrhs, N)) + 1j * rng.normal(size=(nrhs, N))).astype(np.complex64)
     xt = torch_cuda.from_numpy(x).cuda()
-    yt = torch_cuda.empty_like(xt)
-    A.apply(xt, yt, n_levels=-1, fp64_accumulate=False)
-    got = yt.cpu().numpy()
+    ref = np.empty_like(x)
     for r in range(nrhs):
         y1 = torch_cuda.empty((1, N), dtype=torch_cuda.complex64, device="cuda")
         A.apply(xt[r:r + 1].contiguous(), y1, n_levels=-1, fp64_accumulate=False)
-        ref = y1.cpu().numpy()[0]
-        assert np.linalg.norm(got[r] - ref) / np.linalg.norm(ref) < 1e-5, r
+        ref[r] = y1.cpu().numpy()[0]
+    kernels = PRODUCT_KERNELS if nrhs >= 4 else [None]
+    for kern in kernels:
+        if kern is not None:
+            A.set_tuning(nrhs, kern, 0)
+        yt = torch_cuda.empty_like(xt)
+        A.apply(xt, yt, n_levels=-1, fp64_accumulate=False)
+        got = yt.cpu().numpy()
+        for r in range(nrhs):
+            err = np.linalg.norm(got[r] - ref[r]) / np.linalg.norm(ref[r])
+            assert err < 1e-5, (kern, r, err)
 
 
 def test_operators_exercise_both_kernels(operators):
