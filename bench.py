@@ -110,6 +110,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the unrefined / full-level timings")
     p.add_argument("--workload", default="sphere2", choices=sorted(WORKLOADS))
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU time budget of the oracle sample")
+    p.add_argument("--pin-product", type=int, default=None,
+                   help="pin the many-RHS product kernel (0, 8, 16, 32, 1016 = tensor cores) instead of autotuning")
+    p.add_argument("--pin-residual", type=int, default=None, help="pin the many-RHS residual kernel (0, 8, 16)")
     return p.parse_args()
 
 
@@ -327,6 +330,9 @@ def main():
     A.rhs_plane_wave(kh, ph, b)
     x = torch.empty_like(b)
     opts = dict(n_terms=w["n_terms"], n_levels=w["n_levels"], refine=w["refine"])
+    if nrhs >= 4 and (a.pin_product is not None or a.pin_residual is not None):
+        A.set_tuning(nrhs, a.pin_product if a.pin_product is not None else 16,
+                     a.pin_residual if a.pin_residual is not None else 8)
     si = A.solve(b, x, info=True, **opts)
     launches_per_step = si.kernel_launches
     stream = torch.cuda.current_stream()
