@@ -7,5 +7,6 @@ that the CPU oracle and the CUDA path can both consume the same inputs while
 sharing no code of the method.
 """
 
-from .meshes import icosphere, closed_cylinder, box_surface, cube_tets, ball_tets, random_permittivity  # noqa: F401
+from .meshes import (icosphere, closed_cylinder, box_surface, plate, cube_tets, box_tets, ball_tets, shell_tets,  # noqa: F401
+                     random_permittivity)
 from .incidence import plane_wave_z, monostatic_sweep, random_incidences  # noqa: F401

@@ -192,3 +192,91 @@ def _orient_tets(xyz, tet):
 def random_permittivity(n_tet, lo, hi, seed):
     """Relative permittivity per tetrahedron, iid uniform in [lo, hi]."""
     return np.random.default_rng(seed).uniform(lo, hi, n_tet)
+
+
+def plate(size, n):
+    """Open square PEC plate [-sx/2, sx/2] x [-sy/2, sy/2] in z = 0, n = (nx, ny)
+    squares, each split into two triangles along a fixed diagonal; normals +z.
+    Only interior edges carry RWG unknowns (open surface)."""
+    sx, sy = size
+    nx, ny = n
+    xs = np.linspace(-sx / 2, sx / 2, nx + 1)
+    ys = np.linspace(-sy / 2, sy / 2, ny + 1)
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1)
+
+    def vid(i, j):
+        return i * (ny + 1) + j
+
+    tris = []
+    for i in range(nx):
+        for j in range(ny):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            tris.append((a, b, c))
+            tris.append((a, c, d))
+    return xyz, np.array(tris, dtype=np.int32)
+
+
+def box_tets(size, n):
+    """Box [-sx/2, sx/2] x [-sy/2, sy/2] x [-sz/2, sz/2] split into n = (nx, ny, nz)
+    voxels of 6 tetrahedra each (the Freudenthal split of cube_tets), positive
+    orientation."""
+    sx, sy, sz = size
+    nx, ny, nz = n
+    g = [np.linspace(-s / 2, s / 2, k + 1) for s, k in ((sx, nx), (sy, ny), (sz, nz))]
+    X, Y, Z = np.meshgrid(*g, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+    def vid(i, j, k):
+        return (i * (ny + 1) + j) * (nz + 1) + k
+
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for i in range(nx):
+        for j in range(ny):
+            for k in range(nz):
+                for p in perms:
+                    c = [0, 0, 0]
+                    path = [vid(i, j, k)]
+                    for ax in p:
+                        c[ax] = 1
+                        path.append(vid(i + c[0], j + c[1], k + c[2]))
+                    tets.append(path)
+    tet = np.array(tets, dtype=np.int32)
+    _orient_tets(xyz, tet)
+    return xyz, tet
+
+
+def shell_tets(r_in, r_out, length, n):
+    """Hollow circular cylinder along z (radii r_in < r_out, length), a structured
+    (n_r, n_theta, n_z) grid in (r, theta, z), periodic in theta, each cell split
+    into 6 tetrahedra (Freudenthal split of the index cube, so that neighbouring
+    cells share faces), positive orientation."""
+    n_r, n_t, n_z = n
+    rs = np.linspace(r_in, r_out, n_r + 1)
+    ts = 2 * np.pi * np.arange(n_t) / n_t
+    zs = np.linspace(-length / 2, length / 2, n_z + 1)
+
+    def vid(i, j, k):
+        return (i * n_t + (j % n_t)) * (n_z + 1) + k
+
+    xyz = np.zeros(((n_r + 1) * n_t * (n_z + 1), 3))
+    for i, r in enumerate(rs):
+        for j, t in enumerate(ts):
+            for k, z in enumerate(zs):
+                xyz[vid(i, j, k)] = (r * np.cos(t), r * np.sin(t), z)
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for i in range(n_r):
+        for j in range(n_t):
+            for k in range(n_z):
+                for p in perms:
+                    c = [0, 0, 0]
+                    path = [vid(i, j, k)]
+                    for ax in p:
+                        c[ax] = 1
+                        path.append(vid(i + c[0], j + c[1], k + c[2]))
+                    tets.append(path)
+    tet = np.array(tets, dtype=np.int32)
+    _orient_tets(xyz, tet)
+    return xyz, tet
