@@ -44,6 +44,19 @@ WORKLOADS = {
     "serving": dict(name="serving_stream_pec_and_dielectric_catalog", kind="serving", n_requests=2000, seed=5,
                     loads=(0.5, 0.8, 1.0), max_rhs=32, n_slots=4, hbm_budget_gb=64, max_batch_rhs=64,
                     n_terms=2, n_levels=1, refine=True, nrhs=0, unknowns=0),
+    # the paper's three experiments (§IV) as synthetic meshes of the stated dimensions, with its settings
+    # (binary tree, eq. 7 with eta = 1, ACA 1e-3), one normally incident plane wave, leaf level, K = 2,
+    # no refinement (the paper's solve), eps_r = 2 for the dielectrics
+    "paper_plate": dict(name="paper_pec_plate_15lambda_67200rwg", kind="rwg", shape=("plate", (15.0, 15.0), (150, 150)),
+                        leaf_size=64, arity=2, adm=1.0, aca_tol=1e-3, n_terms=2, n_levels=1, refine=False, nrhs=1,
+                        unknowns=67200, triangles=45000),
+    "paper_slab": dict(name="paper_dielectric_slab_10x1x0.1lambda_119984swg", kind="swg",
+                       shape=("box", (10.0, 1.0, 0.1), (218, 21, 2)), eps=2.0, leaf_size=64, arity=2, adm=1.0,
+                       aca_tol=1e-3, n_terms=2, n_levels=1, refine=False, nrhs=1, unknowns=119984, tetrahedra=54936),
+    "paper_cylinder": dict(name="paper_hollow_dielectric_cylinder_6lambda_158730swg", kind="swg",
+                           shape=("shell", (0.35, 0.4, 6.0), (1, 55, 206)), eps=2.0, leaf_size=64, arity=2, adm=1.0,
+                           aca_tol=1e-3, n_terms=2, n_levels=1, refine=False, nrhs=1, unknowns=158730,
+                           tetrahedra=67980),
     # a smaller sphere of the same family (7,680 unknowns), for profiler captures
     "sphere1": dict(name="sefie_pec_sphere_r1lambda_7680rwg", kind="rwg", subdivisions=4, radius=1.0, leaf_size=64,
                     arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=7680,
@@ -64,7 +77,16 @@ METRIC = "power-series solves RHS/s at <=1e-4 rel err vs FP64 oracle; p50/p99 la
 
 def workload_mesh(w):
     """(xyz, cells, eps_r or None) of a workload, from the seeded generators."""
+    import numpy as np
     import synth
+    shape = w.get("shape")
+    if shape is not None:
+        if shape[0] == "plate":
+            xyz, tri = synth.plate(shape[1], shape[2])
+            return xyz, tri, None
+        xyz, tet = (synth.box_tets(shape[1], shape[2]) if shape[0] == "box" else
+                    synth.shell_tets(*shape[1], shape[2]))
+        return xyz, tet, np.full(len(tet), w["eps"])
     if w["kind"] == "rwg":
         xyz, tri = synth.icosphere(w["subdivisions"], w["radius"])
         return xyz, tri, None
@@ -76,6 +98,10 @@ def workload_incidences(w):
     import synth
     if w.get("sweep"):
         return synth.monostatic_sweep(w["nrhs"])
+    if w.get("shape") is not None:                       # normal incidence on the plate / slab, broadside on the cylinder
+        import numpy as np
+        return np.array([[0.0, 0.0, -1.0]]) if w["shape"][0] != "shell" else np.array([[1.0, 0.0, 0.0]]), \
+            np.array([[1.0, 0.0, 0.0]]) if w["shape"][0] != "shell" else np.array([[0.0, 0.0, 1.0]])
     if w["kind"] == "rwg":
         return synth.plane_wave_z()
     return synth.random_incidences(w["nrhs"], seed=w["rhs_seed"])
@@ -83,6 +109,14 @@ def workload_incidences(w):
 
 def workload_config(w):
     c = {"workload": w["name"], "unknowns": w["unknowns"]}
+    if w.get("shape") is not None:
+        c.update({"shape": "%s %s, grid %s" % (w["shape"][0], w["shape"][1], w["shape"][2]),
+                  "eps_r": w.get("eps"), "tree": "binary (median splits)", "admissibility": "dist>=min(diam) (eta=1)",
+                  "rhs": "one plane wave", "leaf_size": w["leaf_size"], "aca_tol": w["aca_tol"],
+                  "n_terms": w["n_terms"], "levels": "leaf level only", "refine": "none (the paper's solve)",
+                  "nrhs": w["nrhs"], "l2": "operator resident in HBM is larger than L2; no flush",
+                  "parallelism": "replicas"})
+        return c
     if w["kind"] == "rwg":
         c.update({"triangles": w["triangles"], "radius_lambda": w["radius"], "tree": "octree (median splits)",
                   "admissibility": "dist>=2*min(diam)",
@@ -316,8 +350,9 @@ def main():
 
     xyz, cells, eps = workload_mesh(w)
     t0 = time.perf_counter()
+    want_fp64 = not a.no_extras and w["nrhs"] == 1          # for the plain FP64 single-solve comparator
     A = HMatrix.build(xyz, cells, eps_r=eps, leaf_size=w["leaf_size"], arity=w["arity"], adm=w["adm"],
-                      aca_tol=w["aca_tol"], levels=-1)
+                      aca_tol=w["aca_tol"], levels=-1, keep_fp64=want_fp64)
     build_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     A.factor_leaf()
@@ -385,12 +420,27 @@ def main():
         s1.record(stream)
         torch.cuda.synchronize()
         return s0.elapsed_time(s1) / n
-    no_refine_ms = full_nested_ms = full_flat_ms = None
+    no_refine_ms = full_nested_ms = full_flat_ms = fp64_ms = None
+    if want_fp64:
+        # the plain FP64 path: complex128 blocks and vectors, one right-hand side per call (no refinement:
+        # it is already FP64)
+        b64 = b.to(torch.complex128)
+        x64 = torch.empty_like(b64)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            A.solve(b64, x64, n_terms=w["n_terms"], n_levels=w["n_levels"], fp64=True)
+        s0.record(stream)
+        for _ in range(20):
+            A.solve(b64, x64, n_terms=w["n_terms"], n_levels=w["n_levels"], fp64=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = s0.elapsed_time(s1) / 20
     if not a.no_extras:
         no_refine_ms = time_solves(200, n_terms=2, n_levels=1, refine=False)
-        # the nested form costs ~(K+1)^levels leaf-level products: few repetitions on deep trees
-        full_nested_ms = time_solves(20 if info.n_levels <= 3 else 2, n_terms=2, n_levels=-1, nested=True,
-                                     refine=False)
+        # the nested form costs ~(K+1)^levels leaf-level products: few repetitions on deep trees, none past 6
+        if info.n_levels <= 6:
+            full_nested_ms = time_solves(20 if info.n_levels <= 3 else 2, n_terms=2, n_levels=-1, nested=True,
+                                         refine=False)
         full_flat_ms = time_solves(100, n_terms=2, n_levels=-1, nested=False, refine=False)
 
     # end to end through the host-buffer entry point
@@ -450,6 +500,8 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches_per_step) * K,
                 "extras": {"eager_ms_per_step": eager_ms, "build_s": build_s, "factor_s": factor_s, "no_refine_ms": no_refine_ms,
+                           "fp64_plain_ms": fp64_ms,
+                           "fp64_plain_rhs_s": (1e3 / fp64_ms) if fp64_ms else None,
                            "full_level_nested_ms": full_nested_ms, "full_level_flat_ms": full_flat_ms,
                            "n_levels": info.n_levels, "near_blocks": info.n_near,
                            "far_blocks": [info.n_far[i] for i in range(info.n_levels)],
