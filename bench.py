@@ -298,6 +298,24 @@ def committed_traffic():
     return None
 
 
+# ---------------------------------------------------------------- ranks ---------
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it): the timed region of a job
+    ends when its last replica ends."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(steps, nrhs, world, ms):
+    """Whole-job right-hand sides per second: every rank is an independent replica
+    solving `steps` x `nrhs` right-hand sides in (at most) `ms` milliseconds."""
+    return steps * nrhs * world / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- main ----------
 def main():
     a = parse()
@@ -400,14 +418,11 @@ def main():
     prof_ms, prof_n, prof_bytes = A.profile_read()
     A.profile(False)
     eager_ms = p0.elapsed_time(p1) / Kp
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     lat = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
-    value = K * nrhs * world / (total_ms / 1e3)
+    value = replica_rate(K, nrhs, world, total_ms)
 
     # extras: unrefined solve and full-level solve (nested, all levels)
     def time_solves(n, **kw):
