@@ -7,12 +7,15 @@
 //
 // One CTA of 128 threads per block, persistent over the item list.  The block
 // (or both low-rank panels) and the two RHS panels are copied to shared memory
-// with cp.async; each small product is then a SIMT GEMM in which a thread owns
-// 2 rows x RB/4 right-hand sides of the output, so every shared-memory load of
-// the block feeds RB/4 complex FMAs.  Shared rows have an odd stride (complex
-// elements) so that the row pairs a warp touches fall in distinct banks, and
-// the shared buffers are sized for the largest block and rank of the level, so
-// that several CTAs per SM overlap one block's copy with another's arithmetic.
+// with cp.async; each small product is then a SIMT GEMM.  In the FP32 product a
+// thread owns 4 rows x RB/4 right-hand sides of the output (the two mirrored
+// products run side by side on the two halves of the CTA), so every
+// shared-memory load of the block feeds RB/4 complex FMAs; in the FP64-class
+// residual (compensated Dot2 sums, FP64 partial slots) it owns 2 rows x RB/4.
+// Block rows have an odd stride (complex elements) so that the rows a warp
+// touches fall in distinct banks, and the shared buffers are sized for the
+// largest block and rank of the level, so that several CTAs per SM overlap one
+// block's copy with another's arithmetic.
 // Results go to z with vector atomics, as in the single-RHS kernel.  Blocks
 // larger than MRHS_MAX_DIM or of rank above MRHS_MAX_RANK stay on the
 // single-RHS kernel.
@@ -50,83 +53,6 @@ __device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src)
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// Y[r][q] = sum_c S[r][c] X[c][q] for rows r < R.  Thread t owns rows 2(t/4),
-// 2(t/4)+1 and right-hand sides (t%4)*TC .. +TC-1.  z given: add into z
-// (column-major, z[q*ldz + base + r]); else store into Y (row stride xld).
-template <int RB>
-__device__ __forceinline__ void mm_rows(const float2 *S, int sld, int R, int C, const float2 *X, int xld, float2 *Y,
-                                        float2 *z, int64_t ldz, int base, int nr)
-{
-    constexpr int TC = RB / 4;
-    const int t = threadIdx.x, q0 = (t & 3) * TC;
-    const int r = 2 * (t >> 2);
-    if (r >= R) return;
-    float2 a0[TC], a1[TC];
-#pragma unroll
-    for (int q = 0; q < TC; ++q) { a0[q] = make_float2(0.f, 0.f); a1[q] = a0[q]; }
-    const float2 *s0 = S + r * sld, *s1 = s0 + sld;
-    const float2 *xc = X + q0;
-    for (int c = 0; c < C; ++c, xc += xld) {
-        const float2 b0 = s0[c], b1 = s1[c];
-#pragma unroll
-        for (int q = 0; q < TC; ++q) {
-            const float2 xv = xc[q];
-            cma(a0[q], b0, xv);
-            cma(a1[q], b1, xv);
-        }
-    }
-    const bool two = r + 1 < R;
-    if (z) {
-#pragma unroll
-        for (int q = 0; q < TC; ++q) {
-            if (q0 + q >= nr) break;
-            float2 *zz = z + (int64_t)(q0 + q) * ldz + base + r;
-            if (two) red2(zz, a0[q], a1[q]);
-            else red1(zz, a0[q]);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < TC; ++q) {
-            Y[r * xld + q0 + q] = a0[q];
-            if (two) Y[(r + 1) * xld + q0 + q] = a1[q];
-        }
-    }
-}
-
-// z[q*ldz + base + c] += sum_r S[r][c] X[r][q] for columns c < C, rows r < R.
-// Thread t owns columns 2(t/4), 2(t/4)+1 and right-hand sides (t%4)*TC .. +TC-1.
-template <int RB>
-__device__ __forceinline__ void mm_cols(const float2 *S, int sld, int R, int C, const float2 *X, int xld, float2 *z,
-                                        int64_t ldz, int base, int nr)
-{
-    constexpr int TC = RB / 4;
-    const int t = threadIdx.x, q0 = (t & 3) * TC;
-    const int c = 2 * (t >> 2);
-    if (c >= C) return;
-    float2 a0[TC], a1[TC];
-#pragma unroll
-    for (int q = 0; q < TC; ++q) { a0[q] = make_float2(0.f, 0.f); a1[q] = a0[q]; }
-    const float2 *sc = S + c;
-    const float2 *xr = X + q0;
-    for (int r = 0; r < R; ++r, sc += sld, xr += xld) {
-        const float2 b0 = sc[0], b1 = sc[1];
-#pragma unroll
-        for (int q = 0; q < TC; ++q) {
-            const float2 xv = xr[q];
-            cma(a0[q], b0, xv);
-            cma(a1[q], b1, xv);
-        }
-    }
-    const bool two = c + 1 < C;
-#pragma unroll
-    for (int q = 0; q < TC; ++q) {
-        if (q0 + q >= nr) break;
-        float2 *zz = z + (int64_t)(q0 + q) * ldz + base + c;
-        if (two) red2(zz, a0[q], a1[q]);
-        else red1(zz, a0[q]);
-    }
 }
 
 // Wider tiles for the FP32 product: 64 threads per product (tid in [0, 64)), each
