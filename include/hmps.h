@@ -341,7 +341,8 @@ hm_status hm_get_info(hm_matrix h, hm_info *info);
  * caller's stream, which it synchronises once) and keeps the fastest: for the product and for the
  * FP64-class residual products, 0 = one right-hand side at a time, 8 / 16 / 32 =
  * blocks staged once in shared memory per chunk of that many right-hand sides,
- * 1016 (product only) = dense blocks on the tensor cores in chunks of 16.
+ * 1016 (product only, timed from 32 right-hand sides on) = the blocks of at most
+ * 64 x 64 (rank <= 32) on the tensor cores in tiles of 128 right-hand sides.
  * prod_ms / res_ms: the measured time of one leaf-level launch of the choice.
  * Any output pointer may be NULL.  HM_ERR_STATE if no call with that nrhs has
  * been made yet (or nrhs < 4, which needs no choice).
@@ -352,7 +353,8 @@ hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double
  * Pin the kernel choice for the bucket of `nrhs` right-hand sides instead of
  * letting the autotuner time it (e.g. for reproducible benchmarks or to test a
  * kernel): prod_rb 0 (one right-hand side at a time), 8 / 16 / 32 (shared-memory
- * SIMT chunks) or 1016 (tensor-core dense blocks, chunks of 16, tcgen05 3xTF32);
+ * SIMT chunks) or 1016 (tensor-core products of the blocks of at most 64 x 64 and
+ * rank <= 32, dense and low-rank, tiles of 128 right-hand sides, tcgen05 3xTF32);
  * res_rb 0, 8 or 16.  Drops captured solve graphs.  HM_ERR_ARG for nrhs < 4 or
  * another value.
  */

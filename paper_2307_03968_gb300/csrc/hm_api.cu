@@ -45,6 +45,77 @@ template <class T> static hm_status upload(hm_matrix h, T **dst, const std::vect
     return HM_OK;
 }
 
+// The tensor-core product's work list: every small item gives two directed
+// products (into its row cluster and, mirrored, into its column cluster), grouped
+// by output cluster; a cluster's products are cut into units of at most `cap`
+// K chunks (units of one cluster add into z with atomics), units sorted by cost,
+// largest first, so that the persistent CTAs taking units in turn stay balanced.
+static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vector<TcUnit> &units,
+                           std::vector<TcProd> &prods, std::vector<int2> &xch)
+{
+    std::map<int32_t, std::vector<TcProd>> by_out;
+    auto add = [&](int32_t out0, const TcProd &p) {
+        if (p.klen > 0 && p.olen > 0) by_out[out0].push_back(p);
+    };
+    for (const Item &it : small) {
+        if (it.k == 0) {
+            const int32_t ld = (int32_t)even(it.n);
+            add(it.row0, TcProd{it.off, 0, it.col0, it.n, 0, ld, 0, 0, it.m, 0});
+            add(it.col0, TcProd{it.off, 0, it.row0, it.m, 0, ld, 0, 1, it.n, 0});
+        } else {
+            const int32_t lm = (int32_t)even(it.m), ln = (int32_t)even(it.n);
+            const int64_t uoff = it.off, voff = it.off + (int64_t)it.k * lm;
+            add(it.row0, TcProd{voff, uoff, it.col0, it.n, it.k, ln, lm, 0, it.m, 0});   // U (V x_J)
+            add(it.col0, TcProd{uoff, voff, it.row0, it.m, it.k, lm, ln, 0, it.n, 0});   // V^T (U^T x_I)
+        }
+    }
+    auto cost = [](const TcProd &p) {
+        return (int64_t)((p.klen + 7) / 8) + (p.rank > 0 ? (int64_t)((p.rank + 7) / 8) : 0);
+    };
+    int64_t total = 0;
+    for (auto &kv : by_out)
+        for (const TcProd &p : kv.second) total += cost(p);
+    const int64_t cap = std::max<int64_t>(256, total / (std::max(num_sms, 1) * 2 * 8));
+    struct U { TcUnit u; int64_t c; std::vector<TcProd> p; };
+    std::vector<U> us;
+    for (auto &kv : by_out) {
+        int32_t mlen = 0;
+        for (const TcProd &p : kv.second) mlen = std::max(mlen, p.olen);
+        U cur{TcUnit{kv.first, mlen, 0, 0}, 0, {}};
+        for (const TcProd &p : kv.second) {
+            if (cur.c > 0 && cur.c + cost(p) > cap) {
+                us.push_back(cur);
+                cur.c = 0;
+                cur.p.clear();
+            }
+            cur.p.push_back(p);
+            cur.c += cost(p);
+        }
+        if (!cur.p.empty()) us.push_back(cur);
+    }
+    std::stable_sort(us.begin(), us.end(), [](const U &a, const U &b) { return a.c > b.c; });
+    // K chunks of the input clusters (each cluster's longest input length)
+    std::map<int32_t, int32_t> in_len;
+    for (const U &x : us)
+        for (const TcProd &p : x.p) in_len[p.in0] = std::max(in_len[p.in0], p.klen);
+    std::map<int32_t, int32_t> in_g0;
+    xch.clear();
+    for (auto &kv : in_len) {
+        in_g0[kv.first] = (int32_t)xch.size();
+        for (int32_t c = 0; c < kv.second; c += 8) xch.push_back(make_int2(kv.first + c, std::min(8, kv.second - c)));
+    }
+    for (U &x : us)
+        for (TcProd &p : x.p) p.xg0 = in_g0[p.in0];
+    units.clear();
+    prods.clear();
+    for (U &x : us) {
+        x.u.p0 = (int32_t)prods.size();
+        prods.insert(prods.end(), x.p.begin(), x.p.end());
+        x.u.p1 = (int32_t)prods.size();
+        units.push_back(x.u);
+    }
+}
+
 hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
 {
     hm_status st;
@@ -63,19 +134,20 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         }
         L.n_small = (int64_t)small.size();
         L.n_big = (int64_t)big.size();
-        std::vector<Item> tc, lr;
-        L.tc_dim = 0;
-        for (const Item &it : small) {
-            (it.k == 0 ? tc : lr).push_back(it);
-            if (it.k == 0) L.tc_dim = std::max(L.tc_dim, std::max(it.m, it.n));
-        }
-        L.n_tc = (int64_t)tc.size();
-        L.n_lr = (int64_t)lr.size();
+        std::vector<TcUnit> tcu;
+        std::vector<TcProd> tcp;
+        std::vector<int2> xch;
+        build_tc_lists(small, h->num_sms > 0 ? h->num_sms : 152, tcu, tcp, xch);
+        L.n_tcu = (int64_t)tcu.size();
+        L.n_tcp = (int64_t)tcp.size();
+        L.n_xch = (int64_t)xch.size();
+        h->tc_max_xch = std::max(h->tc_max_xch, L.n_xch);
+        if ((st = upload(h, &L.d_xch, xch, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_items, L.items, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_small, small, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_big, big, s)) != HM_OK) return st;
-        if ((st = upload(h, &L.d_tc, tc, s)) != HM_OK) return st;
-        if ((st = upload(h, &L.d_lr, lr, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_tcu, tcu, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_tcp, tcp, s)) != HM_OK) return st;
     }
     return HM_OK;
 }
@@ -97,15 +169,16 @@ static void free_handle(hm_matrix h)
         if (p) cudaFree(p);
     void *ptrs[] = {h->d_pperm, h->d_pleaf_off, h->d_dinv_off, h->d_leaf_n, h->d_self_off, h->d_bad_leaf,
                     h->d_self64, h->d_self32, h->d_dinv32, h->d_dinv64, h->d_pool32, h->d_pool64, h->d_status,
-                    h->ws.d_acc64, h->ws.d_io, h->ws.d_part, h->d_csr_off, h->d_csr_idx};
+                    h->ws.d_acc64, h->ws.d_io, h->ws.d_part, h->d_csr_off, h->d_csr_idx, h->ws.d_xpl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &kv : h->levels) {
         if (kv.second.d_items) cudaFree(kv.second.d_items);
         if (kv.second.d_small) cudaFree(kv.second.d_small);
         if (kv.second.d_big) cudaFree(kv.second.d_big);
-        if (kv.second.d_tc) cudaFree(kv.second.d_tc);
-        if (kv.second.d_lr) cudaFree(kv.second.d_lr);
+        if (kv.second.d_tcu) cudaFree(kv.second.d_tcu);
+        if (kv.second.d_tcp) cudaFree(kv.second.d_tcp);
+        if (kv.second.d_xch) cudaFree(kv.second.d_xch);
     }
     for (void *p : h->ws.vec32) if (p) cudaFree(p);
     for (void *p : h->ws.vec64) if (p) cudaFree(p);
@@ -243,6 +316,14 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
         }
     }
     HM_CUDA(cudaMalloc((void **)&ws.d_acc64, 2 * sizeof(double) * r));
+    if (ws.d_xpl) cudaFree(ws.d_xpl);
+    ws.d_xpl = nullptr;
+    ws.xpl_bytes = 0;
+    if (r >= MRHS_MIN_RHS && h->tc_max_xch > 0) {   // split x of the tensor-core product (it can be pinned from 4 RHS)
+        ws.xpl_bytes = tc_xplane_bytes(h->tc_max_xch, r);
+        HM_CUDA(cudaMalloc((void **)&ws.d_xpl, ws.xpl_bytes));
+        ws.dev_bytes += (int64_t)ws.xpl_bytes;
+    }
     ws.part_rhs = std::min(r, RESID_CHUNK);   // the partial slots themselves: ensure_partials
     ws.nrhs = r;
     return HM_OK;
@@ -445,9 +526,8 @@ static hm_status autotune(hm_matrix h, int nrhs_req, int m, cudaStream_t s, bool
     const int prod_c[] = {0, 8, 16, 32, RB_TC};
     for (int rb : prod_c) {
         if (!do_prod) break;
-        const int width = rb == RB_TC ? 16 : rb;
-        if (width > 8 && width / 2 >= nrhs) continue;   // a chunk of twice the RHS count or more only adds idle work
-        if (rb == RB_TC && L.n_tc == 0) continue;
+        if (rb == RB_TC ? (nrhs < TC_MIN_RHS || L.n_tcu == 0) : (rb > 8 && rb / 2 >= nrhs))
+            continue;   // a chunk of twice the RHS count or more only adds idle work; tensor tiles of 128 from 32 RHS
         double ms = 0;
         if ((st = time_it([&] { launch_apply_items(h, L, x, z, nrhs, false, s, rb); }, ms)) != HM_OK) break;
         if (ms < best) { best = ms; t.prod_rb = rb; t.prod_ms = ms; }

@@ -30,7 +30,10 @@ constexpr int MRHS_MAX_DIM = 64;    // largest block side of the multi-RHS produ
 constexpr int MRHS_MAX_RANK = 32;   // largest rank of a low-rank block it takes
 constexpr int MRHS_MIN_RHS = 4;     // from this many right-hand sides on, the multi-RHS kernels take the small blocks
 constexpr int RESID_CHUNK = 16;     // right-hand sides per chunk of the FP64-class residual (partial slots held)
-constexpr int RB_TC = 1016;         // product choice: tensor-core dense blocks, 16 RHS per chunk
+constexpr int RB_TC = 1016;         // product choice: tensor-core products of the small items, RHS tiles of 128
+constexpr int TC_MAX_DIM = MRHS_MAX_DIM;    // the tensor-core product takes the same small items
+constexpr int TC_MAX_RANK = MRHS_MAX_RANK;
+constexpr int TC_MIN_RHS = 32;      // the autotuner times the tensor-core product from this many RHS on
 
 // One stored block = one work item of the product kernels (32 bytes).
 struct Item {
@@ -42,6 +45,27 @@ struct Item {
     int32_t pad;    // offset of the block's FP64 partial slot (row side, then column side)
 };
 static_assert(sizeof(Item) == 32, "Item layout");
+
+// One directed product of a small stored block into an output cluster (the
+// tensor-core product, k_mrhs_tc.cu): Z_out += B X_in with B the block (dense,
+// read row-major or transposed) or, for a low-rank block, Y (W X_in) with the
+// input-side factor W read row-major (rank rows) and the output-side factor Y
+// read transposed.
+struct TcProd {
+    int64_t b_off;   // complex offset of the block (dense) or of W (low-rank)
+    int64_t y_off;   // complex offset of Y (low-rank)
+    int32_t in0;     // padded-tree offset of the input cluster
+    int32_t klen;    // input length (K of the dense product and of stage 1)
+    int32_t rank;    // 0 = dense
+    int32_t b_ld;    // row stride of the block / of W
+    int32_t y_ld;    // row stride of Y as stored (rank rows)
+    int32_t trans;   // dense: 1 = element (out i, in j) is block[j][i] (the mirror product)
+    int32_t olen;    // output length of this product
+    int32_t xg0;     // first K chunk of the input cluster in the level's split-x chunk list
+};
+static_assert(sizeof(TcProd) == 48, "TcProd layout");
+// a work unit: products [p0, p1) into the output cluster at out0 (mlen = largest olen)
+struct TcUnit { int32_t out0, mlen, p0, p1; };
 
 __host__ __device__ inline int64_t even(int64_t v) { return (v + 1) & ~int64_t(1); }
 
@@ -62,11 +86,15 @@ struct LevelList {
     Item *d_small = nullptr, *d_big = nullptr;
     int64_t n_small = 0, n_big = 0;
     int small_dim = 0, small_rank = 0;   // largest (even) side and rank among the small items
-    // the small items split again for the tensor-core path: dense blocks (tcgen05
-    // products) and low-rank blocks (shared-memory SIMT products)
-    Item *d_tc = nullptr, *d_lr = nullptr;
-    int64_t n_tc = 0, n_lr = 0;
-    int tc_dim = 0;                       // largest side among the dense small items
+    // the small items as directed products grouped into work units by output
+    // cluster, for the tensor-core product (both mirrored halves of every block)
+    TcProd *d_tcp = nullptr;
+    TcUnit *d_tcu = nullptr;
+    int64_t n_tcp = 0, n_tcu = 0;
+    // the input clusters' K chunks of 8 unknowns (padded-tree offset, valid length):
+    // the tensor-core product splits x once per launch into these chunks
+    int2 *d_xch = nullptr;
+    int64_t n_xch = 0;
     int64_t n_dense = 0, n_lowrank = 0;
     int64_t elems = 0;            // stored complex elements
 };
@@ -83,6 +111,8 @@ struct Workspace {
     void *d_io = nullptr;         // device b / x for host-buffer solves
     size_t d_io_bytes = 0;
     int64_t dev_bytes = 0;        // device bytes held by the vectors, norms and partial slots
+    float *d_xpl = nullptr;       // split x chunks of the tensor-core product (16 KB per chunk and RHS tile)
+    size_t xpl_bytes = 0;
 };
 
 } // namespace hm
@@ -130,6 +160,7 @@ struct hm_matrix_s {
     hm::Workspace ws;
     int64_t device_bytes = 0;
     int num_sms = 0;
+    int64_t tc_max_xch = 0;           // largest split-x chunk count over the levels
 
     // mesh geometry kept for excitation (operators made by hm_build):
     // b_m = sum over the two sides s of ucoef[m][s] * sum_q w_q (r_q - v) . p exp(-jk k . r_q)
@@ -242,9 +273,11 @@ void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, f
 // the same for an explicit list of small items (k_mrhs.cu)
 void launch_apply_list_mrhs(hm_matrix h, const LevelList &L, const Item *items, int64_t n_items, const float2 *x,
                             float2 *z, int nrhs, int rb, cudaStream_t s);
-// tensor-core products of dense items with sides <= dim <= 64 (k_mrhs_tc.cu)
-void launch_apply_dense_tc(hm_matrix h, const Item *items, int64_t n_items, int dim, const float2 *x, float2 *z,
-                           int nrhs, cudaStream_t s);
+// bytes of the split-x workspace of the tensor-core product for n_xch chunks and nrhs (k_mrhs_tc.cu)
+size_t tc_xplane_bytes(int64_t n_xch, int nrhs);
+// tensor-core products of a level's small items for all right-hand sides (k_mrhs_tc.cu);
+// z accumulates (vector atomics); needs the split-x workspace for nrhs
+void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s);
 // the FP64-class partial-slot products of the small items for many right-hand sides (k_mrhs.cu)
 void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, double2 *part,
                                       int64_t pstride, int nrhs, cudaStream_t s, int rb = -1);

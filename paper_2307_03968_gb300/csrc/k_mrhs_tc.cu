@@ -1,39 +1,72 @@
-// Tensor-core block product for many right-hand sides (arxiv 2307.03968 eq. 6,
-// the dense near blocks, with the half storage of §III):
-//     Z_I += B X_J,   Z_J += B^T X_I        (B complex m x n, m, n <= 64)
-// for a chunk of RB right-hand sides, on the 5th-generation tensor cores
-// (tcgen05.mma kind::tf32, accumulators in tensor memory).
+// Tensor-core block products for many right-hand sides (arxiv 2307.03968 eq. 6
+// and §III: the near blocks and the low-rank far blocks U(V x) of one level,
+// half stored, each block used for both mirrored products):
+//     Z_I += B X_J,   Z_J += B^T X_I
+// on the 5th-generation tensor cores (tcgen05.mma kind::tf32, accumulators in
+// tensor memory).
 //
-// Complex products as real GEMMs.  With B = Br + i Bi and X = Xr + i Xi, the
-// direct product is D = A B' with
-//     A  (64 x 2n8):   [Br | Bi]                       (rows i, K index = plane, j)
-//     B' (2n8 x 2RB):  column 2q   = [ Xr[:,q] ; -Xi[:,q] ]
-//                      column 2q+1 = [ Xi[:,q] ;  Xr[:,q] ]
-// so that D[i][2q] = Re Z_I[i][q] and D[i][2q+1] = Im Z_I[i][q] (n8 = n rounded up
-// to 8, zero padded).  The mirror product uses the transposed planes [Br^T | Bi^T]
-// and the panel of X_I.  Both operands are in shared memory in the K-major
-// layout without swizzle: 8-row x 16-byte core matrices, K-adjacent cores 128 B
-// apart (leading byte offset), 8-row groups KCmax * 128 B apart (stride offset).
+// Orientation.  The right-hand sides are the M dimension: a tile of 128 of them
+// gives the 128 rows of the accumulator (tensor-memory lane r = right-hand side
+// r of the tile).  Every stored block yields two directed products (output
+// cluster O, input cluster J); the host groups them by output cluster into work
+// units, so one CTA keeps the sum for (O, tile) in tensor memory while it streams
+// that unit's blocks, and adds it into z once.
+//
+// Complex arithmetic.  With X = Xr + i Xi (tile rows x input) and B = Br + i Bi
+// (output x input), the accumulator [Re Z | Im Z] (128 x 2*m8) is
+//     Xr [Br ; Bi]^T + Xi [-Bi ; Br]^T
+// where [Br ; Bi] stacks the planes along N.  The B operand of a K step holds the
+// three planes -Bi, Br, Bi one after another, so both products are windows of
+// the same shared-memory rows (start at -Bi or at Br, N = 2*m8).
+//
+// Low-rank blocks (B = U V, rank k).  Stage 1 puts T = X W^T (128 x k; W = V for
+// the forward product, U^T for the mirror) into a second tensor-memory
+// accumulator with the same plane trick; stage 2 reads T back (tcgen05.ld),
+// splits it and multiplies it into the output accumulator with the output-side
+// factor read transposed (U for the forward product, V^T for the mirror).
 //
 // Precision (3xTF32): every FP32 operand a is split as a = hi + lo, hi = a rounded
-// to TF32 (10 mantissa bits), lo = a - hi (exact); each K step accumulates
-// hi*hi + hi*lo + lo*hi in FP32 in tensor memory, which keeps the product within
-// a few FP32 ulps (the dropped lo*lo term and the TF32 rounding of lo are ~2^-22).
+// to TF32, lo = a - hi (exact); each K step accumulates hi*hi + hi*lo + lo*hi in
+// FP32, which keeps the products within a few FP32 ulps (the dropped lo*lo term
+// and the TF32 rounding of lo are ~2^-22 relative).
 //
-// One CTA of 128 threads per block, persistent; thread 0 issues the MMAs, whose
-// completion arrives on an mbarrier; the accumulator (M = 64) sits in tensor-memory
-// lanes 32w .. 32w+15 of warp w, rows 16w .. 16w+15.  Every wait is bounded: on
-// timeout the kernel records HM_ERR_TIMEOUT in the status word, frees its tensor
-// memory and returns.
+// Pipeline (warp-specialised, mbarrier hand-offs, no CTA-wide barrier per chunk).
+// K goes in chunks of 8 (one MMA K step) through a ring of shared-memory slots.
+// Before the launch, x is split once into hi/lo planes per (input-cluster K
+// chunk, RHS tile), already in the operand layout (k_split_x).  Warp 0 (producer)
+// copies a chunk's A planes with one 16 KB cp.async.bulk and the raw complex64
+// rows of the block or factor with cp.async.  Warps 1-4 (converters) split the
+// block rows into the B planes (and, for stage 2, read T from tensor memory into
+// the A planes), and add finished accumulators into z.  Warp 5 issues the six
+// MMAs of a chunk and commits them to the slot's "empty" mbarrier.  Two CTAs
+// share an SM.  Every wait is bounded: on timeout the kernel records
+// HM_ERR_TIMEOUT in the status word, all roles leave, the MMAs in flight are
+// waited for (bounded), and the tensor memory is freed.
 #include "k_common.cuh"
 
 namespace hm {
 namespace {
 
 using namespace kc;
-constexpr int TT = 128;                  // threads per CTA
-constexpr int TM = 64;                   // MMA M (rows of A)
+constexpr int NWARP = 6;                         // 0 producer, 1-4 converters (tensor-memory lanes 32(w%4)..), 5 MMA
+constexpr int TT = NWARP * 32;
+constexpr int NCV = 128;                         // converter threads
+constexpr int TM = 128;                          // MMA M: right-hand sides per tile
+constexpr int KCH = 8;                           // K per chunk (complex unknowns; one MMA K step)
+constexpr int NSLOT = 3;
+constexpr int A_PLANE = TM * KCH * 4;            // bytes of one A plane (Xr/Xi x hi/lo): 4 KB
+constexpr int A_BYTES = 4 * A_PLANE;             // 16 KB, one bulk copy
+constexpr int B_ROWS = 3 * 64;                   // -Bi, Br, Bi rows of one B plane (<= 64 rows each)
+constexpr int B_PLANE = B_ROWS * KCH * 4;        // bytes of one B plane (hi or lo): 6 KB
+constexpr int B_RAW = 64 * KCH * 8;              // raw complex64 block / factor rows: 4 KB
+constexpr int SLOT = A_BYTES + 2 * B_PLANE + B_RAW;   // 32 KB
+constexpr int OFF_B = A_BYTES, OFF_RAW = A_BYTES + 2 * B_PLANE;
+constexpr int SMEM = NSLOT * SLOT;
+constexpr uint32_t TMEM_COLS = 256;              // output accumulator at column 0 (<= 128), T at column 128 (<= 64)
+constexpr uint32_t T_COL = 128;
+constexpr uint32_t GROUP_BYTES = 2 * 128;        // one 8-row group: two K-adjacent core matrices
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
+static_assert(TC_MAX_DIM <= 64 && TC_MAX_RANK <= 32, "operand planes and tensor-memory columns");
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -45,248 +78,483 @@ __device__ __forceinline__ void split_tf32(float a, float &hi, float &lo)
     lo = __fsub_rn(a, hi);
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo)
+// shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x
+// 16 bytes, K-adjacent cores 128 B apart, 8-row groups GROUP_BYTES apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
 {
     uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)(128u >> 4) << 16;              // leading byte offset: K-adjacent core matrices
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;    // stride byte offset: 8-row groups
-    d |= (uint64_t)1 << 46;                        // descriptor version (tcgen05)
-    return d;                                      // no swizzle, base offset 0
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)((GROUP_BYTES >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
 }
 
-// float offset of element (row r, K index k) in a K-major operand with kc K-cores per row
-__device__ __forceinline__ int koff(int r, int k, int kc)
-{
-    return (((r >> 3) * kc + (k >> 2)) << 5) + ((r & 7) << 2) + (k & 3);
-}
+// float offset of (row, K index k < 8) in a plane
+__device__ __forceinline__ int poff(int row, int k) { return (((row >> 3) * 2 + (k >> 2)) << 5) + ((row & 7) << 2) + (k & 3); }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+// bounded wait on an mbarrier phase; gives up early once another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int *abort)
 {
     for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
         if (done) return true;
+        if (*abort) return false;
     }
+    *abort = 1;
     return false;
 }
 
-// RHS operand B' for a panel of `len` unknowns at `base` (K = 2*len8): rows nn = 2q + s
-template <int RB>
-__device__ __forceinline__ void stage_rhs(const float2 *__restrict__ x, int64_t ldx, int base, int len, int len8,
-                                          int nr, float *Bhi, float *Blo, int kc)
+__device__ __forceinline__ void arrive(uint32_t mbar)
 {
-    constexpr int NR = 2 * RB;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int rr = lane >> 2, kk = lane & 3;
-    const int kcores = (2 * len8) >> 2;
-    const int units = (NR >> 3) * kcores;
-    for (int u = w; u < units; u += TT / 32) {
-        const int gn = u / kcores, c = u - gn * kcores;
-        const int nn = 8 * gn + rr, k = 4 * c + kk;
-        const int q = nn >> 1, s = nn & 1;
-        const int half = k >= len8, j = k - half * len8;
-        float v = 0.f;
-        if (q < nr && j < len) {
-            const float2 xv = x[(int64_t)q * ldx + base + j];
-            v = half == 0 ? (s == 0 ? xv.x : xv.y) : (s == 0 ? -xv.y : xv.x);
-        }
-        float h, l;
-        split_tf32(v, h, l);
-        const int o = ((gn * kc + c) << 5) + lane;   // == koff(nn, k, kc)
-        Bhi[o] = h;
-        Blo[o] = l;
-    }
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
-
-// issue the 3xTF32 MMAs of one product (K = 2*len8) into tensor-memory columns at tmem
-template <int RB>
-__device__ __forceinline__ void issue_mma(uint32_t tmem, uint32_t aHi, uint32_t aLo, uint32_t bHi, uint32_t bLo,
-                                          int len8, uint32_t sbo_a, uint32_t sbo_b, uint32_t mbar)
+__device__ __forceinline__ void commit(uint32_t mbar)
 {
-    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)((2 * RB) >> 3) << 17) |
-                               ((uint32_t)(TM >> 4) << 24);
-    const int steps = (2 * len8) >> 3;
-    for (int st = 0; st < steps; ++st) {
-        const uint32_t ko = (uint32_t)st * 256u;     // two K-cores of 128 B per K step of 8
-        const uint64_t ah = smem_desc(aHi + ko, sbo_a), al = smem_desc(aLo + ko, sbo_a);
-        const uint64_t bh = smem_desc(bHi + ko, sbo_b), bl = smem_desc(bLo + ko, sbo_b);
-        const uint32_t acc0 = st > 0 ? 1u : 0u;
-        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem), "l"(ah), "l"(bh),
-                     "r"(IDESC), "r"(acc0));
-        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(ah), "l"(bl),
-                     "r"(IDESC));
-        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(al), "l"(bh),
-                     "r"(IDESC));
-    }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// add the accumulator (rows < rows_valid) into z: row r, right-hand side q at z[q*ldz + base + r]
-template <int RB>
-__device__ __forceinline__ void drain(uint32_t taddr, int rows_valid, float2 *z, int64_t ldz, int base, int nr)
+__device__ __forceinline__ void tld8(uint32_t taddr, float (&v)[8])
 {
-    static_assert(RB == 16, "one 32-column load per warp");
-    uint32_t v[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int row = 16 * w + lane;
-    if (lane < 16 && row < rows_valid) {
 #pragma unroll
-        for (int q = 0; q < RB; ++q)
-            if (q < nr) red1(z + (int64_t)q * ldz + base + row, make_float2(__uint_as_float(v[2 * q]),
-                                                                              __uint_as_float(v[2 * q + 1])));
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ int clamp16(int bytes) { return bytes < 0 ? 0 : bytes > 16 ? 16 : bytes; }
+
+// the A planes of tile row r from 8 complex values: Xr hi, Xr lo, Xi hi, Xi lo
+// (4 planes of A_PLANE bytes, plane-major; the same layout in shared and global memory)
+__device__ __forceinline__ void put_a_row(float4 *p, int r, const float (&re)[8], const float (&im)[8])
+{
+    constexpr int PF4 = A_PLANE / 16;            // float4 per plane
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            split_tf32(re[4 * c + j], rh[j], rl[j]);
+            split_tf32(im[4 * c + j], ih[j], il[j]);
+        }
+        const int o = poff(r, 4 * c) >> 2;
+        p[o] = make_float4(rh[0], rh[1], rh[2], rh[3]);
+        p[PF4 + o] = make_float4(rl[0], rl[1], rl[2], rl[3]);
+        p[2 * PF4 + o] = make_float4(ih[0], ih[1], ih[2], ih[3]);
+        p[3 * PF4 + o] = make_float4(il[0], il[1], il[2], il[3]);
     }
 }
 
-template <int RB>
-__global__ void __launch_bounds__(TT)
-k_apply_mrhs_tc(const Item *__restrict__ items, int64_t n_items, const float2 *__restrict__ pool,
-                const float2 *__restrict__ x, int64_t ldx, float2 *__restrict__ z, int64_t ldz, int nr, int kcmax,
-                int *status)
+// split x once per launch: chunk g of the input clusters (unknowns off .. off+valid-1)
+// for RHS tile t (rows r0 .. r0+127) -> xpl[(t * n_xch + g)], A_BYTES each
+__global__ void __launch_bounds__(TM)
+k_split_x(const int2 *__restrict__ xch, int64_t n_xch, const float2 *__restrict__ x, int64_t ldx, int nrhs,
+          float *__restrict__ xpl)
 {
-    constexpr int NR = 2 * RB;
-    constexpr int MAXU = (TM / 8) * (TM / 4) / (TT / 32);   // block units per warp (8 x 4 elements each)
-    extern __shared__ __align__(1024) float smtc[];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t tmem_base;
-    const int kd = 4 * kcmax;                                // K floats per operand row
-    float *Ahi = smtc, *Alo = Ahi + TM * kd, *Bhi = Alo + TM * kd, *Blo = Bhi + NR * kd;
-    const uint32_t sbo_a = (uint32_t)kcmax * 128u, sbo_b = sbo_a;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int i = tid; i < (2 * TM + 2 * NR) * kd; i += TT) smtc[i] = 0.f;   // pads stay finite
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mbar)));
-        asm volatile("fence.mbarrier_init.release.cluster;");
+    const int64_t g = blockIdx.x;
+    const int t = blockIdx.y, r = threadIdx.x, r0 = t * TM;
+    const int2 ch = xch[g];
+    float re[8], im[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { re[j] = 0.f; im[j] = 0.f; }
+    if (r0 + r < nrhs) {
+        const float2 *src = x + (int64_t)(r0 + r) * ldx + ch.x;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < ch.y) { const float2 v = __ldg(src + j); re[j] = v.x; im[j] = v.y; }
     }
-    if (w == 0) {
+    put_a_row(reinterpret_cast<float4 *>(xpl + ((int64_t)t * n_xch + g) * (A_BYTES / 4)), r, re, im);
+}
+
+// Raw B layouts (16-byte pieces, swizzled so that the conversion reads are free of
+// bank conflicts):
+//   natural: row rho, complex q .. q+1 (piece q/2) at  rho*64 + ((q/2) ^ ((rho>>1)&3))*16
+//   transposed: K row k, rows row .. row+1 (piece row/2) at  k*512 + ((row/2) ^ k)*16
+__device__ __forceinline__ int swz_n(int r, int pc) { return r * 64 + ((pc ^ ((r >> 1) & 3)) << 4); }
+__device__ __forceinline__ int swz_t(int k, int pc) { return k * 512 + ((pc ^ k) << 4); }
+
+// producer lane: raw B rows, natural orientation: element (row, q) = src[row * ld + q]
+// for row < rows_valid, q = k0 + j < klen (else zero); rows < R8
+__device__ __forceinline__ void fetch_b_nat(uint32_t raw, int lane, const float2 *__restrict__ src, int ld, int R8,
+                                            int rows_valid, int k0, int klen)
+{
+    for (int id = lane; id < 4 * R8; id += 32) {
+        const int row = id >> 2, pc = id & 3;
+        const int q = k0 + 2 * pc;
+        const int bytes = row < rows_valid ? clamp16((klen - q) * 8) : 0;
+        cp16(raw + swz_n(row, pc), bytes > 0 ? (const void *)(src + (int64_t)row * ld + q) : (const void *)src, bytes);
+    }
+}
+
+// producer lane: raw B rows, transposed orientation: element (row, q) = src[q * ld + row]
+// for row < rows_valid, q = k0 + k < klen (else zero); rows < R8
+__device__ __forceinline__ void fetch_b_tr(uint32_t raw, int lane, const float2 *__restrict__ src, int ld, int R8,
+                                           int rows_valid, int k0, int klen)
+{
+    const int np = R8 >> 1;                       // pieces per K row
+    for (int id = lane; id < 8 * np; id += 32) {
+        const int k = id / np, pc = id - k * np, row = 2 * pc;
+        const int bytes = (k0 + k < klen) ? clamp16((rows_valid - row) * 8) : 0;
+        cp16(raw + swz_t(k, pc), bytes > 0 ? (const void *)(src + (int64_t)(k0 + k) * ld + row) : (const void *)src,
+             bytes);
+    }
+}
+
+// converter: A planes from the T accumulator (columns k0 .. k0+7 of Re T and of Im T), row r
+__device__ __forceinline__ void conv_a_t(float *slot, uint32_t tmem, int quad, int r, int k8, int k0)
+{
+    float re[8], im[8];
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    tld8(tmem + lane_base + T_COL + (uint32_t)k0, re);
+    tld8(tmem + lane_base + T_COL + (uint32_t)(k8 + k0), im);
+    tld_wait();
+    put_a_row(reinterpret_cast<float4 *>(slot), r, re, im);
+}
+
+// the B planes of one element: -Bi at row, Br at R8 + row, Bi at 2 R8 + row; K index k
+__device__ __forceinline__ void put_b(float *bhi, float *blo, int row, int R8, int k, float2 v)
+{
+    float rh, rl, ih, il;
+    split_tf32(v.x, rh, rl);
+    split_tf32(v.y, ih, il);
+    int o = poff(row, k);
+    bhi[o] = -ih; blo[o] = -il;
+    o = poff(R8 + row, k);
+    bhi[o] = rh; blo[o] = rl;
+    o = poff(2 * R8 + row, k);
+    bhi[o] = ih; blo[o] = il;
+}
+
+// converter thread t (0..127): B planes from a raw natural chunk (rows < R8)
+__device__ __forceinline__ void conv_b_nat(float *bhi, float *blo, const unsigned char *raw, int R8, int t)
+{
+    const int row = t >> 1, half = t & 1;
+    if (row >= R8) return;
+    const float4 a = *reinterpret_cast<const float4 *>(raw + swz_n(row, 2 * half));
+    const float4 b = *reinterpret_cast<const float4 *>(raw + swz_n(row, 2 * half + 1));
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    float nh[4], nl[4], rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        split_tf32(v[2 * j], rh[j], rl[j]);
+        split_tf32(v[2 * j + 1], ih[j], il[j]);
+        nh[j] = -ih[j]; nl[j] = -il[j];
+    }
+    float4 *H = reinterpret_cast<float4 *>(bhi), *L = reinterpret_cast<float4 *>(blo);
+    int o = poff(row, 4 * half) >> 2;
+    H[o] = make_float4(nh[0], nh[1], nh[2], nh[3]); L[o] = make_float4(nl[0], nl[1], nl[2], nl[3]);
+    o = poff(R8 + row, 4 * half) >> 2;
+    H[o] = make_float4(rh[0], rh[1], rh[2], rh[3]); L[o] = make_float4(rl[0], rl[1], rl[2], rl[3]);
+    o = poff(2 * R8 + row, 4 * half) >> 2;
+    H[o] = make_float4(ih[0], ih[1], ih[2], ih[3]); L[o] = make_float4(il[0], il[1], il[2], il[3]);
+}
+
+// converter thread t (0..127): B planes from a raw transposed chunk (rows < R8)
+__device__ __forceinline__ void conv_b_tr(float *bhi, float *blo, const unsigned char *raw, int R8, int t)
+{
+    const int k = t & 7;
+    for (int row = 2 * (t >> 3); row < R8; row += 32) {
+        const float4 v = *reinterpret_cast<const float4 *>(raw + swz_t(k, row >> 1));
+        put_b(bhi, blo, row, R8, k, make_float2(v.x, v.y));
+        put_b(bhi, blo, row + 1, R8, k, make_float2(v.z, v.w));
+    }
+}
+
+// the six MMAs of one chunk into the accumulator at tensor-memory address acc:
+// acc (+)= Xr [Br;Bi]^T + Xi [-Bi;Br]^T in 3xTF32 (N = 2 R8)
+__device__ __forceinline__ void issue_chunk(uint32_t slot, uint32_t acc, int R8, bool accumulate)
+{
+    const uint32_t N = 2u * (uint32_t)R8;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+    const uint32_t a0 = slot, b0 = slot + OFF_B;
+    const uint32_t pos = (uint32_t)(R8 >> 3) * GROUP_BYTES;      // the [Br;Bi] window
+    const uint64_t xr_h = smem_desc(a0), xr_l = smem_desc(a0 + A_PLANE);
+    const uint64_t xi_h = smem_desc(a0 + 2 * A_PLANE), xi_l = smem_desc(a0 + 3 * A_PLANE);
+    const uint64_t bp_h = smem_desc(b0 + pos), bp_l = smem_desc(b0 + B_PLANE + pos);
+    const uint64_t bn_h = smem_desc(b0), bn_l = smem_desc(b0 + B_PLANE);
+    const uint32_t first = accumulate ? 1u : 0u;
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc), "l"(xr_h), "l"(bp_h),
+                 "r"(idesc), "r"(first));
+    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(xr_h), "l"(bp_l), "r"(idesc));
+    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(xr_l), "l"(bp_h), "r"(idesc));
+    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(xi_h), "l"(bn_h), "r"(idesc));
+    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(xi_h), "l"(bn_l), "r"(idesc));
+    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(xi_l), "l"(bn_h), "r"(idesc));
+}
+
+// converter: add the output accumulator rows of lane quadrant quad (tile rows < nr,
+// outputs < mlen) into z
+__device__ __forceinline__ void drain(uint32_t tmem, int quad, int lane, int m8, int mlen, float2 *__restrict__ z,
+                                      int64_t ldz, int r0, int nr, int out0)
+{
+    const int r = 32 * quad + lane;
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    float2 *zr = z + (int64_t)(r0 + r) * ldz + out0;
+    for (int i0 = 0; i0 < m8; i0 += 8) {
+        float re[8], im[8];
+        tld8(tmem + lane_base + (uint32_t)i0, re);
+        tld8(tmem + lane_base + (uint32_t)(m8 + i0), im);
+        tld_wait();
+        if (r < nr) {
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                const int i = i0 + j;
+                if (i + 1 < mlen) red2(zr + i, make_float2(re[j], im[j]), make_float2(re[j + 1], im[j + 1]));
+                else if (i < mlen) red1(zr + i, make_float2(re[j], im[j]));
+            }
+        }
+    }
+}
+
+// Position in a CTA's chunk sequence: unit-tile u (units taken in turn with
+// stride gridDim.x), product p of the unit, stage (0: the dense product or stage 1
+// of a low-rank one, 1: stage 2), chunk c of nch.  Every role walks the same
+// sequence.
+struct Pos {
+    int64_t u;
+    int p, stage, c, nch;
+    int tile, r0, nr, m8, k8;
+    bool valid;
+    TcUnit U;
+    TcProd P;
+    __device__ bool lr1() const { return P.rank > 0 && stage == 0; }
+    __device__ bool lr2() const { return P.rank > 0 && stage == 1; }
+    __device__ bool last_of_unit() const { return c == nch - 1 && (P.rank == 0 || stage == 1) && p == U.p1 - 1; }
+};
+
+struct Seq {
+    const TcUnit *units;
+    const TcProd *prods;
+    int n_tiles, nrhs;
+    int64_t total;
+    __device__ void product(Pos &q) const
+    {
+        q.P = prods[q.p];
+        q.stage = 0;
+        q.c = 0;
+        q.nch = (q.P.klen + KCH - 1) / KCH;
+        q.k8 = (q.P.rank + 7) & ~7;
+    }
+    __device__ void unit(Pos &q) const
+    {
+        q.valid = q.u < total;
+        if (!q.valid) return;
+        q.U = units[q.u / n_tiles];
+        q.tile = (int)(q.u % n_tiles);
+        q.r0 = q.tile * TM;
+        q.nr = min(TM, nrhs - q.r0);
+        q.m8 = (q.U.mlen + 7) & ~7;
+        q.p = q.U.p0;
+        product(q);
+    }
+    __device__ void next(Pos &q) const
+    {
+        if (++q.c < q.nch) return;
+        if (q.P.rank > 0 && q.stage == 0) {
+            q.stage = 1;
+            q.c = 0;
+            q.nch = q.k8 / KCH;
+            return;
+        }
+        if (++q.p < q.U.p1) {
+            product(q);
+            return;
+        }
+        q.u += gridDim.x;
+        unit(q);
+    }
+};
+
+__global__ void __launch_bounds__(TT, 2)
+k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restrict__ prods, int64_t n_xch,
+           const float *__restrict__ xpl, const float2 *__restrict__ pool, float2 *__restrict__ z, int64_t ldz,
+           int nrhs, int *status)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t full[NSLOT], ready[NSLOT], empty[NSLOT];
+    __shared__ __align__(8) uint64_t t_ready, t_empty, acc_full, acc_empty, fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < NSLOT; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[s])), "r"(33));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ready[s])), "r"(NCV));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&t_ready)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&t_empty)), "r"(NCV));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&acc_full)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acc_empty)), "r"(NCV));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&fin)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        abort_flag = 0;
+    }
+    if (w == NWARP - 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
-                     "n"(2 * NR));
+                     "n"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
+    fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t mb = su32(&mbar);
-    const uint32_t aHi = su32(Ahi), aLo = su32(Alo), bHi = su32(Bhi), bLo = su32(Blo);
-    const int rr = lane >> 2, kk = lane & 3;
-    uint32_t phase = 0;
-    bool ok = true;
-    for (int64_t b = blockIdx.x; b < n_items && ok; b += gridDim.x) {
-        const Item it = items[b];
-        const int m = it.m, n = it.n, m8 = (m + 7) & ~7, n8 = (n + 7) & ~7;
-        const int ld = (int)even(n);
-        const float2 *B = pool + it.off;
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();                                     // previous item: tensor memory read, shared free
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- block -> registers and the direct operand [Br | Bi]
-        const int gm = m8 >> 3, cn = n8 >> 2, units = gm * cn;
-        float2 hold[MAXU];
-#pragma unroll
-        for (int t = 0; t < MAXU; ++t) {
-            const int u = w + t * (TT / 32);
-            hold[t] = make_float2(0.f, 0.f);
-            if (u < units) {
-                const int g = u / cn, c = u - g * cn;
-                const int i = 8 * g + rr, j = 4 * c + kk;
-                if (i < m && j < n) hold[t] = __ldcs(B + (int64_t)i * ld + j);
-                float h, l;
-                split_tf32(hold[t].x, h, l);
-                int o = ((g * kcmax + c) << 5) + lane;        // (row i, K index j)
-                Ahi[o] = h; Alo[o] = l;
-                split_tf32(hold[t].y, h, l);
-                o = ((g * kcmax + c + (n8 >> 2)) << 5) + lane; // (row i, K index n8 + j)
-                Ahi[o] = h; Alo[o] = l;
+    const uint32_t sm0 = su32(smraw);
+    const Seq seq{units, prods, (nrhs + TM - 1) / TM, nrhs, (int64_t)n_units * ((nrhs + TM - 1) / TM)};
+    Pos q;
+    q.u = blockIdx.x;
+    seq.unit(q);
+    uint32_t n = 0;
+
+    if (w == 0) {
+        // ---- producer: A planes (one bulk copy) and raw B rows into slot n % NSLOT
+        while (q.valid && !abort_flag) {
+            const int s = (int)(n % NSLOT);
+            if (n >= NSLOT && !mbar_wait(su32(&empty[s]), ((n / NSLOT) + 1) & 1, &abort_flag)) break;
+            const uint32_t slot = sm0 + (uint32_t)(s * SLOT);
+            const int k0 = q.c * KCH;
+            if (lane == 0) {
+                if (!q.lr2()) {
+                    const float *src = xpl + ((int64_t)q.tile * n_xch + q.P.xg0 + q.c) * (A_BYTES / 4);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[s])),
+                                 "r"(A_BYTES) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(slot), "l"(src), "r"(A_BYTES), "r"(su32(&full[s])) : "memory");
+                } else {
+                    arrive(su32(&full[s]));
+                }
             }
-        }
-        stage_rhs<RB>(x, ldx, it.col0, n, n8, nr, Bhi, Blo, kcmax);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) issue_mma<RB>(tmem, aHi, aLo, bHi, bLo, n8, sbo_a, sbo_b, mb);
-        if (!__syncthreads_and(mbar_wait(mb, phase))) { ok = false; break; }   // uniform decision
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        drain<RB>(tmem + ((uint32_t)(32 * w) << 16), m, z, ldz, it.row0, nr);
-        // ---- the mirror operand [Br^T | Bi^T] from the held block, and the panel of X_I
-        const int kcm = m8 >> 2;
-#pragma unroll
-        for (int t = 0; t < MAXU; ++t) {
-            const int u = w + t * (TT / 32);
-            if (u < units) {
-                const int g = u / cn, c = u - g * cn;
-                const int i = 8 * g + rr, j = 4 * c + kk;
-                float h, l;
-                split_tf32(hold[t].x, h, l);
-                int o = koff(j, i, kcmax);                    // (row j, K index i)
-                Ahi[o] = h; Alo[o] = l;
-                split_tf32(hold[t].y, h, l);
-                o = koff(j, i + 4 * kcm, kcmax);              // (row j, K index m8 + i)
-                Ahi[o] = h; Alo[o] = l;
+            const uint32_t raw = slot + OFF_RAW;
+            if (q.P.rank == 0) {
+                if (q.P.trans) fetch_b_tr(raw, lane, pool + q.P.b_off, q.P.b_ld, q.m8, q.P.olen, k0, q.P.klen);
+                else fetch_b_nat(raw, lane, pool + q.P.b_off, q.P.b_ld, q.m8, q.P.olen, k0, q.P.klen);
+            } else if (q.stage == 0) {
+                fetch_b_nat(raw, lane, pool + q.P.b_off, q.P.b_ld, q.k8, q.P.rank, k0, q.P.klen);
+            } else {
+                fetch_b_tr(raw, lane, pool + q.P.y_off, q.P.y_ld, q.m8, q.P.olen, k0, q.P.rank);
             }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&full[s])) : "memory");
+            ++n;
+            seq.next(q);
         }
-        stage_rhs<RB>(x, ldx, it.row0, m, m8, nr, Bhi, Blo, kcmax);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) issue_mma<RB>(tmem + NR, aHi, aLo, bHi, bLo, m8, sbo_a, sbo_b, mb);
-        if (!__syncthreads_and(mbar_wait(mb, phase))) { ok = false; break; }
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        drain<RB>(tmem + ((uint32_t)(32 * w) << 16) + NR, n, z, ldz, it.col0, nr);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (w <= 4) {
+        // ---- converters: B planes (and A planes from T), accumulators into z
+        const int t = tid - 32, quad = w & 3, r = 32 * quad + lane;
+        uint32_t n_t = 0, n_u = 0;
+        while (q.valid && !abort_flag) {
+            const int s = (int)(n % NSLOT);
+            if (!mbar_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag)) break;
+            float *slot = reinterpret_cast<float *>(smraw + s * SLOT);
+            const unsigned char *raw = smraw + s * SLOT + OFF_RAW;
+            float *bh = reinterpret_cast<float *>(smraw + s * SLOT + OFF_B), *bl = bh + B_PLANE / 4;
+            const bool lr1 = q.lr1(), lr2 = q.lr2();
+            if (lr2) {
+                if (q.c == 0 && !mbar_wait(su32(&t_ready), n_t & 1, &abort_flag)) break;
+                fence_after();
+                conv_a_t(slot, tmem, quad, r, q.k8, q.c * KCH);
+            }
+            const int R8 = lr1 ? q.k8 : q.m8;
+            if (q.P.rank == 0 ? q.P.trans != 0 : lr2) conv_b_tr(bh, bl, raw, R8, t);
+            else conv_b_nat(bh, bl, raw, R8, t);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (lr2 && q.c == q.nch - 1) {
+                fence_before();
+                arrive(su32(&t_empty));
+                ++n_t;
+            }
+            arrive(su32(&ready[s]));
+            if (q.last_of_unit()) {
+                if (!mbar_wait(su32(&acc_full), n_u & 1, &abort_flag)) break;
+                fence_after();
+                drain(tmem, quad, lane, q.m8, q.U.mlen, z, ldz, q.r0, q.nr, q.U.out0);
+                fence_before();
+                arrive(su32(&acc_empty));
+                ++n_u;
+            }
+            ++n;
+            seq.next(q);
+        }
+    } else if (lane == 0) {
+        // ---- MMA issuer
+        uint32_t n_lr = 0, n_u = 0;
+        bool started = false;
+        while (q.valid && !abort_flag) {
+            const int s = (int)(n % NSLOT);
+            const bool lr1 = q.lr1();
+            if (lr1 && q.c == 0 && n_lr > 0 && !mbar_wait(su32(&t_empty), (n_lr - 1) & 1, &abort_flag)) break;
+            if (!lr1 && !started && n_u > 0 && !mbar_wait(su32(&acc_empty), (n_u - 1) & 1, &abort_flag)) break;
+            if (!mbar_wait(su32(&ready[s]), (n / NSLOT) & 1, &abort_flag)) break;
+            fence_after();
+            issue_chunk(sm0 + (uint32_t)(s * SLOT), lr1 ? tmem + T_COL : tmem, lr1 ? q.k8 : q.m8,
+                        lr1 ? q.c > 0 : started);
+            commit(su32(&empty[s]));
+            if (lr1 && q.c == q.nch - 1) {
+                commit(su32(&t_ready));
+                ++n_lr;
+            }
+            if (!lr1) started = true;
+            if (q.last_of_unit()) {
+                commit(su32(&acc_full));
+                ++n_u;
+                started = false;
+            }
+            ++n;
+            seq.next(q);
+        }
+        commit(su32(&fin));                         // every MMA issued, then a bounded wait before freeing
+        mbar_wait(su32(&fin), 0, &abort_flag);
     }
-    if (!ok && status) atomicCAS(status, 0, (int)HM_ERR_TIMEOUT);
-    if (!ok) {   // an MMA may still be in flight: wait (bounded) for it before freeing tensor memory
-        mbar_wait(mb, phase);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
+    fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * NR));
+    fence_after();
+    if (abort_flag && status && tid == 0) atomicCAS(status, 0, (int)HM_ERR_TIMEOUT);
+    if (w == NWARP - 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
 }
 
 } // namespace
 
-// dense items with m, n <= 64: tensor-core products, RHS in chunks of 16
-void launch_apply_dense_tc(hm_matrix h, const Item *items, int64_t n_items, int dim, const float2 *x, float2 *z,
-                           int nrhs, cudaStream_t s)
+size_t tc_xplane_bytes(int64_t n_xch, int nrhs) { return (size_t)A_BYTES * (size_t)n_xch * (size_t)((nrhs + TM - 1) / TM); }
+
+// tensor-core products of the level's small items (dense and low-rank) for all
+// right-hand sides, in tiles of 128: split x, then the products
+void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
 {
-    constexpr int RB = 16;
-    if (n_items == 0 || nrhs <= 0) return;
-    const int kcmax = 2 * ((dim + 7) & ~7) / 4;          // K-cores per operand row: 2 * round8(dim) floats
-    const size_t sm = sizeof(float) * (size_t)(2 * TM + 4 * RB) * (size_t)(4 * kcmax);
-    static size_t attr = 0;
-    if (sm > attr) {
-        cudaFuncSetAttribute(k_apply_mrhs_tc<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = sm;
+    if (L.n_tcu == 0 || nrhs <= 0) return;
+    if (!h->ws.d_xpl || h->ws.xpl_bytes < tc_xplane_bytes(L.n_xch, nrhs)) {
+        fail(HM_ERR_STATE, "tensor-core product without its split-x workspace");
+        return;
     }
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        attr = true;
+    }
+    const int n_tiles = (nrhs + TM - 1) / TM;
+    k_split_x<<<dim3((unsigned)L.n_xch, (unsigned)n_tiles), TM, 0, s>>>(L.d_xch, L.n_xch, x, h->pN, nrhs, h->ws.d_xpl);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_mrhs_tc<RB>, TT, sm) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_tc, TT, SMEM) != cudaSuccess) {
         cudaGetLastError();
-        per_sm = (int)((227u << 10) / (sm + (2u << 10)));  // shared memory bound, with the static part
+        per_sm = 1;
     }
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 4) per_sm = 4;                           // tensor memory: 4 x 64 columns of 512
+    if (per_sm > 2) per_sm = 2;                    // tensor memory: 2 x 256 columns of 512
+    const int64_t units = L.n_tcu * (int64_t)n_tiles;
     int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
-    if (g > n_items) g = n_items;
-    for (int r0 = 0; r0 < nrhs; r0 += RB) {
-        const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
-        k_apply_mrhs_tc<RB><<<(unsigned)g, TT, sm, s>>>(items, n_items, h->d_pool32, x + (int64_t)r0 * h->pN, h->pN,
-                                                        z + (int64_t)r0 * h->pN, h->pN, nr, kcmax, h->d_status);
-    }
+    if (g > units) g = units;
+    k_apply_tc<<<(unsigned)g, TT, SMEM, s>>>(L.d_tcu, (int)L.n_tcu, L.d_tcp, L.n_xch, h->ws.d_xpl, h->d_pool32, z,
+                                           h->pN, nrhs, h->d_status);
 }
 
 } // namespace hm

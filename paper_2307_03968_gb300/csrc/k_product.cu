@@ -255,9 +255,8 @@ void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z,
         int64_t cnt = n;
         if (rb < 0) rb = nrhs < MRHS_MIN_RHS ? 0 : nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : 32;
         if (rb == RB_TC && nrhs > 1) {
-            // dense small blocks on the tensor cores, low-rank small blocks on the shared-memory kernel
-            launch_apply_dense_tc(h, L.d_tc, L.n_tc, L.tc_dim, (const float2 *)x, (float2 *)z, nrhs, s);
-            launch_apply_list_mrhs(h, L, L.d_lr, L.n_lr, (const float2 *)x, (float2 *)z, nrhs, 16, s);
+            // the small blocks (dense and low-rank) on the tensor cores
+            launch_apply_tc(h, L, (const float2 *)x, (float2 *)z, nrhs, s);
             list = L.d_big;
             cnt = L.n_big;
             if (cnt == 0) return;

@@ -37,6 +37,9 @@ def operators(torch_cuda):
     # 864 unknowns halved three times: leaves of 108, dense blocks too large for shared memory
     ops["swg_slab_leaf112"] = HMatrix.build(xyz, tet, eps_r=eps, leaf_size=112, arity=2, adm=1.0, aca_tol=1e-6,
                                             levels=-1)
+    # octree leaves of up to 64 unknowns: tensor-core products at full operand width (N = 128)
+    xyz, tri = synth.icosphere(3, 0.3)
+    ops["rwg_octree64"] = HMatrix.build(xyz, tri, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1)
     for A in ops.values():
         A.factor_leaf()
     return ops
@@ -45,7 +48,7 @@ def operators(torch_cuda):
 PRODUCT_KERNELS = [0, 8, 16, 32, 1016]   # one RHS at a time, SIMT chunks, tensor-core dense blocks
 
 
-@pytest.mark.parametrize("name", ["rwg_binary15", "swg_slab", "swg_slab_leaf112"])
+@pytest.mark.parametrize("name", ["rwg_binary15", "swg_slab", "swg_slab_leaf112", "rwg_octree64"])
 @pytest.mark.parametrize("nrhs", [3, 4, 7, 8, 13, 16, 33, 70])
 def test_many_rhs_product_equals_column_products(torch_cuda, operators, name, nrhs):
     A = operators[name]
@@ -68,6 +71,27 @@ def test_many_rhs_product_equals_column_products(torch_cuda, operators, name, nr
         for r in range(nrhs):
             err = np.linalg.norm(got[r] - ref[r]) / np.linalg.norm(ref[r])
             assert err < 1e-5, (kern, r, err)
+
+
+@pytest.mark.parametrize("name", ["rwg_binary15", "swg_slab", "rwg_octree64"])
+@pytest.mark.parametrize("nrhs", [128, 130, 261])
+def test_tensor_core_product_over_several_tiles(torch_cuda, operators, name, nrhs):
+    # tiles of 128 right-hand sides (full, ragged, three tiles) on the tensor cores
+    # against one right-hand side at a time, FP32 rounding apart (3xTF32 products)
+    A = operators[name]
+    N = A.n
+    rng = np.random.default_rng(nrhs + 5)
+    x = (rng.normal(size=(nrhs, N)) + 1j * rng.normal(size=(nrhs, N))).astype(np.complex64)
+    xt = torch_cuda.from_numpy(x).cuda()
+    ref = torch_cuda.empty_like(xt)
+    A.set_tuning(nrhs, 0, 0)
+    A.apply(xt, ref, n_levels=-1, fp64_accumulate=False)
+    A.set_tuning(nrhs, 1016, 0)
+    yt = torch_cuda.empty_like(xt)
+    A.apply(xt, yt, n_levels=-1, fp64_accumulate=False)
+    got, want = yt.cpu().numpy(), ref.cpu().numpy()
+    err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert err.max() < 1e-5, err.max()
 
 
 def test_operators_exercise_both_kernels(operators):
