@@ -382,6 +382,8 @@ void launch_resid_rb(hm_matrix h, const LevelList &L, const float2 *x, double2 *
     static size_t attr = 0;
     if (sm > attr) {
         cudaFuncSetAttribute(k_residual_mrhs<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_residual_mrhs<RB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);   // several CTAs per SM
         attr = sm;
     }
     int per_sm = 0;
@@ -405,6 +407,8 @@ void launch_rb(hm_matrix h, const LevelList &L, const Item *items, int64_t n_ite
     static size_t attr = 0;                                      // largest dynamic size enabled so far
     if (sm > attr) {
         cudaFuncSetAttribute(k_apply_mrhs<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_apply_mrhs<RB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);   // several CTAs per SM
         attr = sm;
     }
     int per_sm = 0;

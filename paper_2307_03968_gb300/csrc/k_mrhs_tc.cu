@@ -128,9 +128,11 @@ __device__ __forceinline__ void tld8(uint32_t taddr, float (&v)[8])
 }
 __device__ __forceinline__ void tld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void cp16(uint32_t dst, const void *src, int bytes)
+// 16-byte copy (bytes < 16: zero-filled) with an L2 eviction policy
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, int bytes, uint64_t pol)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(dst), "l"(src), "r"(bytes),
+                 "l"(pol) : "memory");
 }
 __device__ __forceinline__ int clamp16(int bytes) { return bytes < 0 ? 0 : bytes > 16 ? 16 : bytes; }
 
@@ -186,27 +188,28 @@ __device__ __forceinline__ int swz_t(int k, int pc) { return k * 512 + ((pc ^ k)
 // producer lane: raw B rows, natural orientation: element (row, q) = src[row * ld + q]
 // for row < rows_valid, q = k0 + j < klen (else zero); rows < R8
 __device__ __forceinline__ void fetch_b_nat(uint32_t raw, int lane, const float2 *__restrict__ src, int ld, int R8,
-                                            int rows_valid, int k0, int klen)
+                                            int rows_valid, int k0, int klen, uint64_t pol)
 {
     for (int id = lane; id < 4 * R8; id += 32) {
         const int row = id >> 2, pc = id & 3;
         const int q = k0 + 2 * pc;
         const int bytes = row < rows_valid ? clamp16((klen - q) * 8) : 0;
-        cp16(raw + swz_n(row, pc), bytes > 0 ? (const void *)(src + (int64_t)row * ld + q) : (const void *)src, bytes);
+        cp16(raw + swz_n(row, pc), bytes > 0 ? (const void *)(src + (int64_t)row * ld + q) : (const void *)src, bytes,
+             pol);
     }
 }
 
 // producer lane: raw B rows, transposed orientation: element (row, q) = src[q * ld + row]
 // for row < rows_valid, q = k0 + k < klen (else zero); rows < R8
 __device__ __forceinline__ void fetch_b_tr(uint32_t raw, int lane, const float2 *__restrict__ src, int ld, int R8,
-                                           int rows_valid, int k0, int klen)
+                                           int rows_valid, int k0, int klen, uint64_t pol)
 {
     const int np = R8 >> 1;                       // pieces per K row
     for (int id = lane; id < 8 * np; id += 32) {
         const int k = id / np, pc = id - k * np, row = 2 * pc;
         const int bytes = (k0 + k < klen) ? clamp16((rows_valid - row) * 8) : 0;
         cp16(raw + swz_t(k, pc), bytes > 0 ? (const void *)(src + (int64_t)(k0 + k) * ld + row) : (const void *)src,
-             bytes);
+             bytes, pol);
     }
 }
 
@@ -318,16 +321,17 @@ __device__ __forceinline__ void drain(uint32_t tmem, int quad, int lane, int m8,
 }
 
 // Position in a CTA's chunk sequence: unit-tile u (units taken in turn with
-// stride gridDim.x), product p of the unit, stage (0: the dense product or stage 1
-// of a low-rank one, 1: stage 2), chunk c of nch.  Every role walks the same
-// sequence.
+// stride gridDim.x, tile-major so that one RHS tile's split x stays in L2),
+// product p of the unit (the next one's record loaded ahead), stage (0: the dense
+// product or stage 1 of a low-rank one, 1: stage 2), chunk c of nch.  Every role
+// walks the same sequence.
 struct Pos {
     int64_t u;
     int p, stage, c, nch;
     int tile, r0, nr, m8, k8;
     bool valid;
     TcUnit U;
-    TcProd P;
+    TcProd P, Pn;
     __device__ bool lr1() const { return P.rank > 0 && stage == 0; }
     __device__ bool lr2() const { return P.rank > 0 && stage == 1; }
     __device__ bool last_of_unit() const { return c == nch - 1 && (P.rank == 0 || stage == 1) && p == U.p1 - 1; }
@@ -336,11 +340,11 @@ struct Pos {
 struct Seq {
     const TcUnit *units;
     const TcProd *prods;
-    int n_tiles, nrhs;
+    int n_units, nrhs;
     int64_t total;
-    __device__ void product(Pos &q) const
+    __device__ void start(Pos &q) const
     {
-        q.P = prods[q.p];
+        if (q.p + 1 < q.U.p1) q.Pn = prods[q.p + 1];
         q.stage = 0;
         q.c = 0;
         q.nch = (q.P.klen + KCH - 1) / KCH;
@@ -350,13 +354,14 @@ struct Seq {
     {
         q.valid = q.u < total;
         if (!q.valid) return;
-        q.U = units[q.u / n_tiles];
-        q.tile = (int)(q.u % n_tiles);
+        q.U = units[q.u % n_units];
+        q.tile = (int)(q.u / n_units);
         q.r0 = q.tile * TM;
         q.nr = min(TM, nrhs - q.r0);
         q.m8 = (q.U.mlen + 7) & ~7;
         q.p = q.U.p0;
-        product(q);
+        q.P = prods[q.p];
+        start(q);
     }
     __device__ void next(Pos &q) const
     {
@@ -368,7 +373,8 @@ struct Seq {
             return;
         }
         if (++q.p < q.U.p1) {
-            product(q);
+            q.P = q.Pn;
+            start(q);
             return;
         }
         q.u += gridDim.x;
@@ -411,14 +417,18 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
     fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t sm0 = su32(smraw);
-    const Seq seq{units, prods, (nrhs + TM - 1) / TM, nrhs, (int64_t)n_units * ((nrhs + TM - 1) / TM)};
+    const Seq seq{units, prods, n_units, nrhs, (int64_t)n_units * ((nrhs + TM - 1) / TM)};
     Pos q;
     q.u = blockIdx.x;
     seq.unit(q);
     uint32_t n = 0;
 
     if (w == 0) {
-        // ---- producer: A planes (one bulk copy) and raw B rows into slot n % NSLOT
+        // ---- producer: A planes (one bulk copy) and raw B rows into slot n % NSLOT;
+        // the split x is kept in L2 (evict last), the block stream is not (evict first)
+        uint64_t keep, stream;
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
         while (q.valid && !abort_flag) {
             const int s = (int)(n % NSLOT);
             if (n >= NSLOT && !mbar_wait(su32(&empty[s]), ((n / NSLOT) + 1) & 1, &abort_flag)) break;
@@ -429,20 +439,21 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
                     const float *src = xpl + ((int64_t)q.tile * n_xch + q.P.xg0 + q.c) * (A_BYTES / 4);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[s])),
                                  "r"(A_BYTES) : "memory");
-                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 ::"r"(slot), "l"(src), "r"(A_BYTES), "r"(su32(&full[s])) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                                 " [%0], [%1], %2, [%3], %4;"
+                                 ::"r"(slot), "l"(src), "r"(A_BYTES), "r"(su32(&full[s])), "l"(keep) : "memory");
                 } else {
                     arrive(su32(&full[s]));
                 }
             }
             const uint32_t raw = slot + OFF_RAW;
             if (q.P.rank == 0) {
-                if (q.P.trans) fetch_b_tr(raw, lane, pool + q.P.b_off, q.P.b_ld, q.m8, q.P.olen, k0, q.P.klen);
-                else fetch_b_nat(raw, lane, pool + q.P.b_off, q.P.b_ld, q.m8, q.P.olen, k0, q.P.klen);
+                if (q.P.trans) fetch_b_tr(raw, lane, pool + q.P.b_off, q.P.b_ld, q.m8, q.P.olen, k0, q.P.klen, stream);
+                else fetch_b_nat(raw, lane, pool + q.P.b_off, q.P.b_ld, q.m8, q.P.olen, k0, q.P.klen, stream);
             } else if (q.stage == 0) {
-                fetch_b_nat(raw, lane, pool + q.P.b_off, q.P.b_ld, q.k8, q.P.rank, k0, q.P.klen);
+                fetch_b_nat(raw, lane, pool + q.P.b_off, q.P.b_ld, q.k8, q.P.rank, k0, q.P.klen, stream);
             } else {
-                fetch_b_tr(raw, lane, pool + q.P.y_off, q.P.y_ld, q.m8, q.P.olen, k0, q.P.rank);
+                fetch_b_tr(raw, lane, pool + q.P.y_off, q.P.y_ld, q.m8, q.P.olen, k0, q.P.rank, stream);
             }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&full[s])) : "memory");
             ++n;
@@ -537,19 +548,17 @@ void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z
         return;
     }
     static bool attr = false;
-    if (!attr) {
+    if (!attr) {   // two CTAs of ~98 KB per SM need the largest shared-memory carveout
         cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
         attr = true;
     }
     const int n_tiles = (nrhs + TM - 1) / TM;
     k_split_x<<<dim3((unsigned)L.n_xch, (unsigned)n_tiles), TM, 0, s>>>(L.d_xch, L.n_xch, x, h->pN, nrhs, h->ws.d_xpl);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_tc, TT, SMEM) != cudaSuccess) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 2) per_sm = 2;                    // tensor memory: 2 x 256 columns of 512
+    // two CTAs per SM: tensor memory holds 2 x 256 columns of 512, shared memory 2 x ~98 KB
+    // of 228 KB; the persistent loop is correct for any grid
+    const int per_sm = 2;
     const int64_t units = L.n_tcu * (int64_t)n_tiles;
     int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
     if (g > units) g = units;
