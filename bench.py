@@ -150,12 +150,20 @@ def parse():
     return p.parse_args()
 
 
-def peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+def _measured_peaks():
     try:
-        with open(path) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+PEAKS = _measured_peaks()
+
+
+def peaks():
+    try:
+        return float(PEAKS["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
 
@@ -482,19 +490,38 @@ def main():
     flops_per_launch = 2.0 * per_launch_bytes * nrhs
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
-    alu_bound = flops_per_launch / (alu_peak * 1e12) > per_launch_bytes / (peak * 1e9)
+    prod_choice = A.tuning(nrhs)[0] if nrhs >= 4 else 0
     if not prof_n:
         achieved = None
-    elif alu_bound:
-        achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+    if prod_choice == 1016:
+        # tensor-core product (3xTF32): three TF32 MMAs per useful FP32-accurate product, so its roof is
+        # the TF32 tensor peak / 3; the TF32 peak is the measured sustained bf16 peak x the nominal
+        # TF32/bf16 ratio (1.1 / 2.25 PFLOP/s dense)
+        bf16_s = (PEAKS or {}).get("bf16_tflops_sustained")
+        tf32 = (bf16_s if bf16_s else 1700.0) * 1.1 / 2.25
+        bound, unit, rpeak = "tensor", "TFLOP/s", tf32 / 3.0
+        rkind = ("measured sustained bf16 %.1f TFLOP/s x 1.1/2.25 (TF32) / 3 (3xTF32 products)" % bf16_s if bf16_s
+                 else "fallback 1.7 PFLOP/s bf16 sustained x 1.1/2.25 / 3")
+        kernel = ("k_split_x + k_apply_tc (tcgen05 kind::tf32, 3xTF32; blocks <= 64 x 64, rank <= 32) "
+                  "+ k_apply_items for larger blocks (k_mrhs_tc.cu, k_product.cu)")
+    elif flops_per_launch / (alu_peak * 1e12) > per_launch_bytes / (peak * 1e9):
+        bound, unit, rpeak = "alu", "TFLOP/s", alu_peak
+        rkind = "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
+        kernel = ("k_apply_mrhs<%d> (shared-memory SIMT, %d RHS per chunk) + k_apply_items for larger blocks "
+                  "(k_mrhs.cu, k_product.cu)" % (prod_choice, prod_choice) if prod_choice
+                  else "k_apply_items<float,float,2> (one RHS at a time, k_product.cu)")
     else:
-        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    roof = {"bound": "alu" if alu_bound else "hbm",
-            "kernel": "k_apply_items<float,float,2> (near + leaf-level far block product, k_product.cu)",
-            "achieved": achieved, "peak": alu_peak if alu_bound else peak,
-            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock" if alu_bound else peak_kind,
-            "unit": "TFLOP/s" if alu_bound else "GB/s",
-            "frac": (achieved / (alu_peak if alu_bound else peak)) if achieved else None,
+        bound, unit, rpeak, rkind = "hbm", "GB/s", peak, peak_kind
+        kernel = "k_apply_items<float,float,2> (near + leaf-level far block product, k_product.cu)"
+    if prof_n:
+        achieved = (flops_per_launch / (per_launch_ms * 1e-3) / 1e12 if unit == "TFLOP/s"
+                    else per_launch_bytes / (per_launch_ms * 1e-3) / 1e9)
+    roof = {"bound": bound,
+            "kernel": kernel,
+            "achieved": achieved, "peak": rpeak,
+            "peak_kind": rkind,
+            "unit": unit,
+            "frac": (achieved / rpeak) if achieved else None,
             "traffic": committed_traffic(),
             "bytes_per_launch": per_launch_bytes, "flops_per_launch": flops_per_launch, "nrhs": nrhs,
             "ms_per_launch": per_launch_ms, "launches": prof_n,
