@@ -204,12 +204,13 @@ __device__ __forceinline__ void fetch_b_nat(uint32_t raw, int lane, const float2
 __device__ __forceinline__ void fetch_b_tr(uint32_t raw, int lane, const float2 *__restrict__ src, int ld, int R8,
                                            int rows_valid, int k0, int klen, uint64_t pol)
 {
-    const int np = R8 >> 1;                       // pieces per K row
-    for (int id = lane; id < 8 * np; id += 32) {
-        const int k = id / np, pc = id - k * np, row = 2 * pc;
-        const int bytes = (k0 + k < klen) ? clamp16((rows_valid - row) * 8) : 0;
-        cp16(raw + swz_t(k, pc), bytes > 0 ? (const void *)(src + (int64_t)(k0 + k) * ld + row) : (const void *)src,
-             bytes, pol);
+    const int k = lane & 7;
+    const bool kv = k0 + k < klen;
+    const float2 *p = src + (int64_t)(k0 + k) * ld;
+    for (int pc = lane >> 3; 2 * pc < R8; pc += 4) {
+        const int row = 2 * pc;
+        const int bytes = kv ? clamp16((rows_valid - row) * 8) : 0;
+        cp16(raw + swz_t(k, pc), bytes > 0 ? (const void *)(p + row) : (const void *)src, bytes, pol);
     }
 }
 
@@ -224,28 +225,13 @@ __device__ __forceinline__ void conv_a_t(float *slot, uint32_t tmem, int quad, i
     put_a_row(reinterpret_cast<float4 *>(slot), r, re, im);
 }
 
-// the B planes of one element: -Bi at row, Br at R8 + row, Bi at 2 R8 + row; K index k
-__device__ __forceinline__ void put_b(float *bhi, float *blo, int row, int R8, int k, float2 v)
-{
-    float rh, rl, ih, il;
-    split_tf32(v.x, rh, rl);
-    split_tf32(v.y, ih, il);
-    int o = poff(row, k);
-    bhi[o] = -ih; blo[o] = -il;
-    o = poff(R8 + row, k);
-    bhi[o] = rh; blo[o] = rl;
-    o = poff(2 * R8 + row, k);
-    bhi[o] = ih; blo[o] = il;
-}
+// converter thread t (0..127): B planes from a raw natural chunk (rows < R8): row t/2,
+// K indices 4*(t&1) .. +3
+__device__ __forceinline__ void conv_b_nat(float *bhi, float *blo, const unsigned char *raw, int R8, int t);
 
-// converter thread t (0..127): B planes from a raw natural chunk (rows < R8)
-__device__ __forceinline__ void conv_b_nat(float *bhi, float *blo, const unsigned char *raw, int R8, int t)
+// the B planes of 4 K-consecutive elements of one row (K indices 4*half .. 4*half+3)
+__device__ __forceinline__ void put_b4(float *bhi, float *blo, int row, int R8, int half, const float (&v)[8])
 {
-    const int row = t >> 1, half = t & 1;
-    if (row >= R8) return;
-    const float4 a = *reinterpret_cast<const float4 *>(raw + swz_n(row, 2 * half));
-    const float4 b = *reinterpret_cast<const float4 *>(raw + swz_n(row, 2 * half + 1));
-    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     float nh[4], nl[4], rh[4], rl[4], ih[4], il[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -262,15 +248,31 @@ __device__ __forceinline__ void conv_b_nat(float *bhi, float *blo, const unsigne
     H[o] = make_float4(ih[0], ih[1], ih[2], ih[3]); L[o] = make_float4(il[0], il[1], il[2], il[3]);
 }
 
-// converter thread t (0..127): B planes from a raw transposed chunk (rows < R8)
+// converter thread t (0..127): B planes from a raw transposed chunk (rows < R8): row t/2,
+// K indices 4*(t&1) .. +3, one 8-byte element from each of four K rows
 __device__ __forceinline__ void conv_b_tr(float *bhi, float *blo, const unsigned char *raw, int R8, int t)
 {
-    const int k = t & 7;
-    for (int row = 2 * (t >> 3); row < R8; row += 32) {
-        const float4 v = *reinterpret_cast<const float4 *>(raw + swz_t(k, row >> 1));
-        put_b(bhi, blo, row, R8, k, make_float2(v.x, v.y));
-        put_b(bhi, blo, row + 1, R8, k, make_float2(v.z, v.w));
+    const int row = t >> 1, half = t & 1;
+    if (row >= R8) return;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int k = 4 * half + j;
+        const float2 e = *reinterpret_cast<const float2 *>(raw + swz_t(k, row >> 1) + ((row & 1) << 3));
+        v[2 * j] = e.x;
+        v[2 * j + 1] = e.y;
     }
+    put_b4(bhi, blo, row, R8, half, v);
+}
+
+__device__ __forceinline__ void conv_b_nat(float *bhi, float *blo, const unsigned char *raw, int R8, int t)
+{
+    const int row = t >> 1, half = t & 1;
+    if (row >= R8) return;
+    const float4 a = *reinterpret_cast<const float4 *>(raw + swz_n(row, 2 * half));
+    const float4 b = *reinterpret_cast<const float4 *>(raw + swz_n(row, 2 * half + 1));
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    put_b4(bhi, blo, row, R8, half, v);
 }
 
 // the six MMAs of one chunk into the accumulator at tensor-memory address acc:
