@@ -342,7 +342,11 @@ hm_status hm_get_info(hm_matrix h, hm_info *info);
  * FP64-class residual products, 0 = one right-hand side at a time, 8 / 16 / 32 =
  * blocks staged once in shared memory per chunk of that many right-hand sides,
  * 1016 (product only, timed from 32 right-hand sides on) = the blocks of at most
- * 64 x 64 (rank <= 32) on the tensor cores in tiles of 128 right-hand sides.
+ * 64 x 64 (rank <= 32) on the tensor cores in tiles of 128 right-hand sides;
+ * 1017 (residual only, where every level of the call holds only such blocks) =
+ * owner-computes FP64-class products, one CTA per output cluster and group of 16
+ * right-hand sides, no partial slots.  res_ms of the owner kernel covers all
+ * nrhs right-hand sides at once, of the others one chunk of at most 16.
  * prod_ms / res_ms: the measured time of one leaf-level launch of the choice.
  * Any output pointer may be NULL.  HM_ERR_STATE if no call with that nrhs has
  * been made yet (or nrhs < 4, which needs no choice).
@@ -355,7 +359,8 @@ hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double
  * kernel): prod_rb 0 (one right-hand side at a time), 8 / 16 / 32 (shared-memory
  * SIMT chunks) or 1016 (tensor-core products of the blocks of at most 64 x 64 and
  * rank <= 32, dense and low-rank, tiles of 128 right-hand sides, tcgen05 3xTF32);
- * res_rb 0, 8 or 16.  Drops captured solve graphs.  HM_ERR_ARG for nrhs < 4 or
+ * res_rb 0, 8, 16 or 1017 (owner-computes; calls whose levels hold larger blocks
+ * fall back to the partial-slot kernel of one right-hand side at a time).  Drops captured solve graphs.  HM_ERR_ARG for nrhs < 4 or
  * another value.
  */
 hm_status hm_set_tuning(hm_matrix h, int nrhs, int prod_rb, int res_rb);

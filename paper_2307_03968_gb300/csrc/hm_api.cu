@@ -51,7 +51,8 @@ template <class T> static hm_status upload(hm_matrix h, T **dst, const std::vect
 // K chunks (units of one cluster add into z with atomics), units sorted by cost,
 // largest first, so that the persistent CTAs taking units in turn stay balanced.
 static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vector<TcUnit> &units,
-                           std::vector<TcProd> &prods, std::vector<int2> &xch)
+                           std::vector<TcProd> &prods, std::vector<int2> &xch, std::vector<TcUnit> &runits,
+                           std::vector<TcProd> &rprods)
 {
     std::map<int32_t, std::vector<TcProd>> by_out;
     auto add = [&](int32_t out0, const TcProd &p) {
@@ -75,6 +76,25 @@ static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vec
     int64_t total = 0;
     for (auto &kv : by_out)
         for (const TcProd &p : kv.second) total += cost(p);
+    // the residual's units: one per output cluster (every output row summed by one CTA), largest first
+    {
+        struct R { TcUnit u; int64_t c; const std::vector<TcProd> *p; };
+        std::vector<R> rs;
+        for (auto &kv : by_out) {
+            R r{TcUnit{kv.first, 0, 0, 0}, 0, &kv.second};
+            for (const TcProd &p : kv.second) { r.u.mlen = std::max(r.u.mlen, p.olen); r.c += cost(p); }
+            rs.push_back(r);
+        }
+        std::stable_sort(rs.begin(), rs.end(), [](const R &a, const R &b) { return a.c > b.c; });
+        runits.clear();
+        rprods.clear();
+        for (R &r : rs) {
+            r.u.p0 = (int32_t)rprods.size();
+            rprods.insert(rprods.end(), r.p->begin(), r.p->end());
+            r.u.p1 = (int32_t)rprods.size();
+            runits.push_back(r.u);
+        }
+    }
     const int64_t cap = std::max<int64_t>(256, total / (std::max(num_sms, 1) * 2 * 8));
     struct U { TcUnit u; int64_t c; std::vector<TcProd> p; };
     std::vector<U> us;
@@ -137,7 +157,12 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         std::vector<TcUnit> tcu;
         std::vector<TcProd> tcp;
         std::vector<int2> xch;
-        build_tc_lists(small, h->num_sms > 0 ? h->num_sms : 152, tcu, tcp, xch);
+        std::vector<TcUnit> rcu;
+        std::vector<TcProd> rcp;
+        build_tc_lists(small, h->num_sms > 0 ? h->num_sms : 152, tcu, tcp, xch, rcu, rcp);
+        L.n_rcu = (int64_t)rcu.size();
+        if ((st = upload(h, &L.d_rcu, rcu, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_rcp, rcp, s)) != HM_OK) return st;
         L.n_tcu = (int64_t)tcu.size();
         L.n_tcp = (int64_t)tcp.size();
         L.n_xch = (int64_t)xch.size();
@@ -169,7 +194,7 @@ static void free_handle(hm_matrix h)
         if (p) cudaFree(p);
     void *ptrs[] = {h->d_pperm, h->d_pleaf_off, h->d_dinv_off, h->d_leaf_n, h->d_self_off, h->d_bad_leaf,
                     h->d_self64, h->d_self32, h->d_dinv32, h->d_dinv64, h->d_pool32, h->d_pool64, h->d_status,
-                    h->ws.d_acc64, h->ws.d_io, h->ws.d_part, h->d_csr_off, h->d_csr_idx, h->ws.d_xpl};
+                    h->ws.d_acc64, h->ws.d_io, h->ws.d_part, h->d_csr_off, h->d_csr_idx, h->ws.d_xpl, h->ws.d_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &kv : h->levels) {
@@ -179,6 +204,8 @@ static void free_handle(hm_matrix h)
         if (kv.second.d_tcu) cudaFree(kv.second.d_tcu);
         if (kv.second.d_tcp) cudaFree(kv.second.d_tcp);
         if (kv.second.d_xch) cudaFree(kv.second.d_xch);
+        if (kv.second.d_rcu) cudaFree(kv.second.d_rcu);
+        if (kv.second.d_rcp) cudaFree(kv.second.d_rcp);
     }
     for (void *p : h->ws.vec32) if (p) cudaFree(p);
     for (void *p : h->ws.vec64) if (p) cudaFree(p);
@@ -319,6 +346,9 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
     if (ws.d_xpl) cudaFree(ws.d_xpl);
     ws.d_xpl = nullptr;
     ws.xpl_bytes = 0;
+    if (ws.d_own) cudaFree(ws.d_own);   // owner sums: ensure_own
+    ws.d_own = nullptr;
+    ws.own_bytes = 0;
     if (r >= MRHS_MIN_RHS && h->tc_max_xch > 0) {   // split x of the tensor-core product (it can be pinned from 4 RHS)
         ws.xpl_bytes = tc_xplane_bytes(h->tc_max_xch, r);
         HM_CUDA(cudaMalloc((void **)&ws.d_xpl, ws.xpl_bytes));
@@ -327,6 +357,40 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
     ws.part_rhs = std::min(r, RESID_CHUNK);   // the partial slots themselves: ensure_partials
     ws.nrhs = r;
     return HM_OK;
+}
+
+// FP64 owner sums of the owner-computes residual ([level][RHS][pN] for the
+// workspace's RHS count and m levels); allocated only by the calls that form a
+// residual with that kernel, before any capture
+static hm_status ensure_own(hm_matrix h, int m)
+{
+    hm::Workspace &ws = h->ws;
+    const size_t bytes = sizeof(double2) * (size_t)std::max(m, 1) * (size_t)ws.nrhs * (size_t)h->pN;
+    if (ws.d_own && ws.own_bytes >= bytes) return HM_OK;
+    clear_graphs(h);   // graphs hold the old pointer
+    if (ws.d_own) {
+        cudaFree(ws.d_own);
+        ws.dev_bytes -= (int64_t)ws.own_bytes;
+    }
+    ws.d_own = nullptr;
+    ws.own_bytes = 0;
+    HM_CUDA(cudaMalloc((void **)&ws.d_own, bytes));
+    ws.own_bytes = bytes;
+    ws.dev_bytes += (int64_t)bytes;
+    return HM_OK;
+}
+
+// the owner-computes residual applies when every level 1..m holds only items it takes
+static bool own_applies(hm_matrix h, int m)
+{
+    bool any = false;
+    for (int lev = 1; lev <= m; ++lev) {
+        auto it = h->levels.find(lev);
+        if (it == h->levels.end() || it->second.items.empty()) continue;
+        if (it->second.n_big > 0) return false;
+        any = true;
+    }
+    return any;
 }
 
 // FP64 partial slots of the residual products (ws.part_rhs right-hand sides at a
@@ -451,6 +515,21 @@ static int clamp_levels(hm_matrix h, int n_levels)
 static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *out, double *norms)
 {
     hm_matrix h = c.h;
+    if (c.res_rb == RB_OWN && h->ws.d_own &&
+        h->ws.own_bytes >= sizeof(double2) * (size_t)c.m * (size_t)c.nrhs * (size_t)h->pN && own_applies(h, c.m)) {
+        // owner-computes: each level's sums into its own FP64 [RHS][pN] array, then one gather
+        const int64_t lstride = (int64_t)c.nrhs * h->pN;
+        cudaMemsetAsync(h->ws.d_own, 0, sizeof(double2) * (size_t)c.m * (size_t)lstride, c.s);
+        for (int lev = 1; lev <= c.m; ++lev) {
+            auto it = h->levels.find(lev);
+            if (it == h->levels.end() || it->second.items.empty()) continue;
+            launch_resid_own(h, it->second, xt, h->ws.d_own + (int64_t)(lev - 1) * lstride, c.nrhs, c.s);
+            c.launches++;
+        }
+        launch_gather_own(h, xt, c.m, h->ws.d_own, lstride, bt, out, norms, c.nrhs, c.s);
+        c.launches += 2;
+        return;
+    }
     const int chunk = std::max(1, h->ws.part_rhs);
     for (int r0 = 0; r0 < c.nrhs; r0 += chunk) {
         const int nr = std::min(chunk, c.nrhs - r0);
@@ -532,17 +611,27 @@ static hm_status autotune(hm_matrix h, int nrhs_req, int m, cudaStream_t s, bool
         if ((st = time_it([&] { launch_apply_items(h, L, x, z, nrhs, false, s, rb); }, ms)) != HM_OK) break;
         if (ms < best) { best = ms; t.prod_rb = rb; t.prod_ms = ms; }
     }
+    // residual candidates, compared per right-hand side: the partial-slot kernels time a chunk of nr,
+    // the owner-computes kernel all nrhs at once (when every level of the call takes it)
     const int nr = std::min(nrhs, std::max(1, h->ws.part_rhs));
     best = 1e30;
-    const int res_c[] = {0, 8, 16};
+    const int res_c[] = {0, 8, 16, RB_OWN};
     for (int rb : res_c) {
         if (st != HM_OK || !residual) break;
-        if (rb > 8 && rb / 2 >= nr) continue;
+        if (rb == RB_OWN) {
+            if (!own_applies(h, m) || L.n_rcu == 0) continue;
+            if ((st = ensure_own(h, m)) != HM_OK) break;
+        } else if (rb > 8 && rb / 2 >= nr) {
+            continue;
+        }
         double ms = 0;
-        if ((st = time_it([&] { launch_apply_items_partials(h, L, x, h->ws.d_part, h->partial_elems, nr, s, rb); },
-                          ms)) != HM_OK)
-            break;
-        if (ms < best) { best = ms; t.res_rb = rb; t.res_ms = ms; }
+        if (rb == RB_OWN)
+            st = time_it([&] { launch_resid_own(h, L, x, h->ws.d_own, nrhs, s); }, ms);
+        else
+            st = time_it([&] { launch_apply_items_partials(h, L, x, h->ws.d_part, h->partial_elems, nr, s, rb); }, ms);
+        if (st != HM_OK) break;
+        const double per_rhs = ms / (rb == RB_OWN ? nrhs : nr);
+        if (per_rhs < best) { best = per_rhs; t.res_rb = rb; t.res_ms = ms; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -595,6 +684,7 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
     if (!c.fp64) {
         if ((st = autotune(h, nrhs, c.m, s, resid)) != HM_OK) return st;
         use_tuning(c);
+        if (resid && c.res_rb == RB_OWN && own_applies(h, c.m) && (st = ensure_own(h, c.m)) != HM_OK) return st;
     }
     const bool use_graph = o->graph && !info && !h->prof;
     hm_matrix_s::GraphKey key{b, x, ldb, ldx, nrhs, c.K, c.m, o->nested, o->refine, o->fp64};
@@ -946,6 +1036,8 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
     if (fp64_accumulate && (st = ensure_partials(h)) != HM_OK) return st;
     if ((st = autotune(h, nrhs, c.m, s, fp64_accumulate != 0)) != HM_OK) return st;
     use_tuning(c);
+    if (fp64_accumulate && c.res_rb == RB_OWN && own_applies(h, c.m) && (st = ensure_own(h, c.m)) != HM_OK)
+        return st;
     void *xt = h->ws.vec32[0], *yt = h->ws.vec32[1];
     launch_permute_in(x, ldx, xt, h->pN, h->d_pperm, nrhs, false, s);
     if (fp64_accumulate) {
@@ -978,6 +1070,7 @@ hm_status hm_residual(hm_matrix h, const void *b, int64_t ldb, const void *x, in
     if ((st = ensure_partials(h)) != HM_OK) return st;
     if ((st = autotune(h, nrhs, c.m, s, true)) != HM_OK) return st;
     use_tuning(c);
+    if (c.res_rb == RB_OWN && own_applies(h, c.m) && (st = ensure_own(h, c.m)) != HM_OK) return st;
     void *bt = h->ws.vec32[0], *xt = h->ws.vec32[1], *rt = h->ws.vec32[3];
     launch_permute_in(b, ldb, bt, h->pN, h->d_pperm, nrhs, false, s);
     launch_permute_in(x, ldx, xt, h->pN, h->d_pperm, nrhs, false, s);
@@ -1050,8 +1143,8 @@ hm_status hm_set_tuning(hm_matrix h, int nrhs, int prod_rb, int res_rb)
     if (!h) return fail(HM_ERR_ARG, "null handle");
     if (nrhs < MRHS_MIN_RHS) return fail(HM_ERR_ARG, "kernel choices apply from 4 right-hand sides on");
     const bool pok = prod_rb == 0 || prod_rb == 8 || prod_rb == 16 || prod_rb == 32 || prod_rb == RB_TC;
-    const bool rok = res_rb == 0 || res_rb == 8 || res_rb == 16;
-    if (!pok || !rok) return fail(HM_ERR_ARG, "prod_rb must be 0, 8, 16, 32 or 1016 and res_rb 0, 8 or 16");
+    const bool rok = res_rb == 0 || res_rb == 8 || res_rb == 16 || res_rb == RB_OWN;
+    if (!pok || !rok) return fail(HM_ERR_ARG, "prod_rb must be 0, 8, 16, 32 or 1016 and res_rb 0, 8, 16 or 1017");
     hm_matrix_s::Tune t;
     t.prod_rb = prod_rb;
     t.res_rb = res_rb;

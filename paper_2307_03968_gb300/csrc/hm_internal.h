@@ -34,6 +34,7 @@ constexpr int RB_TC = 1016;         // product choice: tensor-core products of t
 constexpr int TC_MAX_DIM = MRHS_MAX_DIM;    // the tensor-core product takes the same small items
 constexpr int TC_MAX_RANK = MRHS_MAX_RANK;
 constexpr int TC_MIN_RHS = 32;      // the autotuner times the tensor-core product from this many RHS on
+constexpr int RB_OWN = 1017;        // residual choice: owner-computes FP64-class products (levels of small items)
 
 // One stored block = one work item of the product kernels (32 bytes).
 struct Item {
@@ -91,6 +92,11 @@ struct LevelList {
     TcProd *d_tcp = nullptr;
     TcUnit *d_tcu = nullptr;
     int64_t n_tcp = 0, n_tcu = 0;
+    // the same directed products with one unit per output cluster (the owner-computes
+    // FP64-class residual: each output row summed by one CTA in a fixed order)
+    TcProd *d_rcp = nullptr;
+    TcUnit *d_rcu = nullptr;
+    int64_t n_rcu = 0;
     // the input clusters' K chunks of 8 unknowns (padded-tree offset, valid length):
     // the tensor-core product splits x once per launch into these chunks
     int2 *d_xch = nullptr;
@@ -113,6 +119,8 @@ struct Workspace {
     int64_t dev_bytes = 0;        // device bytes held by the vectors, norms and partial slots
     float *d_xpl = nullptr;       // split x chunks of the tensor-core product (16 KB per chunk and RHS tile)
     size_t xpl_bytes = 0;
+    double2 *d_own = nullptr;     // FP64 owner sums of the residual, [level][RHS][pN]
+    size_t own_bytes = 0;
 };
 
 } // namespace hm
@@ -273,6 +281,11 @@ void launch_apply_items_mrhs(hm_matrix h, const LevelList &L, const float2 *x, f
 // the same for an explicit list of small items (k_mrhs.cu)
 void launch_apply_list_mrhs(hm_matrix h, const LevelList &L, const Item *items, int64_t n_items, const float2 *x,
                             float2 *z, int nrhs, int rb, cudaStream_t s);
+// owner-computes FP64-class products of a level's small items into own ([RHS][pN]) and the gather
+// out = b - (D x + sum of the m levels' owner sums) (k_resid_own.cu)
+void launch_resid_own(hm_matrix h, const LevelList &L, const float2 *x, double2 *own, int nrhs, cudaStream_t s);
+void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, int64_t lstride, const float2 *b,
+                       float2 *out, double *norms, int nrhs, cudaStream_t s);
 // bytes of the split-x workspace of the tensor-core product for n_xch chunks and nrhs (k_mrhs_tc.cu)
 size_t tc_xplane_bytes(int64_t n_xch, int nrhs);
 // tensor-core products of a level's small items for all right-hand sides (k_mrhs_tc.cu);

@@ -1,0 +1,217 @@
+// FP64-class residual products for many right-hand sides, owner-computes form
+// (the refinement residual r = b - A_m x of the solve; the block products are
+// eq. 6 and eq. 8 of arxiv 2307.03968 with the half storage of §III).
+//
+// A work unit is one output cluster O of a level and one group of 16 right-hand
+// sides.  The CTA walks every directed product into O (the stored blocks with O
+// as row cluster, and mirrored, those with O as column cluster; dense or
+// low-rank), in a fixed order, and keeps the sums in registers as double-float
+// complex numbers (Dot2: every product split exactly by an FMA, every sum
+// compensated).  Thread t owns output row t % 64 and right-hand sides
+// 8 (t / 64) .. +7.  The unit's sums are stored once, in FP64, into the level's
+// [RHS][pN] array: no partial slots, no atomics, and the result is independent
+// of scheduling.  k_gather_own then forms b - (D x + sum over levels) in FP64.
+//
+// Shared-memory staging keeps every compute read consecutive along the output
+// row: a dense block is stored K-major (element (K index j, output i) at
+// j * 65 + i), whichever orientation the product reads it in; a low-rank
+// block's input-side factor W is stored K-major over its rank rows and its
+// output-side factor Y rank-major.
+#include "k_dot2.cuh"
+
+namespace hm {
+namespace {
+
+using namespace kc;
+using namespace dot2;
+constexpr int RT = 128;          // threads: 64 output rows x 2 groups of 8 right-hand sides
+constexpr int RG = 16;           // right-hand sides per unit
+constexpr int BS = 65;           // float2 stride of a staged K row of a block (odd: conflict-free staging)
+constexpr int WS = 33;           // float2 stride of a staged K row of W (rank <= 32)
+constexpr int XS = 18;           // float2 stride of a staged K row of x (16 RHS, 16-byte aligned rows)
+constexpr int SM_B = 64 * WS + 32 * BS;   // float2: W (64 x WS) then Y (32 x BS), or a dense block (64 x BS)
+constexpr int SM_X = 64 * XS;
+constexpr int SM_T = 32 * RG;    // cdf: T = W x (rank x 16 RHS)
+static_assert(64 * BS <= SM_B, "a dense block fits the block area");
+
+struct alignas(16) Smem {
+    float2 b[SM_B];
+    float2 x[SM_X];
+    cdf t[SM_T];
+};
+
+// stage x of the input cluster: xs[j * XS + q] = x[(r0 + q) * ldx + in0 + j] for j < klen, q < nr (else 0)
+__device__ __forceinline__ void stage_x(float2 *xs, const float2 *__restrict__ x, int64_t ldx, int r0, int nr, int in0,
+                                        int klen)
+{
+    for (int e = threadIdx.x; e < RG * 64; e += RT) {
+        const int q = e >> 6, j = e & 63;
+        if (j >= klen) continue;
+        xs[j * XS + q] = q < nr ? x[(int64_t)(r0 + q) * ldx + in0 + j] : make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(RT, 4)
+k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restrict__ prods,
+            const float2 *__restrict__ pool, const float2 *__restrict__ x, int64_t ldx, int nrhs,
+            double2 *__restrict__ own, int64_t ldo)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Smem &S = *reinterpret_cast<Smem *>(smraw);
+    const int tid = threadIdx.x, i = tid & 63, hh = tid >> 6;
+    const int n_groups = (nrhs + RG - 1) / RG;
+    const int64_t total = (int64_t)n_units * n_groups;
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        const TcUnit U = units[u % n_units];
+        const int r0 = (int)(u / n_units) * RG, nr = min(RG, nrhs - r0);
+        cdf acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = cdf_zero();
+        for (int p = U.p0; p < U.p1; ++p) {
+            const TcProd P = prods[p];
+            __syncthreads();                                  // the previous product's reads are done
+            stage_x(S.x, x, ldx, r0, nr, P.in0, P.klen);
+            if (P.rank == 0) {
+                // block elements (output i < olen, K j < klen) into b[j * BS + i]
+                const float2 *B = pool + P.b_off;
+                const int rows = P.trans ? P.klen : P.olen;
+                for (int e = tid; e < rows * 64; e += RT) {
+                    const int a = e >> 6, c = e & 63;         // source row a, column c (coalesced along c)
+                    if (P.trans) {                            // element (i = c, j = a) = B[a][c]
+                        if (a < P.klen && c < P.olen) S.b[a * BS + c] = B[(int64_t)a * P.b_ld + c];
+                    } else {                                  // element (i = a, j = c) = B[a][c]
+                        if (a < P.olen && c < P.klen) S.b[c * BS + a] = B[(int64_t)a * P.b_ld + c];
+                    }
+                }
+                __syncthreads();
+                if (i < P.olen) {
+                    for (int j = 0; j < P.klen; ++j) {
+                        const float2 bv = S.b[j * BS + i];
+                        const float4 *xv = reinterpret_cast<const float4 *>(S.x + j * XS + 8 * hh);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 v = xv[q];
+                            cdot2(acc[2 * q], bv, make_float2(v.x, v.y));
+                            cdot2(acc[2 * q + 1], bv, make_float2(v.z, v.w));
+                        }
+                    }
+                }
+            } else {
+                // W (rank rows l, K j) into b[j * WS + l]; Y (element (i, l) = Y[l][i]) into y[l * BS + i]
+                float2 *Wsm = S.b, *Ysm = S.b + 64 * WS;
+                const float2 *W = pool + P.b_off, *Y = pool + P.y_off;
+                for (int e = tid; e < P.rank * 64; e += RT) {
+                    const int l = e >> 6, c = e & 63;
+                    if (c < P.klen) Wsm[c * WS + l] = W[(int64_t)l * P.b_ld + c];
+                    if (c < P.olen) Ysm[l * BS + c] = Y[(int64_t)l * P.y_ld + c];
+                }
+                __syncthreads();
+                // stage 1: T[l][q] = sum_j W[l][j] x[j][q], one rank row l per round; thread
+                // (q = (tid / 8) % 16, K slice ks = tid % 8: j = ks, ks + 8, ...), the eight slices
+                // combined by compensated additions across lanes
+                {
+                    const int ks = tid & 7, q = (tid >> 3) & 15;
+                    for (int l = 0; l < P.rank; ++l) {
+                        cdf t = cdf_zero();
+                        for (int j = ks; j < P.klen; j += 8) cdot2(t, Wsm[j * WS + l], S.x[j * XS + q]);
+#pragma unroll
+                        for (int sh = 1; sh < 8; sh <<= 1) t = cdf_add(t, shfl_xor(t, sh));
+                        if (ks == 0) S.t[l * RG + q] = t;
+                    }
+                }
+                __syncthreads();
+                // stage 2: out[i][q] += sum_l Y[i][l] T[l][q]
+                if (i < P.olen) {
+                    for (int l = 0; l < P.rank; ++l) {
+                        const float2 yv = Ysm[l * BS + i];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) cdot2_df(acc[q], yv, S.t[l * RG + 8 * hh + q]);
+                    }
+                }
+            }
+        }
+        if (i < U.mlen) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int r = 8 * hh + q;
+                if (r < nr) own[(int64_t)(r0 + r) * ldo + U.out0 + i] = to_d2(acc[q]);
+            }
+        }
+    }
+}
+
+// Per leaf (blockIdx.x) and right-hand side (blockIdx.y): acc = D_I x_I + the
+// owner sums of levels 1..m at the leaf's rows, in FP64 and in a fixed order.
+// If b is given, out = b - acc (complex64) and |r|^2, |b|^2 go to norms; else
+// out = acc (complex64).
+__global__ void __launch_bounds__(64)
+k_gather_own(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
+             const float2 *__restrict__ self32, const float2 *__restrict__ x, int64_t ld, int m,
+             const double2 *__restrict__ own, int64_t lstride, const float2 *__restrict__ b, float2 *__restrict__ out,
+             double *norms)
+{
+    __shared__ double2 xs[128];
+    const int leaf = blockIdx.x, r = blockIdx.y, tid = threadIdx.x, lane = tid & 31;
+    const int o = pleaf_off[leaf], np = pleaf_off[leaf + 1] - o;
+    double rr = 0.0, bb = 0.0;
+    for (int j = tid; j < np; j += 64) xs[j] = conv<double2>(x[r * ld + o + j]);
+    __syncthreads();
+    const float2 *Sd = self32 + dinv_off[leaf];                 // column-major np x np
+    for (int i = tid; i < np; i += 64) {
+        const int64_t g = r * ld + o + i;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int j = 0; j < np; ++j) cfma(acc, conv<double2>(Sd[(int64_t)j * np + i]), xs[j]);
+        for (int lev = 0; lev < m; ++lev) acc = cadd(acc, own[lev * lstride + g]);
+        if (b) {
+            const double2 bv = conv<double2>(b[g]);
+            const double2 rv = csub(bv, acc);
+            out[g] = make_float2((float)rv.x, (float)rv.y);
+            rr += rv.x * rv.x + rv.y * rv.y;
+            bb += bv.x * bv.x + bv.y * bv.y;
+        } else {
+            out[g] = make_float2((float)acc.x, (float)acc.y);
+        }
+    }
+    if (norms) {
+        for (int s = 16; s >= 1; s >>= 1) {
+            rr += __shfl_xor_sync(FULL, rr, s);
+            bb += __shfl_xor_sync(FULL, bb, s);
+        }
+        if (lane == 0) {
+            atomicAdd(&norms[2 * r], rr);
+            atomicAdd(&norms[2 * r + 1], bb);
+        }
+    }
+}
+
+} // namespace
+
+// owner-computes FP64-class products of a level's small items: own[r * pN + i] = (M_level x_r)_i
+// for the level's output rows (a level whose items are all small; the rest of own is untouched)
+void launch_resid_own(hm_matrix h, const LevelList &L, const float2 *x, double2 *own, int nrhs, cudaStream_t s)
+{
+    if (L.n_rcu == 0 || nrhs <= 0) return;
+    constexpr int SMEM = (int)sizeof(Smem);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_resid_own, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_resid_own, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        attr = true;
+    }
+    // four CTAs of ~50 KB per SM (the occupancy query under-reports with large dynamic shared memory)
+    const int64_t units = L.n_rcu * (int64_t)((nrhs + RG - 1) / RG);
+    int64_t g = 4 * (int64_t)(h->num_sms > 0 ? h->num_sms : 1);
+    if (g > units) g = units;
+    k_resid_own<<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, h->d_pool32, x, h->pN, nrhs, own, h->pN);
+}
+
+void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, int64_t lstride, const float2 *b,
+                       float2 *out, double *norms, int nrhs, cudaStream_t s)
+{
+    dim3 grid((unsigned)h->n_leaves, (unsigned)nrhs);
+    k_gather_own<<<grid, 64, 0, s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_self32, x, h->pN, m, own, lstride, b, out,
+                                     norms);
+}
+
+} // namespace hm

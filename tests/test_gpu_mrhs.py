@@ -144,7 +144,7 @@ def test_autotuner_records_a_choice(torch_cuda, operators):
     yt = torch_cuda.empty_like(xt)
     A.apply(xt, yt, n_levels=-1, fp64_accumulate=False)      # first call with 24 RHS: tunes
     prod_rb, res_rb, prod_ms, res_ms = A.tuning(24)
-    assert prod_rb in (0, 8, 16, 32) and res_rb in (0, 8, 16)
+    assert prod_rb in (0, 8, 16, 32) and res_rb in (0, 8, 16, 1017)
     assert prod_ms > 0 and res_ms > 0
     again = torch_cuda.empty_like(xt)
     A.apply(xt, again, n_levels=-1, fp64_accumulate=False)   # tuned choice is kept
@@ -153,3 +153,41 @@ def test_autotuner_records_a_choice(torch_cuda, operators):
     with pytest.raises(HmError) as e:
         A.tuning(3)                                           # below the many-RHS threshold: nothing to tune
     assert e.value.status == HM_ERR_STATE
+
+
+@pytest.mark.parametrize("name", ["rwg_binary15", "swg_slab", "rwg_octree64"])
+@pytest.mark.parametrize("nrhs", [4, 17, 40])
+def test_owner_residual_equals_partial_slot_residual(torch_cuda, operators, name, nrhs):
+    # the owner-computes FP64-class residual (one CTA per output cluster and 16 RHS,
+    # FP64 sums without partial slots) against the partial-slot kernel (one RHS at a
+    # time) on the leaf level, where every block is small; both are FP64-class, so
+    # they agree far below the complex64 rounding of r
+    A = operators[name]
+    N = A.n
+    rng = np.random.default_rng(200 + nrhs)
+    x = (rng.normal(size=(nrhs, N)) + 1j * rng.normal(size=(nrhs, N))).astype(np.complex64)
+    xt = torch_cuda.from_numpy(x).cuda()
+    ax = torch_cuda.empty_like(xt)
+    A.apply(xt, ax, n_levels=1, fp64_accumulate=True)
+    b = ax.cpu().numpy() + (1e-5 * (rng.normal(size=(nrhs, N)) + 1j * rng.normal(size=(nrhs, N)))).astype(np.complex64)
+    bt = torch_cuda.from_numpy(b).cuda()
+    A.set_tuning(nrhs, 0, 0)
+    r0 = torch_cuda.empty_like(xt)
+    rr0, bb0 = A.residual(bt, xt, r0, n_levels=1)
+    A.set_tuning(nrhs, 0, 1017)
+    r1 = torch_cuda.empty_like(xt)
+    rr1, bb1 = A.residual(bt, xt, r1, n_levels=1)
+    want, got = r0.cpu().numpy(), r1.cpu().numpy()
+    for r in range(nrhs):
+        assert np.abs(got[r] - want[r]).max() <= 1e-6 * np.abs(want[r]).max(), r
+        assert rr1[r] == pytest.approx(rr0[r], rel=1e-9)
+        assert bb1[r] == pytest.approx(bb0[r], rel=1e-12)
+    # a refined solve through the owner residual equals the one through the partial slots
+    A.set_tuning(nrhs, 0, 0)
+    s0 = torch_cuda.empty_like(xt)
+    A.solve(bt, s0, n_terms=2, n_levels=1, refine=True)
+    A.set_tuning(nrhs, 0, 1017)
+    s1 = torch_cuda.empty_like(xt)
+    A.solve(bt, s1, n_terms=2, n_levels=1, refine=True)
+    a0, a1 = s0.cpu().numpy(), s1.cpu().numpy()
+    assert (np.linalg.norm(a1 - a0, axis=1) / np.linalg.norm(a0, axis=1)).max() < 1e-6
