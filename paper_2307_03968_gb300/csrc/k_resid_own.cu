@@ -2,13 +2,14 @@
 // (the refinement residual r = b - A_m x of the solve; the block products are
 // eq. 6 and eq. 8 of arxiv 2307.03968 with the half storage of §III).
 //
-// A work unit is one output cluster O of a level and one group of 16 right-hand
-// sides.  The CTA walks every directed product into O (the stored blocks with O
+// A work unit is one output cluster O of a level and one group of RG right-hand
+// sides (16, or 8 for calls with few right-hand sides, so that there are enough
+// units to balance).  The CTA walks every directed product into O (the stored blocks with O
 // as row cluster, and mirrored, those with O as column cluster; dense or
 // low-rank), in a fixed order, and keeps the sums in registers as double-float
 // complex numbers (Dot2: every product split exactly by an FMA, every sum
 // compensated).  Thread t owns output row t % 64 and right-hand sides
-// 8 (t / 64) .. +7.  The unit's sums are stored once, in FP64, into the level's
+// (RG/2) (t / 64) .. +RG/2-1.  The unit's sums are stored once, in FP64, into the level's
 // [RHS][pN] array: no partial slots, no atomics, and the result is independent
 // of scheduling.  k_gather_own then forms b - (D x + sum over levels) in FP64.
 //
@@ -24,14 +25,14 @@ namespace {
 
 using namespace kc;
 using namespace dot2;
-constexpr int RT = 128;          // threads: 64 output rows x 2 groups of 8 right-hand sides
-constexpr int RG = 16;           // right-hand sides per unit
+constexpr int RT = 128;          // threads: 64 output rows x 2 halves of the unit's right-hand sides
+constexpr int RGMAX = 16;        // right-hand sides per unit (at most)
 constexpr int BS = 65;           // float2 stride of a staged K row of a block (odd: conflict-free staging)
 constexpr int WS = 33;           // float2 stride of a staged K row of W (rank <= 32)
 constexpr int XS = 18;           // float2 stride of a staged K row of x (16 RHS, 16-byte aligned rows)
 constexpr int SM_B = 64 * WS + 32 * BS;   // float2: W (64 x WS) then Y (32 x BS), or a dense block (64 x BS)
 constexpr int SM_X = 64 * XS;
-constexpr int SM_T = 32 * RG;    // cdf: T = W x (rank x 16 RHS)
+constexpr int SM_T = 32 * RGMAX; // cdf: T = W x (rank x RG RHS)
 static_assert(64 * BS <= SM_B, "a dense block fits the block area");
 
 struct alignas(16) Smem {
@@ -41,6 +42,7 @@ struct alignas(16) Smem {
 };
 
 // stage x of the input cluster: xs[j * XS + q] = x[(r0 + q) * ldx + in0 + j] for j < klen, q < nr (else 0)
+template <int RG>
 __device__ __forceinline__ void stage_x(float2 *xs, const float2 *__restrict__ x, int64_t ldx, int r0, int nr, int in0,
                                         int klen)
 {
@@ -51,6 +53,7 @@ __device__ __forceinline__ void stage_x(float2 *xs, const float2 *__restrict__ x
     }
 }
 
+template <int RG>
 __global__ void __launch_bounds__(RT, 4)
 k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restrict__ prods,
             const float2 *__restrict__ pool, const float2 *__restrict__ x, int64_t ldx, int nrhs,
@@ -58,19 +61,20 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     Smem &S = *reinterpret_cast<Smem *>(smraw);
+    constexpr int QN = RG / 2;        // right-hand sides per thread
     const int tid = threadIdx.x, i = tid & 63, hh = tid >> 6;
     const int n_groups = (nrhs + RG - 1) / RG;
     const int64_t total = (int64_t)n_units * n_groups;
     for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
         const TcUnit U = units[u % n_units];
         const int r0 = (int)(u / n_units) * RG, nr = min(RG, nrhs - r0);
-        cdf acc[8];
+        cdf acc[QN];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = cdf_zero();
+        for (int q = 0; q < QN; ++q) acc[q] = cdf_zero();
         for (int p = U.p0; p < U.p1; ++p) {
             const TcProd P = prods[p];
             __syncthreads();                                  // the previous product's reads are done
-            stage_x(S.x, x, ldx, r0, nr, P.in0, P.klen);
+            stage_x<RG>(S.x, x, ldx, r0, nr, P.in0, P.klen);
             if (P.rank == 0) {
                 // block elements (output i < olen, K j < klen) into b[j * BS + i]
                 const float2 *B = pool + P.b_off;
@@ -87,9 +91,9 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
                 if (i < P.olen) {
                     for (int j = 0; j < P.klen; ++j) {
                         const float2 bv = S.b[j * BS + i];
-                        const float4 *xv = reinterpret_cast<const float4 *>(S.x + j * XS + 8 * hh);
+                        const float4 *xv = reinterpret_cast<const float4 *>(S.x + j * XS + QN * hh);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < QN / 2; ++q) {
                             const float4 v = xv[q];
                             cdot2(acc[2 * q], bv, make_float2(v.x, v.y));
                             cdot2(acc[2 * q + 1], bv, make_float2(v.z, v.w));
@@ -106,17 +110,20 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
                     if (c < P.olen) Ysm[l * BS + c] = Y[(int64_t)l * P.y_ld + c];
                 }
                 __syncthreads();
-                // stage 1: T[l][q] = sum_j W[l][j] x[j][q], one rank row l per round; thread
-                // (q = (tid / 8) % 16, K slice ks = tid % 8: j = ks, ks + 8, ...), the eight slices
-                // combined by compensated additions across lanes
+                // stage 1: T[l][q] = sum_j W[l][j] x[j][q]; a round covers 128 / RG rank rows;
+                // thread (row l0 + tid / (8 RG), q = (tid / 8) % RG, K slice ks = tid % 8: j = ks,
+                // ks + 8, ...), the eight slices combined by compensated additions across lanes
                 {
-                    const int ks = tid & 7, q = (tid >> 3) & 15;
-                    for (int l = 0; l < P.rank; ++l) {
+                    constexpr int LR = RT / (8 * RG);              // rank rows per round
+                    const int ks = tid & 7, q = (tid >> 3) % RG, lr = tid / (8 * RG);
+                    for (int l0 = 0; l0 < P.rank; l0 += LR) {
+                        const int l = l0 + lr;
                         cdf t = cdf_zero();
-                        for (int j = ks; j < P.klen; j += 8) cdot2(t, Wsm[j * WS + l], S.x[j * XS + q]);
+                        if (l < P.rank)
+                            for (int j = ks; j < P.klen; j += 8) cdot2(t, Wsm[j * WS + l], S.x[j * XS + q]);
 #pragma unroll
                         for (int sh = 1; sh < 8; sh <<= 1) t = cdf_add(t, shfl_xor(t, sh));
-                        if (ks == 0) S.t[l * RG + q] = t;
+                        if (ks == 0 && l < P.rank) S.t[l * RG + q] = t;
                     }
                 }
                 __syncthreads();
@@ -125,15 +132,15 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
                     for (int l = 0; l < P.rank; ++l) {
                         const float2 yv = Ysm[l * BS + i];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) cdot2_df(acc[q], yv, S.t[l * RG + 8 * hh + q]);
+                        for (int q = 0; q < QN; ++q) cdot2_df(acc[q], yv, S.t[l * RG + QN * hh + q]);
                     }
                 }
             }
         }
         if (i < U.mlen) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int r = 8 * hh + q;
+            for (int q = 0; q < QN; ++q) {
+                const int r = QN * hh + q;
                 if (r < nr) own[(int64_t)(r0 + r) * ldo + U.out0 + i] = to_d2(acc[q]);
             }
         }
@@ -194,16 +201,24 @@ void launch_resid_own(hm_matrix h, const LevelList &L, const float2 *x, double2 
     constexpr int SMEM = (int)sizeof(Smem);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_resid_own, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        cudaFuncSetAttribute(k_resid_own, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+        for (const void *f : {(const void *)k_resid_own<8>, (const void *)k_resid_own<16>}) {
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+            cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        }
         attr = true;
     }
-    // four CTAs of ~50 KB per SM (the occupancy query under-reports with large dynamic shared memory)
-    const int64_t units = L.n_rcu * (int64_t)((nrhs + RG - 1) / RG);
+    // four CTAs of ~50 KB per SM (the occupancy query under-reports with large dynamic shared memory);
+    // groups of 8 right-hand sides up to 32 of them, so that small calls still have enough units
+    const int rg = nrhs <= 32 ? 8 : 16;
+    const int64_t units = L.n_rcu * (int64_t)((nrhs + rg - 1) / rg);
     int64_t g = 4 * (int64_t)(h->num_sms > 0 ? h->num_sms : 1);
     if (g > units) g = units;
-    k_resid_own<<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, h->d_pool32, x, h->pN, nrhs, own, h->pN);
+    if (rg == 8)
+        k_resid_own<8><<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, h->d_pool32, x, h->pN, nrhs, own,
+                                                     h->pN);
+    else
+        k_resid_own<16><<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, h->d_pool32, x, h->pN, nrhs, own,
+                                                      h->pN);
 }
 
 void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, int64_t lstride, const float2 *b,
