@@ -44,8 +44,7 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
                     const float2 xi = xs[8 * q + rr];
                     cdot2(cs0, b.a, xi);
                     cdot2(cs1, b.b, xi);
-                    rp[rr] = cdf_zero();
-                    cdot2(rp[rr], b.a, xj0);
+                    cdot2_first(rp[rr], b.a, xj0);
                     cdot2(rp[rr], b.b, xj1);
                 }
                 reduce_cdf<8>(rp, lane);
@@ -91,11 +90,9 @@ __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__r
             cdf tp[4], t[4];
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
-                tp[l] = cdf_zero();
-                cdot2(tp[l], u[l].a, xi.a);
+                cdot2_first(tp[l], u[l].a, xi.a);
                 cdot2(tp[l], u[l].b, xi.b);
-                t[l] = cdf_zero();
-                cdot2(t[l], v[l].a, xj.a);
+                cdot2_first(t[l], v[l].a, xj.a);
                 cdot2(t[l], v[l].b, xj.b);
             }
             reduce_cdf<4>(tp, lane);
