@@ -393,13 +393,13 @@ static bool own_applies(hm_matrix h, int m)
     return any;
 }
 
-// FP64 partial slots of the residual products (ws.part_rhs right-hand sides at a
+// Double-float partial slots of the residual products (ws.part_rhs right-hand sides at a
 // time); allocated only by the calls that form a residual, before any capture
 static hm_status ensure_partials(hm_matrix h)
 {
     hm::Workspace &ws = h->ws;
     if (ws.d_part) return HM_OK;
-    const size_t bytes = sizeof(double2) * std::max<int64_t>(h->partial_elems, 1) * std::max(ws.part_rhs, 1);
+    const size_t bytes = sizeof(dot2::cdf) * std::max<int64_t>(h->partial_elems, 1) * std::max(ws.part_rhs, 1);
     HM_CUDA(cudaMalloc((void **)&ws.d_part, bytes));
     ws.dev_bytes += (int64_t)bytes;
     return HM_OK;
@@ -511,7 +511,7 @@ static int clamp_levels(hm_matrix h, int n_levels)
 
 // out = b - A_m x (with |r|^2, |b|^2 per column into norms) when b is given, else
 // out = A_m x; complex64 blocks, FP64 products and sums, deterministic order:
-// every block writes its FP64 partial slots, then each leaf gathers its slots.
+// every block writes its double-float partial slots, then each leaf gathers its slots.
 static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *out, double *norms)
 {
     hm_matrix h = c.h;

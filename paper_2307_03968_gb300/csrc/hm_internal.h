@@ -36,6 +36,14 @@ constexpr int TC_MAX_RANK = MRHS_MAX_RANK;
 constexpr int TC_MIN_RHS = 32;      // the autotuner times the tensor-core product from this many RHS on
 constexpr int RB_OWN = 1017;        // residual choice: owner-computes FP64-class products (levels of small items)
 
+// Double-float numbers of the FP64-class residual (hi + lo, |lo| a few ulps of hi at
+// most): a real one, and a complex one of 16 bytes, which is also the element of
+// the residual's partial slots.
+namespace dot2 {
+struct df { float hi, lo; };
+struct alignas(16) cdf { df re, im; };
+} // namespace dot2
+
 // One stored block = one work item of the product kernels (32 bytes).
 struct Item {
     int64_t off;    // complex-element offset into the pool
@@ -43,7 +51,7 @@ struct Item {
     int32_t col0;   // padded-tree offset of the column cluster
     int32_t m, n;   // padded cluster lengths (dense: m = true rows, n = true cols)
     int32_t k;      // rank; 0 = dense block
-    int32_t pad;    // offset of the block's FP64 partial slot (row side, then column side)
+    int32_t pad;    // offset of the block's partial slots (row side, then column side)
 };
 static_assert(sizeof(Item) == 32, "Item layout");
 
@@ -110,7 +118,7 @@ struct Workspace {
     // complex vectors [nrhs][pN], allocated for the current nrhs, per precision
     std::vector<void *> vec32, vec64;
     double *d_acc64 = nullptr;    // norms of the residual (2 doubles per right-hand side)
-    double2 *d_part = nullptr;    // FP64 partial slots for PART_RHS right-hand sides
+    dot2::cdf *d_part = nullptr;  // double-float partial slots for PART_RHS right-hand sides
     int part_rhs = 0;
     void *h_pinned = nullptr;     // pinned staging for host-buffer solves
     size_t h_pinned_bytes = 0;
@@ -157,7 +165,7 @@ struct hm_matrix_s {
     bool has_fp64 = false;
     std::map<int, hm::LevelList> levels;
 
-    // partial slots of the deterministic FP64 products: per leaf and level, the
+    // partial slots of the deterministic FP64-class products: per leaf and level, the
     // list of slot positions holding contributions to that leaf's rows
     int64_t partial_elems = 0;
     int64_t *d_csr_off = nullptr;     // [n_leaves * (n_levels + 1)]
@@ -230,12 +238,12 @@ void launch_zero(void *p, size_t bytes, cudaStream_t s);
 // 8 / 16 / 32 = shared-memory multi-RHS kernel with that chunk for the blocks it takes
 void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
                         cudaStream_t s, int rb = -1);
-// FP64 products of every block of a level into its partial slots (no atomics)
-void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride,
+// FP64-class (Dot2) products of every block of a level into its partial slots (no atomics)
+void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part, int64_t pstride,
                                  int nrhs, cudaStream_t s, int rb = -1);
-// per leaf: acc = D x + sum of the leaf's partial slots of levels 1..m (FP64, fixed order);
+// per leaf: acc = D x + sum of the leaf's partial slots of levels 1..m (double-float, fixed order);
 // out = b - acc (+ norms) when b is given, else out = acc (rounded to complex64)
-void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const double2 *part, int64_t pstride,
+void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const dot2::cdf *part, int64_t pstride,
                          const float2 *b, float2 *out, double *norms, int nrhs, cudaStream_t s);
 void launch_apply_self_f32(hm_matrix h, const float2 *x, float2 *acc, int nrhs, cudaStream_t s);
 // per leaf: out = (y ? y - Dinv zin : Dinv zin); if zero_in, zin is cleared afterwards
@@ -269,7 +277,7 @@ hm_status swg_faces(int64_t nv, int64_t nt, const int32_t *tet, std::vector<int3
 
 // shared construction helpers (hm_api.cu)
 hm_status finalize_layout(hm_matrix h, cudaStream_t s);
-// assigns the FP64 partial slots (Item::pad) and uploads the per-leaf slot lists;
+// assigns the partial slots (Item::pad) and uploads the per-leaf slot lists;
 // call after every level list is complete and before the items are uploaded
 hm_status prepare_partials(hm_matrix h, cudaStream_t s);
 // uploads every level's item list and its multi-RHS split (small / big)
@@ -292,7 +300,7 @@ size_t tc_xplane_bytes(int64_t n_xch, int nrhs);
 // z accumulates (vector atomics); needs the split-x workspace for nrhs
 void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s);
 // the FP64-class partial-slot products of the small items for many right-hand sides (k_mrhs.cu)
-void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, double2 *part,
+void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part,
                                       int64_t pstride, int nrhs, cudaStream_t s, int rb = -1);
 
 } // namespace hm

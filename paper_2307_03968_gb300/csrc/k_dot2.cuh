@@ -20,8 +20,7 @@ using kc::FULL;
 // every sum is compensated (Knuth's TwoSum), so each block's sums are as
 // accurate as if computed in twice the working precision.  The per-block
 // results are stored as FP64 partial slots and summed across blocks in FP64.
-struct df { float hi, lo; };
-struct cdf { df re, im; };
+// df, cdf: hm_internal.h
 
 // The error-free transformations below must not be contracted into FMAs or
 // reassociated, so every operation is an explicitly rounded intrinsic.
@@ -67,13 +66,16 @@ __device__ __forceinline__ void cdot2_df(cdf &acc, float2 a, const cdf &b)
     acc.re.lo += a.x * b.re.lo - a.y * b.im.lo;
     acc.im.lo += a.x * b.im.lo + a.y * b.re.lo;
 }
+// a + b for double-float numbers: the leading parts summed exactly (TwoSum), the
+// error and trailing parts added into the trailing part.  The result is not
+// renormalised: its trailing part stays within a few ulps of the leading one over
+// the short sums it is used in (lane reductions), and hi + lo converts to FP64
+// exactly as it stands.
 __device__ __forceinline__ df df_add(df a, df b)
 {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    const float h = __fadd_rn(s, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+    return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
 }
 __device__ __forceinline__ cdf cdf_add(const cdf &a, const cdf &b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
 __device__ __forceinline__ cdf cdf_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }

@@ -11,7 +11,7 @@
 // thread owns 4 rows x RB/4 right-hand sides of the output (the two mirrored
 // products run side by side on the two halves of the CTA), so every
 // shared-memory load of the block feeds RB/4 complex FMAs; in the FP64-class
-// residual (compensated Dot2 sums, FP64 partial slots) it owns 2 rows x RB/4.
+// residual (compensated Dot2 sums, double-float partial slots) it owns 2 rows x RB/4.
 // Block rows have an odd stride (complex elements) so that the rows a warp
 // touches fall in distinct banks, and the shared buffers are sized for the
 // largest block and rank of the level, so that several CTAs per SM overlap one
@@ -224,7 +224,7 @@ k_apply_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *__re
 // ------------------------------------------------------------------------------
 // FP64-class residual products for many right-hand sides: the same staging, the
 // products accumulated by the error-free Dot2 steps, each block's results
-// stored in its FP64 partial slots (row side: even(m) slots from it.pad, column
+// stored in its double-float partial slots (row side: even(m) slots from it.pad, column
 // side: even(n) slots after them; no atomics, so the per-leaf FP64 gather that
 // follows stays deterministic).  Right-hand side q of the chunk writes
 // part[q * pstride + slot].
@@ -233,7 +233,7 @@ k_apply_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *__re
 // Y given (double-float staging, row stride xld) instead of slots: store there.
 template <int RB>
 __device__ __forceinline__ void mm_rows_c(const float2 *S, int sld, int R, int Rs, int C, const float2 *X, int xld,
-                                          dot2::cdf *Y, double2 *slots, int64_t pstride, int nr)
+                                          dot2::cdf *Y, dot2::cdf *slots, int64_t pstride, int nr)
 {
     using namespace dot2;
     constexpr int TC = RB / 4;
@@ -264,9 +264,9 @@ __device__ __forceinline__ void mm_rows_c(const float2 *S, int sld, int R, int R
             if (r + 1 < Rs) Y[(r + 1) * xld + q0 + q] = two ? a1[q] : cdf_zero();
         } else {
             if (q0 + q >= nr) break;
-            double2 *o = slots + (int64_t)(q0 + q) * pstride + r;
-            o[0] = to_d2(a0[q]);
-            if (r + 1 < Rs) o[1] = two ? to_d2(a1[q]) : make_double2(0.0, 0.0);
+            dot2::cdf *o = slots + (int64_t)(q0 + q) * pstride + r;
+            o[0] = a0[q];
+            if (r + 1 < Rs) o[1] = two ? a1[q] : cdf_zero();
         }
     }
 }
@@ -275,7 +275,7 @@ __device__ __forceinline__ void mm_rows_c(const float2 *S, int sld, int R, int R
 // X in FP32 (XF) or double-float (XD).
 template <int RB>
 __device__ __forceinline__ void mm_cols_c(const float2 *S, int sld, int R, int C, int Cs, const float2 *XF,
-                                          const dot2::cdf *XD, int xld, double2 *slots, int64_t pstride, int nr)
+                                          const dot2::cdf *XD, int xld, dot2::cdf *slots, int64_t pstride, int nr)
 {
     using namespace dot2;
     constexpr int TC = RB / 4;
@@ -311,16 +311,16 @@ __device__ __forceinline__ void mm_cols_c(const float2 *S, int sld, int R, int C
 #pragma unroll
     for (int q = 0; q < TC; ++q) {
         if (q0 + q >= nr) break;
-        double2 *o = slots + (int64_t)(q0 + q) * pstride + c;
-        o[0] = to_d2(a0[q]);
-        if (c + 1 < Cs) o[1] = two ? to_d2(a1[q]) : make_double2(0.0, 0.0);
+        dot2::cdf *o = slots + (int64_t)(q0 + q) * pstride + c;
+        o[0] = a0[q];
+        if (c + 1 < Cs) o[1] = two ? a1[q] : cdf_zero();
     }
 }
 
 template <int RB>
 __global__ void __launch_bounds__(MT)
 k_residual_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *__restrict__ pool,
-                const float2 *__restrict__ x, int64_t ldx, double2 *__restrict__ part, int64_t pstride, int nr,
+                const float2 *__restrict__ x, int64_t ldx, dot2::cdf *__restrict__ part, int64_t pstride, int nr,
                 Geom gm)
 {
     using dot2::cdf;
@@ -335,7 +335,7 @@ k_residual_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *_
         __syncthreads();
         stage_x<RB>(x, ldx, it.row0, it.m, nr, XI, gm.xld);
         stage_x<RB>(x, ldx, it.col0, it.n, nr, XJ, gm.xld);
-        double2 *rows = part + it.pad;
+        dot2::cdf *rows = part + it.pad;
         if (it.k == 0) {
             const int em = (int)even(it.m), en = (int)even(it.n);
             stage(pool + it.off, it.m, it.n, en, S, gm.sld);
@@ -374,7 +374,7 @@ Geom level_geom(const LevelList &L, int xld, size_t t_elem, size_t &bytes)
 }
 
 template <int RB>
-void launch_resid_rb(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride, int nrhs,
+void launch_resid_rb(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part, int64_t pstride, int nrhs,
                      cudaStream_t s)
 {
     size_t sm = 0;
@@ -444,7 +444,7 @@ void launch_apply_list_mrhs(hm_matrix h, const LevelList &L, const Item *items, 
 
 namespace hm {
 
-void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, double2 *part,
+void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part,
                                       int64_t pstride, int nrhs, cudaStream_t s, int rb)
 {
     if (L.n_small == 0 || nrhs <= 0) return;

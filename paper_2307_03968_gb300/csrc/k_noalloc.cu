@@ -14,8 +14,8 @@
 // The array is g_noalloc_scratch, NOALLOC_SCRATCH_BYTES (32 MiB) per GPU.  It
 // exists on every GPU that loads this library and is held until the process
 // exits.  Its layout per call: permuted b, x and r (complex64, padded length
-// times nrhs each), two FP64 norms per right-hand side, then the FP64 partial
-// slots of one right-hand side.  Calls whose sizes do not fit are rejected
+// times nrhs each), two FP64 norms per right-hand side, then the double-float
+// partial slots of one right-hand side.  Calls whose sizes do not fit are rejected
 // with HM_ERR_ARG before any device work.
 #include "hm_internal.h"
 
@@ -69,7 +69,7 @@ extern "C" hm_status hm_residual_noalloc(hm_matrix h, const void *b, int64_t ldb
     if (!h->factored) return fail(HM_ERR_STATE, "hm_factor_leaf has not completed (it also prepares D)");
     const size_t vec = align256(sizeof(float2) * (size_t)h->pN * nrhs);
     const size_t nrm = align256(2 * sizeof(double) * (size_t)nrhs);
-    const size_t part = sizeof(double2) * (size_t)std::max<int64_t>(h->partial_elems, 1);
+    const size_t part = sizeof(dot2::cdf) * (size_t)std::max<int64_t>(h->partial_elems, 1);
     const size_t need = 3 * vec + nrm + part;
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(HM_ERR_ARG, "operator and nrhs need " + std::to_string(need) + " bytes of scratch; the static "
@@ -80,7 +80,7 @@ extern "C" hm_status hm_residual_noalloc(hm_matrix h, const void *b, int64_t ldb
     unsigned char *p = (unsigned char *)base;
     float2 *bt = (float2 *)p, *xt = (float2 *)(p + vec), *rt = (float2 *)(p + 2 * vec);
     double *dn = (double *)(p + 3 * vec);
-    double2 *dpart = (double2 *)(p + 3 * vec + nrm);
+    dot2::cdf *dpart = (dot2::cdf *)(p + 3 * vec + nrm);
     cudaStream_t s = (cudaStream_t)stream;
     int m = (n_levels < 0 || n_levels > h->n_levels) ? h->n_levels : n_levels;
     if (m < 1) m = 1;

@@ -1,8 +1,9 @@
 // FP64-class residual of the refinement step, r = b - A_m x, over complex64
 // blocks (the precision rule of the solve: the final residual check runs at
 // FP64-class accuracy).  k_residual_items writes every block's products into
-// its FP64 partial slots (no atomics); k_gather_acc64 sums each leaf's slots in a
-// fixed order in FP64, adds D_I x_I and forms b - A x.
+// its double-float partial slots (no atomics); k_gather_acc64 sums each leaf's
+// slots in a fixed order with compensated additions, adds D_I x_I (Dot2) and
+// forms b - A x in FP64.
 #include "k_dot2.cuh"
 
 namespace hm {
@@ -14,7 +15,7 @@ constexpr int APPLY_WARPS = 8;
 
 // Dense block: slot rows (even(m)) = B x_J, slot columns (even(n)) = B^T x_I.
 __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__restrict__ pool,
-                                             const float2 *__restrict__ x, double2 *__restrict__ part, float2 *xs,
+                                             const float2 *__restrict__ x, cdf *__restrict__ part, float2 *xs,
                                              int lane)
 {
     const float2 *B = pool + it.off;
@@ -49,12 +50,12 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
                 }
                 reduce_cdf<8>(rp, lane);
                 const int row = rb + lane;
-                if (lane < 8 && row < em) part[it.pad + row] = to_d2(rp[0]);
+                if (lane < 8 && row < em) part[it.pad + row] = rp[0];
             }
         }
         if (jv) {
-            part[it.pad + em + j] = to_d2(cs0);
-            part[it.pad + em + j + 1] = to_d2(cs1);
+            part[it.pad + em + j] = cs0;
+            part[it.pad + em + j + 1] = cs1;
         }
     }
 }
@@ -62,7 +63,7 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
 // Low-rank block U V: slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I);
 // the rank-k intermediates stay in double-float.
 __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__restrict__ pool,
-                                               const float2 *__restrict__ x, double2 *__restrict__ part, int lane)
+                                               const float2 *__restrict__ x, cdf *__restrict__ part, int lane)
 {
     const int m = it.m, n = it.n, k = it.k;
     const float2 *UT = pool + it.off;
@@ -107,8 +108,8 @@ __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__r
                 cdot2_df(oj1, v[l].b, tpl);
             }
         }
-        if (iv) { part[it.pad + i] = to_d2(oi0); part[it.pad + i + 1] = to_d2(oi1); }
-        if (jv) { part[it.pad + m + i] = to_d2(oj0); part[it.pad + m + i + 1] = to_d2(oj1); }
+        if (iv) { part[it.pad + i] = oi0; part[it.pad + i + 1] = oi1; }
+        if (jv) { part[it.pad + m + i] = oj0; part[it.pad + m + i + 1] = oj1; }
         return;
     }
     for (int l0 = 0; l0 < k; l0 += 4) {
@@ -155,10 +156,9 @@ __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__r
                     cdot2_df(o0, u.a, tb[l]);
                     cdot2_df(o1, u.b, tb[l]);
                 }
-            double2 *q = part + it.pad + i;
-            const double2 a0 = to_d2(o0), a1 = to_d2(o1);
-            if (l0 == 0) { q[0] = a0; q[1] = a1; }
-            else { q[0] = cadd(q[0], a0); q[1] = cadd(q[1], a1); }
+            cdf *q = part + it.pad + i;
+            if (l0 == 0) { q[0] = o0; q[1] = o1; }
+            else { q[0] = cdf_add(q[0], o0); q[1] = cdf_add(q[1], o1); }
         }
         for (int c0 = 0; c0 < n; c0 += 64) {
             const int j = c0 + 2 * lane;
@@ -171,17 +171,16 @@ __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__r
                     cdot2_df(o0, v.a, tpb[l]);
                     cdot2_df(o1, v.b, tpb[l]);
                 }
-            double2 *q = part + it.pad + m + j;
-            const double2 a0 = to_d2(o0), a1 = to_d2(o1);
-            if (l0 == 0) { q[0] = a0; q[1] = a1; }
-            else { q[0] = cadd(q[0], a0); q[1] = cadd(q[1], a1); }
+            cdf *q = part + it.pad + m + j;
+            if (l0 == 0) { q[0] = o0; q[1] = o1; }
+            else { q[0] = cdf_add(q[0], o0); q[1] = cdf_add(q[1], o1); }
         }
     }
 }
 
 __global__ void __launch_bounds__(APPLY_WARPS * 32, 2)
 k_residual_items(const Item *__restrict__ items, int64_t n_items, const float2 *__restrict__ pool,
-                 const float2 *__restrict__ x, int64_t ldx, double2 *__restrict__ part, int64_t pstride, int nrhs)
+                 const float2 *__restrict__ x, int64_t ldx, cdf *__restrict__ part, int64_t pstride, int nrhs)
 {
     __shared__ float2 xs_all[APPLY_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -196,50 +195,52 @@ k_residual_items(const Item *__restrict__ items, int64_t n_items, const float2 *
 }
 
 // Per leaf (blockIdx.x) and right-hand side (blockIdx.y): acc = D_I x_I +
-// sum of the leaf's partial slots of levels 1..m, in FP64 and in a fixed order
-// (each of the 4 warps sums every 4th slot, lanes own row pairs; the warps are
-// then added in warp order).  If b is given, out = b - acc (complex64) and
-// |r|^2, |b|^2 go to norms; else out = acc (complex64).  No atomics on sums.
+// sum of the leaf's partial slots of levels 1..m, in double-float arithmetic and
+// in a fixed order (each of the 4 warps sums every 4th slot with compensated
+// additions, lanes own row pairs, warp 0 adds D_I x_I with Dot2; the warps are
+// then added in warp order).  If b is given, out = b - acc (in FP64, rounded to
+// complex64) and |r|^2, |b|^2 go to norms; else out = acc (complex64).  No
+// atomics on sums.
 __global__ void __launch_bounds__(128)
 k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
                const float2 *__restrict__ self32, const float2 *__restrict__ x, int64_t ld,
                const int64_t *__restrict__ csr_off, int csr_stride, int m, const int64_t *__restrict__ csr_idx,
-               const double2 *__restrict__ part, int64_t pstride, const float2 *__restrict__ b,
+               const cdf *__restrict__ part, int64_t pstride, const float2 *__restrict__ b,
                float2 *__restrict__ out, double *norms)
 {
     constexpr int MAXR = 128;
-    __shared__ double2 acc_s[4][MAXR];
-    __shared__ double2 xs[MAXR];
+    __shared__ cdf acc_s[4][MAXR];
+    __shared__ float2 xs[MAXR];
     const int leaf = blockIdx.x, r = blockIdx.y;
     const int o = pleaf_off[leaf], np = pleaf_off[leaf + 1] - o;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int j = tid; j < np; j += blockDim.x) xs[j] = conv<double2>(x[r * ld + o + j]);
+    for (int j = tid; j < np; j += blockDim.x) xs[j] = x[r * ld + o + j];
     __syncthreads();
-    const double2 *P = part + r * pstride;
+    const cdf *P = part + r * pstride;
     const int64_t e0 = csr_off[(int64_t)leaf * csr_stride], e1 = csr_off[(int64_t)leaf * csr_stride + m];
     for (int rc = 0; rc < np; rc += 64) {
         const int i = rc + 2 * lane;
-        double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
+        cdf a0 = cdf_zero(), a1 = cdf_zero();
         if (i < np) {
             int64_t e = e0 + w;
             for (; e + 12 < e1; e += 16) {      // four slots in flight per warp
                 const int64_t q0 = csr_idx[e], q1 = csr_idx[e + 4], q2 = csr_idx[e + 8], q3 = csr_idx[e + 12];
-                const double2 v00 = P[q0 + i], v01 = P[q0 + i + 1], v10 = P[q1 + i], v11 = P[q1 + i + 1];
-                const double2 v20 = P[q2 + i], v21 = P[q2 + i + 1], v30 = P[q3 + i], v31 = P[q3 + i + 1];
-                a0 = cadd(a0, cadd(cadd(v00, v10), cadd(v20, v30)));
-                a1 = cadd(a1, cadd(cadd(v01, v11), cadd(v21, v31)));
+                const cdf v00 = P[q0 + i], v01 = P[q0 + i + 1], v10 = P[q1 + i], v11 = P[q1 + i + 1];
+                const cdf v20 = P[q2 + i], v21 = P[q2 + i + 1], v30 = P[q3 + i], v31 = P[q3 + i + 1];
+                a0 = cdf_add(a0, cdf_add(cdf_add(v00, v10), cdf_add(v20, v30)));
+                a1 = cdf_add(a1, cdf_add(cdf_add(v01, v11), cdf_add(v21, v31)));
             }
             for (; e < e1; e += 4) {
                 const int64_t q = csr_idx[e];
-                a0 = cadd(a0, P[q + i]);
-                a1 = cadd(a1, P[q + i + 1]);
+                a0 = cdf_add(a0, P[q + i]);
+                a1 = cdf_add(a1, P[q + i + 1]);
             }
-            if (w == 0) {   // the self block, FP64
+            if (w == 0) {   // the self block, Dot2
                 const float2 *S = self32 + dinv_off[leaf];   // column-major
                 for (int j = 0; j < np; ++j) {
                     const Pair<float> d = ld_vec(S + (int64_t)j * np + i);
-                    cfma(a0, conv<double2>(d.a), xs[j]);
-                    cfma(a1, conv<double2>(d.b), xs[j]);
+                    cdot2(a0, d.a, xs[j]);
+                    cdot2(a1, d.b, xs[j]);
                 }
             }
         }
@@ -248,8 +249,9 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
         __syncthreads();
         double rr = 0.0, bb = 0.0;
         if (tid < 64 && rc + tid < np) {
-            double2 acc = acc_s[0][tid];
-            for (int q = 1; q < 4; ++q) acc = cadd(acc, acc_s[q][tid]);
+            cdf accf = acc_s[0][tid];
+            for (int q = 1; q < 4; ++q) accf = cdf_add(accf, acc_s[q][tid]);
+            const double2 acc = to_d2(accf);
             const int64_t g = r * ld + o + rc + tid;
             if (b) {
                 const double2 bv = conv<double2>(b[g]);
@@ -277,7 +279,7 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
 
 } // namespace
 
-void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, double2 *part, int64_t pstride,
+void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, cdf *part, int64_t pstride,
                                  int nrhs, cudaStream_t s, int rb)
 {
     const Item *list = L.d_items;
@@ -301,7 +303,7 @@ void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *
     k_residual_items<<<g, APPLY_WARPS * 32, 0, s>>>(list, n, h->d_pool32, x, h->pN, part, pstride, nrhs);
 }
 
-void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const double2 *part, int64_t pstride,
+void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const cdf *part, int64_t pstride,
                          const float2 *b, float2 *out, double *norms, int nrhs, cudaStream_t s)
 {
     dim3 grid((unsigned)h->n_leaves, (unsigned)nrhs);
