@@ -20,6 +20,8 @@
 // output-side factor Y rank-major.
 #include "k_dot2.cuh"
 
+#include <algorithm>
+
 namespace hm {
 namespace {
 
@@ -147,27 +149,30 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
     }
 }
 
-// Per leaf (blockIdx.x) and right-hand side (blockIdx.y): acc = D_I x_I + the
-// owner sums of levels 1..m at the leaf's rows, in FP64 and in a fixed order.
-// If b is given, out = b - acc (complex64) and |r|^2, |b|^2 go to norms; else
-// out = acc (complex64).
+// Per leaf (blockIdx.x) and right-hand side (blockIdx.y): acc = D_I x_I (Dot2) +
+// the owner sums of levels 1..m at the leaf's rows (FP64), in a fixed order.  If b
+// is given, out = b - acc (FP64, rounded to complex64) and |r|^2, |b|^2 go to
+// norms; else out = acc (complex64).  x of the leaf is staged in dynamic shared
+// memory (np entries).
 __global__ void __launch_bounds__(64)
 k_gather_own(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
              const float2 *__restrict__ self32, const float2 *__restrict__ x, int64_t ld, int m,
              const double2 *__restrict__ own, int64_t lstride, const float2 *__restrict__ b, float2 *__restrict__ out,
              double *norms)
 {
-    __shared__ double2 xs[128];
+    extern __shared__ __align__(16) unsigned char gsm[];
+    float2 *xs = reinterpret_cast<float2 *>(gsm);
     const int leaf = blockIdx.x, r = blockIdx.y, tid = threadIdx.x, lane = tid & 31;
     const int o = pleaf_off[leaf], np = pleaf_off[leaf + 1] - o;
     double rr = 0.0, bb = 0.0;
-    for (int j = tid; j < np; j += 64) xs[j] = conv<double2>(x[r * ld + o + j]);
+    for (int j = tid; j < np; j += 64) xs[j] = x[r * ld + o + j];
     __syncthreads();
     const float2 *Sd = self32 + dinv_off[leaf];                 // column-major np x np
     for (int i = tid; i < np; i += 64) {
         const int64_t g = r * ld + o + i;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int j = 0; j < np; ++j) cfma(acc, conv<double2>(Sd[(int64_t)j * np + i]), xs[j]);
+        cdf dx = cdf_zero();
+        for (int j = 0; j < np; ++j) cdot2(dx, Sd[(int64_t)j * np + i], xs[j]);
+        double2 acc = to_d2(dx);
         for (int lev = 0; lev < m; ++lev) acc = cadd(acc, own[lev * lstride + g]);
         if (b) {
             const double2 bv = conv<double2>(b[g]);
@@ -225,8 +230,10 @@ void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, 
                        float2 *out, double *norms, int nrhs, cudaStream_t s)
 {
     dim3 grid((unsigned)h->n_leaves, (unsigned)nrhs);
-    k_gather_own<<<grid, 64, 0, s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_self32, x, h->pN, m, own, lstride, b, out,
-                                     norms);
+    int64_t maxnp = 0;
+    for (int64_t i = 0; i < h->n_leaves; ++i) maxnp = std::max<int64_t>(maxnp, h->pleaf_off[i + 1] - h->pleaf_off[i]);
+    k_gather_own<<<grid, 64, sizeof(float2) * (size_t)std::max<int64_t>(maxnp, 1), s>>>(
+        h->d_pleaf_off, h->d_dinv_off, h->d_self32, x, h->pN, m, own, lstride, b, out, norms);
 }
 
 } // namespace hm

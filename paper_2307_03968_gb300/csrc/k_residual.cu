@@ -208,9 +208,9 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
                const cdf *__restrict__ part, int64_t pstride, const float2 *__restrict__ b,
                float2 *__restrict__ out, double *norms)
 {
-    constexpr int MAXR = 128;
-    __shared__ cdf acc_s[4][MAXR];
-    __shared__ float2 xs[MAXR];
+    __shared__ cdf acc_s[4][64];
+    extern __shared__ __align__(16) unsigned char gsm[];
+    float2 *xs = reinterpret_cast<float2 *>(gsm);                 // x of the leaf, np entries
     const int leaf = blockIdx.x, r = blockIdx.y;
     const int o = pleaf_off[leaf], np = pleaf_off[leaf + 1] - o;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -312,8 +312,7 @@ void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const cdf *part, i
         for (int64_t i = 0; i < h->n_leaves; ++i) v = std::max<int64_t>(v, h->pleaf_off[i + 1] - h->pleaf_off[i]);
         return v;
     }();
-    (void)maxnp;
-    k_gather_acc64<<<grid, 128, 0, s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_self32, x, h->pN,
+    k_gather_acc64<<<grid, 128, sizeof(float2) * (size_t)std::max<int64_t>(maxnp, 1), s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_self32, x, h->pN,
                                                               h->d_csr_off, h->n_levels + 1, m, h->d_csr_idx, part,
                                                               pstride, b, out, norms);
 }
