@@ -328,7 +328,8 @@ class HMatrix:
         return a.value, b.value, c.value, d.value
 
     def set_tuning(self, nrhs, prod_rb, res_rb):
-        """hm_set_tuning: pin the kernel choice for nrhs's bucket (1016 = tensor-core products)."""
+        """hm_set_tuning: pin the kernel choice for nrhs's bucket (product 1016 = tensor-core
+        products; residual 1017 = owner-computes FP64-class residual)."""
         _check(load().hm_set_tuning(self._h, nrhs, prod_rb, res_rb))
 
     @property
