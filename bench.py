@@ -509,10 +509,10 @@ def main():
         rkind = "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
         kernel = ("k_apply_mrhs<%d> (shared-memory SIMT, %d RHS per chunk) + k_apply_items for larger blocks "
                   "(k_mrhs.cu, k_product.cu)" % (prod_choice, prod_choice) if prod_choice
-                  else "k_apply_items<float,float,2> (one RHS at a time, k_product.cu)")
+                  else "k_apply_items<float,float,3> (one RHS at a time, k_product.cu)")
     else:
         bound, unit, rpeak, rkind = "hbm", "GB/s", peak, peak_kind
-        kernel = "k_apply_items<float,float,2> (near + leaf-level far block product, k_product.cu)"
+        kernel = "k_apply_items<float,float,3> (near + leaf-level far block product, k_product.cu)"
     if prof_n:
         achieved = (flops_per_launch / (per_launch_ms * 1e-3) / 1e12 if unit == "TFLOP/s"
                     else per_launch_bytes / (per_launch_ms * 1e-3) / 1e9)

@@ -267,9 +267,9 @@ void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z,
             cnt = L.n_big;
             if (cnt == 0) return;
         }
-        int g = apply_grid<float, float, 2>(h);
+        int g = apply_grid<float, float, 3>(h);
         if ((int64_t)g * APPLY_WARPS > cnt) g = (int)((cnt + APPLY_WARPS - 1) / APPLY_WARPS);
-        k_apply_items<float, float, 2><<<g, APPLY_WARPS * 32, 0, s>>>(
+        k_apply_items<float, float, 3><<<g, APPLY_WARPS * 32, 0, s>>>(
             list, cnt, h->d_pool32, (const float2 *)x, h->pN, (float2 *)z, h->pN, nrhs);
     }
 }
