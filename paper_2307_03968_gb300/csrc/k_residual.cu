@@ -196,19 +196,20 @@ k_residual_items(const Item *__restrict__ items, int64_t n_items, const float2 *
 
 // Per leaf (blockIdx.x) and right-hand side (blockIdx.y): acc = D_I x_I +
 // sum of the leaf's partial slots of levels 1..m, in double-float arithmetic and
-// in a fixed order (each of the 4 warps sums every 4th slot with compensated
-// additions, lanes own row pairs, warp 0 adds D_I x_I with Dot2; the warps are
-// then added in warp order).  If b is given, out = b - acc (in FP64, rounded to
-// complex64) and |r|^2, |b|^2 go to norms; else out = acc (complex64).  No
-// atomics on sums.
-__global__ void __launch_bounds__(128)
+// in a fixed order (each of the GW warps sums every GW-th slot with compensated
+// additions and takes every GW-th column of D_I x_I in Dot2; lanes own row pairs;
+// the warps are then added in warp order).  If b is given, out = b - acc (in FP64,
+// rounded to complex64) and |r|^2, |b|^2 go to norms; else out = acc (complex64).
+// No atomics on sums.
+constexpr int GW = 8;   // warps per leaf
+__global__ void __launch_bounds__(GW * 32)
 k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
                const float2 *__restrict__ self32, const float2 *__restrict__ x, int64_t ld,
                const int64_t *__restrict__ csr_off, int csr_stride, int m, const int64_t *__restrict__ csr_idx,
                const cdf *__restrict__ part, int64_t pstride, const float2 *__restrict__ b,
                float2 *__restrict__ out, double *norms)
 {
-    __shared__ cdf acc_s[4][64];
+    __shared__ cdf acc_s[GW][64];
     extern __shared__ __align__(16) unsigned char gsm[];
     float2 *xs = reinterpret_cast<float2 *>(gsm);                 // x of the leaf, np entries
     const int leaf = blockIdx.x, r = blockIdx.y;
@@ -218,30 +219,28 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
     __syncthreads();
     const cdf *P = part + r * pstride;
     const int64_t e0 = csr_off[(int64_t)leaf * csr_stride], e1 = csr_off[(int64_t)leaf * csr_stride + m];
+    const float2 *S = self32 + dinv_off[leaf];                      // column-major np x np
     for (int rc = 0; rc < np; rc += 64) {
         const int i = rc + 2 * lane;
         cdf a0 = cdf_zero(), a1 = cdf_zero();
         if (i < np) {
             int64_t e = e0 + w;
-            for (; e + 12 < e1; e += 16) {      // four slots in flight per warp
-                const int64_t q0 = csr_idx[e], q1 = csr_idx[e + 4], q2 = csr_idx[e + 8], q3 = csr_idx[e + 12];
+            for (; e + 3 * GW < e1; e += 4 * GW) {   // four slots in flight per warp
+                const int64_t q0 = csr_idx[e], q1 = csr_idx[e + GW], q2 = csr_idx[e + 2 * GW], q3 = csr_idx[e + 3 * GW];
                 const cdf v00 = P[q0 + i], v01 = P[q0 + i + 1], v10 = P[q1 + i], v11 = P[q1 + i + 1];
                 const cdf v20 = P[q2 + i], v21 = P[q2 + i + 1], v30 = P[q3 + i], v31 = P[q3 + i + 1];
                 a0 = cdf_add(a0, cdf_add(cdf_add(v00, v10), cdf_add(v20, v30)));
                 a1 = cdf_add(a1, cdf_add(cdf_add(v01, v11), cdf_add(v21, v31)));
             }
-            for (; e < e1; e += 4) {
+            for (; e < e1; e += GW) {
                 const int64_t q = csr_idx[e];
                 a0 = cdf_add(a0, P[q + i]);
                 a1 = cdf_add(a1, P[q + i + 1]);
             }
-            if (w == 0) {   // the self block, Dot2
-                const float2 *S = self32 + dinv_off[leaf];   // column-major
-                for (int j = 0; j < np; ++j) {
-                    const Pair<float> d = ld_vec(S + (int64_t)j * np + i);
-                    cdot2(a0, d.a, xs[j]);
-                    cdot2(a1, d.b, xs[j]);
-                }
+            for (int j = w; j < np; j += GW) {      // the self block, Dot2, every GW-th column
+                const Pair<float> d = ld_vec(S + (int64_t)j * np + i);
+                cdot2(a0, d.a, xs[j]);
+                cdot2(a1, d.b, xs[j]);
             }
         }
         acc_s[w][2 * lane] = a0;
@@ -250,7 +249,7 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
         double rr = 0.0, bb = 0.0;
         if (tid < 64 && rc + tid < np) {
             cdf accf = acc_s[0][tid];
-            for (int q = 1; q < 4; ++q) accf = cdf_add(accf, acc_s[q][tid]);
+            for (int q = 1; q < GW; ++q) accf = cdf_add(accf, acc_s[q][tid]);
             const double2 acc = to_d2(accf);
             const int64_t g = r * ld + o + rc + tid;
             if (b) {
@@ -312,7 +311,7 @@ void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const cdf *part, i
         for (int64_t i = 0; i < h->n_leaves; ++i) v = std::max<int64_t>(v, h->pleaf_off[i + 1] - h->pleaf_off[i]);
         return v;
     }();
-    k_gather_acc64<<<grid, 128, sizeof(float2) * (size_t)std::max<int64_t>(maxnp, 1), s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_self32, x, h->pN,
+    k_gather_acc64<<<grid, GW * 32, sizeof(float2) * (size_t)std::max<int64_t>(maxnp, 1), s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_self32, x, h->pN,
                                                               h->d_csr_off, h->n_levels + 1, m, h->d_csr_idx, part,
                                                               pstride, b, out, norms);
 }
