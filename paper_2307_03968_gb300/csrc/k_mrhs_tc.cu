@@ -536,6 +536,12 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
     if (w == NWARP - 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
 }
 
+// records a status code in the device status word (first error wins)
+__global__ void k_set_status(int *status, int code)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicCAS(status, 0, code);
+}
+
 } // namespace
 
 size_t tc_xplane_bytes(int64_t n_xch, int nrhs) { return (size_t)A_BYTES * (size_t)n_xch * (size_t)((nrhs + TM - 1) / TM); }
@@ -546,7 +552,10 @@ void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z
 {
     if (L.n_tcu == 0 || nrhs <= 0) return;
     if (!h->ws.d_xpl || h->ws.xpl_bytes < tc_xplane_bytes(L.n_xch, nrhs)) {
+        // not reached through the API (the workspace is sized before every product); the call
+        // reports HM_ERR_STATE through the status word instead of returning an incomplete product
         fail(HM_ERR_STATE, "tensor-core product without its split-x workspace");
+        k_set_status<<<1, 32, 0, s>>>(h->d_status, (int)HM_ERR_STATE);
         return;
     }
     static bool attr = false;
