@@ -88,7 +88,8 @@ typedef struct {
 
 /* Tree, admissibility (eq. 7) and compression (§III) options. */
 typedef struct {
-    int leaf_size;     /* split clusters until every leaf holds <= leaf_size unknowns */
+    int leaf_size;     /* split clusters until every leaf holds <= leaf_size unknowns;
+                          1..1536 (HM_ERR_ARG otherwise) */
     int arity;         /* 2 = binary tree (the paper's runs), 4, or 8 = octree */
     double adm;        /* c in dist(t,s) >= c * min(diam t, diam s); the paper's
                           eta = 1 is c = 1, the 2-diameter rule is c = 2 */
@@ -149,9 +150,13 @@ hm_status hm_build_from_blocks(const hm_blocks *blocks, void *stream, hm_matrix 
 
 /*
  * Factor the leaf self blocks (paper eq. 12, [Z~_N]^{-1}): FP64 Gauss-Jordan
- * with partial pivoting on the device, one block per CTA; the explicit inverse
- * is kept in complex64 (and complex128 with keep_fp64).  Synchronises; returns
- * HM_ERR_SINGULAR if a pivot is exactly zero.
+ * with partial pivoting on the device; the explicit inverse is kept in
+ * complex64 (and complex128 with keep_fp64).  Leaves of up to 112 unknowns are
+ * inverted in shared memory, one block per CTA.  Larger leaves (up to 1536)
+ * are copied into a device workspace of 16 n^2 bytes per leaf, allocated here
+ * and freed before return (HM_ERR_OOM if it cannot be had), and eliminated one
+ * pivot step at a time across all of them.  Synchronises; returns
+ * HM_ERR_SINGULAR if a pivot is exactly zero, HM_ERR_ARG for a leaf above 1536.
  */
 hm_status hm_factor_leaf(hm_matrix h, void *stream);
 

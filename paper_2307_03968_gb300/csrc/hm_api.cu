@@ -789,7 +789,7 @@ static hm_status import_blocks(const hm_blocks *B, cudaStream_t s, hm_matrix h)
     for (int64_t i = 0; i < h->n_leaves; ++i) {
         const int64_t n = h->leaf_off[i + 1] - h->leaf_off[i];
         if (n < 1) return fail(HM_ERR_ARG, "empty leaf");
-        if (n > factor_max_leaf()) return fail(HM_ERR_ARG, "leaf larger than the device factorisation supports (112)");
+        if (n > factor_max_leaf()) return fail(HM_ERR_ARG, "leaf larger than the device factorisation supports");
     }
     h->has_fp64 = B->keep_fp64 != 0;
     hm_status st = finalize_layout(h, s);
@@ -960,7 +960,8 @@ hm_status hm_factor_leaf(hm_matrix h, void *stream)
     if (!h) return fail(HM_ERR_ARG, "null handle");
     cudaStream_t s = (cudaStream_t)stream;
     HM_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
-    launch_factor(h, s);
+    const hm_status fst = launch_factor(h, s);
+    if (fst != HM_OK) return fst;
     HM_CUDA(cudaGetLastError());
     HM_CUDA(cudaStreamSynchronize(s));
     int stv = 0, bad = -1;

@@ -258,7 +258,7 @@ void launch_convert_f32_to_f64(const float2 *a, double2 *b, int64_t n, cudaStrea
 
 // factorisation (k_factor.cu)
 int factor_max_leaf();
-void launch_factor(hm_matrix h, cudaStream_t s);
+hm_status launch_factor(hm_matrix h, cudaStream_t s);
 
 // unknown count of a mesh (RWG edges or SWG faces) with the checks of hm_build (k_build.cu)
 hm_status count_unknowns(const hm_mesh *mesh, int64_t *n);

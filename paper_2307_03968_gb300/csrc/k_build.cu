@@ -287,7 +287,7 @@ hm_status count_unknowns(const hm_mesh *mesh, int64_t *n)
 hm_status build_from_mesh(const hm_mesh *mesh, const hm_build_opts *o, cudaStream_t s, hm_matrix *out)
 {
     if (o->leaf_size < 1 || o->leaf_size > factor_max_leaf())
-        return fail(HM_ERR_ARG, "leaf_size must be in [1, 112]");
+        return fail(HM_ERR_ARG, "leaf_size must be in [1, " + std::to_string(factor_max_leaf()) + "]");
     if (o->arity != 2 && o->arity != 4 && o->arity != 8) return fail(HM_ERR_ARG, "arity must be 2, 4 or 8");
     if (!(o->adm > 0) || !(o->aca_tol > 0) || o->aca_tol >= 1) return fail(HM_ERR_ARG, "bad adm or aca_tol");
     if (!(mesh->wavelength > 0)) return fail(HM_ERR_ARG, "wavelength must be > 0");

@@ -50,7 +50,9 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
                 }
                 reduce_cdf<8>(rp, lane);
                 const int row = rb + lane;
-                if (lane < 8 && row < em) part[it.pad + row] = rp[0];
+                // a block wider than 64 columns is swept in column chunks: the row slot
+                // takes the first chunk's sums and then adds the next ones (same lane, in order)
+                if (lane < 8 && row < em) part[it.pad + row] = c0 == 0 ? rp[0] : cdf_add(part[it.pad + row], rp[0]);
             }
         }
         if (jv) {

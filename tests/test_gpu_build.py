@@ -120,7 +120,7 @@ def test_build_argument_errors(torch_cuda):
     from synth import icosphere
     from paper_2307_03968_gb300.hm import HMatrix, HmError, HM_ERR_ARG
     xyz, tri = icosphere(1, 0.3)
-    for kw in (dict(leaf_size=0), dict(leaf_size=500), dict(arity=3), dict(aca_tol=0.0), dict(adm=-1.0)):
+    for kw in (dict(leaf_size=0), dict(leaf_size=5000), dict(arity=3), dict(aca_tol=0.0), dict(adm=-1.0)):
         with pytest.raises(HmError) as e:
             HMatrix.build(xyz, tri, **kw)
         assert e.value.status == HM_ERR_ARG
