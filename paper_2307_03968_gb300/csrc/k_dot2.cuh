@@ -78,6 +78,90 @@ __device__ __forceinline__ df df_add(df a, df b)
     return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
 }
 __device__ __forceinline__ cdf cdf_add(const cdf &a, const cdf &b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+
+// ---------------------------------------------------------------------------
+// Short error-free chains with a biased accumulator (four operations per real
+// product against ten for Dot2).
+//
+// For a short sum s = sum_k a_k b_k with sum_k |a_k b_k| <= sigma / 4, sigma a
+// power of two, the accumulator tau starts at sigma and stays within
+// [3/4, 5/4] sigma.  Each step
+//   tau' = fma(a, b, tau)     the exact product rounded once onto tau's grid,
+//   q    = tau' - tau         exact (Sterbenz: tau and tau' within a factor 2),
+//   r   += fma(a, b, -q)      the product's remainder below the grid,
+// leaves s = (tau - sigma) + r with tau - sigma exact; only r, whose terms are
+// at most ulp(sigma) ~ 2^-23 sigma, is rounded.  The grid extraction is the
+// ExtractScalar step of Rump, Ogita & Oishi ("Accurate floating-point
+// summation part I: faithful rounding", SIAM J. Sci. Comput. 31(1), 2008),
+// applied here to each exact product through the FMA.  sigma comes from a
+// bound of the chain's own terms (sum of |a|_1 times max |b|_inf), so the
+// grid follows the data and the error stays at Dot2's level, a few units of
+// 2^-48 of sum |a_k b_k| for chains of up to 8 real terms.
+struct xacc { float tau, r; };
+struct cxacc { xacc re, im; };
+
+// the least power of two >= v for finite v >= 0 (0 for 0, 2^-126 for subnormals)
+__device__ __forceinline__ float pow2_ceil(float v)
+{
+    return __uint_as_float((__float_as_uint(v) + 0x007FFFFFu) & 0xFF800000u);
+}
+__device__ __forceinline__ float l1(float2 a) { return __fadd_rn(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float linf(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+// sigma for a chain of complex products a_k b_k with sum_k |a_k|_1 = sa and
+// max_k |b_k|_inf = mb (each real part and each imaginary part sums at most sa * mb)
+__device__ __forceinline__ float chain_sigma(float sa, float mb) { return pow2_ceil(4.f * sa * mb); }
+
+__device__ __forceinline__ void xfirst(xacc &c, float sigma, float a, float b)
+{
+    c.tau = __fmaf_rn(a, b, sigma);
+    c.r = __fmaf_rn(a, b, -__fsub_rn(c.tau, sigma));
+}
+__device__ __forceinline__ void xstep(xacc &c, float a, float b)
+{
+    const float t2 = __fmaf_rn(a, b, c.tau);
+    c.r = __fadd_rn(c.r, __fmaf_rn(a, b, -__fsub_rn(t2, c.tau)));
+    c.tau = t2;
+}
+// c = a * b (the chain's first complex term)
+__device__ __forceinline__ void cxfirst(cxacc &c, float sigma, float2 a, float2 b)
+{
+    xfirst(c.re, sigma, a.x, b.x);
+    xstep(c.re, -a.y, b.y);
+    xfirst(c.im, sigma, a.x, b.y);
+    xstep(c.im, a.y, b.x);
+}
+// c += a * b
+__device__ __forceinline__ void cxstep(cxacc &c, float2 a, float2 b)
+{
+    xstep(c.re, a.x, b.x);
+    xstep(c.re, -a.y, b.y);
+    xstep(c.im, a.x, b.y);
+    xstep(c.im, a.y, b.x);
+}
+// c += a * (b.hi + b.lo) for a double-float b: the leading part through the
+// chain (its bound uses |b.hi|), the trailing part (2^-24 of it) into r
+__device__ __forceinline__ void cx_lo(cxacc &c, float2 a, const cdf &b)
+{
+    c.re.r = __fmaf_rn(a.x, b.re.lo, c.re.r);
+    c.re.r = __fmaf_rn(-a.y, b.im.lo, c.re.r);
+    c.im.r = __fmaf_rn(a.x, b.im.lo, c.im.r);
+    c.im.r = __fmaf_rn(a.y, b.re.lo, c.im.r);
+}
+__device__ __forceinline__ void cxfirst_df(cxacc &c, float sigma, float2 a, const cdf &b)
+{
+    cxfirst(c, sigma, a, make_float2(b.re.hi, b.im.hi));
+    cx_lo(c, a, b);
+}
+__device__ __forceinline__ void cxstep_df(cxacc &c, float2 a, const cdf &b)
+{
+    cxstep(c, a, make_float2(b.re.hi, b.im.hi));
+    cx_lo(c, a, b);
+}
+// the chain's sum as a double-float: the exact grid part and the remainder
+__device__ __forceinline__ cdf cxclose(const cxacc &c, float sigma)
+{
+    return {{__fsub_rn(c.re.tau, sigma), c.re.r}, {__fsub_rn(c.im.tau, sigma), c.im.r}};
+}
 __device__ __forceinline__ cdf cdf_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
 __device__ __forceinline__ cdf shfl_xor(const cdf &v, int s)
 {

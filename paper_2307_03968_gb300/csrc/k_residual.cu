@@ -1,9 +1,10 @@
 // FP64-class residual of the refinement step, r = b - A_m x, over complex64
 // blocks (the precision rule of the solve: the final residual check runs at
 // FP64-class accuracy).  k_residual_items writes every block's products into
-// its double-float partial slots (no atomics); k_gather_acc64 sums each leaf's
-// slots in a fixed order with compensated additions, adds D_I x_I (Dot2) and
-// forms b - A x in FP64.
+// its double-float partial slots (no atomics), summing each block with short
+// error-free chains (biased accumulator, k_dot2.cuh) folded into double-float
+// sums; k_gather_acc64 sums each leaf's slots in a fixed order with compensated
+// additions, adds D_I x_I (Dot2) and forms b - A x in FP64.
 #include "k_dot2.cuh"
 
 namespace hm {
@@ -14,6 +15,9 @@ using namespace dot2;
 constexpr int APPLY_WARPS = 8;
 
 // Dense block: slot rows (even(m)) = B x_J, slot columns (even(n)) = B^T x_I.
+// A lane owns two adjacent columns.  Row side: per row, the lane's two terms form
+// one short error-free chain, then the lanes' double-float sums are reduced.
+// Column side: chains over four rows at a time, folded into a double-float sum.
 __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__restrict__ pool,
                                              const float2 *__restrict__ x, cdf *__restrict__ part, float2 *xs,
                                              int lane)
@@ -28,6 +32,7 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
             xj0 = x[it.col0 + j];
             if (j + 1 < n) xj1 = x[it.col0 + j + 1];
         }
+        const float mxj = fmaxf(linf(xj0), linf(xj1));
         cdf cs0 = cdf_zero(), cs1 = cdf_zero();
         for (int r0 = 0; r0 < m; r0 += 32) {
             __syncwarp();
@@ -36,17 +41,43 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
             for (int q = 0; q < 4; ++q) {
                 const int rb = r0 + 8 * q;
                 if (rb >= m) break;
+                Pair<float> b[8];
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) {
+                    b[rr] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    if (jv && rb + rr < m) b[rr] = ld_stream(B + (int64_t)(rb + rr) * ld + j);
+                }
                 cdf rp[8];
 #pragma unroll
                 for (int rr = 0; rr < 8; ++rr) {
-                    const int i = rb + rr;
-                    Pair<float> b{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                    if (jv && i < m) b = ld_stream(B + (int64_t)i * ld + j);
-                    const float2 xi = xs[8 * q + rr];
-                    cdot2(cs0, b.a, xi);
-                    cdot2(cs1, b.b, xi);
-                    cdot2_first(rp[rr], b.a, xj0);
-                    cdot2(rp[rr], b.b, xj1);
+                    const float sg = chain_sigma(__fadd_rn(l1(b[rr].a), l1(b[rr].b)), mxj);
+                    cxacc c;
+                    cxfirst(c, sg, b[rr].a, xj0);
+                    cxstep(c, b[rr].b, xj1);
+                    rp[rr] = cxclose(c, sg);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float2 xi[4];
+                    float mxi = 0.f, sa0 = 0.f, sa1 = 0.f;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        xi[u] = xs[8 * q + 4 * h + u];
+                        mxi = fmaxf(mxi, linf(xi[u]));
+                        sa0 = __fadd_rn(sa0, l1(b[4 * h + u].a));
+                        sa1 = __fadd_rn(sa1, l1(b[4 * h + u].b));
+                    }
+                    const float s0 = chain_sigma(sa0, mxi), s1 = chain_sigma(sa1, mxi);
+                    cxacc k0, k1;
+                    cxfirst(k0, s0, b[4 * h].a, xi[0]);
+                    cxfirst(k1, s1, b[4 * h].b, xi[0]);
+#pragma unroll
+                    for (int u = 1; u < 4; ++u) {
+                        cxstep(k0, b[4 * h + u].a, xi[u]);
+                        cxstep(k1, b[4 * h + u].b, xi[u]);
+                    }
+                    cs0 = cdf_add(cs0, cxclose(k0, s0));
+                    cs1 = cdf_add(cs1, cxclose(k1, s1));
                 }
                 reduce_cdf<8>(rp, lane);
                 const int row = rb + lane;
@@ -63,7 +94,8 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
 }
 
 // Low-rank block U V: slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I);
-// the rank-k intermediates stay in double-float.
+// the rank-k intermediates stay in double-float.  Blocks of up to 64 x 64 use the
+// short biased chains, larger ones Dot2.
 __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__restrict__ pool,
                                                const float2 *__restrict__ x, cdf *__restrict__ part, int lane)
 {
@@ -78,6 +110,7 @@ __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__r
         Pair<float> xi{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, xj = xi;
         if (iv) xi = ld_vec(x + it.row0 + i);
         if (jv) xj = ld_vec(x + it.col0 + i);
+        const float mxi = fmaxf(linf(xi.a), linf(xi.b)), mxj = fmaxf(linf(xj.a), linf(xj.b));
         cdf oi0 = cdf_zero(), oi1 = cdf_zero(), oj0 = cdf_zero(), oj1 = cdf_zero();
         for (int l0 = 0; l0 < k; l0 += 4) {
             Pair<float> u[4], v[4];
@@ -90,25 +123,57 @@ __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__r
                     if (jv) v[l] = ld_stream(V + (int64_t)(l0 + l) * n + i);
                 }
             }
+            // stage 1: the lane's two terms of every rank row as one short chain,
+            // then the lanes' double-float sums reduced (rank rows past k are zero)
             cdf tp[4], t[4];
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
-                cdot2_first(tp[l], u[l].a, xi.a);
-                cdot2(tp[l], u[l].b, xi.b);
-                cdot2_first(t[l], v[l].a, xj.a);
-                cdot2(t[l], v[l].b, xj.b);
+                const float su = chain_sigma(__fadd_rn(l1(u[l].a), l1(u[l].b)), mxi);
+                const float sv = chain_sigma(__fadd_rn(l1(v[l].a), l1(v[l].b)), mxj);
+                cxacc cu, cv;
+                cxfirst(cu, su, u[l].a, xi.a);
+                cxstep(cu, u[l].b, xi.b);
+                cxfirst(cv, sv, v[l].a, xj.a);
+                cxstep(cv, v[l].b, xj.b);
+                tp[l] = cxclose(cu, su);
+                t[l] = cxclose(cv, sv);
             }
             reduce_cdf<4>(tp, lane);
             reduce_cdf<4>(t, lane);
+            // stage 2: one chain over the chunk's rank rows per output, folded
+            cdf tl[4], tpl[4];
+            float mt = 0.f, mtp = 0.f, si0 = 0.f, si1 = 0.f, sj0 = 0.f, sj1 = 0.f;
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
-                if (l0 + l >= k) break;
-                const cdf tl = shfl_idx(t[0], l), tpl = shfl_idx(tp[0], l);
-                cdot2_df(oi0, u[l].a, tl);
-                cdot2_df(oi1, u[l].b, tl);
-                cdot2_df(oj0, v[l].a, tpl);
-                cdot2_df(oj1, v[l].b, tpl);
+                tl[l] = shfl_idx(t[0], l);
+                tpl[l] = shfl_idx(tp[0], l);
+                mt = fmaxf(mt, fmaxf(fabsf(tl[l].re.hi), fabsf(tl[l].im.hi)));
+                mtp = fmaxf(mtp, fmaxf(fabsf(tpl[l].re.hi), fabsf(tpl[l].im.hi)));
+                si0 = __fadd_rn(si0, l1(u[l].a));
+                si1 = __fadd_rn(si1, l1(u[l].b));
+                sj0 = __fadd_rn(sj0, l1(v[l].a));
+                sj1 = __fadd_rn(sj1, l1(v[l].b));
             }
+            si0 = chain_sigma(si0, mt);
+            si1 = chain_sigma(si1, mt);
+            sj0 = chain_sigma(sj0, mtp);
+            sj1 = chain_sigma(sj1, mtp);
+            cxacc ci0, ci1, cj0, cj1;
+            cxfirst_df(ci0, si0, u[0].a, tl[0]);
+            cxfirst_df(ci1, si1, u[0].b, tl[0]);
+            cxfirst_df(cj0, sj0, v[0].a, tpl[0]);
+            cxfirst_df(cj1, sj1, v[0].b, tpl[0]);
+#pragma unroll
+            for (int l = 1; l < 4; ++l) {
+                cxstep_df(ci0, u[l].a, tl[l]);
+                cxstep_df(ci1, u[l].b, tl[l]);
+                cxstep_df(cj0, v[l].a, tpl[l]);
+                cxstep_df(cj1, v[l].b, tpl[l]);
+            }
+            oi0 = cdf_add(oi0, cxclose(ci0, si0));
+            oi1 = cdf_add(oi1, cxclose(ci1, si1));
+            oj0 = cdf_add(oj0, cxclose(cj0, sj0));
+            oj1 = cdf_add(oj1, cxclose(cj1, sj1));
         }
         if (iv) { part[it.pad + i] = oi0; part[it.pad + i + 1] = oi1; }
         if (jv) { part[it.pad + m + i] = oj0; part[it.pad + m + i + 1] = oj1; }
