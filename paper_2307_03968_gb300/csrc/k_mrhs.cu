@@ -223,7 +223,8 @@ k_apply_mrhs(const Item *__restrict__ items, int64_t n_items, const float2 *__re
 
 // ------------------------------------------------------------------------------
 // FP64-class residual products for many right-hand sides: the same staging, the
-// products accumulated by the error-free Dot2 steps, each block's results
+// products accumulated in short error-free chains of four terms (biased
+// accumulator, k_dot2.cuh) folded into double-float sums, each block's results
 // stored in its double-float partial slots (row side: even(m) slots from it.pad, column
 // side: even(n) slots after them; no atomics, so the per-leaf FP64 gather that
 // follows stays deterministic).  Right-hand side q of the chunk writes
@@ -245,14 +246,38 @@ __device__ __forceinline__ void mm_rows_c(const float2 *S, int sld, int R, int R
     for (int q = 0; q < TC; ++q) { a0[q] = cdf_zero(); a1[q] = cdf_zero(); }
     if (r < R) {
         const float2 *s0 = S + r * sld, *s1 = s0 + sld;
-        const float2 *xc = X + q0;
-        for (int c = 0; c < C; ++c, xc += xld) {
-            const float2 b0 = s0[c], b1 = s1[c];
+        for (int c0 = 0; c0 < C; c0 += 4) {
+            // row r + 1 may be past R (its sums are then discarded), columns past C are zero
+            float2 b0[4], b1[4], xv[4][TC];
+            float sa0 = 0.f, sa1 = 0.f, mq[TC];
+#pragma unroll
+            for (int q = 0; q < TC; ++q) mq[q] = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = c0 + u < C;
+                b0[u] = ok ? s0[c0 + u] : make_float2(0.f, 0.f);
+                b1[u] = ok ? s1[c0 + u] : make_float2(0.f, 0.f);
+                sa0 = __fadd_rn(sa0, l1(b0[u]));
+                sa1 = __fadd_rn(sa1, l1(b1[u]));
+#pragma unroll
+                for (int q = 0; q < TC; ++q) {
+                    xv[u][q] = ok ? X[(c0 + u) * xld + q0 + q] : make_float2(0.f, 0.f);
+                    mq[q] = fmaxf(mq[q], linf(xv[u][q]));
+                }
+            }
 #pragma unroll
             for (int q = 0; q < TC; ++q) {
-                const float2 xv = xc[q];
-                cdot2(a0[q], b0, xv);
-                cdot2(a1[q], b1, xv);
+                const float g0 = chain_sigma(sa0, mq[q]), g1 = chain_sigma(sa1, mq[q]);
+                cxacc k0, k1;
+                cxfirst(k0, g0, b0[0], xv[0][q]);
+                cxfirst(k1, g1, b1[0], xv[0][q]);
+#pragma unroll
+                for (int u = 1; u < 4; ++u) {
+                    cxstep(k0, b0[u], xv[u][q]);
+                    cxstep(k1, b1[u], xv[u][q]);
+                }
+                a0[q] = cdf_add(a0[q], cxclose(k0, g0));
+                a1[q] = cdf_add(a1[q], cxclose(k1, g1));
             }
         }
     }
@@ -287,22 +312,68 @@ __device__ __forceinline__ void mm_cols_c(const float2 *S, int sld, int R, int C
     for (int q = 0; q < TC; ++q) { a0[q] = cdf_zero(); a1[q] = cdf_zero(); }
     if (c < C) {
         const float2 *sc = S + c;
-        for (int r = 0; r < R; ++r, sc += sld) {
-            const float2 b0 = sc[0], b1 = sc[1];
+        for (int r0 = 0; r0 < R; r0 += 4) {
+            // column c + 1 may be past C (its sums are then discarded), rows past R are zero
+            float2 b0[4], b1[4];
+            float sa0 = 0.f, sa1 = 0.f, mq[TC];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = r0 + u < R;
+                b0[u] = ok ? sc[(r0 + u) * sld] : make_float2(0.f, 0.f);
+                b1[u] = ok ? sc[(r0 + u) * sld + 1] : make_float2(0.f, 0.f);
+                sa0 = __fadd_rn(sa0, l1(b0[u]));
+                sa1 = __fadd_rn(sa1, l1(b1[u]));
+            }
+#pragma unroll
+            for (int q = 0; q < TC; ++q) mq[q] = 0.f;
             if (XD) {
-                const cdf *xr = XD + r * xld + q0;
+                // the chain bound uses the leading parts; the trailing parts go to the remainders
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (r0 + u < R)
+#pragma unroll
+                        for (int q = 0; q < TC; ++q) {
+                            const cdf v = XD[(r0 + u) * xld + q0 + q];
+                            mq[q] = fmaxf(mq[q], fmaxf(fabsf(v.re.hi), fabsf(v.im.hi)));
+                        }
 #pragma unroll
                 for (int q = 0; q < TC; ++q) {
-                    cdot2_df(a0[q], b0, xr[q]);
-                    cdot2_df(a1[q], b1, xr[q]);
+                    const float g0 = chain_sigma(sa0, mq[q]), g1 = chain_sigma(sa1, mq[q]);
+                    cxacc k0, k1;
+                    const cdf v0 = XD[r0 * xld + q0 + q];
+                    cxfirst_df(k0, g0, b0[0], v0);
+                    cxfirst_df(k1, g1, b1[0], v0);
+#pragma unroll
+                    for (int u = 1; u < 4; ++u) {
+                        const cdf v = r0 + u < R ? XD[(r0 + u) * xld + q0 + q] : cdf_zero();
+                        cxstep_df(k0, b0[u], v);
+                        cxstep_df(k1, b1[u], v);
+                    }
+                    a0[q] = cdf_add(a0[q], cxclose(k0, g0));
+                    a1[q] = cdf_add(a1[q], cxclose(k1, g1));
                 }
             } else {
-                const float2 *xr = XF + r * xld + q0;
+                float2 xv[4][TC];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int q = 0; q < TC; ++q) {
+                        xv[u][q] = r0 + u < R ? XF[(r0 + u) * xld + q0 + q] : make_float2(0.f, 0.f);
+                        mq[q] = fmaxf(mq[q], linf(xv[u][q]));
+                    }
 #pragma unroll
                 for (int q = 0; q < TC; ++q) {
-                    const float2 xv = xr[q];
-                    cdot2(a0[q], b0, xv);
-                    cdot2(a1[q], b1, xv);
+                    const float g0 = chain_sigma(sa0, mq[q]), g1 = chain_sigma(sa1, mq[q]);
+                    cxacc k0, k1;
+                    cxfirst(k0, g0, b0[0], xv[0][q]);
+                    cxfirst(k1, g1, b1[0], xv[0][q]);
+#pragma unroll
+                    for (int u = 1; u < 4; ++u) {
+                        cxstep(k0, b0[u], xv[u][q]);
+                        cxstep(k1, b1[u], xv[u][q]);
+                    }
+                    a0[q] = cdf_add(a0[q], cxclose(k0, g0));
+                    a1[q] = cdf_add(a1[q], cxclose(k1, g1));
                 }
             }
         }

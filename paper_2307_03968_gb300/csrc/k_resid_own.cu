@@ -7,8 +7,10 @@
 // units to balance).  The CTA walks every directed product into O (the stored blocks with O
 // as row cluster, and mirrored, those with O as column cluster; dense or
 // low-rank), in a fixed order, and keeps the sums in registers as double-float
-// complex numbers (Dot2: every product split exactly by an FMA, every sum
-// compensated).  Thread t owns output row t % 64 and right-hand sides
+// complex numbers.  Products are summed in short error-free chains (biased
+// accumulator, k_dot2.cuh: every product rounded exactly onto a power-of-two
+// grid bounded by the chain's own terms, the remainders summed apart) and each
+// chain is folded into the double-float sum with a compensated addition.  Thread t owns output row t % 64 and right-hand sides
 // (RG/2) (t / 64) .. +RG/2-1.  The unit's sums are stored once, in FP64, into the level's
 // [RHS][pN] array: no partial slots, no atomics, and the result is independent
 // of scheduling.  k_gather_own then forms b - (D x + sum over levels) in FP64.
@@ -41,17 +43,28 @@ struct alignas(16) Smem {
     float2 b[SM_B];
     float2 x[SM_X];
     cdf t[SM_T];
+    float mx[16 * RGMAX];        // max |x|_inf over K indices 4c..4c+3, per right-hand side
+    float mt[8 * RGMAX];         // max |T.hi|_inf over rank rows 4c..4c+3, per right-hand side
 };
 
-// stage x of the input cluster: xs[j * XS + q] = x[(r0 + q) * ldx + in0 + j] for j < klen, q < nr (else 0)
+// stage x of the input cluster: xs[j * XS + q] = x[(r0 + q) * ldx + in0 + j] for j < klen, q < nr,
+// 0 for the rest of j < roundup4(klen); mx[c * RGMAX + q] = max over j = 4c..4c+3 of |x|_inf.
+// Every thread runs the same number of iterations (RG * 64 is a multiple of RT), and a warp
+// covers 32 consecutive j of one q, so aligned groups of four lanes hold one chunk.
 template <int RG>
-__device__ __forceinline__ void stage_x(float2 *xs, const float2 *__restrict__ x, int64_t ldx, int r0, int nr, int in0,
-                                        int klen)
+__device__ __forceinline__ void stage_x(float2 *xs, float *mx, const float2 *__restrict__ x, int64_t ldx, int r0,
+                                        int nr, int in0, int klen)
 {
+    static_assert((RG * 64) % RT == 0, "uniform staging loop");
+    const int k4 = (klen + 3) & ~3;
     for (int e = threadIdx.x; e < RG * 64; e += RT) {
         const int q = e >> 6, j = e & 63;
-        if (j >= klen) continue;
-        xs[j * XS + q] = q < nr ? x[(int64_t)(r0 + q) * ldx + in0 + j] : make_float2(0.f, 0.f);
+        const float2 v = (j < klen && q < nr) ? x[(int64_t)(r0 + q) * ldx + in0 + j] : make_float2(0.f, 0.f);
+        if (j < k4) xs[j * XS + q] = v;
+        float m = linf(v);
+        m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
+        m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
+        if ((j & 3) == 0 && j < k4) mx[(j >> 2) * RGMAX + q] = m;
     }
 }
 
@@ -76,7 +89,7 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
         for (int p = U.p0; p < U.p1; ++p) {
             const TcProd P = prods[p];
             __syncthreads();                                  // the previous product's reads are done
-            stage_x<RG>(S.x, x, ldx, r0, nr, P.in0, P.klen);
+            stage_x<RG>(S.x, S.mx, x, ldx, r0, nr, P.in0, P.klen);
             if (P.rank == 0) {
                 // block elements (output i < olen, K j < klen) into b[j * BS + i]
                 const float2 *B = pool + P.b_off;
@@ -91,15 +104,37 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
                 }
                 __syncthreads();
                 if (i < P.olen) {
-                    for (int j = 0; j < P.klen; ++j) {
-                        const float2 bv = S.b[j * BS + i];
-                        const float4 *xv = reinterpret_cast<const float4 *>(S.x + j * XS + QN * hh);
+                    // one chain per right-hand side over four K indices (x is zero past klen)
+                    for (int j0 = 0; j0 < P.klen; j0 += 4) {
+                        float2 bv[4];
+                        float sb = 0.f;
 #pragma unroll
-                        for (int q = 0; q < QN / 2; ++q) {
-                            const float4 v = xv[q];
-                            cdot2(acc[2 * q], bv, make_float2(v.x, v.y));
-                            cdot2(acc[2 * q + 1], bv, make_float2(v.z, v.w));
+                        for (int u = 0; u < 4; ++u) {
+                            bv[u] = j0 + u < P.klen ? S.b[(j0 + u) * BS + i] : make_float2(0.f, 0.f);
+                            sb = __fadd_rn(sb, l1(bv[u]));
                         }
+                        const float *mq = S.mx + (j0 >> 2) * RGMAX + QN * hh;
+                        float sg[QN];
+                        cxacc c[QN];
+#pragma unroll
+                        for (int q = 0; q < QN; ++q) sg[q] = chain_sigma(sb, mq[q]);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 *xv = reinterpret_cast<const float4 *>(S.x + (j0 + u) * XS + QN * hh);
+#pragma unroll
+                            for (int q = 0; q < QN / 2; ++q) {
+                                const float4 v = xv[q];
+                                if (u == 0) {
+                                    cxfirst(c[2 * q], sg[2 * q], bv[0], make_float2(v.x, v.y));
+                                    cxfirst(c[2 * q + 1], sg[2 * q + 1], bv[0], make_float2(v.z, v.w));
+                                } else {
+                                    cxstep(c[2 * q], bv[u], make_float2(v.x, v.y));
+                                    cxstep(c[2 * q + 1], bv[u], make_float2(v.z, v.w));
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < QN; ++q) acc[q] = cdf_add(acc[q], cxclose(c[q], sg[q]));
                     }
                 }
             } else {
@@ -121,20 +156,64 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
                     for (int l0 = 0; l0 < P.rank; l0 += LR) {
                         const int l = l0 + lr;
                         cdf t = cdf_zero();
-                        if (l < P.rank)
-                            for (int j = ks; j < P.klen; j += 8) cdot2(t, Wsm[j * WS + l], S.x[j * XS + q]);
+                        if (l < P.rank && ks < P.klen) {
+                            // one chain over the slice's K indices, bounded by its own terms
+                            float sw = 0.f, mxq = 0.f;
+                            for (int j = ks; j < P.klen; j += 8) {
+                                sw = __fadd_rn(sw, l1(Wsm[j * WS + l]));
+                                mxq = fmaxf(mxq, linf(S.x[j * XS + q]));
+                            }
+                            const float sg = chain_sigma(sw, mxq);
+                            cxacc c;
+                            cxfirst(c, sg, Wsm[ks * WS + l], S.x[ks * XS + q]);
+                            for (int j = ks + 8; j < P.klen; j += 8) cxstep(c, Wsm[j * WS + l], S.x[j * XS + q]);
+                            t = cxclose(c, sg);
+                        }
 #pragma unroll
                         for (int sh = 1; sh < 8; sh <<= 1) t = cdf_add(t, shfl_xor(t, sh));
                         if (ks == 0 && l < P.rank) S.t[l * RG + q] = t;
                     }
                 }
+                // T rows rank..roundup4(rank)-1 are zero; then the chunk maxima of |T.hi|
+                const int r4 = (P.rank + 3) & ~3;
+                for (int e = tid; e < (r4 - P.rank) * RG; e += RT) S.t[(P.rank + e / RG) * RG + e % RG] = cdf_zero();
+                __syncthreads();
+                if (tid < (r4 >> 2) * RG) {
+                    const int c = tid / RG, q = tid % RG;
+                    float m = 0.f;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const cdf tv = S.t[(4 * c + u) * RG + q];
+                        m = fmaxf(m, fmaxf(fabsf(tv.re.hi), fabsf(tv.im.hi)));
+                    }
+                    S.mt[c * RGMAX + q] = m;
+                }
                 __syncthreads();
                 // stage 2: out[i][q] += sum_l Y[i][l] T[l][q]
                 if (i < P.olen) {
-                    for (int l = 0; l < P.rank; ++l) {
-                        const float2 yv = Ysm[l * BS + i];
+                    // one chain per right-hand side over four rank rows (T is zero past rank)
+                    for (int l0 = 0; l0 < P.rank; l0 += 4) {
+                        float2 yv[4];
+                        float sy = 0.f;
 #pragma unroll
-                        for (int q = 0; q < QN; ++q) cdot2_df(acc[q], yv, S.t[l * RG + QN * hh + q]);
+                        for (int u = 0; u < 4; ++u) {
+                            yv[u] = l0 + u < P.rank ? Ysm[(l0 + u) * BS + i] : make_float2(0.f, 0.f);
+                            sy = __fadd_rn(sy, l1(yv[u]));
+                        }
+                        const float *mq = S.mt + (l0 >> 2) * RGMAX + QN * hh;
+                        float sg[QN];
+                        cxacc c[QN];
+#pragma unroll
+                        for (int q = 0; q < QN; ++q) {
+                            sg[q] = chain_sigma(sy, mq[q]);
+                            cxfirst_df(c[q], sg[q], yv[0], S.t[l0 * RG + QN * hh + q]);
+                        }
+#pragma unroll
+                        for (int u = 1; u < 4; ++u)
+#pragma unroll
+                            for (int q = 0; q < QN; ++q) cxstep_df(c[q], yv[u], S.t[(l0 + u) * RG + QN * hh + q]);
+#pragma unroll
+                        for (int q = 0; q < QN; ++q) acc[q] = cdf_add(acc[q], cxclose(c[q], sg[q]));
                     }
                 }
             }
