@@ -95,8 +95,12 @@ __device__ __forceinline__ cdf cdf_add(const cdf &a, const cdf &b) { return {df_
 // summation part I: faithful rounding", SIAM J. Sci. Comput. 31(1), 2008),
 // applied here to each exact product through the FMA.  sigma comes from a
 // bound of the chain's own terms (sum of |a|_1 times max |b|_inf), so the
-// grid follows the data and the error stays at Dot2's level, a few units of
-// 2^-48 of sum |a_k b_k| for chains of up to 8 real terms.
+// grid follows the data.  Each remainder is rounded once, on a grid of about
+// 2^-23 sigma with sigma 10-30 times the terms' size: over chains of 4-8 real
+// terms the error is typically 3-12 units of 2^-48 of sum |a_k b_k| and stays
+// within 2^-38, against a few units for Dot2 (an exact model of both is in the
+// tests).  That is 10^4 times and more below FP32 summation, and below the
+// complex64 rounding of the residual these sums feed.
 struct xacc { float tau, r; };
 struct cxacc { xacc re, im; };
 

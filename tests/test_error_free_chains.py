@@ -1,0 +1,220 @@
+"""The short error-free chains of the FP64-class residual kernels, modelled in
+exact rational arithmetic.
+
+The residual kernels sum each short run of products a_k b_k (complex64 data)
+with a biased accumulator: sigma is the least power of two >= 4 (sum |a|_1)
+(max |b|_inf), tau starts at sigma, and every step is
+
+    tau' = fma(a, b, tau);  q = tau' - tau;  r += fma(a, b, -q)
+
+so that the run's sum is (tau - sigma) + r.  This is the ExtractScalar step of
+Rump, Ogita & Oishi ("Accurate floating-point summation part I: faithful
+rounding", SIAM J. Sci. Comput. 31(1), 2008) applied through the FMA.  The
+model below rounds every FP32 operation exactly (round to nearest, ties to
+even, with subnormals) and checks what the kernels rely on:
+  * q = tau' - tau is exact at every step, and tau stays within [3/4, 5/4] sigma;
+  * tau - sigma is exact;
+  * the sum's error stays within 2^-38 of sum |a_k b_k| (typically 3-12 units
+    of 2^-48: each remainder is rounded once on a grid of about 2^-23 sigma,
+    and sigma is 10-30 times the terms' size), 10^4 times and more below plain
+    FP32 summation.  Dot2 (Ogita, Rump & Oishi 2005), modelled alongside, stays
+    within a few units of 2^-48: the chains trade about 5 bits of the block
+    sums for 2.5 times fewer operations.
+"""
+from fractions import Fraction as F
+
+import numpy as np
+import pytest
+
+EMIN = -126      # smallest normal exponent of binary32
+
+
+def f32(x):
+    """x (a Fraction) rounded to the nearest binary32 value, ties to even."""
+    if x == 0:
+        return F(0)
+    s = -1 if x < 0 else 1
+    x = abs(x)
+    e = x.numerator.bit_length() - x.denominator.bit_length()
+    if F(2) ** e > x:
+        e -= 1
+    e = max(e, EMIN)                       # subnormals share the grid of 2^-126
+    ulp = F(2) ** (e - 23)
+    m = x / ulp
+    lo = m.numerator // m.denominator
+    rem = m - lo
+    if rem > F(1, 2) or (rem == F(1, 2) and lo % 2 == 1):
+        lo += 1
+    assert lo <= 2 ** 24
+    return s * lo * ulp
+
+
+def fma(a, b, c):
+    return f32(a * b + c)
+
+
+def add(a, b):
+    return f32(a + b)
+
+
+def sub(a, b):
+    return f32(a - b)
+
+
+def pow2_ceil(v):
+    """The least power of two >= v for v > 0 (2^-126 for subnormals), 0 for 0."""
+    if v == 0:
+        return F(0)
+    e = EMIN
+    while F(2) ** e < v:
+        e += 1
+    return F(2) ** e
+
+
+def chain_sigma(sa, mb):
+    return pow2_ceil(f32(f32(4 * sa) * mb))
+
+
+def real_chain(terms, sigma, check=True):
+    """(tau - sigma, r) of a biased chain over real terms (a, b)."""
+    tau, r = sigma, F(0)
+    for a, b in terms:
+        t2 = fma(a, b, tau)
+        q = sub(t2, tau)
+        if check:
+            assert q == t2 - tau                                   # Sterbenz: exact
+            assert F(3, 4) * sigma <= t2 <= F(5, 4) * sigma or sigma == 0
+        r = add(r, fma(a, b, -q))
+        tau = t2
+    S = sub(tau, sigma)
+    if check:
+        assert S == tau - sigma
+    return S, r
+
+
+def complex_chain(a, b):
+    """sum_k a_k b_k for complex64 a, b (lists of (re, im) Fractions), as the
+    kernels run it: one sigma for the real and the imaginary chain."""
+    sa = F(0)
+    for ar, ai in a:
+        sa = add(sa, add(abs(ar), abs(ai)))
+    mb = max(max(abs(br), abs(bi)) for br, bi in b)
+    sigma = chain_sigma(sa, mb)
+    re_terms, im_terms = [], []
+    for (ar, ai), (br, bi) in zip(a, b):
+        re_terms += [(ar, br), (-ai, bi)]
+        im_terms += [(ar, bi), (ai, br)]
+    Sr, rr = real_chain(re_terms, sigma)
+    Si, ri = real_chain(im_terms, sigma)
+    return (Sr + rr, Si + ri)
+
+
+def two_sum(a, b):
+    s = add(a, b)
+    bb = sub(s, a)
+    return s, add(sub(a, sub(s, bb)), sub(b, bb))
+
+
+def dot2_real(terms):
+    """Dot2: every product split exactly (p + ep), every sum compensated."""
+    hi, lo = F(0), F(0)
+    for a, b in terms:
+        p = f32(a * b)
+        ep = fma(a, b, -p)
+        hi, q = two_sum(hi, p)
+        lo = add(lo, add(q, ep))
+    return hi + lo
+
+
+def dot2_complex(a, b):
+    re_terms, im_terms = [], []
+    for (ar, ai), (br, bi) in zip(a, b):
+        re_terms += [(ar, br), (-ai, bi)]
+        im_terms += [(ar, bi), (ai, br)]
+    return dot2_real(re_terms), dot2_real(im_terms)
+
+
+def _c64(rng, n, spread):
+    x = (rng.normal(size=n) + 1j * rng.normal(size=n)) * np.exp(spread * rng.normal(size=n))
+    return [(F(float(np.float32(v.real))), F(float(np.float32(v.imag)))) for v in x]
+
+
+def _exact(a, b):
+    re = sum(ar * br - ai * bi for (ar, ai), (br, bi) in zip(a, b))
+    im = sum(ar * bi + ai * br for (ar, ai), (br, bi) in zip(a, b))
+    mag = sum((abs(ar) + abs(ai)) * (abs(br) + abs(bi)) for (ar, ai), (br, bi) in zip(a, b))
+    return re, im, mag
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("spread", [0.0, 1.5])
+def test_chain_is_exact_where_claimed_and_accurate(L, spread):
+    # runs of L complex products (2L real terms per part), as in the kernels:
+    # L = 2 for a lane's two columns of a row, 4 for four rows / K indices / rank rows
+    rng = np.random.default_rng(10 * L + int(spread))
+    units = 2.0 ** -48
+    chain, dot2 = [], []
+    for _ in range(150):
+        a, b = _c64(rng, L, spread), _c64(rng, L, spread)
+        re, im, mag = _exact(a, b)
+        got_re, got_im = complex_chain(a, b)
+        chain.append(float(max(abs(got_re - re), abs(got_im - im)) / mag) / units)
+        d_re, d_im = dot2_complex(a, b)
+        dot2.append(float(max(abs(d_re - re), abs(d_im - im)) / mag) / units)
+    assert max(chain) < 1024 and np.median(chain) < 32
+    assert max(dot2) < 8
+
+
+def test_chain_beats_fp32_summation_on_cancelling_sums():
+    # sums that cancel to 1e-6 of their terms: FP32 loses about every digit,
+    # the chain keeps the result within 2^-38 of sum |a b|
+    rng = np.random.default_rng(3)
+    worst_chain = worst_fp32 = 0.0
+    for _ in range(100):
+        a, b = _c64(rng, 4, 0.0), _c64(rng, 4, 0.0)
+        re, im, mag = _exact(a, b)
+        # shift the last term so that the real part nearly cancels
+        ar, ai = a[-1]
+        br, bi = b[-1]
+        target = -(re - (ar * br - ai * bi)) + F(float(np.float32(1e-6))) * mag
+        a[-1] = (f32(target / br + ai * bi / br) if br != 0 else ar, ai)
+        re, im, mag = _exact(a, b)
+        got_re, _ = complex_chain(a, b)
+        plain = F(0)
+        for (xr, xi), (yr, yi) in zip(a, b):
+            plain = f32(plain + f32(f32(xr * yr) - f32(xi * yi)))
+        worst_chain = max(worst_chain, float(abs(got_re - re) / mag))
+        worst_fp32 = max(worst_fp32, float(abs(plain - re) / mag))
+    assert worst_chain < 1024 * 2.0 ** -48
+    assert worst_fp32 > 1e4 * worst_chain
+
+
+def test_chain_edge_cases():
+    z = [(F(0), F(0))] * 4
+    one = [(F(1), F(0))] * 4
+    assert complex_chain(z, one) == (0, 0)                 # sigma = 0: every product is zero
+    assert complex_chain(one, z) == (0, 0)
+    # exact cancellation to zero
+    a = [(F(3), F(0)), (F(-3), F(0))]
+    b = [(F(5, 4), F(0)), (F(5, 4), F(0))]
+    assert complex_chain(a, b) == (0, 0)
+    # a subnormal bound: sigma is the smallest normal power of two, the sum still right
+    tiny = F(2) ** -140
+    got = complex_chain([(tiny, F(0))], [(F(1, 2), F(0))])
+    assert got == (tiny / 2, 0)
+    # the bound is met with equality at a power of two: tau still within [3/4, 5/4] sigma
+    a = [(F(1), F(0))] * 4
+    b = [(F(1), F(0))] * 4
+    assert complex_chain(a, b) == (4, 0)
+
+
+def test_pow2_ceil_matches_the_bit_trick():
+    # the kernels take (bits(v) + 0x7FFFFF) & 0xFF800000; the model's definition agrees
+    rng = np.random.default_rng(5)
+    vals = np.concatenate([np.float32(2.0) ** np.arange(-149, 127, 7, dtype=np.float32),
+                           rng.random(200).astype(np.float32) * np.float32(1e3),
+                           np.array([0.0, 1.0, 1.5, 3.0, 1e-40, 1e-45], dtype=np.float32)]).astype(np.float32)
+    bits = vals.view(np.uint32)
+    trick = ((bits.astype(np.uint64) + 0x007FFFFF) & 0xFF800000).astype(np.uint32).view(np.float32)
+    for v, t in zip(vals, trick):
+        assert F(float(t)) == pow2_ceil(F(float(v))), v
