@@ -17,10 +17,11 @@ using kc::FULL;
 // therefore use error-free transformations in FP32 (Ogita, Rump & Oishi,
 // "Accurate sum and dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2):
 // every product a*b is split exactly into p + e with e = fma(a, b, -p), and
-// every sum is compensated (Knuth's TwoSum), so each block's sums are as
-// accurate as if computed in twice the working precision.  The per-block
-// results are stored as FP64 partial slots and summed across blocks in FP64.
-// df, cdf: hm_internal.h
+// every sum is compensated (Knuth's TwoSum), so the sums are as accurate as if
+// computed in twice the working precision.  Dot2 serves the leaf gathers
+// (D x) and the low-rank blocks larger than 64 x 64; the block products of
+// the residual kernels use the cheaper biased chains further down, folded into
+// double-float sums (df_add).  df, cdf: hm_internal.h
 
 // The error-free transformations below must not be contracted into FMAs or
 // reassociated, so every operation is an explicitly rounded intrinsic.
