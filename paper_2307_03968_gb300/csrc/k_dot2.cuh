@@ -84,11 +84,11 @@ __device__ __forceinline__ cdf cdf_add(const cdf &a, const cdf &b) { return {df_
 // Short error-free chains with a biased accumulator (four operations per real
 // product against ten for Dot2).
 //
-// For a short sum s = sum_k a_k b_k with sum_k |a_k b_k| <= sigma / 4, sigma a
+// For a short sum s = sum_k a_k b_k with sum_k |a_k b_k| < sigma / 2, sigma a
 // power of two, the accumulator tau starts at sigma and stays within
-// [3/4, 5/4] sigma.  Each step
+// [1/2, 3/2] sigma, where every float is a multiple of 2^-24 sigma.  Each step
 //   tau' = fma(a, b, tau)     the exact product rounded once onto tau's grid,
-//   q    = tau' - tau         exact (Sterbenz: tau and tau' within a factor 2),
+//   q    = tau' - tau         exact (a multiple of 2^-24 sigma, |q| <= sigma / 2),
 //   r   += fma(a, b, -q)      the product's remainder below the grid,
 // leaves s = (tau - sigma) + r with tau - sigma exact; only r, whose terms are
 // at most ulp(sigma) ~ 2^-23 sigma, is rounded.  The grid extraction is the
@@ -97,9 +97,9 @@ __device__ __forceinline__ cdf cdf_add(const cdf &a, const cdf &b) { return {df_
 // applied here to each exact product through the FMA.  sigma comes from a
 // bound of the chain's own terms (sum of |a|_1 times max |b|_inf), so the
 // grid follows the data.  Each remainder is rounded once, on a grid of about
-// 2^-23 sigma with sigma 10-30 times the terms' size: over chains of 4-8 real
-// terms the error is typically 3-12 units of 2^-48 of sum |a_k b_k| and stays
-// within 2^-38, against a few units for Dot2 (an exact model of both is in the
+// 2^-23 sigma with sigma 5-15 times the terms' size: over chains of 4-8 real
+// terms the error is typically 1.5-6 units of 2^-48 of sum |a_k b_k| and stays
+// within 2^-39, against a few units for Dot2 (an exact model of both is in the
 // tests).  That is 10^4 times and more below FP32 summation, and below the
 // complex64 rounding of the residual these sums feed.
 struct xacc { float tau, r; };
@@ -113,8 +113,11 @@ __device__ __forceinline__ float pow2_ceil(float v)
 __device__ __forceinline__ float l1(float2 a) { return __fadd_rn(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ float linf(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
 // sigma for a chain of complex products a_k b_k with sum_k |a_k|_1 = sa and
-// max_k |b_k|_inf = mb (each real part and each imaginary part sums at most sa * mb)
-__device__ __forceinline__ float chain_sigma(float sa, float mb) { return pow2_ceil(4.f * sa * mb); }
+// max_k |b_k|_inf = mb (each real part and each imaginary part sums at most
+// sa * mb): twice the bound, raised by 2^-17 against the rounding of sa, of the
+// two products and of the grid parts q, so that tau never drops below sigma / 2
+constexpr float CHAIN_MARGIN = 2.0f + 0x1p-16f;
+__device__ __forceinline__ float chain_sigma(float sa, float mb) { return pow2_ceil(CHAIN_MARGIN * sa * mb); }
 
 __device__ __forceinline__ void xfirst(xacc &c, float sigma, float a, float b)
 {

@@ -2,8 +2,8 @@
 exact rational arithmetic.
 
 The residual kernels sum each short run of products a_k b_k (complex64 data)
-with a biased accumulator: sigma is the least power of two >= 4 (sum |a|_1)
-(max |b|_inf), tau starts at sigma, and every step is
+with a biased accumulator: sigma is the least power of two >= 2 (1 + 2^-17)
+(sum |a|_1) (max |b|_inf), tau starts at sigma, and every step is
 
     tau' = fma(a, b, tau);  q = tau' - tau;  r += fma(a, b, -q)
 
@@ -12,11 +12,11 @@ Rump, Ogita & Oishi ("Accurate floating-point summation part I: faithful
 rounding", SIAM J. Sci. Comput. 31(1), 2008) applied through the FMA.  The
 model below rounds every FP32 operation exactly (round to nearest, ties to
 even, with subnormals) and checks what the kernels rely on:
-  * q = tau' - tau is exact at every step, and tau stays within [3/4, 5/4] sigma;
+  * q = tau' - tau is exact at every step, and tau stays within [1/2, 3/2] sigma;
   * tau - sigma is exact;
-  * the sum's error stays within 2^-38 of sum |a_k b_k| (typically 3-12 units
+  * the sum's error stays within 2^-39 of sum |a_k b_k| (typically 1.5-6 units
     of 2^-48: each remainder is rounded once on a grid of about 2^-23 sigma,
-    and sigma is 10-30 times the terms' size), 10^4 times and more below plain
+    and sigma is 5-15 times the terms' size), 10^4 times and more below plain
     FP32 summation.  Dot2 (Ogita, Rump & Oishi 2005), modelled alongside, stays
     within a few units of 2^-48: the chains trade about 5 bits of the block
     sums for 2.5 times fewer operations.
@@ -71,8 +71,11 @@ def pow2_ceil(v):
     return F(2) ** e
 
 
+MARGIN = F(2) + F(2) ** -16     # 2 (1 + 2^-17), exact in binary32
+
+
 def chain_sigma(sa, mb):
-    return pow2_ceil(f32(f32(4 * sa) * mb))
+    return pow2_ceil(f32(f32(MARGIN * sa) * mb))
 
 
 def real_chain(terms, sigma, check=True):
@@ -83,7 +86,7 @@ def real_chain(terms, sigma, check=True):
         q = sub(t2, tau)
         if check:
             assert q == t2 - tau                                   # Sterbenz: exact
-            assert F(3, 4) * sigma <= t2 <= F(5, 4) * sigma or sigma == 0
+            assert sigma / 2 <= t2 <= F(3, 2) * sigma or sigma == 0
         r = add(r, fma(a, b, -q))
         tau = t2
     S = sub(tau, sigma)
@@ -161,13 +164,13 @@ def test_chain_is_exact_where_claimed_and_accurate(L, spread):
         chain.append(float(max(abs(got_re - re), abs(got_im - im)) / mag) / units)
         d_re, d_im = dot2_complex(a, b)
         dot2.append(float(max(abs(d_re - re), abs(d_im - im)) / mag) / units)
-    assert max(chain) < 1024 and np.median(chain) < 32
+    assert max(chain) < 512 and np.median(chain) < 16
     assert max(dot2) < 8
 
 
 def test_chain_beats_fp32_summation_on_cancelling_sums():
     # sums that cancel to 1e-6 of their terms: FP32 loses about every digit,
-    # the chain keeps the result within 2^-38 of sum |a b|
+    # the chain keeps the result within 2^-39 of sum |a b|
     rng = np.random.default_rng(3)
     worst_chain = worst_fp32 = 0.0
     for _ in range(100):
@@ -185,7 +188,7 @@ def test_chain_beats_fp32_summation_on_cancelling_sums():
             plain = f32(plain + f32(f32(xr * yr) - f32(xi * yi)))
         worst_chain = max(worst_chain, float(abs(got_re - re) / mag))
         worst_fp32 = max(worst_fp32, float(abs(plain - re) / mag))
-    assert worst_chain < 1024 * 2.0 ** -48
+    assert worst_chain < 512 * 2.0 ** -48
     assert worst_fp32 > 1e4 * worst_chain
 
 
@@ -202,10 +205,52 @@ def test_chain_edge_cases():
     tiny = F(2) ** -140
     got = complex_chain([(tiny, F(0))], [(F(1, 2), F(0))])
     assert got == (tiny / 2, 0)
-    # the bound is met with equality at a power of two: tau still within [3/4, 5/4] sigma
+    # the bound is met with equality at a power of two: tau still within [1/2, 3/2] sigma
     a = [(F(1), F(0))] * 4
     b = [(F(1), F(0))] * 4
     assert complex_chain(a, b) == (4, 0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_chain_at_the_edge_of_its_bound(seed):
+    # every term of one sign and sum |a b| as large as sigma allows (the bound's
+    # sigma lands exactly on a power of two), each term with low bits below
+    # tau's grid, so that every step rounds: tau must stay >= sigma / 2 and q,
+    # tau - sigma exact (real_chain asserts both)
+    rng = np.random.default_rng(seed)
+    n = 4
+    b = [(F(1), F(0))] * n
+    v = [f32(F(float(x))) for x in rng.uniform(0.05, 0.11, size=n - 1)]
+    sa_rest = F(0)
+    for x in v:
+        sa_rest = add(sa_rest, x)
+    last = f32(1 / MARGIN - sa_rest)
+
+    def ulp(x):
+        e = x.numerator.bit_length() - x.denominator.bit_length()
+        if F(2) ** e > x:
+            e -= 1
+        return F(2) ** (e - 23)
+
+    # the largest last term whose chain still gets sigma = 1 (a few float steps at most)
+    for _ in range(64):
+        if chain_sigma(add(sa_rest, last), F(1)) <= 1:
+            break
+        last = f32(last - ulp(last))
+    for _ in range(64):
+        up = f32(last + ulp(last))
+        if chain_sigma(add(sa_rest, up), F(1)) > 1:
+            break
+        last = up
+    a = [(-x, F(0)) for x in v + [last]]
+    sa = F(0)
+    for ar, ai in a:
+        sa = add(sa, add(abs(ar), abs(ai)))
+    assert chain_sigma(sa, F(1)) == 1
+    got_re, got_im = complex_chain(a, b)
+    exact = sum(ar for ar, _ in a)
+    assert got_im == 0
+    assert abs(got_re - exact) <= 2.0 ** -46 * abs(exact)
 
 
 def test_pow2_ceil_matches_the_bit_trick():
