@@ -214,10 +214,14 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
 
 /*
  * r = b - A_m x, the residual of the refinement step, accumulated to FP64-class
- * accuracy: complex64 blocks and vectors, every product formed exactly (FP32
- * product plus its rounding error from an FMA), sums inside each block
- * compensated (Dot2 of Ogita, Rump & Oishi 2005), sums across blocks in FP64,
- * in a fixed order (no atomics on the sums).  b, x, r: DEVICE complex64,
+ * accuracy without FP64 arithmetic in the block products: complex64 blocks and
+ * vectors; inside each block the products are summed in short error-free runs
+ * (each exact product rounded onto a power-of-two grid bounded by the run's
+ * own terms, ExtractScalar of Rump, Ogita & Oishi 2008 through the FMA, with
+ * the remainders below the grid summed apart) folded into double-float sums.
+ * A block sum errs by at most 2^-39 of sum |a b| (typically 2^-46..2^-47).
+ * Sums across blocks and b - A x are formed in FP64, in a fixed order (no
+ * atomics on the sums).  b, x, r: DEVICE complex64,
  * original order; r must not overlap b or x.  norms: NULL, or HOST array of
  * 2*nrhs doubles receiving |r_j|^2 and |b_j|^2 (the call then synchronises).
  * Needs hm_factor_leaf (it prepares the complex64 copy of D).
