@@ -219,7 +219,7 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
  * (each exact product rounded onto a power-of-two grid bounded by the run's
  * own terms, ExtractScalar of Rump, Ogita & Oishi 2008 through the FMA, with
  * the remainders below the grid summed apart) folded into double-float sums.
- * A block sum errs by at most 2^-39 of sum |a b| (typically 2^-46..2^-47).
+ * A block sum errs by at most 2^-39 of sum |a b| (typically 2^-45..2^-47).
  * Sums across blocks and b - A x are formed in FP64, in a fixed order (no
  * atomics on the sums).  b, x, r: DEVICE complex64,
  * original order; r must not overlap b or x.  norms: NULL, or HOST array of
