@@ -49,17 +49,6 @@ __device__ __forceinline__ void cdot2(cdf &acc, float2 a, float2 b)
     dot2(acc.im, a.x, b.y);
     dot2(acc.im, a.y, b.x);
 }
-// acc = a * b for complex a, b: the same result as cdot2 into a zero accumulator
-// (the first real product of each part is taken as its exact split p + e directly)
-__device__ __forceinline__ void cdot2_first(cdf &acc, float2 a, float2 b)
-{
-    acc.re.hi = __fmul_rn(a.x, b.x);
-    acc.re.lo = __fmaf_rn(a.x, b.x, -acc.re.hi);
-    dot2(acc.re, -a.y, b.y);
-    acc.im.hi = __fmul_rn(a.x, b.y);
-    acc.im.lo = __fmaf_rn(a.x, b.y, -acc.im.hi);
-    dot2(acc.im, a.y, b.x);
-}
 // acc += a * (bh + bl) for complex a and a double-float complex b
 __device__ __forceinline__ void cdot2_df(cdf &acc, float2 a, const cdf &b)
 {
