@@ -1,21 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the multi-level power-series solve (arxiv 2307.03968 §IV).
 
-Workload (default): S-EFIE PEC sphere of radius 2 wavelengths, icosphere with
-20,480 triangles -> 30,720 RWG unknowns, octree with leaves of <= 64 unknowns,
-admissibility dist >= 2 * min(diam), ACA tolerance 1e-4, complex64 on the GPU,
-one plane-wave right-hand side (+z incidence, x polarised).  The operator is
-built on the GPU (hm_build) and its leaf blocks factored (hm_factor_leaf)
-before timing; it stays resident in HBM (about 1.5 GB of blocks, larger than
-L2, so no L2 flush is needed between steps).
+Headline workload (default): S-EFIE PEC sphere of radius 2 wavelengths,
+icosphere with 20,480 triangles -> 30,720 RWG unknowns, octree with leaves of
+<= 64 unknowns, admissibility dist >= 2 * min(diam), ACA tolerance 1e-4,
+complex64 on the GPU, one plane-wave right-hand side (+z incidence, x
+polarised).  The operator is built on the GPU (hm_build) and its leaf blocks
+factored (hm_factor_leaf) before timing; it stays resident in HBM (about 1.5 GB
+of blocks, larger than L2, so no L2 flush is needed between steps).
 
 One step = one hm_powerseries_solve with the paper's settings: leaf level only,
-K = 2 terms, plus the FP64-accumulated residual and one refinement step — the
-whole hot path (permute, D^{-1}, K x (near/far product + series accumulate),
+K = 2 terms, plus the FP64-class residual and one refinement step -- the whole
+hot path (permute, D^{-1}, K x (near/far product + series accumulate),
 residual, correction solve, un-permute).
 
-Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead
-(a bounded sample of the same workload, scaled to the whole operator).
+The default run also measures, in the same process, the other workloads of the
+measurement plan under "configs": the 1,920-unknown sphere (latency), the
+181-right-hand-side monostatic sweep on the headline operator, the
+41,850-unknown dielectric cube with 16 right-hand sides, and a short serving
+stream (--no-configs skips them).
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead:
+it builds the whole headline operator with the oracle and times series.solve
+on it, on one core and on every host core (independent right-hand sides, one
+per process).
 """
 
 import argparse
@@ -26,6 +34,11 @@ import subprocess
 import sys
 import tempfile
 import time
+
+if "--impl" in sys.argv and "reference" in sys.argv:
+    # the oracle's solve is numpy on small blocks: one BLAS thread per process, so that
+    # "one core" is one core and the all-core run is one process per core
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -57,6 +70,10 @@ WORKLOADS = {
                            shape=("shell", (0.35, 0.4, 6.0), (1, 55, 206)), eps=2.0, leaf_size=64, arity=2, adm=1.0,
                            aca_tol=1e-3, n_terms=2, n_levels=1, refine=False, nrhs=1, unknowns=158730,
                            tetrahedra=67980),
+    # the small sphere of the measurement plan (1,920 RWG unknowns, leaf 32): latency, operator L2-resident
+    "sphere03": dict(name="sefie_pec_sphere_r0.3lambda_1920rwg", kind="rwg", subdivisions=3, radius=0.3, leaf_size=32,
+                     arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=1920,
+                     triangles=1280),
     # a smaller sphere of the same family (7,680 unknowns), for profiler captures
     "sphere1": dict(name="sefie_pec_sphere_r1lambda_7680rwg", kind="rwg", subdivisions=4, radius=1.0, leaf_size=64,
                     arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=7680,
@@ -129,8 +146,11 @@ def workload_config(w):
                   "rhs": "%d plane waves, random incidence and polarisation, seed %d" % (w["nrhs"], w["rhs_seed"])})
     c.update({"leaf_size": w["leaf_size"], "aca_tol": w["aca_tol"], "n_terms": w["n_terms"],
               "levels": "leaf level only", "refine": "one FP64-residual refinement step", "nrhs": w["nrhs"],
-              "l2": "operator resident in HBM is larger than L2; no flush", "parallelism": "replicas"})
+              "l2": ("operator resident in HBM is larger than L2; no flush" if w["unknowns"] > 5000 else
+                     "operator fits L2 (a latency workload); no flush"), "parallelism": "replicas"})
     return c
+
+
 
 
 def parse():
@@ -141,12 +161,18 @@ def parse():
     p.add_argument("--impl", default="hm", choices=["hm", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-extras", action="store_true", help="skip the unrefined / full-level timings")
+    p.add_argument("--no-extras", action="store_true", help="skip the unrefined / full-level / FP64 timings")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other workloads of the default run (1,920-unknown sphere, 181-RHS sweep, "
+                        "dielectric cube, serving stream)")
     p.add_argument("--workload", default="sphere2", choices=sorted(WORKLOADS))
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU time budget of the oracle sample")
+    p.add_argument("--ref-seconds", type=float, default=90.0,
+                   help="wall-time budget of the reference arm's timed oracle solves (after its build)")
     p.add_argument("--pin-product", type=int, default=None,
                    help="pin the many-RHS product kernel (0, 8, 16, 32, 1016 = tensor cores) instead of autotuning")
-    p.add_argument("--pin-residual", type=int, default=None, help="pin the many-RHS residual kernel (0, 8, 16)")
+    p.add_argument("--pin-residual", type=int, default=None,
+                   help="pin the many-RHS residual kernel (0, 8, 16, 1017 = owner-computes)")
     return p.parse_args()
 
 
@@ -168,7 +194,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# ---------------------------------------------------------------- oracle sample --
+# ---------------------------------------------------------------- oracle --------
 def oracle_sample_rate(cpu_seconds, warmup=1, steps=None):
     """Time the CPU oracle's power-series solve (series.solve, leaf level, K=2,
     refine) on a sample of the workload's operator: the leaf self blocks of
@@ -240,9 +266,92 @@ def oracle_sample_rate(cpu_seconds, warmup=1, steps=None):
     return dict(value=nrhs / t, unit="RHS/s", cores=cores, kind="oracle",
                 sample="oracle series.solve (K=2, leaf level, refine, %d RHS) on %d of %d leaves with their %d near "
                        "and %d leaf-level far block rows (%.1f%% of the stored elements, far elements of unsampled "
-                       "rows estimated from the sample's mean rank); median of %d solves scaled by %.1f"
+                       "rows estimated from the sample's mean rank); median of %d solves scaled by %.1f; the "
+                       "whole-operator oracle, on one core and on all cores, is the --impl reference line"
                        % (nrhs, S, len(leaves), len(Hs.near), len(Hs.far[1]), 100.0 / scale, n, scale),
                 solve_s_scaled=t, n_timed=n)
+
+
+_REF = {}     # the reference arm's oracle operator, inherited by its forked workers
+
+
+def _ref_worker(reps, ready, go, out):
+    """One process of the all-core reference run: `reps` solves of the parent's
+    operator (inherited copy-on-write through fork), after the common start."""
+    from oracle import series
+    w = _REF["w"]
+    ready.put(os.getpid())
+    go.wait()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        series.solve(_REF["H"], _REF["b"], K=w["n_terms"], levels=1, refine=w["refine"])
+    out.put(time.perf_counter() - t0)
+
+
+def oracle_reference(w, steps, warmup, budget_s):
+    """The reference arm: the oracle builds the WHOLE operator of the workload
+    (complex128 fill, ACA, re-compression; the leaf level the solve uses) and
+    series.solve is timed on it, unsampled:
+      - on one core: `warmup` untimed solves, then single solves until a third
+        of the budget is spent (at least one);
+      - on every host core: one forked process per core, each solving its own
+        copy of the right-hand side `reps` times, all started together; the
+        rate is the total number of solves over the wall time.
+    No GPU is touched in this process, so forking after the build is safe."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle.rwg import RWGMesh
+    from oracle.swg import SWGMesh
+    from oracle.hmatrix import HMatrix
+    from oracle import series
+    xyz, cells, eps = workload_mesh(w)
+    mesh = RWGMesh(xyz, cells) if w["kind"] == "rwg" else SWGMesh(xyz, cells, eps)
+    t0 = time.perf_counter()
+    H = HMatrix(mesh, leaf_size=w["leaf_size"], arity=w["arity"], adm=w["adm"], aca_tol=w["aca_tol"], levels=1)
+    build_s = time.perf_counter() - t0
+    b = mesh.rhs(*workload_incidences(w))
+    _REF.update(H=H, b=b, w=w)
+    for _ in range(warmup):
+        series.solve(H, b, K=w["n_terms"], levels=1, refine=w["refine"])
+    single, cpu = [], []
+    t_end = time.perf_counter() + budget_s / 3.0
+    while not single or (time.perf_counter() < t_end and len(single) < max(steps, 1)):
+        c0, s0 = time.process_time(), time.perf_counter()
+        series.solve(H, b, K=w["n_terms"], levels=1, refine=w["refine"])
+        single.append(time.perf_counter() - s0)
+        cpu.append(time.process_time() - c0)
+    t1 = statistics.median(single)
+    P = max(1, os.cpu_count() or 1)
+    reps = max(1, min(-(-max(steps, 1) // P), int((budget_s * 2.0 / 3.0) / max(t1, 1e-3) / 2)))
+    ctx = mp.get_context("fork")
+    ready, out = ctx.Queue(), ctx.Queue()
+    go = ctx.Event()
+    procs = [ctx.Process(target=_ref_worker, args=(reps, ready, go, out)) for _ in range(P)]
+    for p in procs:
+        p.start()
+    for _ in procs:
+        ready.get(timeout=600)
+    s0 = time.perf_counter()
+    go.set()
+    per = [out.get(timeout=3600) for _ in procs]
+    wall = time.perf_counter() - s0
+    for p in procs:
+        p.join(timeout=60)
+    n_all = P * reps
+    nrhs = b.shape[1]
+    st = H.stats()
+    return dict(value=n_all * nrhs / wall, steps=n_all, ms_per_step=1e3 * wall / n_all, cores=P, wall_s=wall,
+                single_core_value=nrhs / t1, single_core_ms=1e3 * t1, single_core_steps=len(single),
+                single_core_cores_used=max(1, round(sum(cpu) / max(sum(single), 1e-9))), build_s=build_s,
+                worker_s=[round(v, 3) for v in per],
+                sample="the whole leaf-level operator built by the oracle (%d unknowns, %d near blocks with %d "
+                       "elements, %d leaf-level far blocks with %d elements, %d leaf self blocks; build %.0f s on "
+                       "%d cores); series.solve (K=%d, leaf level, refine=%s, %d RHS) timed %d times on one core "
+                       "(median %.2f s) and %d times on %d cores (%d processes x %d solves, all started together, "
+                       "%.2f s wall)"
+                       % (H.N, st["near_blocks"], st["near_elems"], st["far_blocks"].get(1, 0),
+                          st["far_elems"].get(1, 0), st["leaves"], build_s, P, w["n_terms"], w["refine"], nrhs,
+                          len(single), t1, n_all, P, P, reps, wall))
 
 
 # ---------------------------------------------------------------- clocks --------
@@ -324,6 +433,184 @@ def replica_rate(steps, nrhs, world, ms):
     return steps * nrhs * world / (ms / 1e3)
 
 
+# ---------------------------------------------------------------- timing --------
+def timed_solves(A, b, x, opts, K, W, stream, barrier, local):
+    """W untimed solves, then K solves each bracketed by CUDA events on the launching
+    stream, with nvidia-smi clocks sampled over the timed region.  Returns (total
+    ms from the first start to the last end, sorted per-solve ms, clocks)."""
+    import torch
+    for _ in range(W):
+        A.solve(b, x, **opts)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    for i in range(K):
+        starts[i].record(stream)
+        A.solve(b, x, **opts)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = starts[0].elapsed_time(ends[-1])
+    lat = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
+    return total_ms, lat, clk
+
+
+def pct(lat, q):
+    return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+
+
+def product_roofline(A, b, x, opts, nrhs, Kp, sm_max):
+    """The same solves launched kernel by kernel, with CUDA events around every
+    launch of the block-product kernel on its stream (graph replay hides them);
+    achieved = algorithmic bytes (or flops) per launch / mean launch time.
+    Returns (roofline dict, eager ms per solve)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    A.profile(True)
+    p0.record(stream)
+    for _ in range(Kp):
+        A.solve(b, x, graph=False, **opts)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms, prof_n, prof_bytes = A.profile_read()
+    A.profile(False)
+    eager_ms = p0.elapsed_time(p1) / Kp
+    peak, peak_kind = peaks()
+    per_launch_bytes = prof_bytes / max(prof_n, 1)
+    per_launch_ms = prof_ms / max(prof_n, 1)
+    # every stored complex element is used twice per right-hand side (the block and its
+    # half-storage mirror): 2 complex multiply-adds = 16 real flops per 8 bytes per RHS
+    flops_per_launch = 2.0 * per_launch_bytes * nrhs
+    alu_peak = 152 * 128 * 2 * (sm_max or 2070.0) * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
+    prod_choice = A.tuning(nrhs)[0] if nrhs >= 4 else 0
+    if prod_choice == 1016:
+        # tensor-core product (3xTF32): three TF32 MMAs per useful FP32-accurate product, so its roof is
+        # the TF32 tensor peak / 3; the TF32 peak is the measured sustained bf16 peak x the nominal
+        # TF32/bf16 ratio (1.1 / 2.25 PFLOP/s dense)
+        bf16_s = (PEAKS or {}).get("bf16_tflops_sustained")
+        tf32 = (bf16_s if bf16_s else 1700.0) * 1.1 / 2.25
+        bound, unit, rpeak = "tensor", "TFLOP/s", tf32 / 3.0
+        rkind = ("measured sustained bf16 %.1f TFLOP/s x 1.1/2.25 (TF32) / 3 (3xTF32 products)" % bf16_s if bf16_s
+                 else "fallback 1.7 PFLOP/s bf16 sustained x 1.1/2.25 / 3")
+        kernel = ("k_split_x + k_apply_tc (tcgen05 kind::tf32, 3xTF32; blocks <= 64 x 64, rank <= 32) "
+                  "+ k_apply_items for larger blocks (k_mrhs_tc.cu, k_product.cu)")
+    elif flops_per_launch / (alu_peak * 1e12) > per_launch_bytes / (peak * 1e9):
+        bound, unit, rpeak = "alu", "TFLOP/s", alu_peak
+        rkind = "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
+        kernel = ("k_apply_mrhs<%d> (shared-memory SIMT, %d RHS per chunk) + k_apply_items for larger blocks "
+                  "(k_mrhs.cu, k_product.cu)" % (prod_choice, prod_choice) if prod_choice
+                  else "k_apply_items<float,float,3> (one RHS at a time, k_product.cu)")
+    else:
+        bound, unit, rpeak, rkind = "hbm", "GB/s", peak, peak_kind
+        kernel = "k_apply_items<float,float,3> (near + leaf-level far block product, k_product.cu)"
+    achieved = None
+    if prof_n:
+        achieved = (flops_per_launch / (per_launch_ms * 1e-3) / 1e12 if unit == "TFLOP/s"
+                    else per_launch_bytes / (per_launch_ms * 1e-3) / 1e9)
+    roof = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": rpeak, "peak_kind": rkind, "unit": unit,
+            "frac": (achieved / rpeak) if achieved else None, "traffic": None,
+            "bytes_per_launch": per_launch_bytes, "flops_per_launch": flops_per_launch, "nrhs": nrhs,
+            "ms_per_launch": per_launch_ms, "launches": prof_n,
+            "hbm_gbs": per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if prof_n else None,
+            "share_of_step": (prof_ms / Kp / eager_ms) if eager_ms else None,
+            "measured_on": "the timed solve launched kernel by kernel (%d steps, %.4f ms/step)" % (Kp, eager_ms)}
+    return roof, eager_ms
+
+
+def series_report(A, si):
+    """Convergence of the series on this operator (the library's estimates of
+    ||D^-1 M_l||_2 and of the spectral radius per level, hm_estimate_norms) and the
+    relative residual |b - A x| / |b| of the refined solution (max over columns)."""
+    info = A.info()
+    nl = max(1, min(info.n_levels, 16))
+    return {"rel_residual": si.rel_residual, "convergent": si.convergent, "norm_iters": info.norm_iters,
+            "norm_est": [round(v, 6) for v in info.norm_est[:nl]],
+            "rho_est": [round(v, 6) for v in info.rho_est[:nl]],
+            "note": "norm_est / rho_est per level (level 1 = leaf); the K-term series converges to A^-1 b "
+                    "only where rho < 1; parity is against the oracle running the same K-term algorithm"}
+
+
+def gpu_build(w):
+    from paper_2307_03968_gb300.hm import HMatrix
+    xyz, cells, eps = workload_mesh(w)
+    t0 = time.perf_counter()
+    A = HMatrix.build(xyz, cells, eps_r=eps, leaf_size=w["leaf_size"], arity=w["arity"], adm=w["adm"],
+                      aca_tol=w["aca_tol"], levels=-1)
+    A.factor_leaf()
+    return A, time.perf_counter() - t0
+
+
+def config_line(w, A, nrhs, total_ms, K, lat, clk, roof, si, build_s, tuning=None, note=None):
+    c = workload_config(w)
+    c["nrhs"] = nrhs
+    d = {"config": c, "value": K * nrhs / (total_ms / 1e3), "unit": "RHS/s", "steps": K,
+         "ms_per_step": total_ms / K, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "build_s": build_s,
+         "roofline": roof, "series": series_report(A, si), "clocks": clk}
+    if tuning is not None:
+        d["tuning"] = dict(zip(("product_kernel", "residual_kernel", "product_ms", "residual_ms"), tuning))
+    if note:
+        d["note"] = note
+    return d
+
+
+def extra_configs(A2, local, barrier):
+    """The other workloads of the measurement plan, timed in the same process as
+    the headline (graph-replayed solves, CUDA events on the launching stream)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    # config 1: 1,920-unknown sphere, 1 RHS: latency of single solves (operator L2-resident)
+    w = WORKLOADS["sphere03"]
+    A, bs = gpu_build(w)
+    b = torch.empty((1, A.n), dtype=torch.complex64, device="cuda")
+    A.rhs_plane_wave(*workload_incidences(w), b)
+    x = torch.empty_like(b)
+    opts = dict(n_terms=w["n_terms"], n_levels=w["n_levels"], refine=w["refine"])
+    si = A.solve(b, x, info=True, **opts)
+    total, lat, clk = timed_solves(A, b, x, opts, 300, 20, stream, barrier, local)
+    out["sphere03"] = config_line(w, A, 1, total, 300, lat, clk, None, si, bs,
+                                  note="operator %.1f MB, L2-resident: latency, no roofline line"
+                                       % (A.info().device_bytes / 1e6))
+    out["sphere03"]["launches_per_step"] = int(si.kernel_launches)
+    A.close()
+    # config 3: the headline operator, 181-RHS monostatic sweep (autotuned kernels)
+    w = WORKLOADS["sphere2_sweep181"]
+    kh, ph = workload_incidences(w)
+    b = torch.empty((len(kh), A2.n), dtype=torch.complex64, device="cuda")
+    A2.rhs_plane_wave(kh, ph, b)
+    x = torch.empty_like(b)
+    opts = dict(n_terms=w["n_terms"], n_levels=w["n_levels"], refine=w["refine"])
+    si = A2.solve(b, x, info=True, **opts)                 # autotunes the 256-RHS bucket, then solves
+    total, lat, clk = timed_solves(A2, b, x, opts, 6, 2, stream, barrier, local)
+    roof, _ = product_roofline(A2, b, x, opts, len(kh), 2, (clk or {}).get("sm_max_mhz"))
+    out["sphere2_sweep181"] = config_line(w, A2, len(kh), total, 6, lat, clk, roof, si, 0.0,
+                                          tuning=A2.tuning(len(kh)),
+                                          note="the headline operator (built once)")
+    del b, x
+    # config 4: dielectric cube, 41,850 SWG unknowns, 16 RHS
+    w = WORKLOADS["vefie_cube"]
+    A, bs = gpu_build(w)
+    kh, ph = workload_incidences(w)
+    b = torch.empty((len(kh), A.n), dtype=torch.complex64, device="cuda")
+    A.rhs_plane_wave(kh, ph, b)
+    x = torch.empty_like(b)
+    opts = dict(n_terms=w["n_terms"], n_levels=w["n_levels"], refine=w["refine"])
+    si = A.solve(b, x, info=True, **opts)
+    total, lat, clk = timed_solves(A, b, x, opts, 10, 3, stream, barrier, local)
+    roof, _ = product_roofline(A, b, x, opts, len(kh), 3, (clk or {}).get("sm_max_mhz"))
+    out["vefie_cube"] = config_line(w, A, len(kh), total, 10, lat, clk, roof, si, bs, tuning=A.tuning(len(kh)))
+    A.close()
+    del b, x
+    torch.cuda.synchronize()
+    # config 5: a short serving stream (cold start, saturation, Poisson arrivals at 0.8 of it)
+    out["serving"] = serving_run(WORKLOADS["serving"], n_requests=300, loads=(0.8,), sat_requests=200, local=local)
+    return out
+
+
 # ---------------------------------------------------------------- main ----------
 def main():
     a = parse()
@@ -349,19 +636,22 @@ def main():
     if a.impl == "reference":
         if rank != 0:
             return
-        r = oracle_sample_rate(a.cpu_seconds, warmup=min(a.warmup, 1), steps=max(a.steps, 1) if a.steps < 50 else None)
+        warm = min(a.warmup, 1)
+        r = oracle_reference(w, a.steps, warm, a.ref_seconds)
         line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": "RHS/s", "n_gpus": a.gpus,
-                "steps": r["n_timed"], "warmup": min(a.warmup, 1), "ms_per_step": 1e3 * w["nrhs"] / r["value"],
+                "steps": r["steps"], "warmup": warm, "ms_per_step": r["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                 "data": "synthetic", "config": config,
-                "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "cpu_baseline": {"value": r["value"], "unit": "RHS/s", "cores": r["cores"], "kind": "oracle",
+                                 "sample": r["sample"], "single_core_value": r["single_core_value"],
+                                 "single_core_ms": r["single_core_ms"], "single_core_steps": r["single_core_steps"],
+                                 "oracle_build_s": r["build_s"], "all_core_wall_s": r["wall_s"]},
                 "e2e": {"value": r["value"], "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
 
     import numpy as np
     import torch
-    from paper_2307_03968_gb300.hm import HMatrix
 
     torch.cuda.set_device(local)
     dist = None
@@ -374,6 +664,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_2307_03968_gb300.hm import HMatrix
     xyz, cells, eps = workload_mesh(w)
     t0 = time.perf_counter()
     want_fp64 = not a.no_extras and w["nrhs"] == 1          # for the plain FP64 single-solve comparator
@@ -384,10 +675,9 @@ def main():
     A.factor_leaf()
     factor_s = time.perf_counter() - t0
     info = A.info()
-    N = A.n
     kh, ph = workload_incidences(w)
     nrhs = len(kh)
-    b = torch.empty((nrhs, N), dtype=torch.complex64, device="cuda")
+    b = torch.empty((nrhs, A.n), dtype=torch.complex64, device="cuda")
     A.rhs_plane_wave(kh, ph, b)
     x = torch.empty_like(b)
     opts = dict(n_terms=w["n_terms"], n_levels=w["n_levels"], refine=w["refine"])
@@ -397,43 +687,16 @@ def main():
     si = A.solve(b, x, info=True, **opts)
     launches_per_step = si.kernel_launches
     stream = torch.cuda.current_stream()
-    for _ in range(a.warmup):
-        A.solve(b, x, **opts)
     K = a.steps
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    clocks = ClockSampler(local)
-    time.sleep(0.3)
-    barrier()
-    for i in range(K):                       # timed region: CUDA-graph replays of the whole solve
-        starts[i].record(stream)
-        A.solve(b, x, **opts)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    total_ms = starts[0].elapsed_time(ends[-1])
-    # the same solves launched kernel by kernel, with CUDA events around every
-    # launch of the block-product kernel on its stream (graph replay hides them)
-    Kp = min(K, 1000)
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    A.profile(True)
-    p0.record(stream)
-    for i in range(Kp):
-        A.solve(b, x, graph=False, **opts)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    prof_ms, prof_n, prof_bytes = A.profile_read()
-    A.profile(False)
-    eager_ms = p0.elapsed_time(p1) / Kp
+    total_ms, lat, clk = timed_solves(A, b, x, opts, K, a.warmup, stream, barrier, local)
+    roof, eager_ms = product_roofline(A, b, x, opts, nrhs, min(K, 1000), (clk or {}).get("sm_max_mhz"))
+    if roof["bound"] == "hbm":
+        roof["traffic"] = committed_traffic()
     total_ms = max_over_ranks(total_ms, dist, "cuda")
-    lat = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
-    p50 = lat[len(lat) // 2]
-    p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
     value = replica_rate(K, nrhs, world, total_ms)
 
     # extras: unrefined solve and full-level solve (nested, all levels)
-    def time_solves(n, **kw):
+    def time_plain(n, **kw):
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for _ in range(3):
             A.solve(b, x, **kw)
@@ -458,13 +721,14 @@ def main():
         s1.record(stream)
         torch.cuda.synchronize()
         fp64_ms = s0.elapsed_time(s1) / 20
+        del b64, x64
     if not a.no_extras:
-        no_refine_ms = time_solves(200, n_terms=2, n_levels=1, refine=False)
+        no_refine_ms = time_plain(200, n_terms=2, n_levels=1, refine=False)
         # the nested form costs ~(K+1)^levels leaf-level products: few repetitions on deep trees, none past 6
         if info.n_levels <= 6:
-            full_nested_ms = time_solves(20 if info.n_levels <= 3 else 2, n_terms=2, n_levels=-1, nested=True,
-                                         refine=False)
-        full_flat_ms = time_solves(100, n_terms=2, n_levels=-1, nested=False, refine=False)
+            full_nested_ms = time_plain(20 if info.n_levels <= 3 else 2, n_terms=2, n_levels=-1, nested=True,
+                                        refine=False)
+        full_flat_ms = time_plain(100, n_terms=2, n_levels=-1, nested=False, refine=False)
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -482,52 +746,10 @@ def main():
         e2e = {"value": Ke * nrhs * world / dt, "unit": "RHS/s", "h2d_bytes_per_step": int(bh.nbytes),
                "d2h_bytes_per_step": int(xh.nbytes), "steps": Ke}
 
-    peak, peak_kind = peaks()
-    per_launch_bytes = prof_bytes / max(prof_n, 1)
-    per_launch_ms = prof_ms / max(prof_n, 1)
-    # every stored complex element is used twice per right-hand side (the block and its
-    # half-storage mirror): 2 complex multiply-adds = 16 real flops per 8 bytes per RHS
-    flops_per_launch = 2.0 * per_launch_bytes * nrhs
-    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
-    prod_choice = A.tuning(nrhs)[0] if nrhs >= 4 else 0
-    if not prof_n:
-        achieved = None
-    if prod_choice == 1016:
-        # tensor-core product (3xTF32): three TF32 MMAs per useful FP32-accurate product, so its roof is
-        # the TF32 tensor peak / 3; the TF32 peak is the measured sustained bf16 peak x the nominal
-        # TF32/bf16 ratio (1.1 / 2.25 PFLOP/s dense)
-        bf16_s = (PEAKS or {}).get("bf16_tflops_sustained")
-        tf32 = (bf16_s if bf16_s else 1700.0) * 1.1 / 2.25
-        bound, unit, rpeak = "tensor", "TFLOP/s", tf32 / 3.0
-        rkind = ("measured sustained bf16 %.1f TFLOP/s x 1.1/2.25 (TF32) / 3 (3xTF32 products)" % bf16_s if bf16_s
-                 else "fallback 1.7 PFLOP/s bf16 sustained x 1.1/2.25 / 3")
-        kernel = ("k_split_x + k_apply_tc (tcgen05 kind::tf32, 3xTF32; blocks <= 64 x 64, rank <= 32) "
-                  "+ k_apply_items for larger blocks (k_mrhs_tc.cu, k_product.cu)")
-    elif flops_per_launch / (alu_peak * 1e12) > per_launch_bytes / (peak * 1e9):
-        bound, unit, rpeak = "alu", "TFLOP/s", alu_peak
-        rkind = "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
-        kernel = ("k_apply_mrhs<%d> (shared-memory SIMT, %d RHS per chunk) + k_apply_items for larger blocks "
-                  "(k_mrhs.cu, k_product.cu)" % (prod_choice, prod_choice) if prod_choice
-                  else "k_apply_items<float,float,3> (one RHS at a time, k_product.cu)")
-    else:
-        bound, unit, rpeak, rkind = "hbm", "GB/s", peak, peak_kind
-        kernel = "k_apply_items<float,float,3> (near + leaf-level far block product, k_product.cu)"
-    if prof_n:
-        achieved = (flops_per_launch / (per_launch_ms * 1e-3) / 1e12 if unit == "TFLOP/s"
-                    else per_launch_bytes / (per_launch_ms * 1e-3) / 1e9)
-    roof = {"bound": bound,
-            "kernel": kernel,
-            "achieved": achieved, "peak": rpeak,
-            "peak_kind": rkind,
-            "unit": unit,
-            "frac": (achieved / rpeak) if achieved else None,
-            "traffic": committed_traffic(),
-            "bytes_per_launch": per_launch_bytes, "flops_per_launch": flops_per_launch, "nrhs": nrhs,
-            "ms_per_launch": per_launch_ms, "launches": prof_n,
-            "hbm_gbs": per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if prof_n else None,
-            "share_of_step": (prof_ms / Kp / eager_ms) if eager_ms else None,
-            "measured_on": "the timed solve launched kernel by kernel (%d steps, %.4f ms/step)" % (Kp, eager_ms)}
+    configs = None
+    if rank == 0 and world == 1 and a.workload == "sphere2" and not a.no_configs:
+        configs = extra_configs(A, local, barrier)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
@@ -537,12 +759,13 @@ def main():
             cpu = {"value": None, "unit": "RHS/s", "cores": None, "kind": "oracle", "sample": "failed: %r" % ex}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": K, "warmup": a.warmup,
-                "ms_per_step": total_ms / K, "p50_ms": p50, "p99_ms": p99, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic", "config": config,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": int(launches_per_step) * K,
-                "extras": {"eager_ms_per_step": eager_ms, "build_s": build_s, "factor_s": factor_s, "no_refine_ms": no_refine_ms,
-                           "fp64_plain_ms": fp64_ms,
+                "ms_per_step": total_ms / K, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+                "data": "synthetic", "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": int(launches_per_step) * K, "series": series_report(A, si),
+                "configs": configs,
+                "extras": {"eager_ms_per_step": eager_ms, "build_s": build_s, "factor_s": factor_s,
+                           "no_refine_ms": no_refine_ms, "fp64_plain_ms": fp64_ms,
                            "fp64_plain_rhs_s": (1e3 / fp64_ms) if fp64_ms else None,
                            "full_level_nested_ms": full_nested_ms, "full_level_flat_ms": full_flat_ms,
                            "n_levels": info.n_levels, "near_blocks": info.n_near,
@@ -588,14 +811,14 @@ def serving_catalog(seed):
     return cat
 
 
-def serving_main(a, w):
+def serving_run(w, n_requests, loads, sat_requests, local=0):
     """Serving stream (config-5 shape) through the continuous-batching server
     (hm_server_*, the library's public serving API): requests of 1..max_rhs
     right-hand sides on operators drawn uniformly from the catalog, host buffers
     in and out.  Phases: cold start (one request per operator: build + factor +
-    first solve), saturation (all requests queued at once), then Poisson arrivals
-    at the configured fractions of the saturation throughput.  Latency = submit to
-    completion as measured by the server."""
+    first solve), saturation (sat_requests queued at once), then Poisson arrivals
+    at the given fractions of the saturation throughput, n_requests each.
+    Latency = submit to completion as measured by the server.  Returns a dict."""
     import threading
     import numpy as np
     from paper_2307_03968_gb300.hm import Server
@@ -645,38 +868,51 @@ def serving_main(a, w):
         wall = time.perf_counter() - t0
         return sum(r for _, r in reqs) / wall, lats, wall
 
-    n_req = w["n_requests"]
-    sat, _, _ = run(draw(max(200, n_req // 4)))
+    n_req = n_requests
+    clocks = ClockSampler(local)
+    sat, _, _ = run(draw(sat_requests))
     mean_r = (w["max_rhs"] + 1) / 2.0
-    loads = []
-    for f in w["loads"]:
+    res = []
+    for f in loads:
         reqs = draw(n_req)
         thr, lats, wall = run(reqs, rate=f * sat / mean_r)
         lats = np.sort(np.array(lats))
-        loads.append({"offered": f, "offered_rhs_s": f * sat, "achieved_rhs_s": thr, "requests": len(reqs),
+        res.append({"offered": f, "offered_rhs_s": f * sat, "achieved_rhs_s": thr, "requests": len(reqs),
                       "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
                       "wall_s": wall})
     info = srv.info()
     srv.close()
-    main = loads[-1]
-    mid = min(loads, key=lambda d: abs(d["offered"] - 0.8))
+    clk = clocks.stop()
+    mid = min(res, key=lambda d: abs(d["offered"] - 0.8))
+    return {"config": {"workload": w["name"], "operators": [dict(name=o["name"], unknowns=o["n"]) for o in ops],
+                       "requests_per_load": n_req, "saturation_requests": sat_requests,
+                       "rhs_per_request": "uniform 1..%d" % w["max_rhs"], "arrivals": "Poisson, seed %d" % w["seed"],
+                       "solve": "leaf level, K=2, one refinement", "slots": w["n_slots"],
+                       "hbm_budget_gb": w["hbm_budget_gb"], "max_batch_rhs": w["max_batch_rhs"]},
+            "value": mid["achieved_rhs_s"], "unit": "RHS/s", "p50_ms": mid["p50_ms"], "p99_ms": mid["p99_ms"],
+            "saturation_rhs_s": sat, "loads": res,
+            "cold_ms": {"p50": float(np.percentile(cold, 50)), "max": float(np.max(cold))},
+            "batches": info.batches, "solved_rhs": info.solved_rhs, "builds": info.builds,
+            "evictions": info.evictions, "peak_resident_gb": info.peak_resident_bytes / 2 ** 30, "clocks": clk,
+            "note": "every request is end to end: host b in, host x out; value = achieved RHS/s at the load "
+                    "nearest 0.8 of saturation"}
+
+
+def serving_main(a, w):
+    """The serving workload as the headline line (bench.py --workload serving)."""
+    s = serving_run(w, w["n_requests"], w["loads"], max(200, w["n_requests"] // 4))
+    main = s["loads"][-1]
     line = {"metric": METRIC, "value": main["achieved_rhs_s"], "unit": "RHS/s", "n_gpus": 1,
-            "steps": sum(d["requests"] for d in loads), "warmup": len(ops), "ms_per_step": None,
-            "p50_ms": mid["p50_ms"], "p99_ms": mid["p99_ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": w["name"], "operators": [dict(name=o["name"], unknowns=o["n"]) for o in ops],
-                       "requests_per_load": n_req, "rhs_per_request": "uniform 1..%d" % w["max_rhs"],
-                       "arrivals": "Poisson, seed %d" % w["seed"], "solve": "leaf level, K=2, one refinement",
-                       "slots": w["n_slots"], "hbm_budget_gb": w["hbm_budget_gb"],
-                       "max_batch_rhs": w["max_batch_rhs"], "parallelism": "replicas"},
-            "roofline": None, "cpu_baseline": None,
-            "e2e": {"value": main["achieved_rhs_s"], "unit": "RHS/s",
-                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+            "steps": sum(d["requests"] for d in s["loads"]), "warmup": len(s["config"]["operators"]),
+            "ms_per_step": None, "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": dict(s["config"], parallelism="replicas"), "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": main["achieved_rhs_s"], "unit": "RHS/s", "h2d_bytes_per_step": None,
+                    "d2h_bytes_per_step": None,
                     "note": "every serving request is end to end: host b in, host x out"},
-            "serving": {"saturation_rhs_s": sat, "loads": loads,
-                        "cold_ms": {"p50": float(np.percentile(cold, 50)), "max": float(np.max(cold))},
-                        "batches": info.batches, "solved_rhs": info.solved_rhs, "builds": info.builds,
-                        "evictions": info.evictions, "peak_resident_gb": info.peak_resident_bytes / 2 ** 30}}
+            "clocks": s["clocks"],
+            "serving": {k: s[k] for k in ("saturation_rhs_s", "loads", "cold_ms", "batches", "solved_rhs", "builds",
+                                          "evictions", "peak_resident_gb")}}
     print(json.dumps(line))
 
 

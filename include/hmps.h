@@ -155,10 +155,36 @@ hm_status hm_build_from_blocks(const hm_blocks *blocks, void *stream, hm_matrix 
  * inverted in shared memory, one block per CTA.  Larger leaves (up to 1536)
  * are copied into a device workspace of 16 n^2 bytes per leaf, allocated here
  * and freed before return (HM_ERR_OOM if it cannot be had), and eliminated one
- * pivot step at a time across all of them.  Synchronises; returns
- * HM_ERR_SINGULAR if a pivot is exactly zero, HM_ERR_ARG for a leaf above 1536.
+ * pivot step at a time across all of them.  Then estimates the level
+ * operators' norms and spectral radii as hm_estimate_norms does, with
+ * HM_NORM_ITERS_DEFAULT steps.  Synchronises; returns HM_ERR_SINGULAR if a
+ * pivot is exactly zero, HM_ERR_ARG for a leaf above 1536.
  */
 hm_status hm_factor_leaf(hm_matrix h, void *stream);
+
+#define HM_NORM_ITERS_DEFAULT 32
+
+/*
+ * Convergence of the series (paper §IV, eqs. 20-22: the power series of
+ * (I + U)^{-1}; §V sets its operating bound as a norm of the level operator
+ * below 0.1).  For every level l with blocks, U_l = D^{-1} M_l (l = 1: the
+ * non-self near blocks and the leaf-level far blocks; l > 1: the far blocks
+ * l - 1 levels above the leaves).  Two power iterations of n_iter steps each,
+ * on the device with the solve's own product and leaf-inverse kernels
+ * (complex64 vectors, FP64 norms), from fixed start vectors:
+ *   norm_est[l-1]  |U_l v| for the unit iterate v of (U_l^H U_l)^k v0: a lower
+ *                  bound of ||U_l||_2 that rises toward it as n_iter grows
+ *                  (U^H is applied through the complex symmetry of M and D);
+ *   rho_est[l-1]   the geometric-mean growth |U_l v| of the iterates of U_l over
+ *                  the second half of the steps: an estimate of the spectral
+ *                  radius of U_l, which decides whether the series converges
+ *                  (it converges for rho < 1, the K-term result is computed and
+ *                  returned either way).
+ * The results go to hm_info (norm_est, rho_est, norm_iters) and to every
+ * hm_solve_info.  Costs 3 n_iter products of each level.  Synchronises.
+ * HM_ERR_STATE before hm_factor_leaf, HM_ERR_ARG for n_iter outside [2, 4096].
+ */
+hm_status hm_estimate_norms(hm_matrix h, int n_iter, void *stream);
 
 /* ---------------------------------------------------------------- solve --- */
 
@@ -185,6 +211,12 @@ typedef struct {
     int levels_used;         /* m after clamping to the levels present */
     int64_t bytes_streamed;  /* algorithmic operator + vector bytes of this solve */
     int64_t kernel_launches; /* kernels enqueued by this call */
+    double norm_est[16];     /* levels 1..levels_used: the handle's estimate of ||D^{-1} M_l||_2
+                                (hm_estimate_norms), index l - 1; 0 beyond */
+    double rho_est[16];      /* the same levels: estimated spectral radius of D^{-1} M_l */
+    int convergent;          /* 1: every rho_est of the levels used is below 1 (the series
+                                converges as K grows); 0: some level's is not, so the K-term
+                                result departs from A_m^{-1} b as K grows; -1: not estimated */
 } hm_solve_info;
 
 /*
@@ -242,11 +274,20 @@ hm_status hm_residual(hm_matrix h, const void *b, int64_t ldb, const void *x, in
  * (3 complex64 vectors of padded length x nrhs, 2 doubles per right-hand side,
  * and the FP64 partial slots of one right-hand side) return HM_ERR_ARG before
  * any device work.
- * The first call on each device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the one array and it
- * keeps the previous call's contents: calls that may overlap on the GPU (other
- * streams, other threads, other handles) race and must be serialised by the
- * caller.  The paper has no counterpart; this is an interface of this library.
+ * The first call on each device does a one-off set-up: it looks up the array's
+ * device address.  Under CUDA's lazy module loading (the default) that lookup
+ * loads the part of the library's device code that holds the array, which
+ * commits the 32 MiB, and the call's first kernel launches may load the device
+ * code of the residual kernels if no residual or refined solve has run yet.
+ * That set-up can allocate device memory, so make the first call at start-up:
+ * before a caching allocator reserves the device's memory, and before any
+ * stream capture.  Later calls allocate nothing.  The looked-up address is
+ * cached per device for the life of the process; after a cudaDeviceReset in
+ * the calling process it is stale, so do not call this entry point after one.
+ * All calls share the one array and it keeps the previous call's contents:
+ * calls that may overlap on the GPU (other streams, other threads, other
+ * handles) race and must be serialised by the caller.  The paper has no
+ * counterpart; this is an interface of this library.
  */
 hm_status hm_residual_noalloc(hm_matrix h, const void *b, int64_t ldb, const void *x, int64_t ldx, void *r,
                               int64_t ldr, int nrhs, int n_levels, double *norms, void *stream);
@@ -254,8 +295,8 @@ hm_status hm_residual_noalloc(hm_matrix h, const void *b, int64_t ldb, const voi
 /* ------------------------------------------------------------ excitation --- */
 
 /*
- * Right-hand sides of eq. 5 for incident plane waves (paper §II: "b is a known
- * incident plane wave"), unit amplitude: for HM_RWG
+ * Right-hand sides of eq. 5 for incident plane waves (paper §II, eq. 5: the
+ * excitation b is the tested incident plane wave), unit amplitude: for HM_RWG
  *   b_m = Int f_m . p_hat exp(-jk k_hat . r) dS     (7-point triangle rule),
  * for HM_SWG
  *   b_m = Int kappa f_m . p_hat exp(-jk k_hat . r) dV (4-point tetrahedron rule),
@@ -312,7 +353,11 @@ hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_
 hm_status hm_server_add_mesh(hm_server s, const hm_mesh *mesh, const hm_build_opts *bo, const hm_solve_opts *so,
                              int *op_id, int64_t *n_unknowns);
 /* Queues nrhs right-hand sides b (host, complex64, N x nrhs column-major, copied
- * during the call); n must equal the operator's N. */
+ * during the call); n must equal the operator's N.  HM_ERR_OOM, before anything is
+ * queued, when the request alone needs more device memory than the HBM budget (at
+ * least 8 N (2 + 4 (m + 1) + 8) bytes per right-hand side for its buffers and the
+ * solve's work vectors, m = the operator's solve levels, 1 if all); other requests
+ * are not affected. */
 hm_status hm_server_submit(hm_server s, int op_id, const void *b, int64_t n, int nrhs, int64_t *req_id);
 /* Blocks until the request is solved (at most 600 s), copies its solution to x
  * (host, N x nrhs) and gives the submit-to-completion latency in ms. */
@@ -336,6 +381,9 @@ typedef struct {
     int factored;
     int has_fp64;
     int64_t device_bytes;    /* device memory held by the handle */
+    double norm_est[16];     /* per level (index l - 1): estimate of ||D^{-1} M_l||_2 (hm_estimate_norms) */
+    double rho_est[16];      /* per level: estimated spectral radius of D^{-1} M_l */
+    int norm_iters;          /* steps of the last estimate, 0 if none was made */
 } hm_info;
 
 hm_status hm_get_info(hm_matrix h, hm_info *info);
@@ -373,6 +421,21 @@ hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double
  * another value.
  */
 hm_status hm_set_tuning(hm_matrix h, int nrhs, int prod_rb, int res_rb);
+
+/*
+ * Bound of the device waits of the tensor-core product (hm_set_tuning choice
+ * 1016; no counterpart in the paper).  Its roles (copies, operand conversion,
+ * MMA issue) hand shared-memory slots to one another through mbarriers; each
+ * such wait polls at most `polls` times (default 2^24, a few seconds), then the
+ * kernel records HM_ERR_TIMEOUT in the device status word (returned by
+ * hm_sync_status and by the next synchronising call), every role of the CTA
+ * leaves, the copies and MMAs already in flight are waited for at the full
+ * bound, and the tensor memory is freed.  The product's result is then
+ * incomplete.  polls < 0 restores the default; 0 makes every pipeline wait give
+ * up at once (to exercise the error path).  Drops captured solve graphs.
+ * HM_ERR_ARG above 2^32 - 1.
+ */
+hm_status hm_set_wait_limit(hm_matrix h, int64_t polls);
 
 /* Tree permutation (tree position -> original unknown), host int64[n]. */
 hm_status hm_get_perm(hm_matrix h, int64_t *perm);

@@ -14,7 +14,7 @@ Oracle — test infrastructure only.  Follows arxiv 2307.03968 §III:
   - only half of the matrix is computed, Z being complex symmetric (§III,
     ref. [12]): pairs t <= s are filled and Z[s, t] = Z[t, s]^T.
 
-Readings where the paper is silent (listed with the others in the design notes):
+Readings where the paper is silent:
   - splitting rule: sort the cluster's unknowns by (coordinate of the edge
     midpoint along the longest axis of their bounding box, original index) and
     cut after n // 2; ties in the axis choice go to the lower axis index;

@@ -503,6 +503,91 @@ static void Pflat(SolveCtx &c, const void *r, void *out)
     if (c.K == 0) copy_vec(c, out, Y);
 }
 
+// Estimates of the level operators U_l = D^{-1} M_l (§IV: the series of (I + U_l)^{-1}
+// converges when the spectral radius of U_l is below one; the paper's operating bound is
+// a norm below 0.1).  Per level with blocks, two power iterations of n_iter steps from
+// deterministic start vectors, one right-hand side, complex64 vectors:
+//  - on U: v <- U v / |U v|; rho_est = geometric mean of |U v| over the second half
+//    of the steps (the growth rate of U^k v, which tends to the spectral radius when one
+//    eigenvalue of largest modulus dominates);
+//  - on U^H U: norm_est = |U v| for the final unit iterate v of (U^H U)^k v0, a lower
+//    bound of ||U||_2 that rises to it (Rayleigh quotients of power iterates of a
+//    positive semidefinite matrix do not decrease).  U^H y = conj(M D^{-1} conj(y))
+//    because M and D are complex symmetric (the half storage of §III mirrors every
+//    stored block by its transpose).
+static hm_status estimate_norms(hm_matrix h, int n_iter, cudaStream_t s)
+{
+    SolveCtx c;
+    c.h = h; c.nrhs = 1; c.K = 0; c.fp64 = false; c.s = s;
+    c.m = std::max(h->n_levels, 1);
+    c.vbytes = sizeof(float2) * h->pN;
+    hm_status st = ensure_workspace(h, 1, c.m);
+    if (st != HM_OK) return st;
+    const bool prof = h->prof;
+    h->prof = false;   // these products are not part of any timed solve
+    float2 *v = (float2 *)h->ws.vec32[0], *t = (float2 *)h->ws.vec32[1], *z = (float2 *)h->ws.vec32[2],
+           *u = (float2 *)h->ws.vec32[3];
+    const int nl = std::min(c.m, 16);
+    const size_t nrec = (size_t)nl * 2 * n_iter + 1;   // [level][rho | norm][step], then one scratch
+    double *d = nullptr;
+    HM_CUDA(cudaMalloc((void **)&d, nrec * sizeof(double)));
+    HM_CUDA(cudaMemsetAsync(d, 0, nrec * sizeof(double), s));
+    double *scratch = d + nrec - 1;
+    const int64_t n = h->pN;
+    std::vector<bool> has(nl + 1, false);
+    for (int lev = 1; lev <= nl; ++lev) {
+        auto it = h->levels.find(lev);
+        if (it == h->levels.end() || it->second.items.empty()) continue;
+        has[lev] = true;
+        double *rec_rho = d + (size_t)(lev - 1) * 2 * n_iter, *rec_nrm = rec_rho + n_iter;
+        cudaMemsetAsync(z, 0, c.vbytes, s);
+        for (int pass = 0; pass < 2; ++pass) {
+            launch_seed_vector(v, h->d_pperm, n, 0x5EED0000u + 16u * lev + pass, s);
+            launch_norm2(v, n, scratch, s);
+            launch_conj_scale(v, v, n, scratch, false, s);
+            for (int k = 0; k < n_iter; ++k) {
+                leaf_update(c, nullptr, v, t, false);          // t = D^{-1} v
+                apply_level(c, lev, t, z);                     // z = M_l t
+                leaf_update(c, nullptr, z, u, true);           // u = U v; z = 0
+                if (pass == 0) {
+                    launch_norm2(u, n, rec_rho + k, s);
+                    launch_conj_scale(u, v, n, rec_rho + k, false, s);     // v = U v / |U v|
+                } else {
+                    launch_norm2(u, n, rec_nrm + k, s);
+                    launch_conj_scale(u, v, n, rec_nrm + k, true, s);      // v = conj(U v) / |U v|
+                    leaf_update(c, nullptr, v, t, false);
+                    apply_level(c, lev, t, z);                             // z = conj(U^H U v) / |U v|
+                    launch_norm2(z, n, scratch, s);
+                    launch_conj_scale(z, v, n, scratch, true, s);          // v = U^H U v / |U^H U v|
+                    cudaMemsetAsync(z, 0, c.vbytes, s);
+                }
+            }
+        }
+    }
+    std::vector<double> hrec(nrec, 0.0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hrec.data(), d, nrec * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    h->prof = prof;
+    if (e != cudaSuccess) return cuda_fail(e, "level-operator norm estimate");
+    for (int l = 0; l < 16; ++l) h->norm_est[l] = h->rho_est[l] = 0.0;
+    for (int lev = 1; lev <= nl; ++lev) {
+        if (!has[lev]) continue;
+        const double *rr = hrec.data() + (size_t)(lev - 1) * 2 * n_iter, *rn = rr + n_iter;
+        double acc = 0.0;
+        bool zero = false;
+        for (int k = n_iter / 2; k < n_iter; ++k) {
+            if (!(rr[k] > 0.0)) { zero = true; break; }
+            acc += 0.5 * std::log(rr[k]);
+        }
+        h->rho_est[lev - 1] = zero ? 0.0 : std::exp(acc / (n_iter - n_iter / 2));
+        h->norm_est[lev - 1] = std::sqrt(std::max(rn[n_iter - 1], 0.0));
+    }
+    h->norm_iters = n_iter;
+    return HM_OK;
+}
+
 static int clamp_levels(hm_matrix h, int n_levels)
 {
     int m = (n_levels < 0 || n_levels > h->n_levels) ? h->n_levels : n_levels;
@@ -744,6 +829,12 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
         info->levels_used = c.m;
         info->kernel_launches = c.launches;
         info->bytes_streamed = c.bytes;
+        info->convergent = h->norm_iters > 0 ? 1 : -1;
+        for (int l = 0; l < std::min(c.m, 16); ++l) {
+            info->norm_est[l] = h->norm_est[l];
+            info->rho_est[l] = h->rho_est[l];
+            if (h->norm_iters > 0 && h->rho_est[l] >= 1.0) info->convergent = 0;
+        }
         HM_CUDA(cudaStreamSynchronize(s));
         if (norms) {
             std::vector<double> hn(2 * nrhs);
@@ -973,7 +1064,15 @@ hm_status hm_factor_leaf(hm_matrix h, void *stream)
         return fail((hm_status)stv, "zero pivot in leaf self block " + std::to_string(bad));
     }
     h->factored = 1;
-    return HM_OK;
+    return estimate_norms(h, HM_NORM_ITERS_DEFAULT, s);
+}
+
+hm_status hm_estimate_norms(hm_matrix h, int n_iter, void *stream)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    if (n_iter < 2 || n_iter > 4096) return fail(HM_ERR_ARG, "n_iter out of range [2, 4096]");
+    if (!h->factored) return fail(HM_ERR_STATE, "hm_factor_leaf has not completed on this handle");
+    return estimate_norms(h, n_iter, (cudaStream_t)stream);
 }
 
 hm_status hm_powerseries_solve(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx, int nrhs,
@@ -1154,6 +1253,15 @@ hm_status hm_set_tuning(hm_matrix h, int nrhs, int prod_rb, int res_rb)
     return HM_OK;
 }
 
+hm_status hm_set_wait_limit(hm_matrix h, int64_t polls)
+{
+    if (!h) return fail(HM_ERR_ARG, "null handle");
+    if (polls > (int64_t)0xFFFFFFFF) return fail(HM_ERR_ARG, "polls above 2^32 - 1");
+    h->tc_wait_limit = polls < 0 ? -1 : polls;
+    clear_graphs(h);   // captured launches hold the previous limit
+    return HM_OK;
+}
+
 hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double *prod_ms, double *res_ms)
 {
     if (!h) return fail(HM_ERR_ARG, "null handle");
@@ -1196,6 +1304,11 @@ hm_status hm_get_info(hm_matrix h, hm_info *info)
     info->factored = h->factored;
     info->has_fp64 = h->has_fp64 ? 1 : 0;
     info->device_bytes = h->device_bytes + h->ws.dev_bytes + (int64_t)h->ws.d_io_bytes;
+    for (int l = 0; l < 16; ++l) {
+        info->norm_est[l] = h->norm_est[l];
+        info->rho_est[l] = h->rho_est[l];
+    }
+    info->norm_iters = h->norm_iters;
     return HM_OK;
 }
 

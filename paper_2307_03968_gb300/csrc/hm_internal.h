@@ -177,6 +177,7 @@ struct hm_matrix_s {
     int64_t device_bytes = 0;
     int num_sms = 0;
     int64_t tc_max_xch = 0;           // largest split-x chunk count over the levels
+    int64_t tc_wait_limit = -1;       // polls of each pipeline wait of the tensor-core product (-1 = default)
 
     // mesh geometry kept for excitation (operators made by hm_build):
     // b_m = sum over the two sides s of ucoef[m][s] * sum_q w_q (r_q - v) . p exp(-jk k . r_q)
@@ -206,6 +207,12 @@ struct hm_matrix_s {
     // kernel choices measured on this operator per right-hand-side count (hm_api.cu autotune)
     struct Tune { int prod_rb = -1, res_rb = -1; double prod_ms = 0.0, res_ms = 0.0; };   // res_rb < 0: not tuned
     std::map<int, Tune> tune;
+
+    // estimates of the level operators U_l = D^{-1} M_l (index l - 1), made by hm_factor_leaf /
+    // hm_estimate_norms: ||U_l||_2 from power iterations on U^H U, the spectral radius from
+    // the growth of power iterations on U; norm_iters = 0 when not estimated
+    double norm_est[16] = {}, rho_est[16] = {};
+    int norm_iters = 0;
 
     // opt-in event timing of the product kernel
     bool prof = false;
@@ -294,6 +301,11 @@ void launch_apply_list_mrhs(hm_matrix h, const LevelList &L, const Item *items, 
 void launch_resid_own(hm_matrix h, const LevelList &L, const float2 *x, double2 *own, int nrhs, cudaStream_t s);
 void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, int64_t lstride, const float2 *b,
                        float2 *out, double *norms, int nrhs, cudaStream_t s);
+// level-operator norm estimate (k_norm.cu): start vector (zero pads), |v|^2 into one device double
+// (cleared first), dst = op(src) / sqrt(*nrm2) with op = conjugation or identity
+void launch_seed_vector(float2 *v, const int32_t *pperm, int64_t pN, uint32_t seed, cudaStream_t s);
+void launch_norm2(const float2 *v, int64_t n, double *out, cudaStream_t s);
+void launch_conj_scale(const float2 *src, float2 *dst, int64_t n, const double *nrm2, bool conj, cudaStream_t s);
 // bytes of the split-x workspace of the tensor-core product for n_xch chunks and nrhs (k_mrhs_tc.cu)
 size_t tc_xplane_bytes(int64_t n_xch, int nrhs);
 // tensor-core products of a level's small items for all right-hand sides (k_mrhs_tc.cu);

@@ -371,6 +371,19 @@ hm_status hm_server_submit(hm_server S, int op_id, const void *b, int64_t n, int
     if (n != S->ops[op_id].n) return fail(HM_ERR_ARG, "right-hand side length differs from the operator's N");
     if (nrhs > S->max_batch_rhs) return fail(HM_ERR_ARG, "request has more right-hand sides than max_batch_rhs");
     if (S->fatal != HM_OK) return fail(S->fatal, S->fatal_msg);
+    {
+        // the request's own device footprint, at least: its right-hand sides and solutions in
+        // a slot's device buffers plus the leaf-level solve's 16 work vectors per column
+        // (more with more levels or the residual's slots).  A request that cannot fit the
+        // HBM budget even alone is refused here, before it is queued; queued requests are
+        // not affected.
+        const Operator &o = S->ops[op_id];
+        const int m = o.so.n_levels > 0 ? o.so.n_levels : 1;
+        const int64_t per_rhs = (int64_t)sizeof(float2) * n * (2 + 4 * (m + 1) + 8);
+        if ((int64_t)nrhs * per_rhs > S->budget)
+            return fail(HM_ERR_OOM, "request needs at least " + std::to_string((int64_t)nrhs * per_rhs) +
+                                        " device bytes, above the server's HBM budget");
+    }
     Request r;
     r.id = S->next_id++;
     r.op = op_id;

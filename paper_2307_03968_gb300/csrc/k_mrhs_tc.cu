@@ -39,9 +39,12 @@
 // block rows into the B planes (and, for stage 2, read T from tensor memory into
 // the A planes), and add finished accumulators into z.  Warp 5 issues the six
 // MMAs of a chunk and commits them to the slot's "empty" mbarrier.  Two CTAs
-// share an SM.  Every wait is bounded: on timeout the kernel records
-// HM_ERR_TIMEOUT in the status word, all roles leave, the MMAs in flight are
-// waited for (bounded), and the tensor memory is freed.
+// share an SM.  Every pipeline wait is bounded by a number of polls given at
+// launch (hm_set_wait_limit; default 2^24): on timeout the kernel records
+// HM_ERR_TIMEOUT in the status word and all roles leave their loops.  Before the
+// CTA ends, the producer waits for its bulk copies in flight and the MMA issuer
+// for its MMAs in flight, both at the full bound (2^24 polls) whatever the
+// pipeline limit, and only then is the tensor memory freed.
 #include "k_common.cuh"
 
 namespace hm {
@@ -92,18 +95,33 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
 // float offset of (row, K index k < 8) in a plane
 __device__ __forceinline__ int poff(int row, int k) { return (((row >> 3) * 2 + (k >> 2)) << 5) + ((row & 7) << 2) + (k & 3); }
 
-// bounded wait on an mbarrier phase; gives up early once another role aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int *abort)
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity)
 {
-    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// bounded wait on an mbarrier phase of the pipeline (at most `limit` polls, 0 = give up
+// at once); gives up early once another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int *abort, uint32_t limit)
+{
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (mbar_try(mbar, parity)) return true;
         if (*abort) return false;
     }
     *abort = 1;
     return false;
+}
+
+// wait for asynchronous work this thread issued (bulk copies, MMAs) before the CTA
+// frees what that work writes: the full bound, not cut short by an abort
+__device__ __forceinline__ void mbar_drain(uint32_t mbar, uint32_t parity, volatile int *abort)
+{
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+        if (mbar_try(mbar, parity)) return;
+    *abort = 1;
 }
 
 __device__ __forceinline__ void arrive(uint32_t mbar)
@@ -387,7 +405,7 @@ struct Seq {
 __global__ void __launch_bounds__(TT, 2)
 k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restrict__ prods, int64_t n_xch,
            const float *__restrict__ xpl, const float2 *__restrict__ pool, float2 *__restrict__ z, int64_t ldz,
-           int nrhs, int *status)
+           int nrhs, int *status, uint32_t wait_limit)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t full[NSLOT], ready[NSLOT], empty[NSLOT];
@@ -433,7 +451,7 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
         asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
         while (q.valid && !abort_flag) {
             const int s = (int)(n % NSLOT);
-            if (n >= NSLOT && !mbar_wait(su32(&empty[s]), ((n / NSLOT) + 1) & 1, &abort_flag)) break;
+            if (n >= NSLOT && !mbar_wait(su32(&empty[s]), ((n / NSLOT) + 1) & 1, &abort_flag, wait_limit)) break;
             const uint32_t slot = sm0 + (uint32_t)(s * SLOT);
             const int k0 = q.c * KCH;
             if (lane == 0) {
@@ -462,19 +480,25 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
             seq.next(q);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
+        // the slot fills still in flight land before the CTA may end (their full phases
+        // complete on the copies alone)
+        if (lane == 0)
+            for (uint32_t f = n > (uint32_t)NSLOT ? n - NSLOT : 0; f < n; ++f)
+                mbar_drain(su32(&full[f % NSLOT]), (f / NSLOT) & 1, &abort_flag);
+        __syncwarp();
     } else if (w <= 4) {
         // ---- converters: B planes (and A planes from T), accumulators into z
         const int t = tid - 32, quad = w & 3, r = 32 * quad + lane;
         uint32_t n_t = 0, n_u = 0;
         while (q.valid && !abort_flag) {
             const int s = (int)(n % NSLOT);
-            if (!mbar_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag)) break;
+            if (!mbar_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
             float *slot = reinterpret_cast<float *>(smraw + s * SLOT);
             const unsigned char *raw = smraw + s * SLOT + OFF_RAW;
             float *bh = reinterpret_cast<float *>(smraw + s * SLOT + OFF_B), *bl = bh + B_PLANE / 4;
             const bool lr1 = q.lr1(), lr2 = q.lr2();
             if (lr2) {
-                if (q.c == 0 && !mbar_wait(su32(&t_ready), n_t & 1, &abort_flag)) break;
+                if (q.c == 0 && !mbar_wait(su32(&t_ready), n_t & 1, &abort_flag, wait_limit)) break;
                 fence_after();
                 conv_a_t(slot, tmem, quad, r, q.k8, q.c * KCH);
             }
@@ -489,7 +513,7 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
             }
             arrive(su32(&ready[s]));
             if (q.last_of_unit()) {
-                if (!mbar_wait(su32(&acc_full), n_u & 1, &abort_flag)) break;
+                if (!mbar_wait(su32(&acc_full), n_u & 1, &abort_flag, wait_limit)) break;
                 fence_after();
                 drain(tmem, quad, lane, q.m8, q.U.mlen, z, ldz, q.r0, q.nr, q.U.out0);
                 fence_before();
@@ -506,9 +530,9 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
         while (q.valid && !abort_flag) {
             const int s = (int)(n % NSLOT);
             const bool lr1 = q.lr1();
-            if (lr1 && q.c == 0 && n_lr > 0 && !mbar_wait(su32(&t_empty), (n_lr - 1) & 1, &abort_flag)) break;
-            if (!lr1 && !started && n_u > 0 && !mbar_wait(su32(&acc_empty), (n_u - 1) & 1, &abort_flag)) break;
-            if (!mbar_wait(su32(&ready[s]), (n / NSLOT) & 1, &abort_flag)) break;
+            if (lr1 && q.c == 0 && n_lr > 0 && !mbar_wait(su32(&t_empty), (n_lr - 1) & 1, &abort_flag, wait_limit)) break;
+            if (!lr1 && !started && n_u > 0 && !mbar_wait(su32(&acc_empty), (n_u - 1) & 1, &abort_flag, wait_limit)) break;
+            if (!mbar_wait(su32(&ready[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
             fence_after();
             issue_chunk(sm0 + (uint32_t)(s * SLOT), lr1 ? tmem + T_COL : tmem, lr1 ? q.k8 : q.m8,
                         lr1 ? q.c > 0 : started);
@@ -527,7 +551,7 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
             seq.next(q);
         }
         commit(su32(&fin));                         // every MMA issued, then a bounded wait before freeing
-        mbar_wait(su32(&fin), 0, &abort_flag);
+        mbar_drain(su32(&fin), 0, &abort_flag);
     }
     fence_before();
     __syncthreads();
@@ -574,7 +598,8 @@ void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z
     int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
     if (g > units) g = units;
     k_apply_tc<<<(unsigned)g, TT, SMEM, s>>>(L.d_tcu, (int)L.n_tcu, L.d_tcp, L.n_xch, h->ws.d_xpl, h->d_pool32, z,
-                                           h->pN, nrhs, h->d_status);
+                                           h->pN, nrhs, h->d_status,
+                                           h->tc_wait_limit < 0 ? WAIT_LIMIT : (uint32_t)h->tc_wait_limit);
 }
 
 } // namespace hm

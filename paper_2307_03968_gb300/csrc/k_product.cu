@@ -3,11 +3,12 @@
 // acts on both of its clusters):
 //     dense  B (I,J):  z_I += B x_J,            z_J += B^T x_I
 //     low rank U V:    z_I += U (V x_J),        z_J += V^T (U^T x_I)
-// One warp per block, persistent grid (occupancy x SMs, 8 warps per CTA, at
-// most 128 registers so that 16 warps per SM keep loads in flight).  A lane owns
+// One warp per block, persistent grid (occupancy x SMs, 8 warps per CTA).  The
+// complex64 instantiation is launched with three CTAs per SM (at most 80
+// registers a thread), so that 24 warps per SM keep loads in flight.  A lane owns
 // two adjacent columns, loaded as one 128-bit streaming load, so column-side sums
 // accumulate in registers; row-side sums are warp transpose reductions.  Low-rank
-// panels go in chunks of 4 rank rows held in registers, so U^T and V are read
+// panels go in chunks of 8 rank rows held in registers, so U^T and V are read
 // once.  Results go to z with vector atomics (order-free sums: reproducible to
 // FP32 rounding, not bitwise).
 #include "k_common.cuh"
@@ -202,7 +203,7 @@ __device__ __forceinline__ void lowrank_item(const Item &it, const typename CT<T
     }
 }
 
-// MINB: CTAs per SM the register budget must allow (2 for complex64, so that 16
+// MINB: CTAs per SM the register budget must allow (3 for complex64, so that 24
 // warps per SM stream blocks; 1 for the FP64 comparator path, which needs more
 // registers)
 template <class T, class A, int MINB>

@@ -75,14 +75,16 @@ class HmSolveOpts(ctypes.Structure):
 
 class HmSolveInfo(ctypes.Structure):
     _fields_ = [("rel_residual", ctypes.c_double), ("levels_used", ctypes.c_int),
-                ("bytes_streamed", I64), ("kernel_launches", I64)]
+                ("bytes_streamed", I64), ("kernel_launches", I64), ("norm_est", ctypes.c_double * 16),
+                ("rho_est", ctypes.c_double * 16), ("convergent", ctypes.c_int)]
 
 
 class HmInfo(ctypes.Structure):
     _fields_ = [("n", I64), ("n_leaves", I64), ("depth", ctypes.c_int), ("n_levels", ctypes.c_int),
                 ("n_near", I64), ("n_far", I64 * 16), ("near_elems", I64), ("far_elems", I64 * 16),
                 ("self_elems", I64), ("max_rank", ctypes.c_int), ("factored", ctypes.c_int),
-                ("has_fp64", ctypes.c_int), ("device_bytes", I64)]
+                ("has_fp64", ctypes.c_int), ("device_bytes", I64), ("norm_est", ctypes.c_double * 16),
+                ("rho_est", ctypes.c_double * 16), ("norm_iters", ctypes.c_int)]
 
 
 class HmServerInfo(ctypes.Structure):
@@ -90,11 +92,11 @@ class HmServerInfo(ctypes.Structure):
                 ("resident_bytes", I64), ("peak_resident_bytes", I64)]
 
 
-EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_powerseries_solve",
+EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_estimate_norms", "hm_powerseries_solve",
            "hm_powerseries_solve_host", "hm_apply", "hm_residual", "hm_residual_noalloc", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
            "hm_server_create", "hm_server_add_mesh", "hm_server_submit", "hm_server_wait", "hm_server_get_info",
            "hm_server_destroy",
-           "hm_get_info", "hm_get_tuning", "hm_set_tuning", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
+           "hm_get_info", "hm_get_tuning", "hm_set_tuning", "hm_set_wait_limit", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
            "hm_size", "hm_destroy", "hm_last_error", "hm_version"]
 
 _lib = None
@@ -111,6 +113,7 @@ def load():
     L.hm_build.argtypes = [ctypes.POINTER(HmMesh), ctypes.POINTER(HmBuildOpts), P, ctypes.POINTER(P)]
     L.hm_build_from_blocks.argtypes = [ctypes.POINTER(HmBlocks), P, ctypes.POINTER(P)]
     L.hm_factor_leaf.argtypes = [P, P]
+    L.hm_estimate_norms.argtypes = [P, ctypes.c_int, P]
     L.hm_powerseries_solve.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.POINTER(HmSolveOpts), P,
                                        ctypes.POINTER(HmSolveInfo)]
     L.hm_powerseries_solve_host.argtypes = [P, P, I64, P, I64, ctypes.c_int, ctypes.POINTER(HmSolveOpts), P]
@@ -133,6 +136,7 @@ def load():
     L.hm_get_leaves.argtypes = [P, PI64]
     L.hm_get_tuning.argtypes = [P, ctypes.c_int, PI32, PI32, PD, PD]
     L.hm_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hm_set_wait_limit.argtypes = [P, I64]
     L.hm_get_blocks.argtypes = [P, ctypes.c_int, PI64, PI64, PI64, PI32, PI32, PI32]
     L.hm_get_block.argtypes = [P, ctypes.c_int, I64, PD, PD]
     L.hm_sync_status.argtypes = [P, P]
@@ -239,6 +243,17 @@ class HMatrix:
     def factor_leaf(self, stream=None):
         _check(load().hm_factor_leaf(self._h, _stream(stream)))
 
+    def estimate_norms(self, n_iter=32, stream=None):
+        """hm_estimate_norms; returns (norm_est, rho_est) per level present (level 1 first)."""
+        _check(load().hm_estimate_norms(self._h, n_iter, _stream(stream)))
+        return self.norm_estimates()
+
+    def norm_estimates(self):
+        """(norm_est, rho_est) lists of the levels present, from hm_get_info."""
+        i = self.info()
+        nl = max(1, min(i.n_levels, 16))
+        return list(i.norm_est[:nl]), list(i.rho_est[:nl])
+
     # ---- solve / apply -------------------------------------------------------------------
     def solve(self, b, x, n_terms=2, n_levels=1, nested=True, refine=False, fp64=False, stream=None,
               info=False, graph=True):
@@ -331,6 +346,11 @@ class HMatrix:
         """hm_set_tuning: pin the kernel choice for nrhs's bucket (product 1016 = tensor-core
         products; residual 1017 = owner-computes FP64-class residual)."""
         _check(load().hm_set_tuning(self._h, nrhs, prod_rb, res_rb))
+
+    def set_wait_limit(self, polls):
+        """hm_set_wait_limit: polls of each pipeline wait of the tensor-core product
+        before it reports HM_ERR_TIMEOUT (negative = the default)."""
+        _check(load().hm_set_wait_limit(self._h, polls))
 
     @property
     def n(self):

@@ -1,0 +1,91 @@
+"""Solve parity at the benchmark's full size, in the launch configuration
+bench.py times.
+
+Workload: PEC sphere of radius 2 wavelengths, icosphere with 20,480 triangles
+(30,720 RWG unknowns), octree with leaves of at most 64 unknowns, admissibility
+dist >= 2 min(diam), ACA tolerance 1e-4; one plane wave (+z, x-polarised);
+leaf level only, K = 2, one FP64-class refinement step (paper §IV eq. 19 with
+the "two fixed iterations").
+
+- The oracle builds this operator itself (complex128 fill, ACA and
+  re-compression, leaf-level far blocks) and solves it with series.solve; the
+  same blocks go to the library through hm_build_from_blocks, and a
+  graph-replayed hm_powerseries_solve must match within 1e-4 (the metric's
+  parity bar, max-column relative 2-norm).
+- The operator the bench actually times is built on the GPU (hm_build).  It
+  differs from the oracle's at the ACA and FP32-fill level, so its solve is
+  compared with the oracle's at that level (reported; bounded at 5e-2, about
+  ten times the measured gap).
+
+The oracle's build takes minutes on the host cores; the module builds it once.
+"""
+
+import time
+
+import numpy as np
+import pytest
+
+from hm_testutil import gpu_operator, rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_03968_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def full(torch_cuda):
+    from synth import icosphere, plane_wave_z
+    from oracle.rwg import RWGMesh
+    from oracle.hmatrix import HMatrix
+    from oracle import series
+    xyz, tri = icosphere(5, 2.0)
+    mesh = RWGMesh(xyz, tri)
+    t0 = time.perf_counter()
+    H = HMatrix(mesh, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=1)
+    t1 = time.perf_counter()
+    b = mesh.rhs(*plane_wave_z())                                  # (N, 1)
+    ref = series.solve(H, b, K=2, levels=1, refine=True)          # (N, 1)
+    t2 = time.perf_counter()
+    print("oracle build %.0f s, solve %.0f s, N = %d" % (t1 - t0, t2 - t1, H.N))
+    return xyz, tri, H, b, ref
+
+
+def test_oracle_operator_solve_parity(torch_cuda, full):
+    xyz, tri, H, b, ref = full
+    assert H.N == 30720 and len(H.leaves) == 512
+    A = gpu_operator(H)
+    bt = torch_cuda.from_numpy(np.ascontiguousarray(b.T.astype(np.complex64))).cuda()
+    xt = torch_cuda.empty_like(bt)
+    for _ in range(2):                                 # capture, then a graph replay (the timed form)
+        xt.fill_(float("nan"))
+        A.solve(bt, xt, n_terms=2, n_levels=1, refine=True)
+        A.sync_status()
+        err = rel_err(xt.cpu().numpy(), ref.T)
+        print("graph solve vs oracle on the oracle's operator: %.3e" % err)
+        assert err < 1e-4
+    si = A.solve(bt, xt, n_terms=2, n_levels=1, refine=True, info=True)
+    assert rel_err(xt.cpu().numpy(), ref.T) < 1e-4
+    assert si.levels_used == 1 and si.convergent == 0          # rho(D^-1 M_1) > 1 on the PEC sphere
+
+
+def test_gpu_built_operator_solve_vs_oracle(torch_cuda, full):
+    from paper_2307_03968_gb300.hm import HMatrix
+    xyz, tri, H, b, ref = full
+    A = HMatrix.build(xyz, tri, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1)
+    A.factor_leaf()
+    bt = torch_cuda.from_numpy(np.ascontiguousarray(b.T.astype(np.complex64))).cuda()
+    xt = torch_cuda.empty_like(bt)
+    A.solve(bt, xt, n_terms=2, n_levels=1, refine=True)
+    A.sync_status()
+    err = rel_err(xt.cpu().numpy(), ref.T)
+    print("GPU-built operator's solve vs oracle (ACA and FP32 fill level): %.3e" % err)
+    assert np.all(np.isfinite(xt.cpu().numpy()))
+    assert err < 5e-2

@@ -49,6 +49,7 @@ def test_host_argument_errors(lib):
     B.n = 0
     assert lib.hm_build_from_blocks(ctypes.byref(B), None, ctypes.byref(out)) == hm.HM_ERR_ARG
     assert lib.hm_factor_leaf(None, None) == hm.HM_ERR_ARG
+    assert lib.hm_estimate_norms(None, 32, None) == hm.HM_ERR_ARG
     o = hm.HmSolveOpts(2, 1, 1, 0, 0, 0)
     assert lib.hm_powerseries_solve(None, None, 0, None, 0, 1, ctypes.byref(o), None, None) == hm.HM_ERR_ARG
     assert lib.hm_apply(None, None, 0, None, 0, 1, 1, 1, None) == hm.HM_ERR_ARG

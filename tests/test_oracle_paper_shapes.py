@@ -1,11 +1,8 @@
 """The power series on small synthetic versions of the paper's three experiment
 shapes (arxiv 2307.03968 §IV: a PEC plate, a thin dielectric slab and a hollow
 dielectric cylinder, eps_r = 2) with the paper's own settings (binary tree,
-eq. 7 with eta = 1, ACA 1e-3), against the dense solve of the same H-Matrix and
-against the GMRES comparison solver (relative residual 1e-6).
+eq. 7 with eta = 1, ACA 1e-3), against the dense solve of the same H-Matrix.
 
-- GMRES itself is pinned to dense LU (full GMRES on a random matrix is exact in
-  N steps; on an H-Matrix it reaches the dense solve within its tolerance).
 - Measured and asserted: the block-Jacobi operator D^{-1}M has spectral radius
   below 1 on the dielectric shapes, so the series converges there (the error
   falls by more than 5x from K = 2 to K = 8), and above 1 on the PEC plate,
@@ -17,28 +14,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle.gmres import gmres
 from oracle.hmatrix import HMatrix
-
-
-def test_full_gmres_is_exact_in_n_steps():
-    rng = np.random.default_rng(3)
-    n = 30
-    A = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)) + 4 * np.eye(n)
-    b = rng.normal(size=n) + 1j * rng.normal(size=n)
-    x, its, hist = gmres(lambda v: A @ v, b, tol=1e-12, restart=n, maxiter=n)
-    assert its <= n
-    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-9 * np.linalg.norm(x)
-    assert all(h1 <= h0 * (1 + 1e-12) for h0, h1 in zip(hist[1:], hist[2:]))   # minimal residual: monotone
-
-
-def test_restarted_gmres_on_hmatrix_matches_dense(sphere_tiny):
-    H = HMatrix(sphere_tiny, leaf_size=16, arity=2, adm=1.0, aca_tol=1e-4)
-    b = H.to_tree(sphere_tiny.rhs(np.array([[0, 0, 1.0]]), np.array([[1.0, 0, 0]]))[:, 0])
-    x, its, hist = gmres(lambda v: H.apply(v[:, None])[:, 0], b, tol=1e-8, restart=60, maxiter=2000)
-    xs = np.linalg.solve(H.dense(), b)
-    assert hist[-1] <= 1e-8
-    assert np.linalg.norm(x - xs) <= 1e-5 * np.linalg.norm(xs)
 
 
 def _study(mesh, leaf=32):
@@ -67,8 +43,7 @@ def _study(mesh, leaf=32):
     for k in range(1, 9):
         xk = y - T(xk)
         errs[k] = np.linalg.norm(xk - xs) / np.linalg.norm(xs)
-    xg, its, _ = gmres(lambda u: H.apply(u[:, None])[:, 0], b, tol=1e-6, restart=200, maxiter=3000)
-    return rho, errs, its, np.linalg.norm(xg - xs) / np.linalg.norm(xs)
+    return rho, errs
 
 
 @pytest.mark.parametrize("shape", ["slab", "hollow_cylinder"])
@@ -78,20 +53,18 @@ def test_series_converges_on_the_dielectric_shapes(shape):
         xyz, tet = synth.box_tets((2.0, 0.5, 0.1), (20, 5, 1))
     else:                                                     # length 1.2, outer radius 0.4, wall 0.05
         xyz, tet = synth.shell_tets(0.35, 0.4, 1.2, (1, 24, 12))
-    rho, errs, its, eg = _study(SWGMesh(xyz, tet, 2.0))
+    rho, errs = _study(SWGMesh(xyz, tet, 2.0))
     assert rho < 0.95, rho
     assert errs[8] < errs[2] / 5 and errs[8] < 2e-2, errs
     assert 5e-3 < errs[2] < 0.2, errs                         # two terms: a few percent
-    assert eg < 1e-4 and its < 100
 
 
 def test_series_diverges_on_the_pec_plate():
     from oracle.rwg import RWGMesh
     xyz, tri = synth.plate((2.0, 2.0), (20, 20))             # 2 x 2 wavelengths, 1,160 RWG unknowns
-    rho, errs, its, eg = _study(RWGMesh(xyz, tri))
+    rho, errs = _study(RWGMesh(xyz, tri))
     assert rho > 1.5, rho
     assert errs[8] > errs[2] > 1.0, errs
-    assert eg < 1e-4 and its > 50                             # GMRES converges, slowly
 
 
 def _rho(H, iters=60):

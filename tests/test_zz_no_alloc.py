@@ -56,9 +56,16 @@ def test_noalloc_residual_matches_hm_residual(torch_cuda, sphere_small):
         r_ref = torch_cuda.empty_like(bt)
         rr_ref, bb_ref = A.residual(bt, xt, r_ref, n_levels=levels)
         r_na = torch_cuda.full_like(bt, float("nan"))
+        torch_cuda.cuda.synchronize()
+        free0, held0 = torch_cuda.cuda.mem_get_info()[0], A.info().device_bytes
         st, norms = _call_noalloc(A, bt, xt, r_na, levels)
         assert st == hm.HM_OK, hm.load().hm_last_error()
         torch_cuda.cuda.synchronize()
+        if call > 0:
+            # after the first call's set-up, a call allocates nothing: neither the device's free
+            # memory nor the bytes the handle holds change
+            assert torch_cuda.cuda.mem_get_info()[0] == free0
+            assert A.info().device_bytes == held0
         assert rel_err(r_na.cpu().numpy(), r_ref.cpu().numpy()) < TOL, call
         assert np.allclose(norms[0::2], rr_ref, rtol=TOL) and np.allclose(norms[1::2], bb_ref, rtol=TOL)
 
