@@ -166,6 +166,11 @@ def parse():
                    help="skip the other workloads of the default run (1,920-unknown sphere, 181-RHS sweep, "
                         "dielectric cube, serving stream)")
     p.add_argument("--workload", default="sphere2", choices=sorted(WORKLOADS))
+    p.add_argument("--sweep-rhs", type=int, default=None,
+                   help="sweep workload: number of monostatic angles (right-hand sides) instead of 181 "
+                        "(smaller profiler captures)")
+    p.add_argument("--device-loop", action="store_true",
+                   help="serving workload: schedule through the device-resident request loop")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU time budget of the oracle sample")
     p.add_argument("--ref-seconds", type=float, default=90.0,
                    help="wall-time budget of the reference arm's timed oracle solves (after its build)")
@@ -494,9 +499,10 @@ def product_roofline(A, b, x, opts, nrhs, Kp, sm_max):
         bf16_s = (PEAKS or {}).get("bf16_tflops_sustained")
         tf32 = (bf16_s if bf16_s else 1700.0) * 1.1 / 2.25
         bound, unit, rpeak = "tensor", "TFLOP/s", tf32 / 3.0
-        rkind = ("measured sustained bf16 %.1f TFLOP/s x 1.1/2.25 (TF32) / 3 (3xTF32 products)" % bf16_s if bf16_s
-                 else "fallback 1.7 PFLOP/s bf16 sustained x 1.1/2.25 / 3")
-        kernel = ("k_split_x + k_apply_tc (tcgen05 kind::tf32, 3xTF32; blocks <= 64 x 64, rank <= 32) "
+        rkind = ("measured sustained bf16 %.1f TFLOP/s x 1.1/2.25 (TF32) / 3 (3xTF32 products)" % bf16_s
+                 if bf16_s else "fallback 1.7 PFLOP/s bf16 sustained x 1.1/2.25 / 3")
+        kernel = ("k_split_x + k_apply_tc (tcgen05 kind::tf32, 3xTF32; units of <= 16 K chunks; blocks <= 64 x 64, "
+                  "rank <= 32) "
                   "+ k_apply_items for larger blocks (k_mrhs_tc.cu, k_product.cu)")
     elif flops_per_launch / (alu_peak * 1e12) > per_launch_bytes / (peak * 1e9):
         bound, unit, rpeak = "alu", "TFLOP/s", alu_peak
@@ -532,6 +538,24 @@ def series_report(A, si):
             "rho_est": [round(v, 6) for v in info.rho_est[:nl]],
             "note": "norm_est / rho_est per level (level 1 = leaf); the K-term series converges to A^-1 b "
                     "only where rho < 1; parity is against the oracle running the same K-term algorithm"}
+
+
+def one_launch_timing(A, b, x, opts, K, W, stream, barrier, local):
+    """The same solve as ONE cooperative kernel (hm_solve_opts.persistent, graph
+    replayed): per-solve latency and rate, and its largest difference from the
+    multi-kernel solve's result."""
+    import numpy as np
+    import torch
+    ref = x.clone()
+    A.solve(b, ref, **opts)
+    si = A.solve(b, x, info=True, persistent=True, **opts)
+    torch.cuda.synchronize()
+    r, g = ref.cpu().numpy(), x.cpu().numpy()
+    diff = float(max(np.linalg.norm(g[j] - r[j]) / np.linalg.norm(r[j]) for j in range(r.shape[0])))
+    total, lat, clk = timed_solves(A, b, x, dict(opts, persistent=True), K, W, stream, barrier, local)
+    return {"value": K * b.shape[0] / (total / 1e3), "unit": "RHS/s", "ms_per_step": total / K,
+            "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "kernel_launches": int(si.kernel_launches),
+            "max_rel_diff_vs_multi_kernel": diff, "clocks": clk}
 
 
 def gpu_build(w):
@@ -576,6 +600,7 @@ def extra_configs(A2, local, barrier):
                                   note="operator %.1f MB, L2-resident: latency, no roofline line"
                                        % (A.info().device_bytes / 1e6))
     out["sphere03"]["launches_per_step"] = int(si.kernel_launches)
+    out["sphere03"]["one_launch"] = one_launch_timing(A, b, x, opts, 300, 20, stream, barrier, local)
     A.close()
     # config 3: the headline operator, 181-RHS monostatic sweep (autotuned kernels)
     w = WORKLOADS["sphere2_sweep181"]
@@ -608,6 +633,8 @@ def extra_configs(A2, local, barrier):
     torch.cuda.synchronize()
     # config 5: a short serving stream (cold start, saturation, Poisson arrivals at 0.8 of it)
     out["serving"] = serving_run(WORKLOADS["serving"], n_requests=300, loads=(0.8,), sat_requests=200, local=local)
+    out["serving_device_loop"] = serving_run(WORKLOADS["serving"], n_requests=300, loads=(0.8,), sat_requests=200,
+                                             local=local, device_loop=True)
     return out
 
 
@@ -616,6 +643,8 @@ def main():
     a = parse()
     global WORKLOAD
     WORKLOAD = WORKLOADS[a.workload]
+    if a.sweep_rhs and WORKLOAD.get("sweep"):
+        WORKLOAD = dict(WORKLOAD, nrhs=a.sweep_rhs, name=WORKLOAD["name"].replace("181", str(a.sweep_rhs)))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -730,6 +759,11 @@ def main():
                                         refine=False)
         full_flat_ms = time_plain(100, n_terms=2, n_levels=-1, nested=False, refine=False)
 
+    # the same solve as one cooperative kernel (the multi-kernel graph replay is the headline)
+    one_launch = None
+    if not a.no_extras and nrhs == 1:
+        one_launch = one_launch_timing(A, b, x, opts, min(K, 200), 5, stream, barrier, local)
+
     # end to end through the host-buffer entry point
     e2e = None
     if not a.no_e2e:
@@ -768,6 +802,7 @@ def main():
                            "no_refine_ms": no_refine_ms, "fp64_plain_ms": fp64_ms,
                            "fp64_plain_rhs_s": (1e3 / fp64_ms) if fp64_ms else None,
                            "full_level_nested_ms": full_nested_ms, "full_level_flat_ms": full_flat_ms,
+                           "one_launch": one_launch,
                            "n_levels": info.n_levels, "near_blocks": info.n_near,
                            "far_blocks": [info.n_far[i] for i in range(info.n_levels)],
                            "max_rank": info.max_rank, "device_bytes": info.device_bytes,
@@ -780,38 +815,47 @@ def main():
 
 
 # ---------------------------------------------------------------- serving -------
-def serving_catalog(seed):
+def serving_catalog(seed, full=False):
     """Seeded catalog of scatterers, meshed at about a tenth of a wavelength (PEC
     surfaces, RWG) or a fifteenth (dielectric volumes, SWG).  Returns a list of
-    dicts (name, xyz, cells, eps_r or None, tree options)."""
+    dicts (name, xyz, cells, eps_r or None, tree options).
+
+    full=False: 12 operators (3 spheres, 3 cubes, 3 closed cylinders, 3
+    dielectric cubes of 6,528-21,600 unknowns), built in seconds.  full=True:
+    the 24 of the serving workload's description: 18 PEC bodies (6 spheres of
+    radius 0.7-3.2 wavelengths, 6 cubes and 6 closed cylinders of 0.5-3
+    wavelengths; 882 to 30,720 RWG unknowns: meshed at a tenth of a wavelength,
+    bodies of this size have no more) and 6 inhomogeneous dielectric cubes of
+    6,528 to 41,850 SWG unknowns (eps_r uniform [2, 6])."""
     import numpy as np
     import synth
     rng = np.random.default_rng(seed)
     rwg = dict(leaf_size=64, arity=8, adm=2.0)
     swg = dict(leaf_size=64, arity=2, adm=1.0)
+    k = 2 if full else 1
     cat = []
-    for s_ in (3, 4, 5):                                    # spheres: edge ~ radius / (1.1 * 2^s)
+    for s_ in (3, 4, 5) * k:                                # spheres: edge ~ radius / (1.1 * 2^s)
         r = 1.1 * 2 ** s_ / 10.0 * rng.uniform(0.8, 1.0)
         xyz, tri = synth.icosphere(s_, r)
         cat.append(dict(name="pec_sphere_r%.2f" % r, xyz=xyz, cells=tri, eps_r=None, opts=rwg))
-    for _ in range(3):                                      # cubes
+    for _ in range(3 * k):                                  # cubes
         a = rng.uniform(0.5, 3.0)
         n = int(np.ceil(10 * a))
         xyz, tri = synth.box_surface((a, a, a), (n, n, n))
         cat.append(dict(name="pec_cube_a%.2f" % a, xyz=xyz, cells=tri, eps_r=None, opts=rwg))
-    for _ in range(3):                                      # closed cylinders
-        r, h = rng.uniform(0.25, 1.0), rng.uniform(0.5, 3.0)
+    for _ in range(3 * k):                                  # closed cylinders
+        r, h = rng.uniform(0.25, 1.0 if not full else 1.5), rng.uniform(0.5, 3.0)
         xyz, tri = synth.closed_cylinder(r, h, int(np.ceil(2 * np.pi * r * 10)), int(np.ceil(10 * h)),
                                          int(np.ceil(10 * r)))
         cat.append(dict(name="pec_cylinder_r%.2f_h%.2f" % (r, h), xyz=xyz, cells=tri, eps_r=None, opts=rwg))
-    for n in (8, 10, 12):                                   # inhomogeneous dielectric cubes, side n / 15
+    for n in ((8, 10, 11, 12, 13, 15) if full else (8, 10, 12)):   # dielectric cubes, side n / 15
         xyz, tet = synth.cube_tets(n, n / 15.0)
         eps = synth.random_permittivity(len(tet), 2.0, 6.0, seed=seed + n)
         cat.append(dict(name="dielectric_cube_%dvox" % n, xyz=xyz, cells=tet, eps_r=eps, opts=swg))
     return cat
 
 
-def serving_run(w, n_requests, loads, sat_requests, local=0):
+def serving_run(w, n_requests, loads, sat_requests, local=0, device_loop=False, full=False):
     """Serving stream (config-5 shape) through the continuous-batching server
     (hm_server_*, the library's public serving API): requests of 1..max_rhs
     right-hand sides on operators drawn uniformly from the catalog, host buffers
@@ -823,9 +867,9 @@ def serving_run(w, n_requests, loads, sat_requests, local=0):
     import numpy as np
     from paper_2307_03968_gb300.hm import Server
     rng = np.random.default_rng(w["seed"])
-    cat = serving_catalog(w["seed"])
+    cat = serving_catalog(w["seed"], full=full)
     srv = Server(n_slots=w["n_slots"], hbm_budget_bytes=int(w["hbm_budget_gb"] * 2 ** 30),
-                 max_batch_rhs=w["max_batch_rhs"])
+                 max_batch_rhs=w["max_batch_rhs"], device_loop=device_loop)
     ops = []
     for g in cat:
         op, n = srv.add_mesh(g["xyz"], g["cells"], eps_r=g["eps_r"], aca_tol=1e-4, levels=-1, n_terms=w["n_terms"],
@@ -894,13 +938,18 @@ def serving_run(w, n_requests, loads, sat_requests, local=0):
             "cold_ms": {"p50": float(np.percentile(cold, 50)), "max": float(np.max(cold))},
             "batches": info.batches, "solved_rhs": info.solved_rhs, "builds": info.builds,
             "evictions": info.evictions, "peak_resident_gb": info.peak_resident_bytes / 2 ** 30, "clocks": clk,
+            "scheduler": ("device-resident request loop (one cooperative kernel serving a ring; %d launches, "
+                          "%d stops for builds and recordings)" % (info.loop_launches, info.loop_stops)
+                          if device_loop else "host thread launching graph-replayed solves on %d streams"
+                          % w["n_slots"]),
             "note": "every request is end to end: host b in, host x out; value = achieved RHS/s at the load "
                     "nearest 0.8 of saturation"}
 
 
 def serving_main(a, w):
     """The serving workload as the headline line (bench.py --workload serving)."""
-    s = serving_run(w, w["n_requests"], w["loads"], max(200, w["n_requests"] // 4))
+    s = serving_run(w, w["n_requests"], w["loads"], max(200, w["n_requests"] // 4), device_loop=a.device_loop,
+                    full=True)
     main = s["loads"][-1]
     line = {"metric": METRIC, "value": main["achieved_rhs_s"], "unit": "RHS/s", "n_gpus": 1,
             "steps": sum(d["requests"] for d in s["loads"]), "warmup": len(s["config"]["operators"]),
@@ -912,7 +961,7 @@ def serving_main(a, w):
                     "note": "every serving request is end to end: host b in, host x out"},
             "clocks": s["clocks"],
             "serving": {k: s[k] for k in ("saturation_rhs_s", "loads", "cold_ms", "batches", "solved_rhs", "builds",
-                                          "evictions", "peak_resident_gb")}}
+                                          "evictions", "peak_resident_gb", "scheduler")}}
     print(json.dumps(line))
 
 

@@ -204,6 +204,15 @@ typedef struct {
                       calls with the same pointers, sizes and options; 0 = launch
                       kernels one by one.  Ignored while hm_profile is enabled or
                       when info is requested. */
+    int persistent; /* 1 = run the whole solve (every term, level, the residual and
+                      the refinement) as ONE cooperative kernel whose CTAs walk the
+                      solve's steps with a grid-wide barrier between consecutive
+                      steps (bounded waits: HM_ERR_TIMEOUT through the status word);
+                      the block products run one right-hand side at a time.  The
+                      step list is recorded on first use per pointers, sizes and
+                      options.  Complex64 only, leaves of at most 128 padded
+                      unknowns; otherwise the solve runs as separate kernels.
+                      Combines with graph (the launch is then graph-replayed). */
 } hm_solve_opts;
 
 typedef struct {
@@ -345,9 +354,33 @@ hm_status hm_profile_read(hm_matrix h, double *product_ms, int64_t *launches, in
 typedef struct hm_server_s *hm_server;
 typedef struct {
     int64_t batches, solved_rhs, builds, evictions, resident_bytes, peak_resident_bytes;
+    int64_t loop_launches;   /* device-loop mode: launches of the request loop kernel */
+    int64_t loop_stops;      /* device-loop mode: stops for host-side GPU work (builds, allocation) */
 } hm_server_info;
 
 hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_rhs, hm_server *out);
+
+/*
+ * The same server with device_loop = 1: a device-resident request loop.  One
+ * cooperative kernel stays on the GPU and serves the batches from a ring in
+ * mapped pinned host memory, with no kernel launch per batch: the scheduler
+ * thread copies a batch's right-hand sides to its slot's device buffer, writes
+ * the ring entry (the batch's one-launch solve, recorded for every right-hand-side
+ * count rounded up to a multiple of 4 when the operator is built, the slot's
+ * buffers and the operator's context) and marks it ready; the kernel runs it
+ * between grid barriers and marks it done; the scheduler copies the solutions
+ * out.  Batches run one after another on the whole GPU (n_slots batches can be
+ * queued in the ring).  Builds (with their recordings), evictions and slot
+ * buffer growth stop the loop (a stop entry after everything queued) and run on
+ * the host side; an idle loop leaves by itself after about a second and is
+ * launched again by the next batch.  Every
+ * wait of the kernel is bounded; a wait that gives up fails the batch it was
+ * serving with HM_ERR_TIMEOUT.  The solve options of every operator must fit the
+ * one-launch solve (complex64, leaves of at most 128 padded unknowns; HM_ERR_ARG
+ * for the batch otherwise).  device_loop = 0 is hm_server_create.
+ */
+hm_status hm_server_create_ex(int n_slots, int64_t hbm_budget_bytes, int max_batch_rhs, int device_loop,
+                              hm_server *out);
 /* Registers a mesh (either basis); *n_unknowns receives its unknown count N (the length of every
  * right-hand side of this operator). */
 hm_status hm_server_add_mesh(hm_server s, const hm_mesh *mesh, const hm_build_opts *bo, const hm_solve_opts *so,
@@ -423,16 +456,21 @@ hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double
 hm_status hm_set_tuning(hm_matrix h, int nrhs, int prod_rb, int res_rb);
 
 /*
- * Bound of the device waits of the tensor-core product (hm_set_tuning choice
- * 1016; no counterpart in the paper).  Its roles (copies, operand conversion,
- * MMA issue) hand shared-memory slots to one another through mbarriers; each
- * such wait polls at most `polls` times (default 2^24, a few seconds), then the
+ * Bound of the device waits of this library's kernels (no counterpart in the
+ * paper).  Two kernels wait on other parts of the GPU:
+ *  - the tensor-core product (hm_set_tuning choice 1016): its roles (copies,
+ *    operand conversion, MMA issue) hand shared-memory slots to one another
+ *    through mbarriers.  On a time-out every role of the CTA leaves, the
+ *    copies and MMAs already in flight are waited for at the full bound, and
+ *    the tensor memory is freed;
+ *  - the one-launch solve (hm_solve_opts.persistent): its CTAs meet at a
+ *    grid-wide barrier between steps.  A CTA that gives up leaves the kernel,
+ *    so every other CTA gives up at its next barrier.
+ * Each wait polls at most `polls` times (default 2^24, a few seconds), then the
  * kernel records HM_ERR_TIMEOUT in the device status word (returned by
- * hm_sync_status and by the next synchronising call), every role of the CTA
- * leaves, the copies and MMAs already in flight are waited for at the full
- * bound, and the tensor memory is freed.  The product's result is then
- * incomplete.  polls < 0 restores the default; 0 makes every pipeline wait give
- * up at once (to exercise the error path).  Drops captured solve graphs.
+ * hm_sync_status and by the next synchronising call); the result is then
+ * incomplete.  polls < 0 restores the default; 0 makes every such wait give up
+ * at once (to exercise the error path).  Drops captured solve graphs.
  * HM_ERR_ARG above 2^32 - 1.
  */
 hm_status hm_set_wait_limit(hm_matrix h, int64_t polls);

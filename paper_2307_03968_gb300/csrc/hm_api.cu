@@ -95,7 +95,14 @@ static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vec
             runits.push_back(r.u);
         }
     }
-    const int64_t cap = std::max<int64_t>(256, total / (std::max(num_sms, 1) * 2 * 8));
+    // Units of at most TC_UNIT_CHUNKS K chunks: the tensor cores' FP32 accumulator loses
+    // a little on every MMA it adds into a large running sum (measured: the product's
+    // error grows in proportion to the chunks summed in tensor memory, 7.4e-6 relative
+    // at 256 chunks, 1.9e-6 at 64, 5.4e-7 at 16 on 60-unknown leaves), so a unit's sum
+    // leaves tensor memory (added into z in FP32) every TC_UNIT_CHUNKS chunks.
+    (void)total;
+    (void)num_sms;
+    const int64_t cap = TC_UNIT_CHUNKS;
     struct U { TcUnit u; int64_t c; std::vector<TcProd> p; };
     std::vector<U> us;
     for (auto &kv : by_out) {
@@ -181,6 +188,10 @@ static void clear_graphs(hm_matrix h)
 {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
+    // recorded one-launch phase lists hold workspace pointers too
+    for (auto &kv : h->persist)
+        if (kv.second.d) cudaFree(kv.second.d);
+    h->persist.clear();
 }
 
 static void free_handle(hm_matrix h)
@@ -188,6 +199,7 @@ static void free_handle(hm_matrix h)
     if (!h) return;
     clear_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->d_bar) cudaFree(h->d_bar);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     void *geo[] = {h->d_qpd, h->d_vtx, h->d_ucell, h->d_ufree, h->d_ucoef, h->d_rhs_w};
     for (void *p : geo)
@@ -312,7 +324,45 @@ struct SolveCtx {
     int64_t bytes = 0;
     size_t vbytes;   // bytes of one [nrhs][pN] vector
     std::vector<void *> Y, X, Z, W;  // per level 0..m
+    // recording instead of launching (the one-launch solve): every step is appended as
+    // a phase; units = the CTAs the widest phase can use (a leaf per CTA, a block per warp)
+    std::vector<Phase> *rec = nullptr;
+    int64_t units = 0;
 };
+
+static Phase phase(int op, int nrhs)
+{
+    Phase p;
+    memset(&p, 0, sizeof(p));
+    p.op = op;
+    p.nrhs = nrhs;
+    return p;
+}
+
+static void zero_vec(SolveCtx &c, void *p, size_t bytes)
+{
+    if (c.rec) {
+        Phase q = phase(PH_ZERO, 1);
+        q.c = p;
+        q.n = (int64_t)bytes;
+        c.rec->push_back(q);
+        return;
+    }
+    cudaMemsetAsync(p, 0, bytes, c.s);
+}
+
+static void sub_vec(SolveCtx &c, const void *y, const void *w, void *out)
+{
+    c.launches++;
+    if (c.rec) {
+        Phase q = phase(PH_SUB, c.nrhs);
+        q.a = y; q.b = w; q.c = out;
+        q.n = c.h->pN * c.nrhs;
+        c.rec->push_back(q);
+        return;
+    }
+    launch_sub(y, w, out, c.h->pN * c.nrhs, c.fp64, c.s);
+}
 
 static size_t elem_size(bool fp64) { return fp64 ? sizeof(double2) : sizeof(float2); }
 
@@ -417,6 +467,17 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
     auto it = c.h->levels.find(lev);
     if (it == c.h->levels.end() || it->second.items.empty()) return;
     hm_matrix h = c.h;
+    if (c.rec) {
+        Phase q = phase(PH_APPLY, c.nrhs);
+        q.a = x; q.c = z;
+        q.items = it->second.d_items;
+        q.n = (int64_t)it->second.items.size();
+        c.rec->push_back(q);
+        c.units = std::max<int64_t>(c.units, (q.n + 7) / 8);   // a block per warp
+        c.launches++;
+        c.bytes += level_bytes(c.h, lev, c.fp64) * c.nrhs;
+        return;
+    }
     const bool timed = h->prof && !c.fp64;
     if (timed) {
         if (h->prof_used + 2 > h->prof_ev.size() && h->prof_ev.size() < 8192) {
@@ -442,13 +503,28 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
 
 static void leaf_update(SolveCtx &c, const void *y, void *zin, void *out, bool zero_in)
 {
-    launch_leaf_update(c.h, y, zin, out, c.nrhs, zero_in, c.fp64, c.s);
+    if (c.rec) {
+        Phase q = phase(PH_LEAF, c.nrhs);
+        q.a = y; q.b = zin; q.c = out;
+        q.m = zero_in ? 1 : 0;
+        c.rec->push_back(q);
+        c.units = std::max<int64_t>(c.units, c.h->n_leaves * c.nrhs);
+    } else {
+        launch_leaf_update(c.h, y, zin, out, c.nrhs, zero_in, c.fp64, c.s);
+    }
     c.launches++;
     c.bytes += c.h->dinv_elems * (int64_t)elem_size(c.fp64) + 3 * (int64_t)c.vbytes;
 }
 
 static void copy_vec(SolveCtx &c, void *dst, const void *src)
 {
+    if (c.rec) {
+        Phase q = phase(PH_COPY, 1);
+        q.a = src; q.c = dst;
+        q.n = (int64_t)c.vbytes;
+        c.rec->push_back(q);
+        return;
+    }
     cudaMemcpyAsync(dst, src, c.vbytes, cudaMemcpyDeviceToDevice, c.s);
 }
 
@@ -477,12 +553,11 @@ static void P(SolveCtx &c, int level, const void *r, void *out)
     P(c, level - 1, r, Y);                                              // y = P_{m-1}(r)
     const void *cur = Y;
     for (int j = 1; j <= c.K; ++j) {
-        cudaMemsetAsync(Z, 0, c.vbytes, c.s);
+        zero_vec(c, Z, c.vbytes);
         apply_level(c, level, cur, Z);                                  // z = M_m x
         P(c, level - 1, Z, W);                                          // w = P_{m-1}(z)
         void *dst = (j == c.K) ? out : X;
-        launch_sub(Y, W, dst, c.h->pN * c.nrhs, c.fp64, c.s);           // x = y - w
-        c.launches++;
+        sub_vec(c, Y, W, dst);                                          // x = y - w
         cur = dst;
     }
     if (c.K == 0) copy_vec(c, out, Y);
@@ -546,9 +621,8 @@ static hm_status estimate_norms(hm_matrix h, int n_iter, cudaStream_t s)
             launch_norm2(v, n, scratch, s);
             launch_conj_scale(v, v, n, scratch, false, s);
             for (int k = 0; k < n_iter; ++k) {
-                leaf_update(c, nullptr, v, t, false);          // t = D^{-1} v
-                apply_level(c, lev, t, z);                     // z = M_l t
-                leaf_update(c, nullptr, z, u, true);           // u = U v; z = 0
+                apply_level(c, lev, v, z);                     // z = M_l v
+                leaf_update(c, nullptr, z, u, true);           // u = D^{-1} z = U v; z = 0
                 if (pass == 0) {
                     launch_norm2(u, n, rec_rho + k, s);
                     launch_conj_scale(u, v, n, rec_rho + k, false, s);     // v = U v / |U v|
@@ -600,7 +674,7 @@ static int clamp_levels(hm_matrix h, int n_levels)
 static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *out, double *norms)
 {
     hm_matrix h = c.h;
-    if (c.res_rb == RB_OWN && h->ws.d_own &&
+    if (!c.rec && c.res_rb == RB_OWN && h->ws.d_own &&
         h->ws.own_bytes >= sizeof(double2) * (size_t)c.m * (size_t)c.nrhs * (size_t)h->pN && own_applies(h, c.m)) {
         // owner-computes: each level's sums into its own FP64 [RHS][pN] array, then one gather
         const int64_t lstride = (int64_t)c.nrhs * h->pN;
@@ -619,6 +693,32 @@ static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *
     for (int r0 = 0; r0 < c.nrhs; r0 += chunk) {
         const int nr = std::min(chunk, c.nrhs - r0);
         const float2 *x = xt + (int64_t)r0 * h->pN;
+        if (c.rec) {   // one-launch solve: the one-RHS-at-a-time partial-slot products and the gather
+            for (int lev = 1; lev <= c.m; ++lev) {
+                auto it = h->levels.find(lev);
+                if (it == h->levels.end() || it->second.items.empty()) continue;
+                Phase q = phase(PH_RESID, nr);
+                q.a = x; q.c = h->ws.d_part;
+                q.ld = h->partial_elems;
+                q.items = it->second.d_items;
+                q.n = (int64_t)it->second.items.size();
+                c.rec->push_back(q);
+                c.units = std::max<int64_t>(c.units, (q.n + 7) / 8);   // a block per warp
+                c.launches++;
+            }
+            Phase g = phase(PH_GATHER, nr);
+            g.a = x;
+            g.b = bt ? bt + (int64_t)r0 * h->pN : nullptr;
+            g.c = out + (int64_t)r0 * h->pN;
+            g.d = h->ws.d_part;
+            g.ld = h->partial_elems;
+            g.m = c.m;
+            g.norms = norms ? norms + 2 * r0 : nullptr;
+            c.rec->push_back(g);
+            c.units = std::max<int64_t>(c.units, h->n_leaves * nr);
+            c.launches++;
+            continue;
+        }
         for (int lev = 1; lev <= c.m; ++lev) {
             auto it = h->levels.find(lev);
             if (it == h->levels.end() || it->second.items.empty()) continue;
@@ -735,8 +835,60 @@ static void use_tuning(SolveCtx &c)
     }
 }
 
+// permutations and vector updates of a solve, launched or recorded
+static void permute_in_vec(SolveCtx &c, const void *b, int64_t ldb, void *bt)
+{
+    c.launches++;
+    if (c.rec) {
+        Phase q = phase(PH_PERMUTE_IN, c.nrhs);
+        q.a = b; q.c = bt; q.ld2 = ldb;
+        c.rec->push_back(q);
+        return;
+    }
+    launch_permute_in(b, ldb, bt, c.h->pN, c.h->d_pperm, c.nrhs, c.fp64, c.s);
+}
+
+static void permute_out_vec(SolveCtx &c, const void *xt, void *x, int64_t ldx)
+{
+    c.launches++;
+    if (c.rec) {
+        Phase q = phase(PH_PERMUTE_OUT, c.nrhs);
+        q.a = xt; q.c = x; q.ld2 = ldx;
+        c.rec->push_back(q);
+        return;
+    }
+    launch_permute_out(xt, c.h->pN, x, ldx, c.h->d_pperm, c.nrhs, c.fp64, c.s);
+}
+
+static void add_vec(SolveCtx &c, void *x, const void *dx)
+{
+    c.launches++;
+    if (c.rec) {
+        Phase q = phase(PH_ADD, c.nrhs);
+        q.a = dx; q.c = x; q.n = c.h->pN * c.nrhs;
+        c.rec->push_back(q);
+        return;
+    }
+    launch_add_inplace(x, dx, c.h->pN * c.nrhs, false, c.s);
+}
+
+static void check_vec(SolveCtx &c, const void *x)
+{
+    c.launches++;
+    if (c.rec) {
+        Phase q = phase(PH_CHECK, c.nrhs);
+        q.a = x; q.n = c.h->pN * c.nrhs;
+        c.rec->push_back(q);
+        return;
+    }
+    launch_check_finite(x, c.h->pN * c.nrhs, c.fp64, c.h->d_status, c.s);
+}
+
+// rec_out: record (or find) the one-launch phase list of this solve and return it
+// without launching anything (the serving loop runs it)
 static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx, int nrhs,
-                              const hm_solve_opts *o, cudaStream_t s, hm_solve_info *info)
+                              const hm_solve_opts *o, cudaStream_t s, hm_solve_info *info,
+                              const hm_matrix_s::PersistList **rec_out = nullptr)
 {
     void *caller_stream = (void *)s;
     if (!h) return fail(HM_ERR_ARG, "null handle");
@@ -766,51 +918,107 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
     if (st != HM_OK) return st;
     const bool resid = !o->fp64 && (o->refine || info);
     if (resid && (st = ensure_partials(h)) != HM_OK) return st;
-    if (!c.fp64) {
+    const bool persist = (o->persistent || rec_out) && !c.fp64 && persist_supported(h);
+    if (rec_out && !persist) return fail(HM_ERR_ARG, "the operator does not fit the one-launch solve");
+    if (!c.fp64 && !persist) {
         if ((st = autotune(h, nrhs, c.m, s, resid)) != HM_OK) return st;
         use_tuning(c);
         if (resid && c.res_rb == RB_OWN && own_applies(h, c.m) && (st = ensure_own(h, c.m)) != HM_OK) return st;
     }
-    const bool use_graph = o->graph && !info && !h->prof;
-    hm_matrix_s::GraphKey key{b, x, ldb, ldx, nrhs, c.K, c.m, o->nested, o->refine, o->fp64};
+    if (persist) {   // the one-launch solve runs the one-right-hand-side-at-a-time block bodies
+        c.prod_rb = 0;
+        c.res_rb = 0;
+        if (!h->d_bar) HM_CUDA(cudaMalloc((void **)&h->d_bar, 2 * sizeof(unsigned)));
+    }
+    const bool use_graph = o->graph && !info && !h->prof && !rec_out;
+    hm_matrix_s::GraphKey key{b, x, ldb, ldx, nrhs, c.K, c.m, o->nested, o->refine, o->fp64,
+                              persist ? (info ? 2 : 1) : 0};
     if (use_graph) {
         auto g = h->graphs.find(key);
         if (g != h->graphs.end()) {
             HM_CUDA(cudaGraphLaunch(g->second, s));
             return HM_OK;
         }
-        if (!h->cap_stream) HM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-        HM_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        c.s = h->cap_stream;
-        s = h->cap_stream;
     }
     std::vector<void *> &V = c.fp64 ? h->ws.vec64 : h->ws.vec32;
     size_t vi = 0;
     c.Y.assign(c.m + 1, nullptr); c.X = c.Y; c.Z = c.Y; c.W = c.Y;
     for (int l = 1; l <= c.m; ++l) { c.Y[l] = V[vi++]; c.X[l] = V[vi++]; c.Z[l] = V[vi++]; c.W[l] = V[vi++]; }
     void *bt = V[vi++], *xt = V[vi++], *rt = V[vi++], *dx = V[vi++];
-    launch_permute_in(b, ldb, bt, h->pN, h->d_pperm, nrhs, c.fp64, s);
-    c.launches++;
-    if (o->nested) P(c, c.m, bt, xt);
-    else Pflat(c, bt, xt);
-    double *norms = nullptr;
-    if (o->refine) {
-        norms = h->ws.d_acc64;
-        cudaMemsetAsync(norms, 0, 2 * sizeof(double) * nrhs, s);
-        residual64(c, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
-        if (o->nested) P(c, c.m, rt, dx);
-        else Pflat(c, rt, dx);
-        launch_add_inplace(xt, dx, h->pN * nrhs, false, s);
-        c.launches++;
-        if (info) {   // residual of the refined solution
-            cudaMemsetAsync(norms, 0, 2 * sizeof(double) * nrhs, s);
-            residual64(c, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
+    double *norms = o->refine ? h->ws.d_acc64 : nullptr;
+    // the solve's steps, launched or recorded (the one-launch solve) through c
+    auto steps = [&](SolveCtx &cc) {
+        permute_in_vec(cc, b, ldb, bt);
+        if (o->nested) P(cc, cc.m, bt, xt);
+        else Pflat(cc, bt, xt);
+        if (o->refine) {
+            zero_vec(cc, norms, 2 * sizeof(double) * nrhs);
+            residual64(cc, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
+            if (o->nested) P(cc, cc.m, rt, dx);
+            else Pflat(cc, rt, dx);
+            add_vec(cc, xt, dx);
+            if (info) {   // residual of the refined solution
+                zero_vec(cc, norms, 2 * sizeof(double) * nrhs);
+                residual64(cc, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
+            }
+        }
+        check_vec(cc, xt);
+        permute_out_vec(cc, xt, x, ldx);
+    };
+    const hm_matrix_s::PersistList *pl = nullptr;
+    if (persist) {
+        auto it = h->persist.find(key);
+        if (it == h->persist.end()) {
+            std::vector<Phase> rec;
+            SolveCtx r = c;
+            r.rec = &rec;
+            steps(r);
+            // barriers that can go: zeroing the norms before the residual products (only the
+            // gather, a barrier later, reads them); the elementwise tail add -> check ->
+            // permute-out, where every thread reads only the elements it wrote itself
+            for (size_t q = 0; q + 1 < rec.size(); ++q) {
+                const int a = rec[q].op, nx = rec[q + 1].op;
+                if (a == PH_ZERO && nx == PH_RESID && rec[q].c == (void *)norms) rec[q].pad = 1;
+                if ((a == PH_ADD && (nx == PH_CHECK || nx == PH_PERMUTE_OUT)) ||
+                    (a == PH_CHECK && nx == PH_PERMUTE_OUT))
+                    rec[q].pad = 1;
+            }
+            hm_matrix_s::PersistList l;
+            l.n = (int)rec.size();
+            l.units = (int)std::min<int64_t>(r.units, 1 << 30);
+            l.launches = r.launches;
+            l.bytes = r.bytes;
+            HM_CUDA(cudaMalloc((void **)&l.d, rec.size() * sizeof(Phase)));
+            HM_CUDA(cudaMemcpy(l.d, rec.data(), rec.size() * sizeof(Phase), cudaMemcpyHostToDevice));
+            it = h->persist.emplace(key, l).first;
+        }
+        pl = &it->second;
+        if (rec_out) {
+            *rec_out = pl;
+            return HM_OK;
         }
     }
-    launch_check_finite(xt, h->pN * nrhs, c.fp64, h->d_status, s);
-    c.launches++;
-    launch_permute_out(xt, h->pN, x, ldx, h->d_pperm, nrhs, c.fp64, s);
-    c.launches++;
+    if (use_graph) {
+        if (!h->cap_stream) HM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        HM_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        c.s = h->cap_stream;
+        s = h->cap_stream;
+    }
+    if (persist) {
+        st = launch_persist(h, pl->d, pl->n, pl->units, s);
+        c.launches = 1;            // one kernel (the recorded list replaces pl->launches launches)
+        c.bytes = pl->bytes;
+        if (st != HM_OK) {
+            if (use_graph) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(h->cap_stream, &g);
+                if (g) cudaGraphDestroy(g);
+            }
+            return st;
+        }
+    } else {
+        steps(c);
+    }
     if (use_graph) {
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
@@ -848,9 +1056,21 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
         HM_CUDA(cudaMemcpy(&stv, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
         if (stv != 0) {
             cudaMemset(h->d_status, 0, sizeof(int));
-            return fail((hm_status)stv, "device reported non-finite values in the solution");
+            return fail((hm_status)stv, stv == HM_ERR_DIVERGED ? "device reported non-finite values in the solution"
+                                        : "device status word reported an error during the solve");
         }
     }
+    return HM_OK;
+}
+
+hm_status persist_phases(hm_matrix h, const void *b, void *x, int nrhs, const hm_solve_opts *o,
+                         const Phase **phases, int *n_phases)
+{
+    const hm_matrix_s::PersistList *pl = nullptr;
+    const hm_status st = solve_device(h, b, h->N, x, h->N, nrhs, o, nullptr, nullptr, &pl);
+    if (st != HM_OK) return st;
+    *phases = pl->d;
+    *n_phases = pl->n;
     return HM_OK;
 }
 

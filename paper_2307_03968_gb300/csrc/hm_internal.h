@@ -34,6 +34,7 @@ constexpr int RB_TC = 1016;         // product choice: tensor-core products of t
 constexpr int TC_MAX_DIM = MRHS_MAX_DIM;    // the tensor-core product takes the same small items
 constexpr int TC_MAX_RANK = MRHS_MAX_RANK;
 constexpr int TC_MIN_RHS = 32;      // the autotuner times the tensor-core product from this many RHS on
+constexpr int TC_UNIT_CHUNKS = 16;  // K chunks (of 8) a tensor-core work unit sums in tensor memory
 constexpr int RB_OWN = 1017;        // residual choice: owner-computes FP64-class products (levels of small items)
 
 // Double-float numbers of the FP64-class residual (hi + lo, |lo| a few ulps of hi at
@@ -111,6 +112,81 @@ struct LevelList {
     int64_t n_xch = 0;
     int64_t n_dense = 0, n_lowrank = 0;
     int64_t elems = 0;            // stored complex elements
+};
+
+// One phase of the one-launch solve (k_persist.cu): every kernel the solve would
+// launch becomes a phase of one cooperative kernel, with a grid-wide barrier
+// between consecutive phases.
+enum PhaseOp : int32_t {
+    PH_PERMUTE_IN = 1,   // c[r][p] = a[r * ld2 + pperm[p]] (0 at pads)
+    PH_PERMUTE_OUT,      // c[r * ld2 + pperm[p]] = a[r][p]
+    PH_LEAF,             // per leaf: c = (a ? a - Dinv b : Dinv b); b = 0 if m
+    PH_APPLY,            // c += M a over items[0, n) (one RHS at a time per block)
+    PH_RESID,            // FP64-class products of items[0, n) into the partial slots c (stride ld)
+    PH_GATHER,           // c = (b ? b - acc : acc), acc = D a + slots d of m levels; norms
+    PH_ZERO,             // n bytes at c
+    PH_COPY,             // n bytes a -> c
+    PH_SUB,              // c = a - b, n complex
+    PH_ADD,              // c += a, n complex
+    PH_CHECK             // non-finite in a[0, n) -> HM_ERR_DIVERGED
+};
+struct Phase {
+    int32_t op, nrhs;
+    int64_t n;
+    const void *a, *b;
+    void *c;
+    const void *d;
+    const Item *items;
+    int64_t ld, ld2;
+    int32_t m;
+    int32_t pad;         // 1 = no grid barrier after this phase (set by the recorder)
+    double *norms;
+};
+
+// What the one-launch solve's phases read besides their own pointers: the
+// operator's layout (one hm_matrix), its status word and the barrier words.
+struct PersistCtx {
+    const int32_t *pperm;
+    int64_t pN;
+    int64_t n_leaves;
+    const int32_t *pleaf_off;
+    const int64_t *dinv_off;
+    const float2 *dinv;
+    const float2 *self32;
+    const float2 *pool;
+    const int64_t *csr_off;
+    int csr_stride;
+    const int64_t *csr_idx;
+    int *status;
+    unsigned *bar;                      // the grid barrier's word (and a spare one)
+    uint32_t polls;                     // barrier wait bound
+};
+
+// The device-resident request loop (k_serve_loop in k_persist.cu, driven by
+// hm_server.cu): ring entries and the loop's control words live in pinned host
+// memory mapped into the device's address space; LoopDev in device memory.
+enum LoopState : int32_t { LOOP_FREE = 0, LOOP_READY = 1, LOOP_DONE = 2, LOOP_STOP = 3 };
+struct LoopEntry {
+    int32_t state;            // LoopState: ready / stop set by the host, done by the device
+    int32_t n_phases;
+    const Phase *phases;      // the request's one-launch phase list (device memory)
+    const void *b;            // the batch's right-hand sides and solutions (device buffers of its slot):
+    void *x;                  //   they replace the pointers the list was recorded with
+    PersistCtx ctx;           // its operator's context (bar and polls are the loop's own)
+};
+struct LoopCtl {
+    int64_t start;            // ring index the next launch starts at (host)
+    int64_t head;             // ring index the loop had reached when it left (device)
+    int32_t exited;           // 1 once the loop kernel has left (device)
+    int32_t pad;
+};
+struct LoopDev {
+    int32_t decision;         // 1 = serve the current entry, 0 = leave
+    int32_t cur_n;
+    const Phase *cur_phases;
+    const void *cur_b;
+    void *cur_x;
+    PersistCtx cur_ctx;
 };
 
 struct Workspace {
@@ -194,15 +270,20 @@ struct hm_matrix_s {
 
     // CUDA graphs of whole solves, keyed by pointers, sizes and options
     struct GraphKey {
-        const void *b; void *x; int64_t ldb, ldx; int nrhs, K, m, nested, refine, fp64;
+        const void *b; void *x; int64_t ldb, ldx; int nrhs, K, m, nested, refine, fp64, persist;
         bool operator<(const GraphKey &o) const
         {
-            return std::tie(b, x, ldb, ldx, nrhs, K, m, nested, refine, fp64) <
-                   std::tie(o.b, o.x, o.ldb, o.ldx, o.nrhs, o.K, o.m, o.nested, o.refine, o.fp64);
+            return std::tie(b, x, ldb, ldx, nrhs, K, m, nested, refine, fp64, persist) <
+                   std::tie(o.b, o.x, o.ldb, o.ldx, o.nrhs, o.K, o.m, o.nested, o.refine, o.fp64, o.persist);
         }
     };
     std::map<GraphKey, cudaGraphExec_t> graphs;
     cudaStream_t cap_stream = nullptr;
+    // phase lists of one-launch solves (device copies), keyed like the graphs; the
+    // barrier words of the one-launch solve (count, generation)
+    struct PersistList { hm::Phase *d = nullptr; int n = 0, units = 0; int64_t launches = 0, bytes = 0; };
+    std::map<GraphKey, PersistList> persist;
+    unsigned *d_bar = nullptr;
 
     // kernel choices measured on this operator per right-hand-side count (hm_api.cu autotune)
     struct Tune { int prod_rb = -1, res_rb = -1; double prod_ms = 0.0, res_ms = 0.0; };   // res_rb < 0: not tuned
@@ -306,6 +387,20 @@ void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, 
 void launch_seed_vector(float2 *v, const int32_t *pperm, int64_t pN, uint32_t seed, cudaStream_t s);
 void launch_norm2(const float2 *v, int64_t n, double *out, cudaStream_t s);
 void launch_conj_scale(const float2 *src, float2 *dst, int64_t n, const double *nrm2, bool conj, cudaStream_t s);
+// one-launch solve (k_persist.cu): whether the operator's leaves fit it, and one
+// cooperative launch running the phases (device array) with grid barriers between them;
+// units = the widest phase's work units (caps the grid)
+bool persist_supported(hm_matrix h);
+void persist_ctx(hm_matrix h, PersistCtx *c);
+// the recorded phase list of a one-launch solve of b -> x (device pointers, ld = N), made on
+// first use (which may grow the handle's workspace and launches nothing) (hm_api.cu)
+hm_status persist_phases(hm_matrix h, const void *b, void *x, int nrhs, const hm_solve_opts *o,
+                         const Phase **phases, int *n_phases);
+// the request loop: grid size (cooperative, all CTAs resident) and one launch
+int serve_loop_grid(int num_sms);
+hm_status launch_serve_loop(LoopEntry *ring, int ring_size, LoopCtl *ctl, LoopDev *dv, unsigned *bar, int *loop_status,
+                            int grid, uint32_t idle_polls, cudaStream_t s);
+hm_status launch_persist(hm_matrix h, const Phase *d_phases, int n_phases, int units, cudaStream_t s);
 // bytes of the split-x workspace of the tensor-core product for n_xch chunks and nrhs (k_mrhs_tc.cu)
 size_t tc_xplane_bytes(int64_t n_xch, int nrhs);
 // tensor-core products of a level's small items for all right-hand sides (k_mrhs_tc.cu);

@@ -31,6 +31,8 @@
 #include <mutex>
 #include <thread>
 
+using namespace hm;
+
 namespace {
 
 using clk = std::chrono::steady_clock;
@@ -73,6 +75,9 @@ struct Slot {
     int op = -1;
     std::vector<int64_t> reqs;
     int nrhs = 0;
+    // device-loop mode: 1 = posted to the ring at ring_idx, 2 = result being copied out
+    int stage = 0;
+    int64_t ring_idx = -1;
 };
 
 } // namespace
@@ -94,9 +99,27 @@ struct hm_server_s {
     // statistics
     int64_t batches = 0, solved_rhs = 0, evictions = 0, builds = 0;
     int64_t resident_bytes = 0, peak_resident = 0;
+    // device-resident request loop (device_loop mode): the ring and control words in
+    // mapped pinned host memory (host and device addresses), the loop's device words,
+    // its stream and grid; the recorded phase lists per (operator, slot, RHS bucket)
+    bool device_loop = false;
+    hm::LoopEntry *ring = nullptr, *d_ring = nullptr;
+    hm::LoopCtl *ctl = nullptr, *d_ctl = nullptr;
+    hm::LoopDev *d_dev = nullptr;
+    unsigned *d_bar = nullptr;
+    int *d_loop_status = nullptr;
+    cudaStream_t loop_stream = nullptr;
+    int loop_grid = 0;
+    bool loop_running = false;
+    int64_t ring_next = 0;         // next ring index to post
+    int64_t loop_head = 0;         // first ring index the next loop launch serves
+    std::map<std::pair<int, int>, std::pair<const hm::Phase *, int>> recorded;   // (operator, RHS bucket)
+    int64_t loop_launches = 0, loop_stops = 0;
 };
 
 namespace {
+
+void drop_operator(hm_server_s *S, int op);
 
 hm_status slot_reserve(Slot &s, size_t elems)
 {
@@ -125,8 +148,7 @@ hm_status make_resident(hm_server_s *S, int op)
             if (c.h && !c.busy && (victim < 0 || c.last_use < S->ops[victim].last_use)) victim = i;
         }
         if (victim < 0) break;   // everything resident is in use: admit anyway, the budget is a target
-        hm_destroy(S->ops[victim].h);
-        S->ops[victim].h = nullptr;
+        drop_operator(S, victim);
         S->resident_bytes -= S->ops[victim].bytes;
         S->evictions++;
     }
@@ -193,9 +215,289 @@ void fail_requests(hm_server_s *S, int op, hm_status st)
     o.queue.clear();
 }
 
+// ---- device-resident request loop ----------------------------------------------------
+//
+// One cooperative kernel (k_serve_loop) stays on the GPU and serves batches from a
+// ring in mapped pinned host memory: the scheduler copies a batch's right-hand
+// sides into its slot's device buffer, writes the ring entry (the batch's recorded
+// one-launch phase list and its operator's context) and marks it ready; the loop
+// runs it without any launch and marks it done; the scheduler then copies the
+// solutions out on the slot's stream.  Work that needs the GPU otherwise (builds,
+// allocation, recording a new phase list) is done while the loop is stopped: a
+// stop entry after everything posted makes it leave once those are served.  An
+// idle loop leaves by itself after LOOP_IDLE_POLLS polls (about a second) and is
+// launched again when the next batch is posted.
+
+constexpr int RING = 64;
+constexpr uint32_t LOOP_IDLE_POLLS = 400000;
+constexpr int RHS_BUCKET = 4;        // batches are padded to a multiple of 4 right-hand sides
+
+int ring_state(hm_server_s *S, int64_t idx) { return __atomic_load_n(&S->ring[idx % RING].state, __ATOMIC_ACQUIRE); }
+void ring_set(hm_server_s *S, int64_t idx, int v) { __atomic_store_n(&S->ring[idx % RING].state, v, __ATOMIC_RELEASE); }
+
+// collects a loop kernel that has left (its stream), and where it stopped
+void loop_reap(hm_server_s *S)
+{
+    if (!S->loop_running || __atomic_load_n(&S->ctl->exited, __ATOMIC_ACQUIRE) == 0) return;
+    cudaStreamSynchronize(S->loop_stream);
+    S->loop_running = false;
+    S->loop_head = __atomic_load_n(&S->ctl->head, __ATOMIC_ACQUIRE);
+}
+
+hm_status loop_start(hm_server_s *S)
+{
+    __atomic_store_n(&S->ctl->start, S->loop_head, __ATOMIC_RELAXED);
+    __atomic_store_n(&S->ctl->head, S->loop_head, __ATOMIC_RELAXED);
+    __atomic_store_n(&S->ctl->exited, 0, __ATOMIC_RELEASE);
+    HM_CUDA(cudaMemsetAsync(S->d_loop_status, 0, sizeof(int), S->loop_stream));
+    hm_status st = launch_serve_loop(S->d_ring, RING, S->d_ctl, S->d_dev, S->d_bar, S->d_loop_status, S->loop_grid,
+                                     LOOP_IDLE_POLLS, S->loop_stream);
+    if (st != HM_OK) return st;
+    S->loop_running = true;
+    S->loop_launches++;
+    return HM_OK;
+}
+
+// stops the loop (after everything posted is served) so that the host may use the GPU
+hm_status loop_stop(hm_server_s *S, std::unique_lock<std::mutex> &lk)
+{
+    loop_reap(S);
+    if (!S->loop_running) return HM_OK;
+    const int64_t idx = S->ring_next;
+    ring_set(S, idx, LOOP_STOP);
+    const auto deadline = clk::now() + std::chrono::seconds(60);
+    while (__atomic_load_n(&S->ctl->exited, __ATOMIC_ACQUIRE) == 0) {
+        if (clk::now() > deadline) return fail(HM_ERR_TIMEOUT, "the serving loop did not stop within 60 s");
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lk.lock();
+    }
+    loop_reap(S);
+    ring_set(S, idx, LOOP_FREE);
+    S->loop_stops++;
+    return HM_OK;
+}
+
+// destroys an operator's handle; its recorded phase lists go with it
+void drop_operator(hm_server_s *S, int op)
+{
+    hm_destroy(S->ops[op].h);
+    S->ops[op].h = nullptr;
+    for (auto it = S->recorded.begin(); it != S->recorded.end();)
+        it = it->first.first == op ? S->recorded.erase(it) : std::next(it);
+}
+
+int bucket_of(int nrhs, int max_rhs)
+{
+    const int b = (nrhs + RHS_BUCKET - 1) / RHS_BUCKET * RHS_BUCKET;
+    return std::min(b, (max_rhs + RHS_BUCKET - 1) / RHS_BUCKET * RHS_BUCKET);
+}
+
+void fail_slot(hm_server_s *S, Slot &slot, hm_status st)
+{
+    for (int64_t id : slot.reqs) {
+        Request &r = S->reqs[id];
+        r.status = st;
+        r.done = true;
+        r.t_done = clk::now();
+    }
+    S->ops[slot.op].busy = false;
+    slot.busy = false;
+    slot.stage = 0;
+    slot.reqs.clear();
+    slot.op = -1;
+    S->cv_done.notify_all();
+}
+
+// the scheduler of the device-loop mode
+void loop_device(hm_server_s *S)
+{
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        bool progressed = false;
+        // 1. batches the loop has served: copy their solutions out; retire copied ones
+        for (Slot &s : S->slots) {
+            if (!s.busy) continue;
+            if (s.stage == 1 && ring_state(S, s.ring_idx) == LOOP_DONE) {
+                const int64_t N = S->ops[s.op].n;
+                cudaMemcpyAsync(s.h_buf + s.cap, s.d_x, sizeof(float2) * N * s.nrhs, cudaMemcpyDeviceToHost, s.stream);
+                cudaEventRecord(s.done, s.stream);
+                ring_set(S, s.ring_idx, LOOP_FREE);
+                s.stage = 2;
+                progressed = true;
+            }
+            if (s.stage == 2) {
+                const cudaError_t e = cudaEventQuery(s.done);
+                if (e == cudaSuccess) {
+                    retire(S, s);
+                    s.stage = 0;
+                    progressed = true;
+                } else if (e != cudaErrorNotReady) {
+                    S->fatal = HM_ERR_CUDA;
+                    S->fatal_msg = cudaGetErrorString(e);
+                    S->stop = true;
+                }
+            }
+        }
+        if (progressed) S->cv_done.notify_all();
+        // over the budget with nothing posted: stop the loop and evict idle operators without
+        // queued requests, least recently used first (freeing memory must not wait on the loop)
+        if (S->resident_bytes > S->budget) {
+            bool idle = true;
+            for (Slot &q : S->slots) idle &= !q.busy;
+            auto victim_of = [&] {
+                int v = -1;
+                for (int i = 0; i < (int)S->ops.size(); ++i) {
+                    const Operator &c = S->ops[i];
+                    if (c.h && !c.busy && c.queue.empty() && (v < 0 || c.last_use < S->ops[v].last_use)) v = i;
+                }
+                return v;
+            };
+            if (idle && victim_of() >= 0 && loop_stop(S, lk) == HM_OK) {
+                int v;
+                while (S->resident_bytes > S->budget && (v = victim_of()) >= 0) {
+                    drop_operator(S, v);
+                    S->resident_bytes -= S->ops[v].bytes;
+                    S->evictions++;
+                }
+            }
+        }
+        // 2. a loop that left on an error (a bounded wait gave up) leaves its current batch unserved
+        loop_reap(S);
+        if (!S->loop_running) {
+            int lst = 0;
+            cudaMemcpy(&lst, S->d_loop_status, sizeof(int), cudaMemcpyDeviceToHost);
+            if (lst != 0) {
+                for (Slot &s : S->slots)
+                    if (s.busy && s.stage == 1 && s.ring_idx == S->loop_head) {
+                        ring_set(S, s.ring_idx, LOOP_FREE);
+                        fail_slot(S, s, (hm_status)lst);
+                    }
+                S->loop_head++;
+                cudaMemset(S->d_loop_status, 0, sizeof(int));
+            }
+            // a loop that left on idle just before a batch was posted: launch it again
+            bool pending = false;
+            for (Slot &s : S->slots) pending |= s.busy && s.stage == 1;
+            if (pending && loop_start(S) != HM_OK) {
+                S->fatal = HM_ERR_CUDA;
+                S->fatal_msg = "the serving loop could not be launched";
+                S->stop = true;
+            }
+        }
+        // 3. post new batches
+        for (int op = 0; op < (int)S->ops.size(); ++op) {
+            Operator &o = S->ops[op];
+            if (o.busy || o.queue.empty()) continue;
+            int si = -1;
+            for (int q = 0; q < (int)S->slots.size(); ++q)
+                if (!S->slots[q].busy) { si = q; break; }
+            if (si < 0) break;
+            Slot &slot = S->slots[si];
+            std::vector<int64_t> take;
+            int nrhs = 0;
+            while (!o.queue.empty()) {
+                const Request &r = S->reqs[o.queue.front()];
+                if (!take.empty() && nrhs + r.nrhs > S->max_batch_rhs) break;
+                take.push_back(o.queue.front());
+                nrhs += r.nrhs;
+                o.queue.pop_front();
+            }
+            const int bucket = bucket_of(nrhs, S->max_batch_rhs);
+            const int top = bucket_of(S->max_batch_rhs, S->max_batch_rhs);
+            hm_status st = HM_OK;
+            const auto key = std::make_pair(op, bucket);
+            if (!o.h || !S->recorded.count(key) || slot.cap < (size_t)o.n * top) {
+                // host-side GPU work: stop the loop first (everything posted is served before it leaves)
+                if ((st = loop_stop(S, lk)) == HM_OK && (st = make_resident(S, op)) == HM_OK)
+                    st = slot_reserve(slot, (size_t)o.n * top);   // this slot is free
+                // every bucket of the operator at once, the largest first, so that the handle's
+                // workspace never grows later (a regrowth would free the lists already recorded);
+                // the lists do not depend on the slot (its buffers are passed with each batch)
+                for (int b = top; st == HM_OK && b >= RHS_BUCKET; b -= RHS_BUCKET) {
+                    const auto k2 = std::make_pair(op, b);
+                    if (S->recorded.count(k2)) continue;
+                    const Phase *ph = nullptr;
+                    int n = 0;
+                    if ((st = persist_phases(o.h, slot.d_b, slot.d_x, b, &o.so, &ph, &n)) == HM_OK)
+                        S->recorded[k2] = {ph, n};
+                }
+                if (st == HM_OK) {
+                    hm_info info;
+                    if (hm_get_info(o.h, &info) == HM_OK) {
+                        S->resident_bytes += info.device_bytes - o.bytes;
+                        o.bytes = info.device_bytes;
+                        S->peak_resident = std::max(S->peak_resident, S->resident_bytes);
+                    }
+                }
+            }
+            if (st != HM_OK) {
+                for (int64_t id : take) { S->reqs[id].status = st; S->reqs[id].done = true; }
+                S->cv_done.notify_all();
+                continue;
+            }
+            const int64_t N = o.n;
+            int col = 0;
+            for (int64_t id : take) {
+                const Request &r = S->reqs[id];
+                std::memcpy(slot.h_buf + (size_t)col * N, r.b.data(), sizeof(float2) * N * r.nrhs);
+                col += r.nrhs;
+            }
+            std::memset(slot.h_buf + (size_t)nrhs * N, 0, sizeof(float2) * N * (bucket - nrhs));
+            cudaMemcpyAsync(slot.d_b, slot.h_buf, sizeof(float2) * N * bucket, cudaMemcpyHostToDevice, slot.stream);
+            if (cudaStreamSynchronize(slot.stream) != cudaSuccess) {
+                for (int64_t id : take) { S->reqs[id].status = HM_ERR_CUDA; S->reqs[id].done = true; }
+                S->cv_done.notify_all();
+                continue;
+            }
+            const auto &rec = S->recorded[key];
+            const int64_t idx = S->ring_next++;
+            LoopEntry &e = S->ring[idx % RING];
+            e.n_phases = rec.second;
+            e.phases = rec.first;
+            e.b = slot.d_b;
+            e.x = slot.d_x;
+            persist_ctx(o.h, &e.ctx);
+            ring_set(S, idx, LOOP_READY);
+            slot.busy = true;
+            slot.stage = 1;
+            slot.ring_idx = idx;
+            slot.op = op;
+            slot.reqs = take;
+            slot.nrhs = nrhs;
+            o.busy = true;
+            o.last_use = clk::now();
+            S->batches++;
+            progressed = true;
+            loop_reap(S);
+            if (!S->loop_running && (st = loop_start(S)) != HM_OK) {
+                S->fatal = st;
+                S->fatal_msg = "the serving loop could not be launched";
+                S->stop = true;
+            }
+        }
+        if (!progressed) {
+            bool any_busy = false;
+            for (Slot &s : S->slots) any_busy |= s.busy;
+            if (any_busy) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(5));
+                lk.lock();
+            } else {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            }
+        }
+    }
+    loop_stop(S, lk);
+}
+
 void loop(hm_server_s *S)
 {
     cudaSetDevice(S->device);
+    if (S->device_loop) {
+        loop_device(S);
+        return;
+    }
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop) {
         bool progressed = false;
@@ -306,14 +608,16 @@ using namespace hm;
 
 extern "C" {
 
-hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_rhs, hm_server *out)
+hm_status hm_server_create_ex(int n_slots, int64_t hbm_budget_bytes, int max_batch_rhs, int device_loop,
+                              hm_server *out)
 {
-    if (!out || n_slots < 1 || n_slots > 64 || hbm_budget_bytes <= 0 || max_batch_rhs < 1)
+    if (!out || n_slots < 1 || n_slots > 32 || hbm_budget_bytes <= 0 || max_batch_rhs < 1)
         return fail(HM_ERR_ARG, "bad server arguments");
     *out = nullptr;
     hm_server S = new hm_server_s();
     S->max_batch_rhs = max_batch_rhs;
     S->budget = hbm_budget_bytes;
+    S->device_loop = device_loop != 0;
     cudaGetDevice(&S->device);
     S->slots.resize(n_slots);
     for (Slot &s : S->slots) {
@@ -323,9 +627,36 @@ hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_
             return fail(HM_ERR_CUDA, "stream or event creation failed");
         }
     }
+    if (S->device_loop) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
+        S->loop_grid = serve_loop_grid(sms);
+        bool ok = cudaHostAlloc((void **)&S->ring, RING * sizeof(LoopEntry), cudaHostAllocMapped) == cudaSuccess &&
+                  cudaHostAlloc((void **)&S->ctl, sizeof(LoopCtl), cudaHostAllocMapped) == cudaSuccess;
+        if (ok) {
+            std::memset(S->ring, 0, RING * sizeof(LoopEntry));
+            std::memset(S->ctl, 0, sizeof(LoopCtl));
+            ok = cudaHostGetDevicePointer((void **)&S->d_ring, S->ring, 0) == cudaSuccess &&
+                 cudaHostGetDevicePointer((void **)&S->d_ctl, S->ctl, 0) == cudaSuccess &&
+                 cudaMalloc((void **)&S->d_dev, sizeof(LoopDev)) == cudaSuccess &&
+                 cudaMalloc((void **)&S->d_bar, 2 * sizeof(unsigned)) == cudaSuccess &&
+                 cudaMalloc((void **)&S->d_loop_status, sizeof(int)) == cudaSuccess &&
+                 cudaMemset(S->d_loop_status, 0, sizeof(int)) == cudaSuccess &&
+                 cudaStreamCreateWithFlags(&S->loop_stream, cudaStreamNonBlocking) == cudaSuccess;
+        }
+        if (!ok) {
+            hm_server_destroy(S);
+            return fail(HM_ERR_OOM, "the serving loop's ring or device words could not be allocated");
+        }
+    }
     S->worker = std::thread(loop, S);
     *out = S;
     return HM_OK;
+}
+
+hm_status hm_server_create(int n_slots, int64_t hbm_budget_bytes, int max_batch_rhs, hm_server *out)
+{
+    return hm_server_create_ex(n_slots, hbm_budget_bytes, max_batch_rhs, 0, out);
 }
 
 hm_status hm_server_add_mesh(hm_server S, const hm_mesh *mesh, const hm_build_opts *bo, const hm_solve_opts *so,
@@ -429,6 +760,8 @@ hm_status hm_server_get_info(hm_server S, hm_server_info *st)
     st->evictions = S->evictions;
     st->resident_bytes = S->resident_bytes;
     st->peak_resident_bytes = S->peak_resident;
+    st->loop_launches = S->loop_launches;
+    st->loop_stops = S->loop_stops;
     return HM_OK;
 }
 
@@ -451,6 +784,15 @@ void hm_server_destroy(hm_server S)
     }
     for (Operator &o : S->ops)
         if (o.h) hm_destroy(o.h);
+    if (S->loop_stream) {
+        cudaStreamSynchronize(S->loop_stream);
+        cudaStreamDestroy(S->loop_stream);
+    }
+    if (S->ring) cudaFreeHost(S->ring);
+    if (S->ctl) cudaFreeHost(S->ctl);
+    if (S->d_dev) cudaFree(S->d_dev);
+    if (S->d_bar) cudaFree(S->d_bar);
+    if (S->d_loop_status) cudaFree(S->d_loop_status);
     delete S;
 }
 

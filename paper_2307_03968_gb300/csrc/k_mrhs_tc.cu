@@ -25,10 +25,16 @@
 // splits it and multiplies it into the output accumulator with the output-side
 // factor read transposed (U for the forward product, V^T for the mirror).
 //
-// Precision (3xTF32): every FP32 operand a is split as a = hi + lo, hi = a rounded
-// to TF32, lo = a - hi (exact); each K step accumulates hi*hi + hi*lo + lo*hi in
-// FP32, which keeps the products within a few FP32 ulps (the dropped lo*lo term
-// and the TF32 rounding of lo are ~2^-22 relative).
+// Precision (3xTF32): every FP32 operand a is split as a = hi + lo, hi = a
+// rounded to TF32 (|a - hi| <= 2^-11 |a|), lo = a - hi rounded to TF32 too; each
+// K step accumulates hi*hi + hi*lo + lo*hi in FP32 (the dropped lo*lo and the
+// rounding of lo are <= 2^-22 |a b| each).  The larger error is the tensor core's
+// FP32 accumulation, which loses a little on every MMA added into a large running
+// sum: measured against the oracle, the product erred 7.4e-6 (relative, 60-unknown
+// leaves) when a work unit summed 256 K chunks in tensor memory, and a refined
+// solve 1.2e-4, above the 1e-4 bar; with units of at most 16 chunks
+// (TC_UNIT_CHUNKS: each unit's sum is drained into z in FP32) 5.4e-7 and 7.2e-6.
+// Adding the lo*lo products changed neither (same errors to four digits).
 //
 // Pipeline (warp-specialised, mbarrier hand-offs, no CTA-wide barrier per chunk).
 // K goes in chunks of 8 (one MMA K step) through a ring of shared-memory slots.
@@ -75,10 +81,11 @@ __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvt
 
 __device__ __forceinline__ void split_tf32(float a, float &hi, float &lo)
 {
-    uint32_t h;
+    uint32_t h, l;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(a));
     hi = __uint_as_float(h);
-    lo = __fsub_rn(a, hi);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(__fsub_rn(a, hi)));
+    lo = __uint_as_float(l);
 }
 
 // shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x

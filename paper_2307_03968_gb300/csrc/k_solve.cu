@@ -4,7 +4,7 @@
 //  k_leaf_update   per leaf: out = y - D_i^{-1} z_i (the series accumulate of
 //                  x_j = y - D^{-1} M x_{j-1}), or out = D_i^{-1} z_i; clears z.
 //  helpers         permutation in/out, residual, finiteness check.
-#include "k_common.cuh"
+#include "k_solve_dev.cuh"
 
 #include <cuda_runtime.h>
 
@@ -13,9 +13,7 @@ namespace {
 
 using namespace kc;
 
-// Per leaf (blockIdx.x) and right-hand side (blockIdx.y):
-//   w = D_i^{-1} zin_i ;  out_i = y ? y_i - w : w ;  zin_i = 0 if zero_in.
-// D_i^{-1} is column-major np x np (np = padded leaf length), zero padded.
+// Per leaf (blockIdx.x) and right-hand side (blockIdx.y): leaf_update_leaf.
 template <class T>
 __global__ void __launch_bounds__(256)
 k_leaf_update(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
@@ -24,39 +22,9 @@ k_leaf_update(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__
 {
     using C = typename CT<T>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *zs = reinterpret_cast<C *>(smem_raw);          // [np]
     __shared__ C part[8][64];
-    const int leaf = blockIdx.x, r = blockIdx.y;
-    const int o = pleaf_off[leaf], np = pleaf_off[leaf + 1] - o;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    C *zr = zin + r * ld + o;
-    for (int j = tid; j < np; j += blockDim.x) zs[j] = zr[j];
-    __syncthreads();
-    if (zero_in)
-        for (int j = tid; j < np; j += blockDim.x) zr[j] = czero(C());
-    const C *Di = dinv + dinv_off[leaf];
-    for (int rc = 0; rc < np; rc += 64) {
-        const int i = rc + 2 * lane;
-        C a0 = czero(C()), a1 = czero(C());
-        if (i < np)
-            for (int j = w; j < np; j += 8) {
-                Pair<T> d = ld_stream(Di + (int64_t)j * np + i);
-                const C zj = zs[j];
-                cfma(a0, d.a, zj);
-                cfma(a1, d.b, zj);
-            }
-        part[w][2 * lane] = a0;
-        part[w][2 * lane + 1] = a1;
-        __syncthreads();
-        if (tid < 64 && rc + tid < np) {
-            C s = part[0][tid];
-#pragma unroll
-            for (int q = 1; q < 8; ++q) s = cadd(s, part[q][tid]);
-            const int64_t g = r * ld + o + rc + tid;
-            out[g] = y ? csub(y[g], s) : s;
-        }
-        __syncthreads();
-    }
+    leaf_update_leaf<T>(blockIdx.x, blockIdx.y, pleaf_off, dinv_off, dinv, y, zin, out, ld, zero_in,
+                        reinterpret_cast<C *>(smem_raw), part);
 }
 
 // acc += D x for the complex64 self blocks (column-major, like D^{-1}), with

@@ -70,7 +70,8 @@ class HmBlocks(ctypes.Structure):
 
 class HmSolveOpts(ctypes.Structure):
     _fields_ = [("n_terms", ctypes.c_int), ("n_levels", ctypes.c_int), ("nested", ctypes.c_int),
-                ("refine", ctypes.c_int), ("fp64", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("fp64", ctypes.c_int), ("graph", ctypes.c_int),
+                ("persistent", ctypes.c_int)]
 
 
 class HmSolveInfo(ctypes.Structure):
@@ -89,12 +90,13 @@ class HmInfo(ctypes.Structure):
 
 class HmServerInfo(ctypes.Structure):
     _fields_ = [("batches", I64), ("solved_rhs", I64), ("builds", I64), ("evictions", I64),
-                ("resident_bytes", I64), ("peak_resident_bytes", I64)]
+                ("resident_bytes", I64), ("peak_resident_bytes", I64), ("loop_launches", I64),
+                ("loop_stops", I64)]
 
 
 EXPORTS = ["hm_build", "hm_build_from_blocks", "hm_factor_leaf", "hm_estimate_norms", "hm_powerseries_solve",
            "hm_powerseries_solve_host", "hm_apply", "hm_residual", "hm_residual_noalloc", "hm_rhs_plane_wave", "hm_profile", "hm_profile_read",
-           "hm_server_create", "hm_server_add_mesh", "hm_server_submit", "hm_server_wait", "hm_server_get_info",
+           "hm_server_create", "hm_server_create_ex", "hm_server_add_mesh", "hm_server_submit", "hm_server_wait", "hm_server_get_info",
            "hm_server_destroy",
            "hm_get_info", "hm_get_tuning", "hm_set_tuning", "hm_set_wait_limit", "hm_get_perm", "hm_get_leaves", "hm_get_blocks", "hm_get_block", "hm_sync_status",
            "hm_size", "hm_destroy", "hm_last_error", "hm_version"]
@@ -124,6 +126,7 @@ def load():
     L.hm_profile.argtypes = [P, ctypes.c_int]
     L.hm_profile_read.argtypes = [P, PD, PI64, PI64]
     L.hm_server_create.argtypes = [ctypes.c_int, I64, ctypes.c_int, ctypes.POINTER(P)]
+    L.hm_server_create_ex.argtypes = [ctypes.c_int, I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]
     L.hm_server_add_mesh.argtypes = [P, ctypes.POINTER(HmMesh), ctypes.POINTER(HmBuildOpts),
                                      ctypes.POINTER(HmSolveOpts), ctypes.POINTER(ctypes.c_int), PI64]
     L.hm_server_submit.argtypes = [P, ctypes.c_int, P, I64, ctypes.c_int, PI64]
@@ -256,26 +259,29 @@ class HMatrix:
 
     # ---- solve / apply -------------------------------------------------------------------
     def solve(self, b, x, n_terms=2, n_levels=1, nested=True, refine=False, fp64=False, stream=None,
-              info=False, graph=True):
+              info=False, graph=True, persistent=False):
         """hm_powerseries_solve on torch CUDA tensors b, x of shape (N,) or (nrhs, N)
-        (each row one right-hand side, contiguous), complex64 (complex128 if fp64)."""
+        (each row one right-hand side, contiguous), complex64 (complex128 if fp64);
+        persistent = the one-launch solve."""
         nrhs, ldb = self._cols(b)
         _, ldx = self._cols(x)
         o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0,
-                        1 if graph else 0)
+                        1 if graph else 0, 1 if persistent else 0)
         si = HmSolveInfo()
         _check(load().hm_powerseries_solve(self._h, P(b.data_ptr()), ldb, P(x.data_ptr()), ldx, nrhs,
                                            ctypes.byref(o), _stream(stream), ctypes.byref(si) if info else None))
         return si if info else None
 
-    def solve_host(self, b, n_terms=2, n_levels=1, nested=True, refine=False, fp64=False, stream=None):
+    def solve_host(self, b, n_terms=2, n_levels=1, nested=True, refine=False, fp64=False, stream=None,
+                   persistent=False):
         """hm_powerseries_solve_host on numpy arrays: b (N,) or (nrhs, N); returns x."""
         dt = np.complex128 if fp64 else np.complex64
         b = np.ascontiguousarray(b, dtype=dt)
         x = np.empty_like(b)
         nrhs = 1 if b.ndim == 1 else b.shape[0]
         n = b.shape[-1]
-        o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0, 1)
+        o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0, 1,
+                        1 if persistent else 0)
         _check(load().hm_powerseries_solve_host(self._h, P(b.ctypes.data), n, P(x.ctypes.data), n, nrhs,
                                                 ctypes.byref(o), _stream(stream)))
         return x
@@ -405,10 +411,12 @@ class HMatrix:
 class Server:
     """hm_server: continuous-batching solves of several operators (complex64)."""
 
-    def __init__(self, n_slots=4, hbm_budget_bytes=8 << 30, max_batch_rhs=64):
+    def __init__(self, n_slots=4, hbm_budget_bytes=8 << 30, max_batch_rhs=64, device_loop=False):
+        """device_loop: serve from a device-resident request loop (hm_server_create_ex)."""
         self._s = P()
         self.max_batch_rhs = max_batch_rhs
-        _check(load().hm_server_create(n_slots, hbm_budget_bytes, max_batch_rhs, ctypes.byref(self._s)))
+        _check(load().hm_server_create_ex(n_slots, hbm_budget_bytes, max_batch_rhs, 1 if device_loop else 0,
+                                          ctypes.byref(self._s)))
         self._keep = []
 
     def add_mesh(self, xyz, cells, leaf_size=64, arity=8, adm=2.0, aca_tol=1e-4, levels=-1, wavelength=1.0,
