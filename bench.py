@@ -70,6 +70,20 @@ WORKLOADS = {
                            shape=("shell", (0.35, 0.4, 6.0), (1, 55, 206)), eps=2.0, leaf_size=64, arity=2, adm=1.0,
                            aca_tol=1e-3, n_terms=2, n_levels=1, refine=False, nrhs=1, unknowns=158730,
                            tetrahedra=67980),
+    # the same three at the paper's tree depths (binary levels 6, 10 and 8: leaves of about 1,050, 118 and
+    # 621 unknowns), where the paper reports its two-term solve
+    "paper_plate_depth6": dict(name="paper_pec_plate_15lambda_67200rwg_depth6", kind="rwg",
+                               shape=("plate", (15.0, 15.0), (150, 150)), leaf_size=1050, arity=2, adm=1.0,
+                               aca_tol=1e-3, n_terms=2, n_levels=1, refine=False, nrhs=1, unknowns=67200,
+                               triangles=45000),
+    "paper_slab_depth10": dict(name="paper_dielectric_slab_10x1x0.1lambda_119984swg_depth10", kind="swg",
+                               shape=("box", (10.0, 1.0, 0.1), (218, 21, 2)), eps=2.0, leaf_size=118, arity=2,
+                               adm=1.0, aca_tol=1e-3, n_terms=2, n_levels=1, refine=False, nrhs=1, unknowns=119984,
+                               tetrahedra=54936),
+    "paper_cylinder_depth8": dict(name="paper_hollow_dielectric_cylinder_6lambda_158730swg_depth8", kind="swg",
+                                  shape=("shell", (0.35, 0.4, 6.0), (1, 55, 206)), eps=2.0, leaf_size=621, arity=2,
+                                  adm=1.0, aca_tol=1e-3, n_terms=2, n_levels=1, refine=False, nrhs=1,
+                                  unknowns=158730, tetrahedra=67980),
     # the small sphere of the measurement plan (1,920 RWG unknowns, leaf 32): latency, operator L2-resident
     "sphere03": dict(name="sefie_pec_sphere_r0.3lambda_1920rwg", kind="rwg", subdivisions=3, radius=0.3, leaf_size=32,
                      arity=8, adm=2.0, aca_tol=1e-4, n_terms=2, n_levels=1, refine=True, nrhs=1, unknowns=1920,
@@ -405,14 +419,16 @@ class ClockSampler:
 # ---------------------------------------------------------------- traffic -------
 def committed_traffic():
     """Per-launch DRAM traffic of the product kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+    summary, if it was taken on the current kernel source (k_product.cu and the
+    headers holding its device code); else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2307_03968_gb300", "csrc", "k_product.cu")
+    csrc = os.path.join(ROOT, "paper_2307_03968_gb300", "csrc")
     try:
         with open(path) as f:
             d = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256(b"".join(open(os.path.join(csrc, f), "rb").read()
+                                    for f in ("k_product.cu", "k_product_dev.cuh", "k_common.cuh"))).hexdigest()[:16]
         if d.get("k_product_sha256_16") == h and d.get("workload") == WORKLOAD["name"]:
             return d.get("bytes_per_launch")
     except Exception:

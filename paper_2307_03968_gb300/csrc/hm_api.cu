@@ -180,6 +180,31 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         if ((st = upload(h, &L.d_big, big, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_tcu, tcu, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_tcp, tcp, s)) != HM_OK) return st;
+        // the product's lists with tall dense blocks cut into row panels: a panel of rows
+        // [r, r + mr) of a row-major block is itself a dense item with the same row stride
+        auto panels = [](const std::vector<Item> &in, std::vector<Item> &out) {
+            bool cut = false;
+            for (const Item &it : in) {
+                if (it.k != 0 || it.m <= PROD_PANEL) { out.push_back(it); continue; }
+                cut = true;
+                for (int32_t r = 0; r < it.m; r += PROD_PANEL) {
+                    Item q = it;
+                    q.off = it.off + (int64_t)r * even(it.n);
+                    q.row0 = it.row0 + r;
+                    q.m = std::min<int32_t>(PROD_PANEL, it.m - r);
+                    out.push_back(q);
+                }
+            }
+            return cut;
+        };
+        std::vector<Item> pa, pb;
+        if (panels(L.items, pa)) {
+            panels(big, pb);
+            L.n_prod = (int64_t)pa.size();
+            L.n_prod_big = (int64_t)pb.size();
+            if ((st = upload(h, &L.d_prod, pa, s)) != HM_OK) return st;
+            if ((st = upload(h, &L.d_prod_big, pb, s)) != HM_OK) return st;
+        }
     }
     return HM_OK;
 }
@@ -211,6 +236,8 @@ static void free_handle(hm_matrix h)
         if (p) cudaFree(p);
     for (auto &kv : h->levels) {
         if (kv.second.d_items) cudaFree(kv.second.d_items);
+        if (kv.second.d_prod) cudaFree(kv.second.d_prod);
+        if (kv.second.d_prod_big) cudaFree(kv.second.d_prod_big);
         if (kv.second.d_small) cudaFree(kv.second.d_small);
         if (kv.second.d_big) cudaFree(kv.second.d_big);
         if (kv.second.d_tcu) cudaFree(kv.second.d_tcu);
@@ -470,8 +497,8 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
     if (c.rec) {
         Phase q = phase(PH_APPLY, c.nrhs);
         q.a = x; q.c = z;
-        q.items = it->second.d_items;
-        q.n = (int64_t)it->second.items.size();
+        q.items = it->second.d_prod ? it->second.d_prod : it->second.d_items;
+        q.n = it->second.d_prod ? it->second.n_prod : (int64_t)it->second.items.size();
         c.rec->push_back(q);
         c.units = std::max<int64_t>(c.units, (q.n + 7) / 8);   // a block per warp
         c.launches++;

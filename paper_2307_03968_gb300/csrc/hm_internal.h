@@ -112,7 +112,14 @@ struct LevelList {
     int64_t n_xch = 0;
     int64_t n_dense = 0, n_lowrank = 0;
     int64_t elems = 0;            // stored complex elements
+    // the FP32 product's own copies of the item list and of its big part, with every dense
+    // block of more than PROD_PANEL rows cut into row panels (the product kernel gives each
+    // item to one warp: a leaf of ~1,000 unknowns would otherwise leave the GPU idle); null
+    // when no block needs it (the lists above serve)
+    Item *d_prod = nullptr, *d_prod_big = nullptr;
+    int64_t n_prod = 0, n_prod_big = 0;
 };
+constexpr int PROD_PANEL = 64;
 
 // One phase of the one-launch solve (k_persist.cu): every kernel the solve would
 // launch becomes a phase of one cooperative kernel, with a grid-wide barrier

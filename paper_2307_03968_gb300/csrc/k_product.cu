@@ -69,20 +69,21 @@ void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z,
         k_apply_items<double, double, 1><<<g, APPLY_WARPS * 32, 0, s>>>(
             L.d_items, n, h->d_pool64, (const double2 *)x, h->pN, (double2 *)z, h->pN, nrhs);
     } else {
-        const Item *list = L.d_items;
-        int64_t cnt = n;
+        // tall dense blocks go as row panels (LevelList::d_prod), one warp each
+        const Item *list = L.d_prod ? L.d_prod : L.d_items;
+        int64_t cnt = L.d_prod ? L.n_prod : n;
         if (rb < 0) rb = nrhs < MRHS_MIN_RHS ? 0 : nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : 32;
         if (rb == RB_TC && nrhs > 1) {
             // the small blocks (dense and low-rank) on the tensor cores
             launch_apply_tc(h, L, (const float2 *)x, (float2 *)z, nrhs, s);
-            list = L.d_big;
-            cnt = L.n_big;
+            list = L.d_prod ? L.d_prod_big : L.d_big;
+            cnt = L.d_prod ? L.n_prod_big : L.n_big;
             if (cnt == 0) return;
         } else if (rb > 0 && nrhs > 1 && L.n_small > 0) {
             // many right-hand sides: blocks that fit shared memory are read once per RHS chunk
             launch_apply_items_mrhs(h, L, (const float2 *)x, (float2 *)z, nrhs, rb, s);
-            list = L.d_big;
-            cnt = L.n_big;
+            list = L.d_prod ? L.d_prod_big : L.d_big;
+            cnt = L.d_prod ? L.n_prod_big : L.n_big;
             if (cnt == 0) return;
         }
         int g = apply_grid<float, float, 3>(h);
