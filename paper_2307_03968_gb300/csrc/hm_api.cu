@@ -983,11 +983,21 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
             residual64(cc, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
             if (o->nested) P(cc, cc.m, rt, dx);
             else Pflat(cc, rt, dx);
+            if (!cc.rec && !info) {   // add, check and un-permute in one kernel
+                launch_finish((const float2 *)xt, (const float2 *)dx, h->pN, (float2 *)x, ldx, h->d_pperm, nrhs,
+                              h->d_status, cc.s);
+                cc.launches++;
+                return;
+            }
             add_vec(cc, xt, dx);
             if (info) {   // residual of the refined solution
                 zero_vec(cc, norms, 2 * sizeof(double) * nrhs);
                 residual64(cc, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
             }
+        } else if (!cc.rec && !cc.fp64) {
+            launch_finish((const float2 *)xt, nullptr, h->pN, (float2 *)x, ldx, h->d_pperm, nrhs, h->d_status, cc.s);
+            cc.launches++;
+            return;
         }
         check_vec(cc, xt);
         permute_out_vec(cc, xt, x, ldx);

@@ -348,6 +348,9 @@ void launch_leaf_update(hm_matrix h, const void *y, void *zin, void *out, int nr
 void launch_sub(const void *y, const void *w, void *out, int64_t n, bool fp64, cudaStream_t s);
 void launch_add_inplace(void *x, const void *dx, int64_t n, bool fp64, cudaStream_t s);
 void launch_check_finite(const void *x, int64_t n, bool fp64, int *status, cudaStream_t s);
+// complex64: v = xt (+ dx if given), non-finite -> HM_ERR_DIVERGED, x[r * ldx + pperm[p]] = v
+void launch_finish(const float2 *xt, const float2 *dx, int64_t pN, float2 *x, int64_t ldx, const int32_t *pperm,
+                   int nrhs, int *status, cudaStream_t s);
 void launch_convert_f64_to_f32(const double2 *a, float2 *b, int64_t n, cudaStream_t s);
 void launch_convert_f32_to_f64(const float2 *a, double2 *b, int64_t n, cudaStream_t s);
 

@@ -117,6 +117,24 @@ __global__ void k_check_finite(const C *x, int64_t n, int *status)
     }
 }
 
+// the end of a complex64 solve in one pass: v = xt (+ dx), non-finite v -> HM_ERR_DIVERGED,
+// x[r * ldx + pperm[p]] = v (the refinement's add, the check and the un-permutation)
+__global__ void k_finish(const float2 *__restrict__ xt, const float2 *__restrict__ dx, int64_t pN, float2 *__restrict__ x,
+                         int64_t ldx, const int32_t *__restrict__ pperm, int nrhs, int *status)
+{
+    const int64_t total = pN * nrhs;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = xt[t];
+        if (dx) v = cadd(v, dx[t]);
+        bad |= !isfinite(v.x) || !isfinite(v.y);
+        const int64_t r = t / pN, p = t - r * pN;
+        const int32_t dst = pperm[p];
+        if (dst >= 0) x[r * ldx + dst] = v;
+    }
+    if (bad) atomicCAS(status, 0, (int)HM_ERR_DIVERGED);
+}
+
 __global__ void k_f32_to_f64(const float2 *a, double2 *b, int64_t n)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -209,6 +227,12 @@ void launch_check_finite(const void *x, int64_t n, bool fp64, int *status, cudaS
     const int g = grid_for(n);
     if (fp64) k_check_finite<double2><<<g, 256, 0, s>>>((const double2 *)x, n, status);
     else k_check_finite<float2><<<g, 256, 0, s>>>((const float2 *)x, n, status);
+}
+
+void launch_finish(const float2 *xt, const float2 *dx, int64_t pN, float2 *x, int64_t ldx, const int32_t *pperm,
+                   int nrhs, int *status, cudaStream_t s)
+{
+    k_finish<<<grid_for(pN * nrhs), 256, 0, s>>>(xt, dx, pN, x, ldx, pperm, nrhs, status);
 }
 
 void launch_convert_f32_to_f64(const float2 *a, double2 *b, int64_t n, cudaStream_t s)
