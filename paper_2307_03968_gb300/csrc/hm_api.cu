@@ -170,6 +170,8 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         L.n_rcu = (int64_t)rcu.size();
         if ((st = upload(h, &L.d_rcu, rcu, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_rcp, rcp, s)) != HM_OK) return st;
+        if ((st = dev_alloc(h, (void **)&L.d_rcb, sizeof(float2) * rcp.size())) != HM_OK) return st;
+        launch_prod_bounds(L.d_rcp, (int64_t)rcp.size(), h->d_pool32, L.d_rcb, s);
         L.n_tcu = (int64_t)tcu.size();
         L.n_tcp = (int64_t)tcp.size();
         L.n_xch = (int64_t)xch.size();
@@ -178,6 +180,11 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         if ((st = upload(h, &L.d_items, L.items, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_small, small, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_big, big, s)) != HM_OK) return st;
+        if ((st = dev_alloc(h, (void **)&L.d_bnd, sizeof(float4) * L.items.size())) != HM_OK) return st;
+        if ((st = dev_alloc(h, (void **)&L.d_bnd_big, sizeof(float4) * big.size())) != HM_OK) return st;
+        launch_item_bounds(L.d_items, (int64_t)L.items.size(), h->d_pool32, L.d_bnd, s);
+        launch_item_bounds(L.d_big, L.n_big, h->d_pool32, L.d_bnd_big, s);
+        HM_CUDA(cudaGetLastError());
         if ((st = upload(h, &L.d_tcu, tcu, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_tcp, tcp, s)) != HM_OK) return st;
         // the product's lists with tall dense blocks cut into row panels: a panel of rows
@@ -240,11 +247,14 @@ static void free_handle(hm_matrix h)
         if (kv.second.d_prod_big) cudaFree(kv.second.d_prod_big);
         if (kv.second.d_small) cudaFree(kv.second.d_small);
         if (kv.second.d_big) cudaFree(kv.second.d_big);
+        if (kv.second.d_bnd) cudaFree(kv.second.d_bnd);
+        if (kv.second.d_bnd_big) cudaFree(kv.second.d_bnd_big);
         if (kv.second.d_tcu) cudaFree(kv.second.d_tcu);
         if (kv.second.d_tcp) cudaFree(kv.second.d_tcp);
         if (kv.second.d_xch) cudaFree(kv.second.d_xch);
         if (kv.second.d_rcu) cudaFree(kv.second.d_rcu);
         if (kv.second.d_rcp) cudaFree(kv.second.d_rcp);
+        if (kv.second.d_rcb) cudaFree(kv.second.d_rcb);
     }
     for (void *p : h->ws.vec32) if (p) cudaFree(p);
     for (void *p : h->ws.vec64) if (p) cudaFree(p);
@@ -728,6 +738,7 @@ static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *
                 q.a = x; q.c = h->ws.d_part;
                 q.ld = h->partial_elems;
                 q.items = it->second.d_items;
+                q.d = it->second.d_bnd;
                 q.n = (int64_t)it->second.items.size();
                 c.rec->push_back(q);
                 c.units = std::max<int64_t>(c.units, (q.n + 7) / 8);   // a block per warp

@@ -95,6 +95,9 @@ struct LevelList {
     // in shared memory, and the rest
     Item *d_small = nullptr, *d_big = nullptr;
     int64_t n_small = 0, n_big = 0;
+    // per item of d_items / d_big: the block bounds of the common-grid residual
+    // products (k_item_bounds: largest row and column 1-norms of the stored factors)
+    float4 *d_bnd = nullptr, *d_bnd_big = nullptr;
     int small_dim = 0, small_rank = 0;   // largest (even) side and rank among the small items
     // the small items as directed products grouped into work units by output
     // cluster, for the tensor-core product (both mirrored halves of every block)
@@ -106,6 +109,7 @@ struct LevelList {
     TcProd *d_rcp = nullptr;
     TcUnit *d_rcu = nullptr;
     int64_t n_rcu = 0;
+    float2 *d_rcb = nullptr;      // per product of d_rcp: its common-grid bounds (k_prod_bounds)
     // the input clusters' K chunks of 8 unknowns (padded-tree offset, valid length):
     // the tensor-core product splits x once per launch into these chunks
     int2 *d_xch = nullptr;
@@ -129,7 +133,7 @@ enum PhaseOp : int32_t {
     PH_PERMUTE_OUT,      // c[r * ld2 + pperm[p]] = a[r][p]
     PH_LEAF,             // per leaf: c = (a ? a - Dinv b : Dinv b); b = 0 if m
     PH_APPLY,            // c += M a over items[0, n) (one RHS at a time per block)
-    PH_RESID,            // FP64-class products of items[0, n) into the partial slots c (stride ld)
+    PH_RESID,            // FP64-class products of items[0, n) (block bounds d) into the partial slots c (stride ld)
     PH_GATHER,           // c = (b ? b - acc : acc), acc = D a + slots d of m levels; norms
     PH_ZERO,             // n bytes at c
     PH_COPY,             // n bytes a -> c
@@ -334,6 +338,8 @@ void launch_zero(void *p, size_t bytes, cudaStream_t s);
 void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
                         cudaStream_t s, int rb = -1);
 // FP64-class (Dot2) products of every block of a level into its partial slots (no atomics)
+// the residual products' block bounds of items[0 .. n) (k_residual.cu)
+void launch_item_bounds(const Item *items, int64_t n, const float2 *pool, float4 *bnd, cudaStream_t s);
 void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part, int64_t pstride,
                                  int nrhs, cudaStream_t s, int rb = -1);
 // per leaf: acc = D x + sum of the leaf's partial slots of levels 1..m (double-float, fixed order);
@@ -390,6 +396,8 @@ void launch_apply_list_mrhs(hm_matrix h, const LevelList &L, const Item *items, 
 // owner-computes FP64-class products of a level's small items into own ([RHS][pN]) and the gather
 // out = b - (D x + sum of the m levels' owner sums) (k_resid_own.cu)
 void launch_resid_own(hm_matrix h, const LevelList &L, const float2 *x, double2 *own, int nrhs, cudaStream_t s);
+// the owner-computes products' common-grid bounds of prods[0 .. n) (k_resid_own.cu)
+void launch_prod_bounds(const TcProd *prods, int64_t n, const float2 *pool, float2 *out, cudaStream_t s);
 void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, int64_t lstride, const float2 *b,
                        float2 *out, double *norms, int nrhs, cudaStream_t s);
 // level-operator norm estimate (k_norm.cu): start vector (zero pads), |v|^2 into one device double

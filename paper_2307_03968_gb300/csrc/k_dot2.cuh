@@ -159,6 +159,75 @@ __device__ __forceinline__ cdf cxclose(const cxacc &c, float sigma)
 {
     return {{__fsub_rn(c.re.tau, sigma), c.re.r}, {__fsub_rn(c.im.tau, sigma), c.im.r}};
 }
+// ---------------------------------------------------------------------------
+// Chains on a common grid.  When every chain that feeds one output sum takes the
+// same sigma, and sigma bounds the whole output sum (all its terms, whichever
+// lane or chain holds them), the chains' grid parts tau - sigma are multiples of
+// 2^-24 sigma and so is every partial sum of them, of magnitude at most sigma / 2:
+// the grid parts of the lanes then add EXACTLY in plain FP32, and only the
+// remainders r are rounded.  sigma comes from a bound of the block (its largest
+// row or column 1-norm, precomputed per block in FP64 and rounded up) times the
+// largest input component.  A chain of L real steps drifts from the exact grid
+// sum by at most L 2^-24 sigma, so the margin 2 + 2^-10 keeps tau within
+// [1/2, 3/2] sigma for output sums of up to 2^12 real steps per part (2,048
+// complex products).  The error of a sum is then a few units of 2^-48 sigma per
+// chain step, sigma being at most 4.01 times the bound of the sum.
+constexpr float GRID_MARGIN = 2.0f + 0x1p-10f;
+__device__ __forceinline__ float grid_sigma(float bound, float mb) { return pow2_ceil(GRID_MARGIN * bound * mb); }
+__device__ __forceinline__ void cx_start(cxacc &c, float sigma) { c = {{sigma, 0.f}, {sigma, 0.f}}; }
+// c += a * b for an FP32 or a double-float b
+__device__ __forceinline__ void cxstep_in(cxacc &c, float2 a, float2 b) { cxstep(c, a, b); }
+__device__ __forceinline__ void cxstep_in(cxacc &c, float2 a, const cdf &b) { cxstep_df(c, a, b); }
+// one step of a transposing warp reduction: of the pair (v[j], v[j + H]) this lane
+// keeps the upper one when its lane bit `mask` is set, and adds the partner lane's
+// copy of it; after the steps for masks M, M/2, ..., 1 over V values, each lane
+// holds V / (2M) sums over the 2M lanes, the value index bits above taken from the
+// lane bits (exact for the grid parts of a common grid)
+template <int H>
+__device__ __forceinline__ void xreduce_step(float *v, int lane, int mask)
+{
+    const bool up = (lane & mask) != 0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const float send = up ? v[j] : v[j + H];
+        const float keep = up ? v[j + H] : v[j];
+        v[j] = __fadd_rn(keep, __shfl_xor_sync(FULL, send, mask));
+    }
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, s));
+    return v;
+}
+
+// 1-norm bounds of a row-major rows x cols array (row stride ld): the largest row
+// sum and the largest column sum of |re| + |im|, in FP64 (warp-wide results)
+__device__ __forceinline__ void l1_bounds(const float2 *__restrict__ A, int rows, int cols, int ld, double &rmax, double &cmax,
+                          int lane)
+{
+    rmax = 0.0;
+    for (int i = 0; i < rows; ++i) {
+        double v = 0.0;
+        for (int j = lane; j < cols; j += 32) {
+            const float2 a = A[(int64_t)i * ld + j];
+            v += (double)fabsf(a.x) + (double)fabsf(a.y);
+        }
+        for (int s = 16; s >= 1; s >>= 1) v += __shfl_xor_sync(FULL, v, s);
+        rmax = fmax(rmax, v);
+    }
+    cmax = 0.0;
+    for (int j = lane; j < cols; j += 32) {
+        double v = 0.0;
+        for (int i = 0; i < rows; ++i) {
+            const float2 a = A[(int64_t)i * ld + j];
+            v += (double)fabsf(a.x) + (double)fabsf(a.y);
+        }
+        cmax = fmax(cmax, v);
+    }
+    for (int s = 16; s >= 1; s >>= 1) cmax = fmax(cmax, __shfl_xor_sync(FULL, cmax, s));
+}
+
 __device__ __forceinline__ cdf cdf_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
 __device__ __forceinline__ cdf shfl_xor(const cdf &v, int s)
 {

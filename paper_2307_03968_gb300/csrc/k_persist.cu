@@ -125,15 +125,13 @@ __device__ bool run_phases(const Phase *phases, int n_phases, const PersistCtx &
             break;
         }
         case PH_RESID: {
-            float2 *xs = reinterpret_cast<float2 *>(sm) + 32 * w;
             const float2 *x = (const float2 *)P.a;
             cdf *part = (cdf *)P.c;
             for (int64_t t = (int64_t)blockIdx.x * PW + w; t < P.n; t += (int64_t)gridDim.x * PW) {
                 const Item it = P.items[t];
-                for (int r = 0; r < P.nrhs; ++r) {
-                    if (it.k == 0) dense_item_c(it, c.pool, x + r * c.pN, part + r * P.ld, xs, lane);
-                    else lowrank_item_c(it, c.pool, x + r * c.pN, part + r * P.ld, lane);
-                }
+                for (int r = 0; r < P.nrhs; ++r)
+                    resid_item(it, (const float4 *)P.d, t, c.pool, x + r * c.pN, part + r * P.ld,
+                               reinterpret_cast<float2 *>(sm) + GRID_MAX * w, lane);
             }
             break;
         }

@@ -7,10 +7,12 @@
 // units to balance).  The CTA walks every directed product into O (the stored blocks with O
 // as row cluster, and mirrored, those with O as column cluster; dense or
 // low-rank), in a fixed order, and keeps the sums in registers as double-float
-// complex numbers.  Products are summed in short error-free chains (biased
-// accumulator, k_dot2.cuh: every product rounded exactly onto a power-of-two
-// grid bounded by the chain's own terms, the remainders summed apart) and each
-// chain is folded into the double-float sum with a compensated addition.  Thread t owns output row t % 64 and right-hand sides
+// complex numbers.  Each directed product is summed, per output row and right-hand
+// side, as one error-free chain on a common grid (k_dot2.cuh: every product rounded
+// exactly onto a power-of-two grid whose sigma comes from the product's
+// precomputed bound, k_prod_bounds, and the input's largest component; the
+// remainders summed apart), folded once into the double-float sum with a
+// compensated addition.  Thread t owns output row t % 64 and right-hand sides
 // (RG/2) (t / 64) .. +RG/2-1.  The unit's sums are stored once, in FP64, into the level's
 // [RHS][pN] array: no partial slots, no atomics, and the result is independent
 // of scheduling.  k_gather_own then forms b - (D x + sum over levels) in FP64.
@@ -43,14 +45,13 @@ struct alignas(16) Smem {
     float2 b[SM_B];
     float2 x[SM_X];
     cdf t[SM_T];
-    float mx[16 * RGMAX];        // max |x|_inf over K indices 4c..4c+3, per right-hand side
-    float mt[8 * RGMAX];         // max |T.hi|_inf over rank rows 4c..4c+3, per right-hand side
+    float mx[2 * RGMAX];         // max |x|_inf over K indices 32h..32h+31 (h = 0, 1), per right-hand side
 };
 
 // stage x of the input cluster: xs[j * XS + q] = x[(r0 + q) * ldx + in0 + j] for j < klen, q < nr,
-// 0 for the rest of j < roundup4(klen); mx[c * RGMAX + q] = max over j = 4c..4c+3 of |x|_inf.
+// 0 for the rest of j < roundup4(klen); mx[2 q + h] = max over j = 32h..32h+31 of |x|_inf.
 // Every thread runs the same number of iterations (RG * 64 is a multiple of RT), and a warp
-// covers 32 consecutive j of one q, so aligned groups of four lanes hold one chunk.
+// covers 32 consecutive j of one q.
 template <int RG>
 __device__ __forceinline__ void stage_x(float2 *xs, float *mx, const float2 *__restrict__ x, int64_t ldx, int r0,
                                         int nr, int in0, int klen)
@@ -61,18 +62,18 @@ __device__ __forceinline__ void stage_x(float2 *xs, float *mx, const float2 *__r
         const int q = e >> 6, j = e & 63;
         const float2 v = (j < klen && q < nr) ? x[(int64_t)(r0 + q) * ldx + in0 + j] : make_float2(0.f, 0.f);
         if (j < k4) xs[j * XS + q] = v;
-        float m = linf(v);
-        m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
-        m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
-        if ((j & 3) == 0 && j < k4) mx[(j >> 2) * RGMAX + q] = m;
+        const float m = warp_max(linf(v));
+        if ((j & 31) == 0) mx[2 * q + (j >> 5)] = m;
     }
 }
+// the largest |x|_inf of right-hand side q over the staged input
+__device__ __forceinline__ float x_max(const float *mx, int q) { return fmaxf(mx[2 * q], mx[2 * q + 1]); }
 
 template <int RG>
 __global__ void __launch_bounds__(RT, 4)
 k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restrict__ prods,
-            const float2 *__restrict__ pool, const float2 *__restrict__ x, int64_t ldx, int nrhs,
-            double2 *__restrict__ own, int64_t ldo)
+            const float2 *__restrict__ pbnd, const float2 *__restrict__ pool, const float2 *__restrict__ x,
+            int64_t ldx, int nrhs, double2 *__restrict__ own, int64_t ldo)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     Smem &S = *reinterpret_cast<Smem *>(smraw);
@@ -104,38 +105,29 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
                 }
                 __syncthreads();
                 if (i < P.olen) {
-                    // one chain per right-hand side over four K indices (x is zero past klen)
-                    for (int j0 = 0; j0 < P.klen; j0 += 4) {
-                        float2 bv[4];
-                        float sb = 0.f;
+                    // one chain per right-hand side over all K indices, on the grid of the
+                    // product's largest output-row 1-norm times the input's largest component
+                    const float bo = pbnd[p].x;
+                    float sg[QN];
+                    cxacc c[QN];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            bv[u] = j0 + u < P.klen ? S.b[(j0 + u) * BS + i] : make_float2(0.f, 0.f);
-                            sb = __fadd_rn(sb, l1(bv[u]));
-                        }
-                        const float *mq = S.mx + (j0 >> 2) * RGMAX + QN * hh;
-                        float sg[QN];
-                        cxacc c[QN];
-#pragma unroll
-                        for (int q = 0; q < QN; ++q) sg[q] = chain_sigma(sb, mq[q]);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float4 *xv = reinterpret_cast<const float4 *>(S.x + (j0 + u) * XS + QN * hh);
-#pragma unroll
-                            for (int q = 0; q < QN / 2; ++q) {
-                                const float4 v = xv[q];
-                                if (u == 0) {
-                                    cxfirst(c[2 * q], sg[2 * q], bv[0], make_float2(v.x, v.y));
-                                    cxfirst(c[2 * q + 1], sg[2 * q + 1], bv[0], make_float2(v.z, v.w));
-                                } else {
-                                    cxstep(c[2 * q], bv[u], make_float2(v.x, v.y));
-                                    cxstep(c[2 * q + 1], bv[u], make_float2(v.z, v.w));
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int q = 0; q < QN; ++q) acc[q] = cdf_add(acc[q], cxclose(c[q], sg[q]));
+                    for (int q = 0; q < QN; ++q) {
+                        sg[q] = grid_sigma(bo, x_max(S.mx, QN * hh + q));
+                        cx_start(c[q], sg[q]);
                     }
+#pragma unroll 4
+                    for (int j = 0; j < P.klen; ++j) {
+                        const float2 bv = S.b[j * BS + i];
+                        const float4 *xv = reinterpret_cast<const float4 *>(S.x + j * XS + QN * hh);
+#pragma unroll
+                        for (int q = 0; q < QN / 2; ++q) {
+                            const float4 v = xv[q];
+                            cxstep(c[2 * q], bv, make_float2(v.x, v.y));
+                            cxstep(c[2 * q + 1], bv, make_float2(v.z, v.w));
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < QN; ++q) acc[q] = cdf_add(acc[q], cxclose(c[q], sg[q]));
                 }
             } else {
                 // W (rank rows l, K j) into b[j * WS + l]; Y (element (i, l) = Y[l][i]) into y[l * BS + i]
@@ -149,72 +141,46 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
                 __syncthreads();
                 // stage 1: T[l][q] = sum_j W[l][j] x[j][q]; a round covers 128 / RG rank rows;
                 // thread (row l0 + tid / (8 RG), q = (tid / 8) % RG, K slice ks = tid % 8: j = ks,
-                // ks + 8, ...), the eight slices combined by compensated additions across lanes
+                // ks + 8, ...); the eight slices' chains share the grid of W's largest rank-row
+                // 1-norm times x's largest component, so their grid parts add exactly across lanes
+                const float2 bb = pbnd[p];
                 {
                     constexpr int LR = RT / (8 * RG);              // rank rows per round
                     const int ks = tid & 7, q = (tid >> 3) % RG, lr = tid / (8 * RG);
+                    const float s1 = grid_sigma(bb.x, x_max(S.mx, q));
                     for (int l0 = 0; l0 < P.rank; l0 += LR) {
                         const int l = l0 + lr;
-                        cdf t = cdf_zero();
-                        if (l < P.rank && ks < P.klen) {
-                            // one chain over the slice's K indices, bounded by its own terms
-                            float sw = 0.f, mxq = 0.f;
-                            for (int j = ks; j < P.klen; j += 8) {
-                                sw = __fadd_rn(sw, l1(Wsm[j * WS + l]));
-                                mxq = fmaxf(mxq, linf(S.x[j * XS + q]));
-                            }
-                            const float sg = chain_sigma(sw, mxq);
-                            cxacc c;
-                            cxfirst(c, sg, Wsm[ks * WS + l], S.x[ks * XS + q]);
-                            for (int j = ks + 8; j < P.klen; j += 8) cxstep(c, Wsm[j * WS + l], S.x[j * XS + q]);
-                            t = cxclose(c, sg);
-                        }
+                        cxacc c;
+                        cx_start(c, s1);
+                        if (l < P.rank)
+                            for (int j = ks; j < P.klen; j += 8) cxstep(c, Wsm[j * WS + l], S.x[j * XS + q]);
+                        float v[4] = {__fsub_rn(c.re.tau, s1), c.re.r, __fsub_rn(c.im.tau, s1), c.im.r};
 #pragma unroll
-                        for (int sh = 1; sh < 8; sh <<= 1) t = cdf_add(t, shfl_xor(t, sh));
-                        if (ks == 0 && l < P.rank) S.t[l * RG + q] = t;
+                        for (int sh = 1; sh < 8; sh <<= 1)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) v[e] = __fadd_rn(v[e], __shfl_xor_sync(FULL, v[e], sh));
+                        if (ks == 0 && l < P.rank) S.t[l * RG + q] = {{v[0], v[1]}, {v[2], v[3]}};
                     }
                 }
-                // T rows rank..roundup4(rank)-1 are zero; then the chunk maxima of |T.hi|
-                const int r4 = (P.rank + 3) & ~3;
-                for (int e = tid; e < (r4 - P.rank) * RG; e += RT) S.t[(P.rank + e / RG) * RG + e % RG] = cdf_zero();
                 __syncthreads();
-                if (tid < (r4 >> 2) * RG) {
-                    const int c = tid / RG, q = tid % RG;
-                    float m = 0.f;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const cdf tv = S.t[(4 * c + u) * RG + q];
-                        m = fmaxf(m, fmaxf(fabsf(tv.re.hi), fabsf(tv.im.hi)));
-                    }
-                    S.mt[c * RGMAX + q] = m;
-                }
-                __syncthreads();
-                // stage 2: out[i][q] += sum_l Y[i][l] T[l][q]
+                // stage 2: out[i][q] += sum_l Y[i][l] T[l][q], one chain per right-hand side over
+                // all rank rows: the leading part of T[l][q] is a grid sum, at most half of
+                // stage 1's sigma, which bounds the inputs with Y's largest output-row 1-norm
                 if (i < P.olen) {
-                    // one chain per right-hand side over four rank rows (T is zero past rank)
-                    for (int l0 = 0; l0 < P.rank; l0 += 4) {
-                        float2 yv[4];
-                        float sy = 0.f;
+                    float sg[QN];
+                    cxacc c[QN];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            yv[u] = l0 + u < P.rank ? Ysm[(l0 + u) * BS + i] : make_float2(0.f, 0.f);
-                            sy = __fadd_rn(sy, l1(yv[u]));
-                        }
-                        const float *mq = S.mt + (l0 >> 2) * RGMAX + QN * hh;
-                        float sg[QN];
-                        cxacc c[QN];
-#pragma unroll
-                        for (int q = 0; q < QN; ++q) {
-                            sg[q] = chain_sigma(sy, mq[q]);
-                            cxfirst_df(c[q], sg[q], yv[0], S.t[l0 * RG + QN * hh + q]);
-                        }
-#pragma unroll
-                        for (int u = 1; u < 4; ++u)
-#pragma unroll
-                            for (int q = 0; q < QN; ++q) cxstep_df(c[q], yv[u], S.t[(l0 + u) * RG + QN * hh + q]);
-#pragma unroll
-                        for (int q = 0; q < QN; ++q) acc[q] = cdf_add(acc[q], cxclose(c[q], sg[q]));
+                    for (int q = 0; q < QN; ++q) {
+                        sg[q] = grid_sigma(bb.y, 0.5f * grid_sigma(bb.x, x_max(S.mx, QN * hh + q)));
+                        cx_start(c[q], sg[q]);
                     }
+                    for (int l = 0; l < P.rank; ++l) {
+                        const float2 yv = Ysm[l * BS + i];
+#pragma unroll
+                        for (int q = 0; q < QN; ++q) cxstep_df(c[q], yv, S.t[l * RG + QN * hh + q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < QN; ++q) acc[q] = cdf_add(acc[q], cxclose(c[q], sg[q]));
                 }
             }
         }
@@ -275,7 +241,38 @@ k_gather_own(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ 
     }
 }
 
+// Per directed product, the bounds its common grids take (k_resid_own): x = the
+// largest 1-norm of an output row of the oriented block (dense) or of a rank row of
+// the input-side factor W (low-rank, stage 1); y = the largest 1-norm, over the rank
+// rows, of an output row of Y (low-rank, stage 2).  FP64 sums rounded up; one warp
+// per product.
+__global__ void __launch_bounds__(256)
+k_prod_bounds(const TcProd *__restrict__ prods, int64_t n, const float2 *__restrict__ pool, float2 *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < n; t += nw) {
+        const TcProd P = prods[t];
+        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+        if (P.rank == 0) {
+            if (P.trans) l1_bounds(pool + P.b_off, P.klen, P.olen, P.b_ld, c, a, lane);   // output i = column i
+            else l1_bounds(pool + P.b_off, P.olen, P.klen, P.b_ld, a, c, lane);
+        } else {
+            l1_bounds(pool + P.b_off, P.rank, P.klen, P.b_ld, a, c, lane);
+            l1_bounds(pool + P.y_off, P.rank, P.olen, P.y_ld, d, b, lane);
+        }
+        if (lane == 0) out[t] = make_float2(__double2float_ru(a), __double2float_ru(b));
+    }
+}
+
 } // namespace
+
+void launch_prod_bounds(const TcProd *prods, int64_t n, const float2 *pool, float2 *out, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int g = (int)std::min<int64_t>((n + 7) / 8, 152 * 16);
+    k_prod_bounds<<<g, 256, 0, s>>>(prods, n, pool, out);
+}
 
 // owner-computes FP64-class products of a level's small items: own[r * pN + i] = (M_level x_r)_i
 // for the level's output rows (a level whose items are all small; the rest of own is untouched)
@@ -298,11 +295,11 @@ void launch_resid_own(hm_matrix h, const LevelList &L, const float2 *x, double2 
     int64_t g = 4 * (int64_t)(h->num_sms > 0 ? h->num_sms : 1);
     if (g > units) g = units;
     if (rg == 8)
-        k_resid_own<8><<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, h->d_pool32, x, h->pN, nrhs, own,
-                                                     h->pN);
+        k_resid_own<8><<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, L.d_rcb, h->d_pool32, x, h->pN,
+                                                     nrhs, own, h->pN);
     else
-        k_resid_own<16><<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, h->d_pool32, x, h->pN, nrhs, own,
-                                                      h->pN);
+        k_resid_own<16><<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, L.d_rcb, h->d_pool32, x, h->pN,
+                                                      nrhs, own, h->pN);
 }
 
 void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, int64_t lstride, const float2 *b,

@@ -99,92 +99,241 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
     }
 }
 
-// Low-rank block U V: slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I);
-// the rank-k intermediates stay in double-float.  Blocks of up to 64 x 64 use the
-// short biased chains, larger ones Dot2.
+// ---------------------------------------------------------------------------
+// Blocks of up to 64 x 64 (and rank <= 64) on common grids: every output sum of a
+// block side takes one sigma from the block's precomputed bound (k_item_bounds:
+// largest row / column 1-norm) and the largest input component, so the lanes'
+// grid parts add exactly in plain FP32 (k_dot2.cuh).  The warp covers the block
+// as 4 row groups x 8 column groups: lane (rg, cg) takes rows i = 4 s + rg and
+// the column pairs (16 t + 2 cg, +1), t = 0..3, so that each row is summed over 8
+// lanes and each column over 4 (instead of a 32-lane double-float reduction per
+// row), and every load of a row quarter is one 128-byte segment.
+constexpr int GRID_MAX = 64;
+
+// one row quarter of a dense block: the lane's column pairs of row i (zero past the block)
+__device__ __forceinline__ void grid_row_load(Pair<float> (&b)[4], const float2 *__restrict__ A, int i, int rows,
+                                              int cols, int ld, int cg)
+{
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        b[t] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (i < rows && 16 * t + 2 * cg < cols) b[t] = ld_stream(A + (int64_t)i * ld + 16 * t + 2 * cg);
+    }
+}
+
+// One row of the dense common-grid pass: the row's sum over the lane's 8 columns
+// (one chain), reduced over the row group's 8 lanes and written to rdst[i] (i < rlim),
+// and the row's terms added to the lane's 8 column chains.
+__device__ __forceinline__ void grid_row(const Pair<float> (&b)[4], int i, int rows, const float2 (&u)[4][2],
+                                         float sR, cdf *rdst, int rlim, const float2 *v, cxacc (&acc)[4][2], int lane)
+{
+    const int cg = lane & 7;
+    cxacc c;
+    cx_start(c, sR);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        cxstep(c, b[t].a, u[t][0]);
+        cxstep(c, b[t].b, u[t][1]);
+    }
+    if (i < rows) {
+        const float2 vi = v[i];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            cxstep(acc[t][0], b[t].a, vi);
+            cxstep(acc[t][1], b[t].b, vi);
+        }
+    }
+    float rv[4] = {__fsub_rn(c.re.tau, sR), c.re.r, __fsub_rn(c.im.tau, sR), c.im.r};
+    // value index bit 1 (re / im) by cg bit 2, bit 0 (grid part / remainder) by cg bit 1,
+    // then the pair of lanes cg, cg ^ 1 adds its two partial sums
+    xreduce_step<2>(rv, lane, 4);
+    xreduce_step<1>(rv, lane, 2);
+    rv[0] = __fadd_rn(rv[0], __shfl_xor_sync(FULL, rv[0], 1));
+    if ((cg & 1) == 0 && i < rlim) reinterpret_cast<float *>(rdst + i)[2 * ((cg >> 2) & 1) + ((cg >> 1) & 1)] = rv[0];
+}
+
+// Dense block of at most 64 x 64 on common grids, one pass: rsum_i = sum_j A_ij u_j
+// (grid sR, to rdst[i] for i < rlim) and csum_j = sum_i A_ij v_i (grid sC, to
+// cdst[j], cdst[j + 1] for even j < cols).  A row-major, rows x cols, row stride ld;
+// each row is loaded one row ahead of its arithmetic.
+__device__ __forceinline__ void grid_pass(const float2 *__restrict__ A, int rows, int cols, int ld,
+                                          const float2 (&u)[4][2], float sR, cdf *rdst, int rlim, const float2 *v,
+                                          float sC, cdf *cdst, int lane)
+{
+    const int cg = lane & 7, rg = lane >> 3;
+    cxacc acc[4][2];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) { cx_start(acc[t][0], sC); cx_start(acc[t][1], sC); }
+    const int ns = (rows + 3) >> 2;
+    Pair<float> b0[4], b1[4];
+    grid_row_load(b0, A, rg, rows, cols, ld, cg);
+#pragma unroll 1
+    for (int s = 0; s < ns; s += 2) {
+        const int i = 4 * s + rg;
+        grid_row_load(b1, A, i + 4, rows, cols, ld, cg);
+        grid_row(b0, i, rows, u, sR, rdst, rlim, v, acc, lane);
+        if (s + 1 < ns) {
+            grid_row_load(b0, A, i + 8, rows, cols, ld, cg);
+            grid_row(b1, i + 4, rows, u, sR, rdst, rlim, v, acc, lane);
+        }
+    }
+    float w[32];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            w[8 * t + 4 * e] = __fsub_rn(acc[t][e].re.tau, sC);
+            w[8 * t + 4 * e + 1] = acc[t][e].re.r;
+            w[8 * t + 4 * e + 2] = __fsub_rn(acc[t][e].im.tau, sC);
+            w[8 * t + 4 * e + 3] = acc[t][e].im.r;
+        }
+    // over the column group's 4 lanes: index bit 4 (t bit 1) by rg bit 1, bit 3 (t bit 0)
+    // by rg bit 0, so lane (rg, cg) ends with its pair of t = rg
+    xreduce_step<16>(w, lane, 16);
+    xreduce_step<8>(w, lane, 8);
+    const int j = 16 * rg + 2 * cg;
+    if (j < cols) {
+        cdst[j] = {{w[0], w[1]}, {w[2], w[3]}};
+        cdst[j + 1] = {{w[4], w[5]}, {w[6], w[7]}};
+    }
+}
+
+// the lane's column-pair inputs x[16 t + 2 cg], x[... + 1] (pairs at j < len) and the
+// largest input component over the warp
+__device__ __forceinline__ float grid_inputs(const float2 *HM_XR x, int len, float2 (&u)[4][2], int lane)
+{
+    const int cg = lane & 7;
+    float mx = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int j = 16 * t + 2 * cg;
+        u[t][0] = u[t][1] = make_float2(0.f, 0.f);
+        if (j < len) {
+            u[t][0] = x[j];
+            if (j + 1 < len) u[t][1] = x[j + 1];
+        }
+        mx = fmaxf(mx, fmaxf(linf(u[t][0]), linf(u[t][1])));
+    }
+    return warp_max(mx);
+}
+
+// Dense block of at most 64 x 64: slot rows (even(m)) = B x_J, slot columns
+// (even(n)) = B^T x_I.  bnd.x / bnd.y: largest row / column 1-norm of B.
+__device__ __forceinline__ void dense_item_g(const Item &it, float4 bnd, const float2 *__restrict__ pool,
+                                             const float2 *HM_XR x, cdf *HM_XR part, float2 *xs, int lane)
+{
+    const int m = it.m, n = it.n;
+    float2 u[4][2];
+    const float mxj = grid_inputs(x + it.col0, n, u, lane);
+    __syncwarp();
+    const float2 xa = 2 * lane < m ? x[it.row0 + 2 * lane] : make_float2(0.f, 0.f);
+    const float2 xb = 2 * lane + 1 < m ? x[it.row0 + 2 * lane + 1] : make_float2(0.f, 0.f);
+    xs[2 * lane] = xa;
+    xs[2 * lane + 1] = xb;
+    const float mxi = warp_max(fmaxf(linf(xa), linf(xb)));
+    __syncwarp();
+    grid_pass(pool + it.off, m, n, even_d(n), u, grid_sigma(bnd.x, mxj), part + it.pad, even_d(m), xs,
+              grid_sigma(bnd.y, mxi), part + it.pad + even_d(m), lane);
+}
+
+// Low-rank block U V of at most 64 x 64 (U^T k x m, V k x n, m, n padded even):
+// slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I), one pass over chunks
+// of 4 rank rows.  A lane owns the rows / columns 2 lane, 2 lane + 1 of both panels.
+// Both stages run on common grids.  Stage 1 (the rank-k intermediates tp = U^T x_I,
+// t = V x_J; bnd.x, bnd.y: largest rank-row 1-norms of U^T and V): the 32-lane
+// reductions add the grid parts exactly in plain FP32.  Stage 2 (the outputs; bnd.z,
+// bnd.w: largest column 1-norms of U^T and V): the leading part of each intermediate
+// is a grid sum, at most half its grid's sigma, which bounds the inputs, so each
+// output is one chain over all rank rows, closed once.
+__device__ __forceinline__ void lowrank_item_g(const Item &it, float4 bnd, const float2 *__restrict__ pool,
+                                               const float2 *HM_XR x, cdf *HM_XR part, int lane)
+{
+    const int m = it.m, n = it.n, k = it.k;
+    const float2 *UT = pool + it.off;
+    const float2 *V = UT + (int64_t)k * m;
+    const int i = 2 * lane;
+    const bool iv = i < m, jv = i < n;
+    Pair<float> xi{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, xj = xi;
+    if (iv) xi = ld_vec(x + it.row0 + i);
+    if (jv) xj = ld_vec(x + it.col0 + i);
+    const float s1u = grid_sigma(bnd.x, warp_max(fmaxf(linf(xi.a), linf(xi.b))));
+    const float s1v = grid_sigma(bnd.y, warp_max(fmaxf(linf(xj.a), linf(xj.b))));
+    const float s2i = grid_sigma(bnd.z, 0.5f * s1v), s2j = grid_sigma(bnd.w, 0.5f * s1u);
+    cxacc ci0, ci1, cj0, cj1;
+    cx_start(ci0, s2i);
+    cx_start(ci1, s2i);
+    cx_start(cj0, s2j);
+    cx_start(cj1, s2j);
+    for (int l0 = 0; l0 < k; l0 += 4) {
+        Pair<float> u[4], v[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            u[l] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            v[l] = u[l];
+            if (l0 + l < k) {
+                if (iv) u[l] = ld_stream(UT + (int64_t)(l0 + l) * m + i);
+                if (jv) v[l] = ld_stream(V + (int64_t)(l0 + l) * n + i);
+            }
+        }
+        // stage 1: each lane's two terms of a rank row as one chain on the common grid;
+        // value index 4 l + (grid re, rem re, grid im, rem im)
+        float gu[16], gv[16];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            cxacc cu, cv;
+            cx_start(cu, s1u);
+            cxstep(cu, u[l].a, xi.a);
+            cxstep(cu, u[l].b, xi.b);
+            cx_start(cv, s1v);
+            cxstep(cv, v[l].a, xj.a);
+            cxstep(cv, v[l].b, xj.b);
+            gu[4 * l] = __fsub_rn(cu.re.tau, s1u);
+            gu[4 * l + 1] = cu.re.r;
+            gu[4 * l + 2] = __fsub_rn(cu.im.tau, s1u);
+            gu[4 * l + 3] = cu.im.r;
+            gv[4 * l] = __fsub_rn(cv.re.tau, s1v);
+            gv[4 * l + 1] = cv.re.r;
+            gv[4 * l + 2] = __fsub_rn(cv.im.tau, s1v);
+            gv[4 * l + 3] = cv.im.r;
+        }
+        // over the warp: index bits 3..0 by lane bits 4..1, then lanes 2 q, 2 q + 1 add
+        // their halves: lane L ends with value L / 2 summed over all lanes
+        xreduce_step<8>(gu, lane, 16);
+        xreduce_step<8>(gv, lane, 16);
+        xreduce_step<4>(gu, lane, 8);
+        xreduce_step<4>(gv, lane, 8);
+        xreduce_step<2>(gu, lane, 4);
+        xreduce_step<2>(gv, lane, 4);
+        xreduce_step<1>(gu, lane, 2);
+        xreduce_step<1>(gv, lane, 2);
+        gu[0] = __fadd_rn(gu[0], __shfl_xor_sync(FULL, gu[0], 1));
+        gv[0] = __fadd_rn(gv[0], __shfl_xor_sync(FULL, gv[0], 1));
+        // stage 2: the chunk's rank rows into the outputs' chains (rank rows past k
+        // have zero factors and zero intermediates)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const cdf tl = {{__shfl_sync(FULL, gv[0], 8 * l), __shfl_sync(FULL, gv[0], 8 * l + 2)},
+                            {__shfl_sync(FULL, gv[0], 8 * l + 4), __shfl_sync(FULL, gv[0], 8 * l + 6)}};
+            const cdf tpl = {{__shfl_sync(FULL, gu[0], 8 * l), __shfl_sync(FULL, gu[0], 8 * l + 2)},
+                             {__shfl_sync(FULL, gu[0], 8 * l + 4), __shfl_sync(FULL, gu[0], 8 * l + 6)}};
+            cxstep_df(ci0, u[l].a, tl);
+            cxstep_df(ci1, u[l].b, tl);
+            cxstep_df(cj0, v[l].a, tpl);
+            cxstep_df(cj1, v[l].b, tpl);
+        }
+    }
+    if (iv) { part[it.pad + i] = cxclose(ci0, s2i); part[it.pad + i + 1] = cxclose(ci1, s2i); }
+    if (jv) { part[it.pad + m + i] = cxclose(cj0, s2j); part[it.pad + m + i + 1] = cxclose(cj1, s2j); }
+}
+
+// Low-rank block U V larger than 64 x 64: slot rows (m) = U (V x_J), slot columns
+// (n) = V^T (U^T x_I), in Dot2; the rank-k intermediates stay in double-float.
 __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__restrict__ pool,
                                                const float2 *HM_XR x, cdf *HM_XR part, int lane)
 {
     const int m = it.m, n = it.n, k = it.k;
     const float2 *UT = pool + it.off;
     const float2 *V = UT + (int64_t)k * m;
-    if (m <= 64 && n <= 64) {
-        // registers hold a chunk of 4 rank rows of both panels; outputs stay in
-        // registers across chunks and are stored once
-        const int i = 2 * lane;
-        const bool iv = i < m, jv = i < n;
-        Pair<float> xi{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, xj = xi;
-        if (iv) xi = ld_vec(x + it.row0 + i);
-        if (jv) xj = ld_vec(x + it.col0 + i);
-        const float mxi = fmaxf(linf(xi.a), linf(xi.b)), mxj = fmaxf(linf(xj.a), linf(xj.b));
-        cdf oi0 = cdf_zero(), oi1 = cdf_zero(), oj0 = cdf_zero(), oj1 = cdf_zero();
-        for (int l0 = 0; l0 < k; l0 += 4) {
-            Pair<float> u[4], v[4];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                u[l] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                v[l] = u[l];
-                if (l0 + l < k) {
-                    if (iv) u[l] = ld_stream(UT + (int64_t)(l0 + l) * m + i);
-                    if (jv) v[l] = ld_stream(V + (int64_t)(l0 + l) * n + i);
-                }
-            }
-            // stage 1: the lane's two terms of every rank row as one short chain,
-            // then the lanes' double-float sums reduced (rank rows past k are zero)
-            cdf tp[4], t[4];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const float su = chain_sigma(__fadd_rn(l1(u[l].a), l1(u[l].b)), mxi);
-                const float sv = chain_sigma(__fadd_rn(l1(v[l].a), l1(v[l].b)), mxj);
-                cxacc cu, cv;
-                cxfirst(cu, su, u[l].a, xi.a);
-                cxstep(cu, u[l].b, xi.b);
-                cxfirst(cv, sv, v[l].a, xj.a);
-                cxstep(cv, v[l].b, xj.b);
-                tp[l] = cxclose(cu, su);
-                t[l] = cxclose(cv, sv);
-            }
-            reduce_cdf<4>(tp, lane);
-            reduce_cdf<4>(t, lane);
-            // stage 2: one chain over the chunk's rank rows per output, folded
-            cdf tl[4], tpl[4];
-            float mt = 0.f, mtp = 0.f, si0 = 0.f, si1 = 0.f, sj0 = 0.f, sj1 = 0.f;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                tl[l] = shfl_idx(t[0], l);
-                tpl[l] = shfl_idx(tp[0], l);
-                mt = fmaxf(mt, fmaxf(fabsf(tl[l].re.hi), fabsf(tl[l].im.hi)));
-                mtp = fmaxf(mtp, fmaxf(fabsf(tpl[l].re.hi), fabsf(tpl[l].im.hi)));
-                si0 = __fadd_rn(si0, l1(u[l].a));
-                si1 = __fadd_rn(si1, l1(u[l].b));
-                sj0 = __fadd_rn(sj0, l1(v[l].a));
-                sj1 = __fadd_rn(sj1, l1(v[l].b));
-            }
-            si0 = chain_sigma(si0, mt);
-            si1 = chain_sigma(si1, mt);
-            sj0 = chain_sigma(sj0, mtp);
-            sj1 = chain_sigma(sj1, mtp);
-            cxacc ci0, ci1, cj0, cj1;
-            cxfirst_df(ci0, si0, u[0].a, tl[0]);
-            cxfirst_df(ci1, si1, u[0].b, tl[0]);
-            cxfirst_df(cj0, sj0, v[0].a, tpl[0]);
-            cxfirst_df(cj1, sj1, v[0].b, tpl[0]);
-#pragma unroll
-            for (int l = 1; l < 4; ++l) {
-                cxstep_df(ci0, u[l].a, tl[l]);
-                cxstep_df(ci1, u[l].b, tl[l]);
-                cxstep_df(cj0, v[l].a, tpl[l]);
-                cxstep_df(cj1, v[l].b, tpl[l]);
-            }
-            oi0 = cdf_add(oi0, cxclose(ci0, si0));
-            oi1 = cdf_add(oi1, cxclose(ci1, si1));
-            oj0 = cdf_add(oj0, cxclose(cj0, sj0));
-            oj1 = cdf_add(oj1, cxclose(cj1, sj1));
-        }
-        if (iv) { part[it.pad + i] = oi0; part[it.pad + i + 1] = oi1; }
-        if (jv) { part[it.pad + m + i] = oj0; part[it.pad + m + i + 1] = oj1; }
-        return;
-    }
     for (int l0 = 0; l0 < k; l0 += 4) {
         cdf tp[4], t[4];
 #pragma unroll
@@ -248,6 +397,29 @@ __device__ __forceinline__ void lowrank_item_c(const Item &it, const float2 *__r
             if (l0 == 0) { q[0] = o0; q[1] = o1; }
             else { q[0] = cdf_add(q[0], o0); q[1] = cdf_add(q[1], o1); }
         }
+    }
+}
+
+// The residual products of one block (item t of a list with bounds bnd): on the
+// common grids where it fits (at most 64 x 64, rank <= 64), else the short-chain
+// and Dot2 bodies above.  xs: GRID_MAX float2 of the warp's shared memory.
+__device__ __forceinline__ void resid_item(const Item &it, const float4 *__restrict__ bnd, int64_t t,
+                                           const float2 *__restrict__ pool, const float2 *HM_XR x,
+                                           cdf *HM_XR part, float2 *xs, int lane)
+{
+    if (it.m <= GRID_MAX && it.n <= GRID_MAX) {
+        // the whole block into L2 first: the row (chunk) loads after the first then hit L2
+        const char *blk = reinterpret_cast<const char *>(pool + it.off);
+        const int64_t bytes = item_elems(it) * (int64_t)sizeof(float2);
+        for (int64_t o = (int64_t)lane * 128; o < bytes; o += 32 * 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + o));
+        const float4 bb = bnd[t];
+        if (it.k == 0) dense_item_g(it, bb, pool, x, part, xs, lane);
+        else lowrank_item_g(it, bb, pool, x, part, lane);
+    } else if (it.k == 0) {
+        dense_item_c(it, pool, x, part, xs, lane);
+    } else {
+        lowrank_item_c(it, pool, x, part, lane);
     }
 }
 

@@ -263,3 +263,149 @@ def test_pow2_ceil_matches_the_bit_trick():
     trick = ((bits.astype(np.uint64) + 0x007FFFFF) & 0xFF800000).astype(np.uint32).view(np.float32)
     for v, t in zip(vals, trick):
         assert F(float(t)) == pow2_ceil(F(float(v))), v
+
+
+# ---------------------------------------------------------------------------
+# Chains on a common grid (the residual kernels' blocks of up to 64 x 64): every
+# chain feeding one output sum takes sigma = pow2_ceil((2 + 2^-10) * bound * mb),
+# bound the block's largest row 1-norm (rounded up), mb the largest input
+# component; the lanes' grid parts tau - sigma are added in plain FP32 (the kernel
+# asserts nothing: the model checks every such addition is exact) and so are the
+# remainders.
+
+GRID_MARGIN = F(2) + F(2) ** -10
+
+
+def grid_sigma(bound, mb):
+    return pow2_ceil(f32(f32(GRID_MARGIN * bound) * mb))
+
+
+def grid_row(a, x, bound, lanes):
+    """sum_j a_j x_j for one row (complex64 a, x) split over `lanes` chains (lane l
+    takes the terms j with j % lanes == l), as the kernels run it; returns the sum
+    and checks the exactness claims."""
+    mb = max(max(abs(xr), abs(xi)) for xr, xi in x)
+    sigma = grid_sigma(bound, mb)
+    parts = []
+    for l in range(lanes):
+        re_t, im_t = [], []
+        for (ar, ai), (xr, xi) in list(zip(a, x))[l::lanes]:
+            re_t += [(ar, xr), (-ai, xi)]
+            im_t += [(ar, xi), (ai, xr)]
+        parts.append((real_chain(re_t, sigma), real_chain(im_t, sigma)))
+    out = []
+    for c in range(2):
+        g, r = F(0), F(0)
+        for p in parts:                       # lane order of the warp reduction
+            g2 = add(g, p[c][0])
+            assert g2 == g + p[c][0]              # grid parts add exactly
+            g = g2
+            r = add(r, p[c][1])
+        out.append(g + r)
+    return out
+
+
+def _bound_ru(rows):
+    """largest row 1-norm, rounded up to binary32 (the kernels' FP64 sum, rounded up)"""
+    v = max(sum(abs(ar) + abs(ai) for ar, ai in row) for row in rows)
+    w = f32(v)
+    while w < v:
+        w = f32(w + w * F(2) ** -24)
+    return w
+
+
+@pytest.mark.parametrize("spread", [0.0, 1.5])
+def test_common_grid_rows_exact_where_claimed_and_accurate(spread):
+    # a 16 x 64 block (one row group's share of a 64 x 64 block): each row over 8
+    # lanes of 8 columns, sigma from the whole block's bound
+    rng = np.random.default_rng(20 + int(spread))
+    rows = [_c64(rng, 64, spread) for _ in range(16)]
+    x = _c64(rng, 64, spread)
+    bound = _bound_ru(rows)
+    mb = max(max(abs(xr), abs(xi)) for xr, xi in x)
+    sigma = grid_sigma(bound, mb)
+    worst = 0.0
+    for a in rows:
+        re, im, mag = _exact(a, x)
+        got = grid_row(a, x, bound, 8)
+        worst = max(worst, float(max(abs(got[0] - re), abs(got[1] - im)) / sigma))
+    # a few units of 2^-48 sigma per chain step (16 real steps per lane chain)
+    assert worst < 64 * 2.0 ** -48
+
+
+def test_common_grid_keeps_fp64_class_accuracy_on_cancelling_rows():
+    # a row whose sum cancels to 1e-7 of its terms: FP32 summation keeps no digit,
+    # the common grid keeps the sum within 2^-40 of sigma (sigma ~ 2-4 x the bound)
+    rng = np.random.default_rng(7)
+    a = _c64(rng, 64, 0.0)
+    x = _c64(rng, 64, 0.0)
+    re, im, mag = _exact(a, x)
+    ar, ai = a[-1]
+    xr, xi = x[-1]
+    target = -(re - (ar * xr - ai * xi)) + F(float(np.float32(1e-7))) * mag
+    a[-1] = (f32((target + ai * xi) / xr), ai)
+    re, im, mag = _exact(a, x)
+    bound = _bound_ru([a])
+    mb = max(max(abs(v), abs(w)) for v, w in x)
+    got = grid_row(a, x, bound, 8)
+    assert abs(got[0] - re) <= grid_sigma(bound, mb) * F(2) ** -40
+    plain = F(0)
+    for (p, q), (s, t) in zip(a, x):
+        plain = f32(plain + f32(f32(p * s) - f32(q * t)))
+    assert abs(plain - re) > 1e3 * abs(got[0] - re)
+
+
+def test_common_grid_at_the_edge_of_its_bound():
+    # every term of one sign, the row's 1-norm equal to the block bound, and 64
+    # terms per output: the partial sums reach bound * mb < sigma / 2 and the
+    # lane sums must still be exact (grid_row asserts it)
+    rng = np.random.default_rng(11)
+    vals = [f32(F(float(v))) for v in rng.uniform(0.5, 1.0, size=64)]
+    a = [(v, F(0)) for v in vals]
+    x = [(F(1), F(0))] * 64
+    bound = _bound_ru([a])
+    got = grid_row(a, x, bound, 8)
+    assert abs(got[0] - sum(vals)) <= grid_sigma(bound, F(1)) * F(2) ** -44
+    assert got[1] == 0
+    # a bound of zero (a zero block): every sum is zero
+    z = [(F(0), F(0))] * 8
+    assert grid_row(z, x[:8], F(0), 8) == [0, 0]
+
+
+def test_common_grid_two_stage_low_rank():
+    # a low-rank block's second stage: o_i = sum_l Y_il t_l with t_l = G_l + R_l the
+    # first stage's grid sum and remainder; sigma_2 from the bound |G_l| <= sigma_1 / 2
+    # (the leading parts through the chain, the trailing parts into r).  The chain's
+    # claims hold (real_chain asserts them) and the output is within 2^-38 of sigma_2.
+    rng = np.random.default_rng(13)
+    k, n = 8, 64
+    V = [_c64(rng, n, 0.5) for _ in range(k)]
+    x = _c64(rng, n, 0.0)
+    bV = _bound_ru(V)
+    mb = max(max(abs(p), abs(q)) for p, q in x)
+    s1 = grid_sigma(bV, mb)
+    t = []
+    for row in V:
+        g = grid_row(row, x, bV, 32)                  # the kernels' 32-lane stage 1
+        re, im, _ = _exact(row, x)
+        # 32 lanes' remainders, each up to 2^-22 sigma_1, summed in FP32: a few units of 2^-41
+        assert abs(g[0] - re) <= s1 * F(2) ** -38 and abs(g[1] - im) <= s1 * F(2) ** -38
+        t.append(g)
+    Y = _c64(rng, k, 0.5)                             # one output row of U (rank entries)
+    bY = _bound_ru([Y])
+    s2 = grid_sigma(bY, s1 / 2)
+    # split each t_l into the FP32 leading part the chain takes and the trailing rest
+    hi = [(f32(a), f32(b)) for a, b in t]
+    lo = [(a - h[0], b - h[1]) for (a, b), h in zip(t, hi)]
+    assert max(max(abs(a), abs(b)) for a, b in hi) <= s1 / 2
+    re_t, im_t = [], []
+    for (yr, yi), (hr, hh) in zip(Y, hi):
+        re_t += [(yr, hr), (-yi, hh)]
+        im_t += [(yr, hh), (yi, hr)]
+    Sr, rr = real_chain(re_t, s2)
+    Si, ri = real_chain(im_t, s2)
+    got_re = Sr + rr + sum(yr * lr - yi * li for (yr, yi), (lr, li) in zip(Y, lo))
+    got_im = Si + ri + sum(yr * li + yi * lr for (yr, yi), (lr, li) in zip(Y, lo))
+    ex_re = sum(yr * a - yi * b for (yr, yi), (a, b) in zip(Y, t))
+    ex_im = sum(yr * b + yi * a for (yr, yi), (a, b) in zip(Y, t))
+    assert abs(got_re - ex_re) <= s2 * F(2) ** -38 and abs(got_im - ex_im) <= s2 * F(2) ** -38
