@@ -237,14 +237,83 @@ __device__ __forceinline__ void dense_item_g(const Item &it, float4 bnd, const f
 }
 
 // Low-rank block U V of at most 64 x 64 (U^T k x m, V k x n, m, n padded even):
-// slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I), one pass over chunks
-// of 4 rank rows.  A lane owns the rows / columns 2 lane, 2 lane + 1 of both panels.
-// Both stages run on common grids.  Stage 1 (the rank-k intermediates tp = U^T x_I,
-// t = V x_J; bnd.x, bnd.y: largest rank-row 1-norms of U^T and V): the 32-lane
-// reductions add the grid parts exactly in plain FP32.  Stage 2 (the outputs; bnd.z,
-// bnd.w: largest column 1-norms of U^T and V): the leading part of each intermediate
-// is a grid sum, at most half its grid's sigma, which bounds the inputs, so each
-// output is one chain over all rank rows, closed once.
+// slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I), one pass over pairs
+// of rank rows (loaded one pair ahead).  A lane owns the rows / columns 2 lane,
+// 2 lane + 1 of both panels.  Both stages run on common grids.  Stage 1 (the rank-k
+// intermediates tp = U^T x_I, t = V x_J; bnd.x, bnd.y: largest rank-row 1-norms of
+// U^T and V): the 32-lane reductions add the grid parts exactly in plain FP32.
+// Stage 2 (the outputs; bnd.z, bnd.w: largest column 1-norms of U^T and V): the
+// leading part of each intermediate is a grid sum, at most half its grid's sigma,
+// which bounds the inputs, so each output is one chain over all rank rows.
+__device__ __forceinline__ void lr_load(Pair<float> (&u)[2], Pair<float> (&v)[2], const float2 *__restrict__ UT,
+                                        const float2 *__restrict__ V, int l0, int k, int m, int n, int i, bool iv,
+                                        bool jv)
+{
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        u[l] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        v[l] = u[l];
+        if (l0 + l < k) {
+            if (iv) u[l] = ld_stream(UT + (int64_t)(l0 + l) * m + i);
+            if (jv) v[l] = ld_stream(V + (int64_t)(l0 + l) * n + i);
+        }
+    }
+}
+
+// one pair of rank rows l0, l0 + 1 of a low-rank block (u: U^T, v: V, the lane's two
+// columns each): stage 1 on the common grids s1u, s1v, reduced over the warp, then
+// the pair's rank rows into the outputs' stage-2 chains
+__device__ __forceinline__ void lr_pair(const Pair<float> (&u)[2], const Pair<float> (&v)[2], const Pair<float> &xi,
+                                        const Pair<float> &xj, float s1u, float s1v, cxacc &ci0, cxacc &ci1,
+                                        cxacc &cj0, cxacc &cj1, int lane)
+{
+    // value index 4 l + (grid re, rem re, grid im, rem im)
+    float gu[8], gv[8];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        cxacc cu, cv;
+        cx_start(cu, s1u);
+        cxstep(cu, u[l].a, xi.a);
+        cxstep(cu, u[l].b, xi.b);
+        cx_start(cv, s1v);
+        cxstep(cv, v[l].a, xj.a);
+        cxstep(cv, v[l].b, xj.b);
+        gu[4 * l] = __fsub_rn(cu.re.tau, s1u);
+        gu[4 * l + 1] = cu.re.r;
+        gu[4 * l + 2] = __fsub_rn(cu.im.tau, s1u);
+        gu[4 * l + 3] = cu.im.r;
+        gv[4 * l] = __fsub_rn(cv.re.tau, s1v);
+        gv[4 * l + 1] = cv.re.r;
+        gv[4 * l + 2] = __fsub_rn(cv.im.tau, s1v);
+        gv[4 * l + 3] = cv.im.r;
+    }
+    // over the warp: index bits 2..0 by lane bits 4..2, then the four lanes 4 q .. 4 q + 3
+    // add their quarters: lane L ends with value L / 4 summed over all lanes
+    xreduce_step<4>(gu, lane, 16);
+    xreduce_step<4>(gv, lane, 16);
+    xreduce_step<2>(gu, lane, 8);
+    xreduce_step<2>(gv, lane, 8);
+    xreduce_step<1>(gu, lane, 4);
+    xreduce_step<1>(gv, lane, 4);
+#pragma unroll
+    for (int sh = 1; sh <= 2; sh <<= 1) {
+        gu[0] = __fadd_rn(gu[0], __shfl_xor_sync(FULL, gu[0], sh));
+        gv[0] = __fadd_rn(gv[0], __shfl_xor_sync(FULL, gv[0], sh));
+    }
+    // stage 2 (rank rows past k have zero factors and zero intermediates)
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const cdf tl = {{__shfl_sync(FULL, gv[0], 16 * l), __shfl_sync(FULL, gv[0], 16 * l + 4)},
+                        {__shfl_sync(FULL, gv[0], 16 * l + 8), __shfl_sync(FULL, gv[0], 16 * l + 12)}};
+        const cdf tpl = {{__shfl_sync(FULL, gu[0], 16 * l), __shfl_sync(FULL, gu[0], 16 * l + 4)},
+                         {__shfl_sync(FULL, gu[0], 16 * l + 8), __shfl_sync(FULL, gu[0], 16 * l + 12)}};
+        cxstep_df(ci0, u[l].a, tl);
+        cxstep_df(ci1, u[l].b, tl);
+        cxstep_df(cj0, v[l].a, tpl);
+        cxstep_df(cj1, v[l].b, tpl);
+    }
+}
+
 __device__ __forceinline__ void lowrank_item_g(const Item &it, float4 bnd, const float2 *__restrict__ pool,
                                                const float2 *HM_XR x, cdf *HM_XR part, int lane)
 {
@@ -253,6 +322,8 @@ __device__ __forceinline__ void lowrank_item_g(const Item &it, float4 bnd, const
     const float2 *V = UT + (int64_t)k * m;
     const int i = 2 * lane;
     const bool iv = i < m, jv = i < n;
+    Pair<float> u[2], v[2];
+    lr_load(u, v, UT, V, 0, k, m, n, i, iv, jv);
     Pair<float> xi{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, xj = xi;
     if (iv) xi = ld_vec(x + it.row0 + i);
     if (jv) xj = ld_vec(x + it.col0 + i);
@@ -264,63 +335,13 @@ __device__ __forceinline__ void lowrank_item_g(const Item &it, float4 bnd, const
     cx_start(ci1, s2i);
     cx_start(cj0, s2j);
     cx_start(cj1, s2j);
-    for (int l0 = 0; l0 < k; l0 += 4) {
-        Pair<float> u[4], v[4];
+#pragma unroll 1
+    for (int l0 = 0; l0 < k; l0 += 2) {
+        Pair<float> un[2], vn[2];
+        lr_load(un, vn, UT, V, l0 + 2, k, m, n, i, iv, jv);
+        lr_pair(u, v, xi, xj, s1u, s1v, ci0, ci1, cj0, cj1, lane);
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            u[l] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-            v[l] = u[l];
-            if (l0 + l < k) {
-                if (iv) u[l] = ld_stream(UT + (int64_t)(l0 + l) * m + i);
-                if (jv) v[l] = ld_stream(V + (int64_t)(l0 + l) * n + i);
-            }
-        }
-        // stage 1: each lane's two terms of a rank row as one chain on the common grid;
-        // value index 4 l + (grid re, rem re, grid im, rem im)
-        float gu[16], gv[16];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            cxacc cu, cv;
-            cx_start(cu, s1u);
-            cxstep(cu, u[l].a, xi.a);
-            cxstep(cu, u[l].b, xi.b);
-            cx_start(cv, s1v);
-            cxstep(cv, v[l].a, xj.a);
-            cxstep(cv, v[l].b, xj.b);
-            gu[4 * l] = __fsub_rn(cu.re.tau, s1u);
-            gu[4 * l + 1] = cu.re.r;
-            gu[4 * l + 2] = __fsub_rn(cu.im.tau, s1u);
-            gu[4 * l + 3] = cu.im.r;
-            gv[4 * l] = __fsub_rn(cv.re.tau, s1v);
-            gv[4 * l + 1] = cv.re.r;
-            gv[4 * l + 2] = __fsub_rn(cv.im.tau, s1v);
-            gv[4 * l + 3] = cv.im.r;
-        }
-        // over the warp: index bits 3..0 by lane bits 4..1, then lanes 2 q, 2 q + 1 add
-        // their halves: lane L ends with value L / 2 summed over all lanes
-        xreduce_step<8>(gu, lane, 16);
-        xreduce_step<8>(gv, lane, 16);
-        xreduce_step<4>(gu, lane, 8);
-        xreduce_step<4>(gv, lane, 8);
-        xreduce_step<2>(gu, lane, 4);
-        xreduce_step<2>(gv, lane, 4);
-        xreduce_step<1>(gu, lane, 2);
-        xreduce_step<1>(gv, lane, 2);
-        gu[0] = __fadd_rn(gu[0], __shfl_xor_sync(FULL, gu[0], 1));
-        gv[0] = __fadd_rn(gv[0], __shfl_xor_sync(FULL, gv[0], 1));
-        // stage 2: the chunk's rank rows into the outputs' chains (rank rows past k
-        // have zero factors and zero intermediates)
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const cdf tl = {{__shfl_sync(FULL, gv[0], 8 * l), __shfl_sync(FULL, gv[0], 8 * l + 2)},
-                            {__shfl_sync(FULL, gv[0], 8 * l + 4), __shfl_sync(FULL, gv[0], 8 * l + 6)}};
-            const cdf tpl = {{__shfl_sync(FULL, gu[0], 8 * l), __shfl_sync(FULL, gu[0], 8 * l + 2)},
-                             {__shfl_sync(FULL, gu[0], 8 * l + 4), __shfl_sync(FULL, gu[0], 8 * l + 6)}};
-            cxstep_df(ci0, u[l].a, tl);
-            cxstep_df(ci1, u[l].b, tl);
-            cxstep_df(cj0, v[l].a, tpl);
-            cxstep_df(cj1, v[l].b, tpl);
-        }
+        for (int l = 0; l < 2; ++l) { u[l] = un[l]; v[l] = vn[l]; }
     }
     if (iv) { part[it.pad + i] = cxclose(ci0, s2i); part[it.pad + i + 1] = cxclose(ci1, s2i); }
     if (jv) { part[it.pad + m + i] = cxclose(cj0, s2j); part[it.pad + m + i + 1] = cxclose(cj1, s2j); }
