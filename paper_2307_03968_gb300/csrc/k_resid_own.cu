@@ -81,9 +81,12 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
     const int tid = threadIdx.x, i = tid & 63, hh = tid >> 6;
     const int n_groups = (nrhs + RG - 1) / RG;
     const int64_t total = (int64_t)n_units * n_groups;
+    // cluster-major: the RHS groups of one output cluster are consecutive units, so they
+    // run on neighbouring CTAs at the same time and read the cluster's blocks from DRAM
+    // once between them (the later reads hit L2)
     for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
-        const TcUnit U = units[u % n_units];
-        const int r0 = (int)(u / n_units) * RG, nr = min(RG, nrhs - r0);
+        const TcUnit U = units[u / n_groups];
+        const int r0 = (int)(u % n_groups) * RG, nr = min(RG, nrhs - r0);
         cdf acc[QN];
 #pragma unroll
         for (int q = 0; q < QN; ++q) acc[q] = cdf_zero();
