@@ -143,6 +143,24 @@ static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vec
     }
 }
 
+// items reordered for a persistent kernel whose nw warps take items t, t + nw, ...:
+// sorted by cost (stored bytes plus a fixed 2 KB for the per-block latencies), largest
+// first, and every odd round of nw reversed (a snake), so that the warps' sums match
+static std::vector<Item> balanced_order(const std::vector<Item> &in, int64_t nw)
+{
+    std::vector<Item> v = in;
+    auto cost = [](const Item &it) { return item_elems(it) * 8 + 2048; };
+    std::stable_sort(v.begin(), v.end(), [&](const Item &a, const Item &b) { return cost(a) > cost(b); });
+    const int64_t n = (int64_t)v.size();
+    nw = std::min<int64_t>(std::max<int64_t>(nw, 1), std::max<int64_t>(n, 1));
+    std::vector<Item> out(v.size());
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t q = t / nw, p = t % nw, rem = std::min<int64_t>(nw, n - q * nw);
+        out[t] = v[q * nw + ((q & 1) ? rem - 1 - p : p)];
+    }
+    return out;
+}
+
 hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
 {
     hm_status st;
@@ -205,13 +223,16 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
             return cut;
         };
         std::vector<Item> pa, pb;
-        if (panels(L.items, pa)) {
-            panels(big, pb);
-            L.n_prod = (int64_t)pa.size();
-            L.n_prod_big = (int64_t)pb.size();
-            if ((st = upload(h, &L.d_prod, pa, s)) != HM_OK) return st;
-            if ((st = upload(h, &L.d_prod_big, pb, s)) != HM_OK) return st;
-        }
+        panels(L.items, pa);
+        panels(big, pb);
+        // the product kernel hands items to its warps round-robin: sorted by cost, largest
+        // first, with every other round reversed, each warp gets an even share
+        pa = balanced_order(pa, product_warps(h));
+        pb = balanced_order(pb, product_warps(h));
+        L.n_prod = (int64_t)pa.size();
+        L.n_prod_big = (int64_t)pb.size();
+        if ((st = upload(h, &L.d_prod, pa, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_prod_big, pb, s)) != HM_OK) return st;
     }
     return HM_OK;
 }

@@ -118,8 +118,8 @@ struct LevelList {
     int64_t elems = 0;            // stored complex elements
     // the FP32 product's own copies of the item list and of its big part, with every dense
     // block of more than PROD_PANEL rows cut into row panels (the product kernel gives each
-    // item to one warp: a leaf of ~1,000 unknowns would otherwise leave the GPU idle); null
-    // when no block needs it (the lists above serve)
+    // item to one warp: a leaf of ~1,000 unknowns would otherwise leave the GPU idle), in the
+    // order that balances the kernel's round-robin warps (largest first, snake rounds)
     Item *d_prod = nullptr, *d_prod_big = nullptr;
     int64_t n_prod = 0, n_prod_big = 0;
 };
@@ -338,6 +338,8 @@ void launch_zero(void *p, size_t bytes, cudaStream_t s);
 void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
                         cudaStream_t s, int rb = -1);
 // FP64-class (Dot2) products of every block of a level into its partial slots (no atomics)
+// warps of the FP32 product kernel's persistent grid (k_product.cu)
+int64_t product_warps(hm_matrix h);
 // the residual products' block bounds of items[0 .. n) (k_residual.cu)
 void launch_item_bounds(const Item *items, int64_t n, const float2 *pool, float4 *bnd, cudaStream_t s);
 void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part, int64_t pstride,

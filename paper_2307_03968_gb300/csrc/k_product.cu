@@ -58,6 +58,16 @@ int apply_grid(hm_matrix h)
 
 } // namespace
 
+int64_t product_warps(hm_matrix h)
+{
+    if (h->num_sms <= 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return (int64_t)apply_grid<float, float, 3>(h) * APPLY_WARPS;
+}
+
 void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
                         cudaStream_t s, int rb)
 {
