@@ -239,8 +239,10 @@ hm_status hm_powerseries_solve(hm_matrix h, const void *b, int64_t ldb, void *x,
 
 /*
  * Same as hm_powerseries_solve with HOST buffers b and x (any host memory):
- * copies b to the device through pinned staging, solves, copies x back, and
- * synchronises before returning.
+ * copies b to the device, solves, copies x back, and synchronises before
+ * returning.  A buffer that is page-locked (cudaMallocHost / cudaHostRegister)
+ * and has leading dimension N is copied directly; any other goes through the
+ * handle's page-locked staging buffer (allocated on first use, kept).
  */
 hm_status hm_powerseries_solve_host(hm_matrix h, const void *b, int64_t ldb, void *x, int64_t ldx,
                                     int nrhs, const hm_solve_opts *opts, void *stream);

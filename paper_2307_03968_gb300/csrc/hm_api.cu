@@ -1380,7 +1380,18 @@ hm_status hm_powerseries_solve_host(hm_matrix h, const void *b, int64_t ldb, voi
     const size_t es = opts->fp64 ? sizeof(double2) : sizeof(float2);
     const size_t bytes = es * (size_t)h->N * nrhs;
     hm::Workspace &ws = h->ws;
-    if (ws.h_pinned_bytes < 2 * bytes) {
+    // page-locked caller buffers with leading dimension N are copied directly; pageable ones
+    // (or strided) go through the handle's page-locked staging buffer
+    auto pinned = [](const void *p) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return a.type == cudaMemoryTypeHost;
+    };
+    const bool b_direct = ldb == h->N && pinned(b), x_direct = ldx == h->N && pinned(x);
+    if (!(b_direct && x_direct) && ws.h_pinned_bytes < 2 * bytes) {
         if (ws.h_pinned) cudaFreeHost(ws.h_pinned);
         ws.h_pinned = nullptr;
         ws.h_pinned_bytes = 0;
@@ -1394,17 +1405,22 @@ hm_status hm_powerseries_solve_host(hm_matrix h, const void *b, int64_t ldb, voi
         HM_CUDA(cudaMalloc(&ws.d_io, 2 * bytes));
         ws.d_io_bytes = 2 * bytes;
     }
-    char *hb = (char *)ws.h_pinned, *hx = hb + bytes;
+    char *hb = (char *)ws.h_pinned, *hx = hb ? hb + bytes : nullptr;
     char *db = (char *)ws.d_io, *dxp = db + bytes;
-    for (int r = 0; r < nrhs; ++r)
-        std::memcpy(hb + es * h->N * r, (const char *)b + es * (size_t)ldb * r, es * h->N);
-    HM_CUDA(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, s));
+    if (b_direct) {
+        HM_CUDA(cudaMemcpyAsync(db, b, bytes, cudaMemcpyHostToDevice, s));
+    } else {
+        for (int r = 0; r < nrhs; ++r)
+            std::memcpy(hb + es * h->N * r, (const char *)b + es * (size_t)ldb * r, es * h->N);
+        HM_CUDA(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, s));
+    }
     hm_status st = solve_device(h, db, h->N, dxp, h->N, nrhs, opts, s, nullptr);
     if (st != HM_OK) return st;
-    HM_CUDA(cudaMemcpyAsync(hx, dxp, bytes, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(x_direct ? (char *)x : hx, dxp, bytes, cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
-    for (int r = 0; r < nrhs; ++r)
-        std::memcpy((char *)x + es * (size_t)ldx * r, hx + es * h->N * r, es * h->N);
+    if (!x_direct)
+        for (int r = 0; r < nrhs; ++r)
+            std::memcpy((char *)x + es * (size_t)ldx * r, hx + es * h->N * r, es * h->N);
     return HM_OK;
 }
 

@@ -273,11 +273,18 @@ class HMatrix:
         return si if info else None
 
     def solve_host(self, b, n_terms=2, n_levels=1, nested=True, refine=False, fp64=False, stream=None,
-                   persistent=False):
-        """hm_powerseries_solve_host on numpy arrays: b (N,) or (nrhs, N); returns x."""
+                   persistent=False, out=None):
+        """hm_powerseries_solve_host on numpy arrays: b (N,) or (nrhs, N); returns x (written
+        into `out` when given: a contiguous array of b's shape and dtype).  Page-locked
+        arrays (for example numpy views of pinned torch tensors) are copied directly."""
         dt = np.complex128 if fp64 else np.complex64
         b = np.ascontiguousarray(b, dtype=dt)
-        x = np.empty_like(b)
+        if out is None:
+            x = np.empty_like(b)
+        else:
+            if out.shape != b.shape or out.dtype != b.dtype or not out.flags.c_contiguous:
+                raise ValueError("out must be a contiguous array of b's shape and dtype")
+            x = out
         nrhs = 1 if b.ndim == 1 else b.shape[0]
         n = b.shape[-1]
         o = HmSolveOpts(n_terms, n_levels, 1 if nested else 0, 1 if refine else 0, 1 if fp64 else 0, 1,

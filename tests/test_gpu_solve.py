@@ -132,6 +132,17 @@ def test_host_buffer_solve_equals_device_solve(torch_cuda, sphere_small, cfg1):
     xh = A.solve_host(b.T, n_terms=2, n_levels=1)
     assert rel_err(xh, xd) < 1e-6
     assert rel_err(xh, series.solve(cfg1, b, K=2, levels=1).T) < TOL32
+    # page-locked buffers with leading dimension N go without the staging copies, with a
+    # refined solve too; the result must be the same
+    bp = torch_cuda.from_numpy(np.ascontiguousarray(b.T.astype(np.complex64))).pin_memory().numpy()
+    xp = torch_cuda.empty(bp.shape, dtype=torch_cuda.complex64).pin_memory().numpy()
+    xp[:] = np.nan
+    out = A.solve_host(bp, n_terms=2, n_levels=1, out=xp)
+    assert out is xp and rel_err(xp, xd) < 1e-6
+    xr = A.solve_host(b.T, n_terms=2, n_levels=1, refine=True)
+    xp[:] = np.nan
+    A.solve_host(bp, n_terms=2, n_levels=1, refine=True, out=xp)
+    assert rel_err(xp, xr) < 1e-6
 
 
 def test_single_leaf_is_exact_solve(torch_cuda):
