@@ -144,12 +144,16 @@ static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vec
 }
 
 // items reordered for a persistent kernel whose nw warps take items t, t + nw, ...:
-// sorted by cost (stored bytes plus a fixed 2 KB for the per-block latencies), largest
-// first, and every odd round of nw reversed (a snake), so that the warps' sums match
-static std::vector<Item> balanced_order(const std::vector<Item> &in, int64_t nw)
+// sorted by cost, largest first, and every odd round of nw reversed (a snake), so that
+// the warps' sums match.  Cost of the product: stored bytes plus a fixed 2 KB for the
+// per-block latencies; of the FP64-class residual (instruction-bound): about 39 lane
+// instructions per stored element of a dense block, 52 of a low-rank one, plus 3,000.
+static int64_t product_cost(const Item &it) { return item_elems(it) * 8 + 2048; }
+static int64_t residual_cost(const Item &it) { return item_elems(it) * (it.k == 0 ? 39 : 52) + 3000; }
+template <class Cost>
+static std::vector<Item> balanced_order(const std::vector<Item> &in, int64_t nw, Cost cost)
 {
     std::vector<Item> v = in;
-    auto cost = [](const Item &it) { return item_elems(it) * 8 + 2048; };
     std::stable_sort(v.begin(), v.end(), [&](const Item &a, const Item &b) { return cost(a) > cost(b); });
     const int64_t n = (int64_t)v.size();
     nw = std::min<int64_t>(std::max<int64_t>(nw, 1), std::max<int64_t>(n, 1));
@@ -198,9 +202,13 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         if ((st = upload(h, &L.d_items, L.items, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_small, small, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_big, big, s)) != HM_OK) return st;
-        if ((st = dev_alloc(h, (void **)&L.d_bnd, sizeof(float4) * L.items.size())) != HM_OK) return st;
+        // the residual's own list (balanced for its round-robin warps) and the block bounds
+        // of that list and of the big part
+        const std::vector<Item> res = balanced_order(L.items, residual_warps(h), residual_cost);
+        if ((st = upload(h, &L.d_res, res, s)) != HM_OK) return st;
+        if ((st = dev_alloc(h, (void **)&L.d_bnd, sizeof(float4) * res.size())) != HM_OK) return st;
         if ((st = dev_alloc(h, (void **)&L.d_bnd_big, sizeof(float4) * big.size())) != HM_OK) return st;
-        launch_item_bounds(L.d_items, (int64_t)L.items.size(), h->d_pool32, L.d_bnd, s);
+        launch_item_bounds(L.d_res, (int64_t)res.size(), h->d_pool32, L.d_bnd, s);
         launch_item_bounds(L.d_big, L.n_big, h->d_pool32, L.d_bnd_big, s);
         HM_CUDA(cudaGetLastError());
         if ((st = upload(h, &L.d_tcu, tcu, s)) != HM_OK) return st;
@@ -227,8 +235,8 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         panels(big, pb);
         // the product kernel hands items to its warps round-robin: sorted by cost, largest
         // first, with every other round reversed, each warp gets an even share
-        pa = balanced_order(pa, product_warps(h));
-        pb = balanced_order(pb, product_warps(h));
+        pa = balanced_order(pa, product_warps(h), product_cost);
+        pb = balanced_order(pb, product_warps(h), product_cost);
         L.n_prod = (int64_t)pa.size();
         L.n_prod_big = (int64_t)pb.size();
         if ((st = upload(h, &L.d_prod, pa, s)) != HM_OK) return st;
@@ -268,6 +276,7 @@ static void free_handle(hm_matrix h)
         if (kv.second.d_prod_big) cudaFree(kv.second.d_prod_big);
         if (kv.second.d_small) cudaFree(kv.second.d_small);
         if (kv.second.d_big) cudaFree(kv.second.d_big);
+        if (kv.second.d_res) cudaFree(kv.second.d_res);
         if (kv.second.d_bnd) cudaFree(kv.second.d_bnd);
         if (kv.second.d_bnd_big) cudaFree(kv.second.d_bnd_big);
         if (kv.second.d_tcu) cudaFree(kv.second.d_tcu);
@@ -758,7 +767,7 @@ static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *
                 Phase q = phase(PH_RESID, nr);
                 q.a = x; q.c = h->ws.d_part;
                 q.ld = h->partial_elems;
-                q.items = it->second.d_items;
+                q.items = it->second.d_res;
                 q.d = it->second.d_bnd;
                 q.n = (int64_t)it->second.items.size();
                 c.rec->push_back(q);

@@ -95,8 +95,10 @@ struct LevelList {
     // in shared memory, and the rest
     Item *d_small = nullptr, *d_big = nullptr;
     int64_t n_small = 0, n_big = 0;
-    // per item of d_items / d_big: the block bounds of the common-grid residual
-    // products (k_item_bounds: largest row and column 1-norms of the stored factors)
+    // the FP64-class residual's copy of the item list, in the order that balances its
+    // round-robin warps, and per item of it / of d_big the block bounds of the
+    // common-grid residual products (k_item_bounds: largest row and column 1-norms)
+    Item *d_res = nullptr;
     float4 *d_bnd = nullptr, *d_bnd_big = nullptr;
     int small_dim = 0, small_rank = 0;   // largest (even) side and rank among the small items
     // the small items as directed products grouped into work units by output
@@ -338,8 +340,10 @@ void launch_zero(void *p, size_t bytes, cudaStream_t s);
 void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
                         cudaStream_t s, int rb = -1);
 // FP64-class (Dot2) products of every block of a level into its partial slots (no atomics)
-// warps of the FP32 product kernel's persistent grid (k_product.cu)
+// warps of the FP32 product kernel's persistent grid (k_product.cu) and of the
+// FP64-class residual kernel's (k_residual.cu)
 int64_t product_warps(hm_matrix h);
+int64_t residual_warps(hm_matrix h);
 // the residual products' block bounds of items[0 .. n) (k_residual.cu)
 void launch_item_bounds(const Item *items, int64_t n, const float2 *pool, float4 *bnd, cudaStream_t s);
 void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part, int64_t pstride,

@@ -142,24 +142,25 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
                     if (c < P.olen) Ysm[l * BS + c] = Y[(int64_t)l * P.y_ld + c];
                 }
                 __syncthreads();
-                // stage 1: T[l][q] = sum_j W[l][j] x[j][q]; a round covers 128 / RG rank rows;
-                // thread (row l0 + tid / (8 RG), q = (tid / 8) % RG, K slice ks = tid % 8: j = ks,
-                // ks + 8, ...); the eight slices' chains share the grid of W's largest rank-row
+                // stage 1: T[l][q] = sum_j W[l][j] x[j][q]; a round covers 128 / (4 RG) rank rows;
+                // thread (row l0 + tid / (4 RG), q = (tid / 4) % RG, K slice ks = tid % 4: j = ks,
+                // ks + 4, ...); the four slices' chains share the grid of W's largest rank-row
                 // 1-norm times x's largest component, so their grid parts add exactly across lanes
                 const float2 bb = pbnd[p];
                 {
-                    constexpr int LR = RT / (8 * RG);              // rank rows per round
-                    const int ks = tid & 7, q = (tid >> 3) % RG, lr = tid / (8 * RG);
+                    constexpr int NS = 2;                          // K slices per rank row and RHS
+                    constexpr int LR = RT / (NS * RG);             // rank rows per round
+                    const int ks = tid % NS, q = (tid / NS) % RG, lr = tid / (NS * RG);
                     const float s1 = grid_sigma(bb.x, x_max(S.mx, q));
                     for (int l0 = 0; l0 < P.rank; l0 += LR) {
                         const int l = l0 + lr;
                         cxacc c;
                         cx_start(c, s1);
                         if (l < P.rank)
-                            for (int j = ks; j < P.klen; j += 8) cxstep(c, Wsm[j * WS + l], S.x[j * XS + q]);
+                            for (int j = ks; j < P.klen; j += NS) cxstep(c, Wsm[j * WS + l], S.x[j * XS + q]);
                         float v[4] = {__fsub_rn(c.re.tau, s1), c.re.r, __fsub_rn(c.im.tau, s1), c.im.r};
 #pragma unroll
-                        for (int sh = 1; sh < 8; sh <<= 1)
+                        for (int sh = 1; sh < NS; sh <<= 1)
 #pragma unroll
                             for (int e = 0; e < 4; ++e) v[e] = __fadd_rn(v[e], __shfl_xor_sync(FULL, v[e], sh));
                         if (ks == 0 && l < P.rank) S.t[l * RG + q] = {{v[0], v[1]}, {v[2], v[3]}};

@@ -77,7 +77,7 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
 void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, cdf *part, int64_t pstride,
                                  int nrhs, cudaStream_t s, int rb)
 {
-    const Item *list = L.d_items;
+    const Item *list = L.d_res;
     const float4 *bnd = L.d_bnd;
     int64_t n = (int64_t)L.items.size();
     if (rb < 0) rb = nrhs < MRHS_MIN_RHS ? 0 : nrhs <= 8 ? 8 : 16;
@@ -89,15 +89,25 @@ void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *
         n = L.n_big;
     }
     if (n == 0) return;
+    int g = (int)(residual_warps(h) / APPLY_WARPS);
+    if ((int64_t)g * APPLY_WARPS > n) g = (int)((n + APPLY_WARPS - 1) / APPLY_WARPS);
+    k_residual_items<<<g, APPLY_WARPS * 32, 0, s>>>(list, bnd, n, h->d_pool32, x, h->pN, part, pstride, nrhs);
+}
+
+int64_t residual_warps(hm_matrix h)
+{
     static int per_sm = -1;
     if (per_sm < 0) {
         int v = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_residual_items, APPLY_WARPS * 32, 0);
         per_sm = v > 0 ? v : 1;
     }
-    int g = per_sm * (h->num_sms > 0 ? h->num_sms : 1);
-    if ((int64_t)g * APPLY_WARPS > n) g = (int)((n + APPLY_WARPS - 1) / APPLY_WARPS);
-    k_residual_items<<<g, APPLY_WARPS * 32, 0, s>>>(list, bnd, n, h->d_pool32, x, h->pN, part, pstride, nrhs);
+    if (h->num_sms <= 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return (int64_t)per_sm * h->num_sms * APPLY_WARPS;
 }
 
 void launch_item_bounds(const Item *items, int64_t n, const float2 *pool, float4 *bnd, cudaStream_t s)
