@@ -12,8 +12,8 @@
 // exactly onto a power-of-two grid whose sigma comes from the product's
 // precomputed bound, k_prod_bounds, and the input's largest component; the
 // remainders summed apart), folded once into the double-float sum with a
-// compensated addition.  Thread t owns output row t % 64 and right-hand sides
-// (RG/2) (t / 64) .. +RG/2-1.  The unit's sums are stored once, in FP64, into the level's
+// compensated addition.  Thread t of the RT-thread CTA owns output row t % 64 and
+// the right-hand sides QN (t / 64) .. + QN - 1 of the group, QN = RG / (RT / 64).  The unit's sums are stored once, in FP64, into the level's
 // [RHS][pN] array: no partial slots, no atomics, and the result is independent
 // of scheduling.  k_gather_own then forms b - (D x + sum over levels) in FP64.
 //
@@ -31,7 +31,7 @@ namespace {
 
 using namespace kc;
 using namespace dot2;
-constexpr int RT = 128;          // threads: 64 output rows x 2 halves of the unit's right-hand sides
+// CTA of RT threads (128 or 256): 64 output rows x RT / 64 parts of the unit's right-hand sides
 constexpr int RGMAX = 16;        // right-hand sides per unit (at most)
 constexpr int BS = 65;           // float2 stride of a staged K row of a block (odd: conflict-free staging)
 constexpr int WS = 33;           // float2 stride of a staged K row of W (rank <= 32)
@@ -52,7 +52,7 @@ struct alignas(16) Smem {
 // 0 for the rest of j < roundup4(klen); mx[2 q + h] = max over j = 32h..32h+31 of |x|_inf.
 // Every thread runs the same number of iterations (RG * 64 is a multiple of RT), and a warp
 // covers 32 consecutive j of one q.
-template <int RG>
+template <int RG, int RT>
 __device__ __forceinline__ void stage_x(float2 *xs, float *mx, const float2 *__restrict__ x, int64_t ldx, int r0,
                                         int nr, int in0, int klen)
 {
@@ -69,15 +69,15 @@ __device__ __forceinline__ void stage_x(float2 *xs, float *mx, const float2 *__r
 // the largest |x|_inf of right-hand side q over the staged input
 __device__ __forceinline__ float x_max(const float *mx, int q) { return fmaxf(mx[2 * q], mx[2 * q + 1]); }
 
-template <int RG>
-__global__ void __launch_bounds__(RT, 4)
+template <int RG, int RT>
+__global__ void __launch_bounds__(RT, RT == 128 ? 4 : 3)
 k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restrict__ prods,
             const float2 *__restrict__ pbnd, const float2 *__restrict__ pool, const float2 *__restrict__ x,
             int64_t ldx, int nrhs, double2 *__restrict__ own, int64_t ldo)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     Smem &S = *reinterpret_cast<Smem *>(smraw);
-    constexpr int QN = RG / 2;        // right-hand sides per thread
+    constexpr int QN = RG / (RT / 64);   // right-hand sides per thread
     const int tid = threadIdx.x, i = tid & 63, hh = tid >> 6;
     const int n_groups = (nrhs + RG - 1) / RG;
     const int64_t total = (int64_t)n_units * n_groups;
@@ -93,7 +93,7 @@ k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restr
         for (int p = U.p0; p < U.p1; ++p) {
             const TcProd P = prods[p];
             __syncthreads();                                  // the previous product's reads are done
-            stage_x<RG>(S.x, S.mx, x, ldx, r0, nr, P.in0, P.klen);
+            stage_x<RG, RT>(S.x, S.mx, x, ldx, r0, nr, P.in0, P.klen);
             if (P.rank == 0) {
                 // block elements (output i < olen, K j < klen) into b[j * BS + i]
                 const float2 *B = pool + P.b_off;
@@ -286,24 +286,28 @@ void launch_resid_own(hm_matrix h, const LevelList &L, const float2 *x, double2 
     constexpr int SMEM = (int)sizeof(Smem);
     static bool attr = false;
     if (!attr) {
-        for (const void *f : {(const void *)k_resid_own<8>, (const void *)k_resid_own<16>}) {
+        for (const void *f : {(const void *)k_resid_own<8, 128>, (const void *)k_resid_own<16, 128>,
+                              (const void *)k_resid_own<8, 256>, (const void *)k_resid_own<16, 256>}) {
             cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
             cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
         }
         attr = true;
     }
-    // four CTAs of ~50 KB per SM (the occupancy query under-reports with large dynamic shared memory);
-    // groups of 8 right-hand sides up to 32 of them, so that small calls still have enough units
+    // groups of 8 right-hand sides up to 32 of them, so that small calls still have enough units.
+    // CTAs of 256 threads (4 RHS per thread, three CTAs of ~50 KB per SM) up to 128 RHS, of 128
+    // threads (8 RHS per thread, four CTAs per SM) above: measured on the 30,720-unknown sphere,
+    // 0.540 / 0.371 / 0.388 ms per RHS at 16 / 64 / 181 RHS against 0.587 / 0.406 / 0.378
     const int rg = nrhs <= 32 ? 8 : 16;
+    const bool wide = nrhs <= 128;
     const int64_t units = L.n_rcu * (int64_t)((nrhs + rg - 1) / rg);
-    int64_t g = 4 * (int64_t)(h->num_sms > 0 ? h->num_sms : 1);
+    int64_t g = (wide ? 3 : 4) * (int64_t)(h->num_sms > 0 ? h->num_sms : 1);
     if (g > units) g = units;
-    if (rg == 8)
-        k_resid_own<8><<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, L.d_rcb, h->d_pool32, x, h->pN,
-                                                     nrhs, own, h->pN);
-    else
-        k_resid_own<16><<<(unsigned)g, RT, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, L.d_rcb, h->d_pool32, x, h->pN,
-                                                      nrhs, own, h->pN);
+    auto go = [&](auto kern, int rt) {
+        kern<<<(unsigned)g, rt, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, L.d_rcb, h->d_pool32, x, h->pN, nrhs, own,
+                                           h->pN);
+    };
+    if (rg == 8) wide ? go(k_resid_own<8, 256>, 256) : go(k_resid_own<8, 128>, 128);
+    else wide ? go(k_resid_own<16, 256>, 256) : go(k_resid_own<16, 128>, 128);
 }
 
 void launch_gather_own(hm_matrix h, const float2 *x, int m, const double2 *own, int64_t lstride, const float2 *b,
