@@ -472,11 +472,18 @@ __device__ __forceinline__ void gather_leaf(int leaf, int r, const int32_t *__re
         const int i = rc + 2 * lane;
         cdf a0 = cdf_zero(), a1 = cdf_zero();
         if (i < np) {
+            // four slots in flight per warp; the next round's slot indices are loaded with this
+            // round's slots, so that only the first round waits for its indices
             int64_t e = e0 + w;
-            for (; e + 3 * GW < e1; e += 4 * GW) {   // four slots in flight per warp
-                const int64_t q0 = csr_idx[e], q1 = csr_idx[e + GW], q2 = csr_idx[e + 2 * GW], q3 = csr_idx[e + 3 * GW];
+            bool more = e + 3 * GW < e1;
+            int64_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+            if (more) { q0 = csr_idx[e]; q1 = csr_idx[e + GW]; q2 = csr_idx[e + 2 * GW]; q3 = csr_idx[e + 3 * GW]; }
+            while (more) {
                 const cdf v00 = P[q0 + i], v01 = P[q0 + i + 1], v10 = P[q1 + i], v11 = P[q1 + i + 1];
                 const cdf v20 = P[q2 + i], v21 = P[q2 + i + 1], v30 = P[q3 + i], v31 = P[q3 + i + 1];
+                e += 4 * GW;
+                more = e + 3 * GW < e1;
+                if (more) { q0 = csr_idx[e]; q1 = csr_idx[e + GW]; q2 = csr_idx[e + 2 * GW]; q3 = csr_idx[e + 3 * GW]; }
                 a0 = cdf_add(a0, cdf_add(cdf_add(v00, v10), cdf_add(v20, v30)));
                 a1 = cdf_add(a1, cdf_add(cdf_add(v01, v11), cdf_add(v21, v31)));
             }
