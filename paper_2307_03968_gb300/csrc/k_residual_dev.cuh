@@ -314,6 +314,42 @@ __device__ __forceinline__ void lr_pair(const Pair<float> (&u)[2], const Pair<fl
     }
 }
 
+// the last rank row of an odd rank (u, v: that row's two columns of U^T and V): as
+// lr_pair for one row
+__device__ __forceinline__ void lr_single(const Pair<float> &u, const Pair<float> &v, const Pair<float> &xi,
+                                          const Pair<float> &xj, float s1u, float s1v, cxacc &ci0, cxacc &ci1,
+                                          cxacc &cj0, cxacc &cj1, int lane)
+{
+    cxacc cu, cv;
+    cx_start(cu, s1u);
+    cxstep(cu, u.a, xi.a);
+    cxstep(cu, u.b, xi.b);
+    cx_start(cv, s1v);
+    cxstep(cv, v.a, xj.a);
+    cxstep(cv, v.b, xj.b);
+    float gu[4] = {__fsub_rn(cu.re.tau, s1u), cu.re.r, __fsub_rn(cu.im.tau, s1u), cu.im.r};
+    float gv[4] = {__fsub_rn(cv.re.tau, s1v), cv.re.r, __fsub_rn(cv.im.tau, s1v), cv.im.r};
+    // index bits 1..0 by lane bits 4..3, then the eight lanes 8 c .. 8 c + 7 add their
+    // eighths: lane L ends with value L / 8 summed over all lanes
+    xreduce_step<2>(gu, lane, 16);
+    xreduce_step<2>(gv, lane, 16);
+    xreduce_step<1>(gu, lane, 8);
+    xreduce_step<1>(gv, lane, 8);
+#pragma unroll
+    for (int sh = 1; sh <= 4; sh <<= 1) {
+        gu[0] = __fadd_rn(gu[0], __shfl_xor_sync(FULL, gu[0], sh));
+        gv[0] = __fadd_rn(gv[0], __shfl_xor_sync(FULL, gv[0], sh));
+    }
+    const cdf tl = {{__shfl_sync(FULL, gv[0], 0), __shfl_sync(FULL, gv[0], 8)},
+                    {__shfl_sync(FULL, gv[0], 16), __shfl_sync(FULL, gv[0], 24)}};
+    const cdf tpl = {{__shfl_sync(FULL, gu[0], 0), __shfl_sync(FULL, gu[0], 8)},
+                     {__shfl_sync(FULL, gu[0], 16), __shfl_sync(FULL, gu[0], 24)}};
+    cxstep_df(ci0, u.a, tl);
+    cxstep_df(ci1, u.b, tl);
+    cxstep_df(cj0, v.a, tpl);
+    cxstep_df(cj1, v.b, tpl);
+}
+
 __device__ __forceinline__ void lowrank_item_g(const Item &it, float4 bnd, const float2 *__restrict__ pool,
                                                const float2 *HM_XR x, cdf *HM_XR part, int lane)
 {
@@ -336,13 +372,14 @@ __device__ __forceinline__ void lowrank_item_g(const Item &it, float4 bnd, const
     cx_start(cj0, s2j);
     cx_start(cj1, s2j);
 #pragma unroll 1
-    for (int l0 = 0; l0 < k; l0 += 2) {
+    for (int l0 = 0; l0 + 1 < k; l0 += 2) {
         Pair<float> un[2], vn[2];
         lr_load(un, vn, UT, V, l0 + 2, k, m, n, i, iv, jv);
         lr_pair(u, v, xi, xj, s1u, s1v, ci0, ci1, cj0, cj1, lane);
 #pragma unroll
         for (int l = 0; l < 2; ++l) { u[l] = un[l]; v[l] = vn[l]; }
     }
+    if (k & 1) lr_single(u[0], v[0], xi, xj, s1u, s1v, ci0, ci1, cj0, cj1, lane);   // row k - 1
     if (iv) { part[it.pad + i] = cxclose(ci0, s2i); part[it.pad + i + 1] = cxclose(ci1, s2i); }
     if (jv) { part[it.pad + m + i] = cxclose(cj0, s2j); part[it.pad + m + i + 1] = cxclose(cj1, s2j); }
 }
