@@ -135,3 +135,58 @@ def test_fp64_class_residual_every_choice(torch_cuda, opers, name, levels):
         yt = torch_cuda.full_like(xt, float("nan"))
         A.apply(xt, yt, n_levels=levels, fp64_accumulate=True)
         assert rel_err(yt.cpu().numpy(), y) < 1e-6, res
+
+
+def _abs_operator(G):
+    """The operator with every stored factor replaced by its elementwise modulus: applied to
+    |x| it gives, per row, the sum of the moduli of the terms the residual sums (for a
+    low-rank block, sum_l |U_il| |V_lj| |x_j|), the scale of error-free summation."""
+    import copy
+    Q = copy.copy(G)
+    Q.D = [np.abs(d) for d in G.D]
+    Q.near = [(a, b, c, d, np.abs(B)) for (a, b, c, d, B) in G.near]
+    Q.far = {lev: [(a, b, c, d, np.abs(U), np.abs(V)) for (a, b, c, d, U, V) in lst] for lev, lst in G.far.items()}
+    return Q
+
+
+@pytest.mark.parametrize("name", ["leaf32", "leaf64"])
+@pytest.mark.parametrize("levels", [1, -1])
+def test_fp64_class_residual_special_cases(torch_cuda, opers, name, levels):
+    """Cases with exact answers, through every residual choice.  x = 0: every grid
+    is zero and r = b bit for bit.  b = 0, x = c_q e_{j_q} (one scaled unit vector
+    per right-hand side): r = -c_q A e_{j_q}, a column of the operator.  Each entry
+    must be within the complex64 rounding of r (2^-23 |r_i|) plus an FP64-class share
+    of the sum of the moduli of its terms (s_i = sum_l |U_il| |V_lj| |c| for a low-rank
+    block): a dropped term, a wrong sign or a transposed block is off by O(s_i)."""
+    H = opers[name]
+    G = _rounded(H)
+    nr = 20
+    rng = np.random.default_rng(134)
+    A = gpu_operator(H)
+    b = (rng.normal(size=(nr, H.N)) + 1j * rng.normal(size=(nr, H.N))).astype(np.complex64)
+    bt = torch_cuda.from_numpy(b).cuda()
+    x0 = torch_cuda.zeros_like(bt)
+    js = rng.choice(H.N, nr, replace=False)
+    c = (rng.normal(size=nr) + 1j * rng.normal(size=nr)).astype(np.complex64)
+    X = np.zeros((nr, H.N), dtype=np.complex64)
+    X[np.arange(nr), js] = c
+    apply = lambda Q, v: np.ascontiguousarray(Q.from_tree(Q.apply(Q.to_tree(v.T.astype(np.complex128)), levels)).T)
+    ref = -apply(G, X)
+    scale = np.abs(apply(_abs_operator(G), np.abs(X))).real
+    xt = torch_cuda.from_numpy(X).cuda()
+    zt = torch_cuda.zeros_like(bt)
+    for res in (0, 8, 16, 1017):
+        A.set_tuning(nr, 0, res)
+        rt = torch_cuda.full_like(bt, float("nan"))
+        A.residual(bt, x0, rt, n_levels=levels)
+        assert np.array_equal(rt.cpu().numpy(), b), res
+        rt = torch_cuda.full_like(bt, float("nan"))
+        A.residual(zt, xt, rt, n_levels=levels)
+        r = rt.cpu().numpy().astype(np.complex128)
+        assert np.all(np.isfinite(r)), res
+        has = scale > 0
+        assert np.all(r[~has] == 0), res                     # entries without terms are exactly zero
+        excess = np.maximum(np.abs(r - ref) - 2.0 ** -23 * np.abs(ref), 0.0)[has] / scale[has]
+        print("residual choice %d: worst error beyond the output rounding, in units of sum|terms|: %.2e"
+              % (res, float(excess.max())))
+        assert float(excess.max()) < 2.0 ** -30, res
