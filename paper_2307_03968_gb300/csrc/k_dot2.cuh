@@ -175,9 +175,6 @@ __device__ __forceinline__ cdf cxclose(const cxacc &c, float sigma)
 constexpr float GRID_MARGIN = 2.0f + 0x1p-10f;
 __device__ __forceinline__ float grid_sigma(float bound, float mb) { return pow2_ceil(GRID_MARGIN * bound * mb); }
 __device__ __forceinline__ void cx_start(cxacc &c, float sigma) { c = {{sigma, 0.f}, {sigma, 0.f}}; }
-// c += a * b for an FP32 or a double-float b
-__device__ __forceinline__ void cxstep_in(cxacc &c, float2 a, float2 b) { cxstep(c, a, b); }
-__device__ __forceinline__ void cxstep_in(cxacc &c, float2 a, const cdf &b) { cxstep_df(c, a, b); }
 // one step of a transposing warp reduction: of the pair (v[j], v[j + H]) this lane
 // keeps the upper one when its lane bit `mask` is set, and adds the partner lane's
 // copy of it; after the steps for masks M, M/2, ..., 1 over V values, each lane
@@ -203,8 +200,8 @@ __device__ __forceinline__ float warp_max(float v)
 
 // 1-norm bounds of a row-major rows x cols array (row stride ld): the largest row
 // sum and the largest column sum of |re| + |im|, in FP64 (warp-wide results)
-__device__ __forceinline__ void l1_bounds(const float2 *__restrict__ A, int rows, int cols, int ld, double &rmax, double &cmax,
-                          int lane)
+__device__ __forceinline__ void l1_bounds(const float2 *__restrict__ A, int rows, int cols, int ld, double &rmax,
+                                          double &cmax, int lane)
 {
     rmax = 0.0;
     for (int i = 0; i < rows; ++i) {

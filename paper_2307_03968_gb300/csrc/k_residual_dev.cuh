@@ -100,7 +100,7 @@ __device__ __forceinline__ void dense_item_c(const Item &it, const float2 *__res
 }
 
 // ---------------------------------------------------------------------------
-// Blocks of up to 64 x 64 (and rank <= 64) on common grids: every output sum of a
+// Blocks of up to 64 x 64 (dense, or low-rank of any rank) on common grids: every output sum of a
 // block side takes one sigma from the block's precomputed bound (k_item_bounds:
 // largest row / column 1-norm) and the largest input component, so the lanes'
 // grid parts add exactly in plain FP32 (k_dot2.cuh).  The warp covers the block
@@ -236,15 +236,8 @@ __device__ __forceinline__ void dense_item_g(const Item &it, float4 bnd, const f
               grid_sigma(bnd.y, mxi), part + it.pad + even_d(m), lane);
 }
 
-// Low-rank block U V of at most 64 x 64 (U^T k x m, V k x n, m, n padded even):
-// slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I), one pass over pairs
-// of rank rows (loaded one pair ahead).  A lane owns the rows / columns 2 lane,
-// 2 lane + 1 of both panels.  Both stages run on common grids.  Stage 1 (the rank-k
-// intermediates tp = U^T x_I, t = V x_J; bnd.x, bnd.y: largest rank-row 1-norms of
-// U^T and V): the 32-lane reductions add the grid parts exactly in plain FP32.
-// Stage 2 (the outputs; bnd.z, bnd.w: largest column 1-norms of U^T and V): the
-// leading part of each intermediate is a grid sum, at most half its grid's sigma,
-// which bounds the inputs, so each output is one chain over all rank rows.
+// the lane's two columns (i, i + 1) of the rank rows l0, l0 + 1 of U^T and V (zero
+// past the rank or the panel)
 __device__ __forceinline__ void lr_load(Pair<float> (&u)[2], Pair<float> (&v)[2], const float2 *__restrict__ UT,
                                         const float2 *__restrict__ V, int l0, int k, int m, int n, int i, bool iv,
                                         bool jv)
@@ -350,6 +343,15 @@ __device__ __forceinline__ void lr_single(const Pair<float> &u, const Pair<float
     cxstep_df(cj1, v.b, tpl);
 }
 
+// Low-rank block U V of at most 64 x 64 (U^T k x m, V k x n, m, n padded even):
+// slot rows (m) = U (V x_J), slot columns (n) = V^T (U^T x_I), one pass over pairs
+// of rank rows (loaded one pair ahead).  A lane owns the rows / columns 2 lane,
+// 2 lane + 1 of both panels.  Both stages run on common grids.  Stage 1 (the rank-k
+// intermediates tp = U^T x_I, t = V x_J; bnd.x, bnd.y: largest rank-row 1-norms of
+// U^T and V): the 32-lane reductions add the grid parts exactly in plain FP32.
+// Stage 2 (the outputs; bnd.z, bnd.w: largest column 1-norms of U^T and V): the
+// leading part of each intermediate is a grid sum, at most half its grid's sigma,
+// which bounds the inputs, so each output is one chain over all rank rows.
 __device__ __forceinline__ void lowrank_item_g(const Item &it, float4 bnd, const float2 *__restrict__ pool,
                                                const float2 *HM_XR x, cdf *HM_XR part, int lane)
 {
