@@ -4,18 +4,19 @@
 //
 // A work unit is one output cluster O of a level and one group of RG right-hand
 // sides (16, or 8 for calls with few right-hand sides, so that there are enough
-// units to balance).  The CTA walks every directed product into O (the stored blocks with O
-// as row cluster, and mirrored, those with O as column cluster; dense or
-// low-rank), in a fixed order, and keeps the sums in registers as double-float
-// complex numbers.  Each directed product is summed, per output row and right-hand
-// side, as one error-free chain on a common grid (k_dot2.cuh: every product rounded
-// exactly onto a power-of-two grid whose sigma comes from the product's
-// precomputed bound, k_prod_bounds, and the input's largest component; the
-// remainders summed apart), folded once into the double-float sum with a
-// compensated addition.  Thread t of the RT-thread CTA owns output row t % 64 and
-// the right-hand sides QN (t / 64) .. + QN - 1 of the group, QN = RG / (RT / 64).  The unit's sums are stored once, in FP64, into the level's
-// [RHS][pN] array: no partial slots, no atomics, and the result is independent
-// of scheduling.  k_gather_own then forms b - (D x + sum over levels) in FP64.
+// units to balance).  The CTA walks every directed product into O (the stored
+// blocks with O as row cluster, and mirrored, those with O as column cluster;
+// dense or low-rank), in a fixed order, and keeps the sums in registers as
+// double-float complex numbers.  Each directed product is summed, per output row
+// and right-hand side, as one error-free chain on a common grid (k_dot2.cuh: every
+// product rounded exactly onto a power-of-two grid whose sigma comes from the
+// product's precomputed bound, k_prod_bounds, and the input's largest component;
+// the remainders summed apart), folded once into the double-float sum with a
+// compensated addition.  Thread t of the RT-thread CTA (RT = 128 or 256) owns
+// output row t % 64 and the right-hand sides QN (t / 64) .. + QN - 1 of the group,
+// QN = RG / (RT / 64).  The unit's sums are stored once, in FP64, into the level's
+// [RHS][pN] array: no partial slots, no atomics, and the result is independent of
+// scheduling.  k_gather_own then forms b - (D x + sum over levels) in FP64.
 //
 // Shared-memory staging keeps every compute read consecutive along the output
 // row: a dense block is stored K-major (element (K index j, output i) at
@@ -31,7 +32,6 @@ namespace {
 
 using namespace kc;
 using namespace dot2;
-// CTA of RT threads (128 or 256): 64 output rows x RT / 64 parts of the unit's right-hand sides
 constexpr int RGMAX = 16;        // right-hand sides per unit (at most)
 constexpr int BS = 65;           // float2 stride of a staged K row of a block (odd: conflict-free staging)
 constexpr int WS = 33;           // float2 stride of a staged K row of W (rank <= 32)
