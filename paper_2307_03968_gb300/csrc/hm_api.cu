@@ -395,6 +395,9 @@ struct SolveCtx {
     // a phase; units = the CTAs the widest phase can use (a leaf per CTA, a block per warp)
     std::vector<Phase> *rec = nullptr;
     int64_t units = 0;
+    // a vector r whose first series step y = D^{-1} r (into Y[1]) a fused kernel has already
+    // done (the permutation of b, the residual gather): the next P / Pflat on r skips it
+    const void *y_ready = nullptr;
 };
 
 static Phase phase(int op, int nrhs)
@@ -568,6 +571,12 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
     c.bytes += level_bytes(c.h, lev, c.fp64) * c.nrhs;
 }
 
+// bytes a leaf update streams (D^{-1}, and the y / z / out vectors)
+static int64_t leaf_update_bytes(const SolveCtx &c)
+{
+    return c.h->dinv_elems * (int64_t)elem_size(c.fp64) + 3 * (int64_t)c.vbytes;
+}
+
 static void leaf_update(SolveCtx &c, const void *y, void *zin, void *out, bool zero_in)
 {
     if (c.rec) {
@@ -580,7 +589,7 @@ static void leaf_update(SolveCtx &c, const void *y, void *zin, void *out, bool z
         launch_leaf_update(c.h, y, zin, out, c.nrhs, zero_in, c.fp64, c.s);
     }
     c.launches++;
-    c.bytes += c.h->dinv_elems * (int64_t)elem_size(c.fp64) + 3 * (int64_t)c.vbytes;
+    c.bytes += leaf_update_bytes(c);
 }
 
 static void copy_vec(SolveCtx &c, void *dst, const void *src)
@@ -605,7 +614,8 @@ static void P(SolveCtx &c, int level, const void *r, void *out)
     }
     if (level == 1) {
         void *Y = c.Y[1], *X = c.X[1], *Z = c.Z[1];
-        leaf_update(c, nullptr, const_cast<void *>(r), Y, false);     // y = D^{-1} r
+        if (c.y_ready == r) c.y_ready = nullptr;                       // y = D^{-1} r done with r
+        else leaf_update(c, nullptr, const_cast<void *>(r), Y, false); // y = D^{-1} r
         const void *cur = Y;
         for (int j = 1; j <= c.K; ++j) {
             apply_level(c, 1, cur, Z);                                 // z = M_1 x_{j-1}
@@ -634,7 +644,8 @@ static void P(SolveCtx &c, int level, const void *r, void *out)
 static void Pflat(SolveCtx &c, const void *r, void *out)
 {
     void *Y = c.Y[1], *X = c.X[1], *Z = c.Z[1];
-    leaf_update(c, nullptr, const_cast<void *>(r), Y, false);
+    if (c.y_ready == r) c.y_ready = nullptr;                           // y = D^{-1} r done with r
+    else leaf_update(c, nullptr, const_cast<void *>(r), Y, false);
     const void *cur = Y;
     for (int j = 1; j <= c.K; ++j) {
         for (int lev = 1; lev <= c.m; ++lev) apply_level(c, lev, cur, Z);
@@ -738,7 +749,11 @@ static int clamp_levels(hm_matrix h, int n_levels)
 // out = b - A_m x (with |r|^2, |b|^2 per column into norms) when b is given, else
 // out = A_m x; complex64 blocks, FP64 products and sums, deterministic order:
 // every block writes its double-float partial slots, then each leaf gathers its slots.
-static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *out, double *norms)
+// y_next: when given, the series step that follows (y = D^{-1} out into Y[1]) is done in
+// the gather's pass where that applies (one chunk of partial slots, launched), and
+// c.y_ready tells the next P / Pflat so
+static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *out, double *norms,
+                       float2 *y_next = nullptr)
 {
     hm_matrix h = c.h;
     if (!c.rec && c.res_rb == RB_OWN && h->ws.d_own &&
@@ -793,8 +808,14 @@ static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *
             launch_apply_items_partials(h, it->second, x, h->ws.d_part, h->partial_elems, nr, c.s, c.res_rb);
             c.launches++;
         }
-        launch_gather_acc64(h, x, c.m, h->ws.d_part, h->partial_elems, bt ? bt + (int64_t)r0 * h->pN : nullptr,
-                            out + (int64_t)r0 * h->pN, norms ? norms + 2 * r0 : nullptr, nr, c.s);
+        if (y_next && nr == c.nrhs) {
+            launch_gather_leaf_update(h, x, c.m, h->ws.d_part, h->partial_elems, bt, out, norms, y_next, nr, c.s);
+            c.bytes += leaf_update_bytes(c);
+            c.y_ready = out;
+        } else {
+            launch_gather_acc64(h, x, c.m, h->ws.d_part, h->partial_elems, bt ? bt + (int64_t)r0 * h->pN : nullptr,
+                                out + (int64_t)r0 * h->pN, norms ? norms + 2 * r0 : nullptr, nr, c.s);
+        }
         c.launches++;
     }
 }
@@ -1016,12 +1037,22 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
     double *norms = o->refine ? h->ws.d_acc64 : nullptr;
     // the solve's steps, launched or recorded (the one-launch solve) through c
     auto steps = [&](SolveCtx &cc) {
-        permute_in_vec(cc, b, ldb, bt);
+        // complex64, launched: the permutation of b and the series' first step in one pass
+        const bool fuse = !cc.rec && !cc.fp64;
+        if (fuse) {
+            launch_permute_leaf(h, (const float2 *)b, ldb, (float2 *)bt, (float2 *)cc.Y[1], nrhs, cc.s);
+            cc.launches++;
+            cc.bytes += leaf_update_bytes(cc);
+            cc.y_ready = bt;
+        } else {
+            permute_in_vec(cc, b, ldb, bt);
+        }
         if (o->nested) P(cc, cc.m, bt, xt);
         else Pflat(cc, bt, xt);
         if (o->refine) {
             zero_vec(cc, norms, 2 * sizeof(double) * nrhs);
-            residual64(cc, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
+            residual64(cc, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms,
+                       fuse ? (float2 *)cc.Y[1] : nullptr);
             if (o->nested) P(cc, cc.m, rt, dx);
             else Pflat(cc, rt, dx);
             if (!cc.rec && !info) {   // add, check and un-permute in one kernel

@@ -8,6 +8,7 @@
 // leaf's slots in a fixed order with compensated additions, adds D_I x_I (Dot2)
 // and forms b - A x in FP64.
 #include "k_residual_dev.cuh"
+#include "k_solve_dev.cuh"
 
 namespace hm {
 namespace {
@@ -72,7 +73,38 @@ k_gather_acc64(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict_
                 pstride, b, out, norms, acc_s, reinterpret_cast<float2 *>(gsm));
 }
 
+// The gather, then the next series step of the refinement in the same CTA: out = b - acc
+// for the leaf (as k_gather_acc64), then y = D_i^{-1} out_i (the first step of the
+// correction's series) from the out_i this CTA just wrote.
+__global__ void __launch_bounds__(GW * 32)
+k_gather_leaf_update(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
+                     const float2 *__restrict__ self32, const float2 *__restrict__ dinv32, const float2 *__restrict__ x,
+                     int64_t ld, const int64_t *__restrict__ csr_off, int csr_stride, int m,
+                     const int64_t *__restrict__ csr_idx, const cdf *__restrict__ part, int64_t pstride,
+                     const float2 *__restrict__ b, float2 *out, double *norms, float2 *y)
+{
+    __shared__ cdf acc_s[GW][64];
+    __shared__ float2 lpart[8][64];
+    extern __shared__ __align__(16) unsigned char gsm[];
+    gather_leaf(blockIdx.x, blockIdx.y, pleaf_off, dinv_off, self32, x, ld, csr_off, csr_stride, m, csr_idx, part,
+                pstride, b, out, norms, acc_s, reinterpret_cast<float2 *>(gsm));
+    __syncthreads();                                       // this CTA's writes of out_i, read back below
+    leaf_update_leaf<float>(blockIdx.x, blockIdx.y, pleaf_off, dinv_off, dinv32, nullptr, out, y, ld, 0,
+                            reinterpret_cast<float2 *>(gsm), lpart);
+}
+
 } // namespace
+
+void launch_gather_leaf_update(hm_matrix h, const float2 *x, int m, const cdf *part, int64_t pstride,
+                               const float2 *b, float2 *out, double *norms, float2 *y, int nrhs, cudaStream_t s)
+{
+    dim3 grid((unsigned)h->n_leaves, (unsigned)nrhs);
+    int64_t maxnp = 1;
+    for (int64_t i = 0; i < h->n_leaves; ++i) maxnp = std::max<int64_t>(maxnp, h->pleaf_off[i + 1] - h->pleaf_off[i]);
+    k_gather_leaf_update<<<grid, GW * 32, sizeof(float2) * (size_t)maxnp, s>>>(
+        h->d_pleaf_off, h->d_dinv_off, h->d_self32, h->d_dinv32, x, h->pN, h->d_csr_off, h->n_levels + 1, m,
+        h->d_csr_idx, part, pstride, b, out, norms, y);
+}
 
 void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, cdf *part, int64_t pstride,
                                  int nrhs, cudaStream_t s, int rb)

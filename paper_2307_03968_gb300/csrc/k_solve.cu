@@ -79,6 +79,27 @@ __global__ void k_permute_in(const C *__restrict__ b, int64_t ldb, C *__restrict
     }
 }
 
+// Per leaf (blockIdx.x) and right-hand side (blockIdx.y), complex64: the leaf's rows
+// of bt = P b (0 at pads), then y = D_i^{-1} bt_i (the first step of the series, eq. 12
+// applied to the permuted right-hand side) in the same CTA.
+__global__ void __launch_bounds__(256)
+k_permute_leaf(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
+               const float2 *__restrict__ dinv, const int32_t *__restrict__ pperm, const float2 *__restrict__ b,
+               int64_t ldb, float2 *bt, float2 *y, int64_t pN)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float2 part[8][64];
+    const int leaf = blockIdx.x, r = blockIdx.y;
+    const int o = pleaf_off[leaf], np = pleaf_off[leaf + 1] - o;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const int32_t src = pperm[o + j];
+        bt[r * pN + o + j] = src >= 0 ? b[r * ldb + src] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();                                       // this CTA's writes of bt_i, read back below
+    leaf_update_leaf<float>(leaf, r, pleaf_off, dinv_off, dinv, nullptr, bt, y, pN, 0,
+                            reinterpret_cast<float2 *>(smem_raw), part);
+}
+
 template <class C>
 __global__ void k_permute_out(const C *__restrict__ xt, int64_t pN, C *__restrict__ x, int64_t ldx,
                               const int32_t *__restrict__ pperm, int nrhs)
@@ -191,6 +212,13 @@ void launch_apply_self_f32(hm_matrix h, const float2 *x, float2 *acc, int nrhs, 
     dim3 grid((unsigned)h->n_leaves, (unsigned)nrhs);
     k_apply_self<float><<<grid, 256, max_padded_leaf(h) * sizeof(float2), s>>>(h->d_pleaf_off, h->d_dinv_off,
                                                                               h->d_self32, x, acc, h->pN);
+}
+
+void launch_permute_leaf(hm_matrix h, const float2 *b, int64_t ldb, float2 *bt, float2 *y, int nrhs, cudaStream_t s)
+{
+    dim3 grid((unsigned)h->n_leaves, (unsigned)nrhs);
+    k_permute_leaf<<<grid, 256, max_padded_leaf(h) * sizeof(float2), s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_dinv32,
+                                                                          h->d_pperm, b, ldb, bt, y, h->pN);
 }
 
 void launch_leaf_update(hm_matrix h, const void *y, void *zin, void *out, int nrhs, bool zero_in, bool fp64,
