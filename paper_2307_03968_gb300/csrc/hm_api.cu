@@ -398,6 +398,13 @@ struct SolveCtx {
     // a vector r whose first series step y = D^{-1} r (into Y[1]) a fused kernel has already
     // done (the permutation of b, the residual gather): the next P / Pflat on r skips it
     const void *y_ready = nullptr;
+    // the end of the solve fused into the series step that writes fin_target (a leaf
+    // update, launched): x = P^T (fin_base + fin_target) or P^T fin_target; fin_done when it ran
+    const void *fin_target = nullptr;
+    const float2 *fin_base = nullptr;
+    float2 *fin_x = nullptr;
+    int64_t fin_ldx = 0;
+    bool fin_done = false;
 };
 
 static Phase phase(int op, int nrhs)
@@ -604,6 +611,20 @@ static void copy_vec(SolveCtx &c, void *dst, const void *src)
     cudaMemcpyAsync(dst, src, c.vbytes, cudaMemcpyDeviceToDevice, c.s);
 }
 
+// x_j = y - D^{-1} z into dst (z cleared), fused with the end of the solve when dst is its target
+static void last_leaf_update(SolveCtx &c, const void *Y, void *Z, void *dst)
+{
+    if (!c.rec && !c.fp64 && c.fin_target == dst) {
+        launch_leaf_finish(c.h, (const float2 *)Y, (float2 *)Z, (float2 *)dst, c.fin_base, c.fin_x, c.fin_ldx, c.nrhs,
+                           c.s);
+        c.launches++;
+        c.bytes += leaf_update_bytes(c);
+        c.fin_done = true;
+        return;
+    }
+    leaf_update(c, Y, Z, dst, true);
+}
+
 // P_level(r) -> out (eq. 19 nested recursion); out must not alias r.
 // Invariant: Z[1] is all zero on entry and on exit.
 static void P(SolveCtx &c, int level, const void *r, void *out)
@@ -620,7 +641,7 @@ static void P(SolveCtx &c, int level, const void *r, void *out)
         for (int j = 1; j <= c.K; ++j) {
             apply_level(c, 1, cur, Z);                                 // z = M_1 x_{j-1}
             void *dst = (j == c.K) ? out : X;
-            leaf_update(c, Y, Z, dst, true);                           // x_j = y - D^{-1} z
+            last_leaf_update(c, Y, Z, dst);                            // x_j = y - D^{-1} z
             cur = dst;
         }
         if (c.K == 0) copy_vec(c, out, Y);
@@ -650,7 +671,7 @@ static void Pflat(SolveCtx &c, const void *r, void *out)
     for (int j = 1; j <= c.K; ++j) {
         for (int lev = 1; lev <= c.m; ++lev) apply_level(c, lev, cur, Z);
         void *dst = (j == c.K) ? out : X;
-        leaf_update(c, Y, Z, dst, true);
+        last_leaf_update(c, Y, Z, dst);
         cur = dst;
     }
     if (c.K == 0) copy_vec(c, out, Y);
@@ -1047,14 +1068,29 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
         } else {
             permute_in_vec(cc, b, ldb, bt);
         }
+        // the end of the solve (add, check, un-permute) goes with the last leaf update where one
+        // writes the solve's last vector (leaf-level nested, or flat), else as its own pass
+        auto finish_with = [&](const void *target, const float2 *base) {
+            if (!fuse || info) return;
+            cc.fin_target = target;
+            cc.fin_base = base;
+            cc.fin_x = (float2 *)x;
+            cc.fin_ldx = ldx;
+            cc.fin_done = false;
+        };
+        if (!o->refine) finish_with(xt, nullptr);
         if (o->nested) P(cc, cc.m, bt, xt);
         else Pflat(cc, bt, xt);
+        cc.fin_target = nullptr;
         if (o->refine) {
             zero_vec(cc, norms, 2 * sizeof(double) * nrhs);
             residual64(cc, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms,
                        fuse ? (float2 *)cc.Y[1] : nullptr);
+            finish_with(dx, (const float2 *)xt);
             if (o->nested) P(cc, cc.m, rt, dx);
             else Pflat(cc, rt, dx);
+            cc.fin_target = nullptr;
+            if (cc.fin_done) return;
             if (!cc.rec && !info) {   // add, check and un-permute in one kernel
                 launch_finish((const float2 *)xt, (const float2 *)dx, h->pN, (float2 *)x, ldx, h->d_pperm, nrhs,
                               h->d_status, cc.s);
@@ -1067,6 +1103,7 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
                 residual64(cc, (const float2 *)xt, (const float2 *)bt, (float2 *)rt, norms);
             }
         } else if (!cc.rec && !cc.fp64) {
+            if (cc.fin_done) return;
             launch_finish((const float2 *)xt, nullptr, h->pN, (float2 *)x, ldx, h->d_pperm, nrhs, h->d_status, cc.s);
             cc.launches++;
             return;

@@ -354,6 +354,10 @@ void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const dot2::cdf *p
                          const float2 *b, float2 *out, double *norms, int nrhs, cudaStream_t s);
 void launch_apply_self_f32(hm_matrix h, const float2 *x, float2 *acc, int nrhs, cudaStream_t s);
 // per leaf: out = (y ? y - Dinv zin : Dinv zin); if zero_in, zin is cleared afterwards
+// the last series step out = y - D^{-1} z (z cleared) and the end of the solve (v = base + out
+// or out, finiteness into the status word, x = P^T v) in one pass per leaf (complex64; k_solve.cu)
+void launch_leaf_finish(hm_matrix h, const float2 *y, float2 *z, float2 *out, const float2 *base, float2 *x,
+                        int64_t ldx, int nrhs, cudaStream_t s);
 // bt = P b and y = D^{-1} bt in one pass per leaf (complex64; k_solve.cu)
 void launch_permute_leaf(hm_matrix h, const float2 *b, int64_t ldb, float2 *bt, float2 *y, int nrhs, cudaStream_t s);
 // the residual gather (out = b - acc, norms) and y = D^{-1} out in one pass per leaf (k_residual.cu)

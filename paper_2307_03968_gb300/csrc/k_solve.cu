@@ -156,6 +156,34 @@ __global__ void k_finish(const float2 *__restrict__ xt, const float2 *__restrict
     if (bad) atomicCAS(status, 0, (int)HM_ERR_DIVERGED);
 }
 
+// The last series step of a complex64 solve and the end of the solve, per leaf
+// (blockIdx.x) and right-hand side (blockIdx.y): out_i = y_i - D_i^{-1} z_i (z_i cleared),
+// then v = (base ? base_i + out_i : out_i), non-finite v -> HM_ERR_DIVERGED, and
+// x[r * ldx + pperm[p]] = v (k_leaf_update followed by k_finish, in one CTA).
+__global__ void __launch_bounds__(256)
+k_leaf_finish(const int32_t *__restrict__ pleaf_off, const int64_t *__restrict__ dinv_off,
+              const float2 *__restrict__ dinv, const float2 *y, float2 *z, float2 *out, const float2 *base,
+              int64_t pN, float2 *__restrict__ x, int64_t ldx, const int32_t *__restrict__ pperm, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float2 part[8][64];
+    const int leaf = blockIdx.x, r = blockIdx.y;
+    leaf_update_leaf<float>(leaf, r, pleaf_off, dinv_off, dinv, y, z, out, pN, 1,
+                            reinterpret_cast<float2 *>(smem_raw), part);
+    __syncthreads();                                       // this CTA's writes of out_i, read back below
+    const int o = pleaf_off[leaf], np = pleaf_off[leaf + 1] - o;
+    bool bad = false;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const int64_t g = r * pN + o + j;
+        float2 v = out[g];
+        if (base) v = cadd(v, base[g]);
+        bad |= !isfinite(v.x) || !isfinite(v.y);
+        const int32_t dst = pperm[o + j];
+        if (dst >= 0) x[r * ldx + dst] = v;
+    }
+    if (bad) atomicCAS(status, 0, (int)HM_ERR_DIVERGED);
+}
+
 __global__ void k_f32_to_f64(const float2 *a, double2 *b, int64_t n)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -255,6 +283,15 @@ void launch_check_finite(const void *x, int64_t n, bool fp64, int *status, cudaS
     const int g = grid_for(n);
     if (fp64) k_check_finite<double2><<<g, 256, 0, s>>>((const double2 *)x, n, status);
     else k_check_finite<float2><<<g, 256, 0, s>>>((const float2 *)x, n, status);
+}
+
+void launch_leaf_finish(hm_matrix h, const float2 *y, float2 *z, float2 *out, const float2 *base, float2 *x,
+                        int64_t ldx, int nrhs, cudaStream_t s)
+{
+    dim3 grid((unsigned)h->n_leaves, (unsigned)nrhs);
+    k_leaf_finish<<<grid, 256, max_padded_leaf(h) * sizeof(float2), s>>>(h->d_pleaf_off, h->d_dinv_off, h->d_dinv32, y,
+                                                                         z, out, base, h->pN, x, ldx, h->d_pperm,
+                                                                         h->d_status);
 }
 
 void launch_finish(const float2 *xt, const float2 *dx, int64_t pN, float2 *x, int64_t ldx, const int32_t *pperm,
