@@ -70,7 +70,7 @@ __device__ __forceinline__ void stage_x(float2 *xs, float *mx, const float2 *__r
 __device__ __forceinline__ float x_max(const float *mx, int q) { return fmaxf(mx[2 * q], mx[2 * q + 1]); }
 
 template <int RG, int RT>
-__global__ void __launch_bounds__(RT, RT == 128 ? 4 : 3)
+__global__ void __launch_bounds__(RT, 4)
 k_resid_own(const TcUnit *__restrict__ units, int n_units, const TcProd *__restrict__ prods,
             const float2 *__restrict__ pbnd, const float2 *__restrict__ pool, const float2 *__restrict__ x,
             int64_t ldx, int nrhs, double2 *__restrict__ own, int64_t ldo)
@@ -294,13 +294,14 @@ void launch_resid_own(hm_matrix h, const LevelList &L, const float2 *x, double2 
         attr = true;
     }
     // groups of 8 right-hand sides up to 32 of them, so that small calls still have enough units.
-    // CTAs of 256 threads (4 RHS per thread, three CTAs of ~50 KB per SM) up to 128 RHS, of 128
-    // threads (8 RHS per thread, four CTAs per SM) above: measured on the 30,720-unknown sphere,
-    // 0.540 / 0.371 / 0.388 ms per RHS at 16 / 64 / 181 RHS against 0.587 / 0.406 / 0.378
+    // four CTAs of ~50 KB per SM: of 256 threads (4 RHS per thread, 64 registers) up to 128 RHS,
+    // of 128 threads (8 RHS per thread) above: measured on the 30,720-unknown sphere, 0.499 /
+    // 0.365 ms per RHS at 16 / 64 RHS against 0.587 / 0.406 for 128 threads, and 0.382 against
+    // 0.386 for 256 threads at 181
     const int rg = nrhs <= 32 ? 8 : 16;
     const bool wide = nrhs <= 128;
     const int64_t units = L.n_rcu * (int64_t)((nrhs + rg - 1) / rg);
-    int64_t g = (wide ? 3 : 4) * (int64_t)(h->num_sms > 0 ? h->num_sms : 1);
+    int64_t g = 4 * (int64_t)(h->num_sms > 0 ? h->num_sms : 1);
     if (g > units) g = units;
     auto go = [&](auto kern, int rt) {
         kern<<<(unsigned)g, rt, SMEM, s>>>(L.d_rcu, (int)L.n_rcu, L.d_rcp, L.d_rcb, h->d_pool32, x, h->pN, nrhs, own,
