@@ -517,7 +517,7 @@ def product_roofline(A, b, x, opts, nrhs, Kp, sm_max):
         bound, unit, rpeak = "tensor", "TFLOP/s", tf32 / 3.0
         rkind = ("measured sustained bf16 %.1f TFLOP/s x 1.1/2.25 (TF32) / 3 (3xTF32 products)" % bf16_s
                  if bf16_s else "fallback 1.7 PFLOP/s bf16 sustained x 1.1/2.25 / 3")
-        kernel = ("k_split_x + k_apply_tc (tcgen05 kind::tf32, 3xTF32; units of <= 16 K chunks; blocks <= 64 x 64, "
+        kernel = ("k_split_x + k_apply_tc (tcgen05 kind::tf32, 3xTF32; units of <= 64 K chunks; blocks <= 64 x 64, "
                   "rank <= 32) "
                   "+ k_apply_items for larger blocks (k_mrhs_tc.cu, k_product.cu)")
     elif flops_per_launch / (alu_peak * 1e12) > per_launch_bytes / (peak * 1e9):

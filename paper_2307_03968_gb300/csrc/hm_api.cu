@@ -99,7 +99,8 @@ static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vec
     // a little on every MMA it adds into a large running sum (measured: the product's
     // error grows in proportion to the chunks summed in tensor memory, 7.4e-6 relative
     // at 256 chunks, 1.9e-6 at 64, 5.4e-7 at 16 on 60-unknown leaves), so a unit's sum
-    // leaves tensor memory (added into z in FP32) every TC_UNIT_CHUNKS chunks.
+    // leaves tensor memory (added into z in FP32) every TC_UNIT_CHUNKS chunks (64: the
+    // 181-RHS sweep of the 30,720-unknown sphere within 2.3e-5 of the oracle).
     (void)total;
     (void)num_sms;
     const int64_t cap = TC_UNIT_CHUNKS;

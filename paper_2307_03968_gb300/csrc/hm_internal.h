@@ -34,7 +34,7 @@ constexpr int RB_TC = 1016;         // product choice: tensor-core products of t
 constexpr int TC_MAX_DIM = MRHS_MAX_DIM;    // the tensor-core product takes the same small items
 constexpr int TC_MAX_RANK = MRHS_MAX_RANK;
 constexpr int TC_MIN_RHS = 32;      // the autotuner times the tensor-core product from this many RHS on
-constexpr int TC_UNIT_CHUNKS = 16;  // K chunks (of 8) a tensor-core work unit sums in tensor memory
+constexpr int TC_UNIT_CHUNKS = 64;  // K chunks (of 8) a tensor-core work unit sums in tensor memory
 constexpr int RB_OWN = 1017;        // residual choice: owner-computes FP64-class products (levels of small items)
 
 // Double-float numbers of the FP64-class residual (hi + lo, |lo| a few ulps of hi at
