@@ -45,14 +45,9 @@ template <class T> static hm_status upload(hm_matrix h, T **dst, const std::vect
     return HM_OK;
 }
 
-// The tensor-core product's work list: every small item gives two directed
-// products (into its row cluster and, mirrored, into its column cluster), grouped
-// by output cluster; a cluster's products are cut into units of at most `cap`
-// K chunks (units of one cluster add into z with atomics), units sorted by cost,
-// largest first, so that the persistent CTAs taking units in turn stay balanced.
-static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vector<TcUnit> &units,
-                           std::vector<TcProd> &prods, std::vector<int2> &xch, std::vector<TcUnit> &runits,
-                           std::vector<TcProd> &rprods)
+// The directed products of the small items: every item gives two (into its row
+// cluster and, mirrored, into its column cluster), grouped by output cluster.
+static std::map<int32_t, std::vector<TcProd>> directed_products(const std::vector<Item> &small)
 {
     std::map<int32_t, std::vector<TcProd>> by_out;
     auto add = [&](int32_t out0, const TcProd &p) {
@@ -70,78 +65,159 @@ static void build_tc_lists(const std::vector<Item> &small, int num_sms, std::vec
             add(it.col0, TcProd{uoff, voff, it.row0, it.m, it.k, lm, ln, 0, it.n, 0});   // V^T (U^T x_I)
         }
     }
+    return by_out;
+}
+
+// The owner-computes residual's list: one unit per output cluster (every output row
+// summed by one CTA in a fixed order), largest first.
+static void build_owner_lists(const std::map<int32_t, std::vector<TcProd>> &by_out, std::vector<TcUnit> &runits,
+                              std::vector<TcProd> &rprods)
+{
     auto cost = [](const TcProd &p) {
         return (int64_t)((p.klen + 7) / 8) + (p.rank > 0 ? (int64_t)((p.rank + 7) / 8) : 0);
     };
-    int64_t total = 0;
-    for (auto &kv : by_out)
-        for (const TcProd &p : kv.second) total += cost(p);
-    // the residual's units: one per output cluster (every output row summed by one CTA), largest first
-    {
-        struct R { TcUnit u; int64_t c; const std::vector<TcProd> *p; };
-        std::vector<R> rs;
-        for (auto &kv : by_out) {
-            R r{TcUnit{kv.first, 0, 0, 0}, 0, &kv.second};
-            for (const TcProd &p : kv.second) { r.u.mlen = std::max(r.u.mlen, p.olen); r.c += cost(p); }
-            rs.push_back(r);
-        }
-        std::stable_sort(rs.begin(), rs.end(), [](const R &a, const R &b) { return a.c > b.c; });
-        runits.clear();
-        rprods.clear();
-        for (R &r : rs) {
-            r.u.p0 = (int32_t)rprods.size();
-            rprods.insert(rprods.end(), r.p->begin(), r.p->end());
-            r.u.p1 = (int32_t)rprods.size();
-            runits.push_back(r.u);
-        }
+    struct R { TcUnit u; int64_t c; const std::vector<TcProd> *p; };
+    std::vector<R> rs;
+    for (auto &kv : by_out) {
+        R r{TcUnit{kv.first, 0, 0, 0}, 0, &kv.second};
+        for (const TcProd &p : kv.second) { r.u.mlen = std::max(r.u.mlen, p.olen); r.c += cost(p); }
+        rs.push_back(r);
     }
-    // Units of at most TC_UNIT_CHUNKS K chunks: the tensor cores' FP32 accumulator loses
-    // a little on every MMA it adds into a large running sum (measured: the product's
-    // error grows in proportion to the chunks summed in tensor memory, 7.4e-6 relative
-    // at 256 chunks, 1.9e-6 at 64, 5.4e-7 at 16 on 60-unknown leaves), so a unit's sum
-    // leaves tensor memory (added into z in FP32) every TC_UNIT_CHUNKS chunks (64: the
-    // 181-RHS sweep of the 30,720-unknown sphere within 2.3e-5 of the oracle).
-    (void)total;
-    (void)num_sms;
+    std::stable_sort(rs.begin(), rs.end(), [](const R &a, const R &b) { return a.c > b.c; });
+    runits.clear();
+    rprods.clear();
+    for (R &r : rs) {
+        r.u.p0 = (int32_t)rprods.size();
+        rprods.insert(rprods.end(), r.p->begin(), r.p->end());
+        r.u.p1 = (int32_t)rprods.size();
+        runits.push_back(r.u);
+    }
+}
+
+// The tensor-core product's lists (k_mrhs_tc.cu), two launches.
+//  - Stage 1 of every low-rank directed product, T = W X_in (W = V forward, U^T mirrored),
+//    is batched over the products that share an input cluster: each product takes
+//    roundup8(rank) stacked rows (rows past its rank are zero) and as many T chunks, and a
+//    batch stacks up to 64 rows, so one K chunk of split x feeds MMAs of N up to 128.
+//  - The second launch takes, per output cluster, the dense products and the second
+//    stages Y T (Y = U forward, V^T mirrored; T read back by chunk), cut into units of at
+//    most TC_UNIT_CHUNKS K chunks (units of one cluster add into z with atomics) and sorted
+//    by cost, largest first, so that the persistent CTAs taking units in turn stay balanced.
+// Returns false when a list would break an index bound the kernels rely on.
+struct TcLists {
+    std::vector<TcUnit> units;
+    std::vector<TcOp> ops;
+    std::vector<int2> xch;
+    std::vector<TcBatch> batches;
+    std::vector<int64_t> rows;
+    std::vector<int32_t> tchunks;
+    int64_t n_tchunk = 0;
+};
+static bool build_tc_lists(const std::map<int32_t, std::vector<TcProd>> &by_out, TcLists &T)
+{
+    // K chunks of the input clusters (each cluster's longest input length)
+    std::map<int32_t, int32_t> in_len;
+    for (auto &kv : by_out)
+        for (const TcProd &p : kv.second) in_len[p.in0] = std::max(in_len[p.in0], p.klen);
+    std::map<int32_t, int32_t> in_g0;
+    T.xch.clear();
+    for (auto &kv : in_len) {
+        in_g0[kv.first] = (int32_t)T.xch.size();
+        for (int32_t c = 0; c < kv.second; c += 8) T.xch.push_back(make_int2(kv.first + c, std::min(8, kv.second - c)));
+    }
+    // stage-1 jobs by (input cluster, K length), each with its first T chunk
+    struct Job { int64_t w_off; int32_t w_ld, rank; int64_t t0; };
+    std::map<std::pair<int32_t, int32_t>, std::vector<Job>> by_in;
+    T.n_tchunk = 0;
+    // second-launch operations per output cluster
+    auto chunks = [](int32_t klen) { return (int64_t)((klen + 7) / 8); };
     const int64_t cap = TC_UNIT_CHUNKS;
-    struct U { TcUnit u; int64_t c; std::vector<TcProd> p; };
+    struct U { TcUnit u; int64_t c; std::vector<TcOp> p; };
     std::vector<U> us;
     for (auto &kv : by_out) {
         int32_t mlen = 0;
         for (const TcProd &p : kv.second) mlen = std::max(mlen, p.olen);
         U cur{TcUnit{kv.first, mlen, 0, 0}, 0, {}};
         for (const TcProd &p : kv.second) {
-            if (cur.c > 0 && cur.c + cost(p) > cap) {
+            TcOp op{};
+            op.olen = p.olen;
+            if (p.rank == 0) {
+                op.src = p.b_off;
+                op.kind = p.trans ? 1 : 0;
+                op.klen = p.klen;
+                op.ld = p.b_ld;
+                op.xg0 = in_g0[p.in0];
+            } else {
+                op.src = p.y_off;
+                op.t0 = T.n_tchunk;
+                op.kind = 2;
+                op.klen = p.rank;
+                op.ld = p.y_ld;
+                by_in[{p.in0, p.klen}].push_back(Job{p.b_off, p.b_ld, p.rank, T.n_tchunk});
+                T.n_tchunk += chunks(p.rank);
+            }
+            // Units of at most TC_UNIT_CHUNKS K chunks: the tensor cores' FP32 accumulator loses
+            // a little on every MMA it adds into a large running sum (measured: the product's
+            // error grows in proportion to the chunks summed in tensor memory, 7.4e-6 relative
+            // at 256 chunks, 1.9e-6 at 64, 5.4e-7 at 16 on 60-unknown leaves), so a unit's sum
+            // leaves tensor memory (added into z in FP32) every TC_UNIT_CHUNKS chunks.
+            if (cur.c > 0 && cur.c + chunks(op.klen) > cap) {
                 us.push_back(cur);
                 cur.c = 0;
                 cur.p.clear();
             }
-            cur.p.push_back(p);
-            cur.c += cost(p);
+            cur.p.push_back(op);
+            cur.c += chunks(op.klen);
         }
         if (!cur.p.empty()) us.push_back(cur);
     }
     std::stable_sort(us.begin(), us.end(), [](const U &a, const U &b) { return a.c > b.c; });
-    // K chunks of the input clusters (each cluster's longest input length)
-    std::map<int32_t, int32_t> in_len;
-    for (const U &x : us)
-        for (const TcProd &p : x.p) in_len[p.in0] = std::max(in_len[p.in0], p.klen);
-    std::map<int32_t, int32_t> in_g0;
-    xch.clear();
-    for (auto &kv : in_len) {
-        in_g0[kv.first] = (int32_t)xch.size();
-        for (int32_t c = 0; c < kv.second; c += 8) xch.push_back(make_int2(kv.first + c, std::min(8, kv.second - c)));
-    }
-    for (U &x : us)
-        for (TcProd &p : x.p) p.xg0 = in_g0[p.in0];
-    units.clear();
-    prods.clear();
+    T.units.clear();
+    T.ops.clear();
     for (U &x : us) {
-        x.u.p0 = (int32_t)prods.size();
-        prods.insert(prods.end(), x.p.begin(), x.p.end());
-        x.u.p1 = (int32_t)prods.size();
-        units.push_back(x.u);
+        x.u.p0 = (int32_t)T.ops.size();
+        T.ops.insert(T.ops.end(), x.p.begin(), x.p.end());
+        x.u.p1 = (int32_t)T.ops.size();
+        T.units.push_back(x.u);
     }
+    // stage-1 batches of at most 64 stacked rows
+    T.batches.clear();
+    T.rows.clear();
+    T.tchunks.clear();
+    for (auto &kv : by_in) {
+        const int32_t xg0 = in_g0[kv.first.first], klen = kv.first.second;
+        TcBatch b{xg0, klen, (int32_t)T.rows.size(), 0};
+        for (const Job &j : kv.second) {
+            const int32_t k8 = (j.rank + 7) & ~7;
+            if (b.nrows + k8 > 64) {
+                T.batches.push_back(b);
+                b = TcBatch{xg0, klen, (int32_t)T.rows.size(), 0};
+            }
+            for (int32_t l = 0; l < k8; ++l) T.rows.push_back(l < j.rank ? j.w_off + (int64_t)l * j.w_ld : -1);
+            for (int32_t g = 0; g < k8 / 8; ++g) T.tchunks.push_back((int32_t)(j.t0 + g));
+            b.nrows += k8;
+        }
+        if (b.nrows > 0) T.batches.push_back(b);
+    }
+    // the bounds the kernels index by
+    if (T.n_tchunk > INT32_MAX || (int64_t)T.rows.size() > INT32_MAX || T.ops.size() > (size_t)INT32_MAX) return false;
+    if ((int64_t)T.tchunks.size() * 8 != (int64_t)T.rows.size()) return false;
+    for (const TcBatch &b : T.batches)
+        if (b.nrows <= 0 || b.nrows > 64 || (b.nrows & 7) || b.row0 < 0 || (b.row0 & 7) ||
+            b.row0 + (int64_t)b.nrows > (int64_t)T.rows.size() ||
+            b.xg0 + chunks(b.klen) > (int64_t)T.xch.size())
+            return false;
+    for (int32_t t : T.tchunks)
+        if (t < 0 || t >= T.n_tchunk) return false;
+    for (const TcOp &o : T.ops) {
+        if (o.olen <= 0 || o.olen > TC_MAX_DIM || o.klen <= 0) return false;
+        if (o.kind == 2 ? (o.klen > TC_MAX_RANK || o.t0 + chunks(o.klen) > T.n_tchunk)
+                        : (o.klen > TC_MAX_DIM || o.xg0 + chunks(o.klen) > (int64_t)T.xch.size()))
+            return false;
+    }
+    for (const TcUnit &u : T.units)
+        if (u.mlen > TC_MAX_DIM || u.p0 < 0 || u.p1 <= u.p0 || u.p1 > (int32_t)T.ops.size()) return false;
+    return true;
 }
 
 // items reordered for a persistent kernel whose nw warps take items t, t + nw, ...:
@@ -184,22 +260,26 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         }
         L.n_small = (int64_t)small.size();
         L.n_big = (int64_t)big.size();
-        std::vector<TcUnit> tcu;
-        std::vector<TcProd> tcp;
-        std::vector<int2> xch;
+        const std::map<int32_t, std::vector<TcProd>> by_out = directed_products(small);
         std::vector<TcUnit> rcu;
         std::vector<TcProd> rcp;
-        build_tc_lists(small, h->num_sms > 0 ? h->num_sms : 152, tcu, tcp, xch, rcu, rcp);
+        build_owner_lists(by_out, rcu, rcp);
+        TcLists tc;
+        if (!build_tc_lists(by_out, tc)) return fail(HM_ERR_STATE, "tensor-core work lists out of their index bounds");
         L.n_rcu = (int64_t)rcu.size();
         if ((st = upload(h, &L.d_rcu, rcu, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_rcp, rcp, s)) != HM_OK) return st;
         if ((st = dev_alloc(h, (void **)&L.d_rcb, sizeof(float2) * rcp.size())) != HM_OK) return st;
         launch_prod_bounds(L.d_rcp, (int64_t)rcp.size(), h->d_pool32, L.d_rcb, s);
-        L.n_tcu = (int64_t)tcu.size();
-        L.n_tcp = (int64_t)tcp.size();
-        L.n_xch = (int64_t)xch.size();
+        L.n_tcu = (int64_t)tc.units.size();
+        L.n_tco = (int64_t)tc.ops.size();
+        L.n_xch = (int64_t)tc.xch.size();
+        L.n_tcb = (int64_t)tc.batches.size();
+        L.n_tcr = (int64_t)tc.rows.size();
+        L.n_tchunk = tc.n_tchunk;
         h->tc_max_xch = std::max(h->tc_max_xch, L.n_xch);
-        if ((st = upload(h, &L.d_xch, xch, s)) != HM_OK) return st;
+        h->tc_max_tchunk = std::max(h->tc_max_tchunk, L.n_tchunk);
+        if ((st = upload(h, &L.d_xch, tc.xch, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_items, L.items, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_small, small, s)) != HM_OK) return st;
         if ((st = upload(h, &L.d_big, big, s)) != HM_OK) return st;
@@ -212,8 +292,11 @@ hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
         launch_item_bounds(L.d_res, (int64_t)res.size(), h->d_pool32, L.d_bnd, s);
         launch_item_bounds(L.d_big, L.n_big, h->d_pool32, L.d_bnd_big, s);
         HM_CUDA(cudaGetLastError());
-        if ((st = upload(h, &L.d_tcu, tcu, s)) != HM_OK) return st;
-        if ((st = upload(h, &L.d_tcp, tcp, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_tcu, tc.units, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_tco, tc.ops, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_tcb, tc.batches, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_tcr, tc.rows, s)) != HM_OK) return st;
+        if ((st = upload(h, &L.d_tcc, tc.tchunks, s)) != HM_OK) return st;
         // the product's lists with tall dense blocks cut into row panels: a panel of rows
         // [r, r + mr) of a row-major block is itself a dense item with the same row stride
         auto panels = [](const std::vector<Item> &in, std::vector<Item> &out) {
@@ -268,7 +351,8 @@ static void free_handle(hm_matrix h)
         if (p) cudaFree(p);
     void *ptrs[] = {h->d_pperm, h->d_pleaf_off, h->d_dinv_off, h->d_leaf_n, h->d_self_off, h->d_bad_leaf,
                     h->d_self64, h->d_self32, h->d_dinv32, h->d_dinv64, h->d_pool32, h->d_pool64, h->d_status,
-                    h->ws.d_acc64, h->ws.d_io, h->ws.d_part, h->d_csr_off, h->d_csr_idx, h->ws.d_xpl, h->ws.d_own};
+                    h->ws.d_acc64, h->ws.d_io, h->ws.d_part, h->d_csr_off, h->d_csr_idx, h->ws.d_xpl, h->ws.d_tct,
+                    h->ws.d_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &kv : h->levels) {
@@ -281,7 +365,10 @@ static void free_handle(hm_matrix h)
         if (kv.second.d_bnd) cudaFree(kv.second.d_bnd);
         if (kv.second.d_bnd_big) cudaFree(kv.second.d_bnd_big);
         if (kv.second.d_tcu) cudaFree(kv.second.d_tcu);
-        if (kv.second.d_tcp) cudaFree(kv.second.d_tcp);
+        if (kv.second.d_tco) cudaFree(kv.second.d_tco);
+        if (kv.second.d_tcb) cudaFree(kv.second.d_tcb);
+        if (kv.second.d_tcr) cudaFree(kv.second.d_tcr);
+        if (kv.second.d_tcc) cudaFree(kv.second.d_tcc);
         if (kv.second.d_xch) cudaFree(kv.second.d_xch);
         if (kv.second.d_rcu) cudaFree(kv.second.d_rcu);
         if (kv.second.d_rcp) cudaFree(kv.second.d_rcp);
@@ -477,6 +564,9 @@ static hm_status ensure_workspace(hm_matrix h, int nrhs, int m)
     if (ws.d_own) cudaFree(ws.d_own);   // owner sums: ensure_own
     ws.d_own = nullptr;
     ws.own_bytes = 0;
+    if (ws.d_tct) cudaFree(ws.d_tct);   // stage-1 results of the tensor-core product: ensure_tct
+    ws.d_tct = nullptr;
+    ws.tct_bytes = 0;
     if (r >= MRHS_MIN_RHS && h->tc_max_xch > 0) {   // split x of the tensor-core product (it can be pinned from 4 RHS)
         ws.xpl_bytes = tc_xplane_bytes(h->tc_max_xch, r);
         HM_CUDA(cudaMalloc((void **)&ws.d_xpl, ws.xpl_bytes));
@@ -504,6 +594,27 @@ static hm_status ensure_own(hm_matrix h, int m)
     ws.own_bytes = 0;
     HM_CUDA(cudaMalloc((void **)&ws.d_own, bytes));
     ws.own_bytes = bytes;
+    ws.dev_bytes += (int64_t)bytes;
+    return HM_OK;
+}
+
+// stage-1 results of the tensor-core product (T chunks of the largest level for the
+// workspace's RHS tiles); allocated only by the calls that run that product, before
+// any capture
+static hm_status ensure_tct(hm_matrix h)
+{
+    hm::Workspace &ws = h->ws;
+    const size_t bytes = tc_t_bytes(h->tc_max_tchunk, ws.nrhs);
+    if (bytes == 0 || (ws.d_tct && ws.tct_bytes >= bytes)) return HM_OK;
+    clear_graphs(h);   // graphs hold the old pointer
+    if (ws.d_tct) {
+        cudaFree(ws.d_tct);
+        ws.dev_bytes -= (int64_t)ws.tct_bytes;
+    }
+    ws.d_tct = nullptr;
+    ws.tct_bytes = 0;
+    HM_CUDA(cudaMalloc((void **)&ws.d_tct, bytes));
+    ws.tct_bytes = bytes;
     ws.dev_bytes += (int64_t)bytes;
     return HM_OK;
 }
@@ -904,6 +1015,7 @@ static hm_status autotune(hm_matrix h, int nrhs_req, int m, cudaStream_t s, bool
         if (rb == RB_TC ? (nrhs < TC_MIN_RHS || L.n_tcu == 0) : (rb > 8 && rb / 2 >= nrhs))
             continue;   // a chunk of twice the RHS count or more only adds idle work; tensor tiles of 128 from 32 RHS
         double ms = 0;
+        if (rb == RB_TC && (st = ensure_tct(h)) != HM_OK) break;
         if ((st = time_it([&] { launch_apply_items(h, L, x, z, nrhs, false, s, rb); }, ms)) != HM_OK) break;
         if (ms < best) { best = ms; t.prod_rb = rb; t.prod_ms = ms; }
     }
@@ -936,14 +1048,17 @@ static hm_status autotune(hm_matrix h, int nrhs_req, int m, cudaStream_t s, bool
     return HM_OK;
 }
 
-static void use_tuning(SolveCtx &c)
+// the autotuner's (or hm_set_tuning's) kernel choices for the call, with the
+// workspace the chosen product needs
+static hm_status use_tuning(SolveCtx &c)
 {
-    if (c.nrhs < MRHS_MIN_RHS) return;
+    if (c.nrhs < MRHS_MIN_RHS) return HM_OK;
     auto tn = c.h->tune.find(tune_bucket(c.nrhs));
     if (tn != c.h->tune.end()) {
         c.prod_rb = tn->second.prod_rb;
         c.res_rb = tn->second.res_rb;
     }
+    return c.prod_rb == RB_TC ? ensure_tct(c.h) : HM_OK;
 }
 
 // permutations and vector updates of a solve, launched or recorded
@@ -1033,7 +1148,7 @@ static hm_status solve_device(hm_matrix h, const void *b, int64_t ldb, void *x, 
     if (rec_out && !persist) return fail(HM_ERR_ARG, "the operator does not fit the one-launch solve");
     if (!c.fp64 && !persist) {
         if ((st = autotune(h, nrhs, c.m, s, resid)) != HM_OK) return st;
-        use_tuning(c);
+        if ((st = use_tuning(c)) != HM_OK) return st;
         if (resid && c.res_rb == RB_OWN && own_applies(h, c.m) && (st = ensure_own(h, c.m)) != HM_OK) return st;
     }
     if (persist) {   // the one-launch solve runs the one-right-hand-side-at-a-time block bodies
@@ -1518,7 +1633,7 @@ hm_status hm_apply(hm_matrix h, const void *x, int64_t ldx, void *y, int64_t ldy
     if (st != HM_OK) return st;
     if (fp64_accumulate && (st = ensure_partials(h)) != HM_OK) return st;
     if ((st = autotune(h, nrhs, c.m, s, fp64_accumulate != 0)) != HM_OK) return st;
-    use_tuning(c);
+    if ((st = use_tuning(c)) != HM_OK) return st;
     if (fp64_accumulate && c.res_rb == RB_OWN && own_applies(h, c.m) && (st = ensure_own(h, c.m)) != HM_OK)
         return st;
     void *xt = h->ws.vec32[0], *yt = h->ws.vec32[1];
@@ -1552,7 +1667,7 @@ hm_status hm_residual(hm_matrix h, const void *b, int64_t ldb, const void *x, in
     if (st != HM_OK) return st;
     if ((st = ensure_partials(h)) != HM_OK) return st;
     if ((st = autotune(h, nrhs, c.m, s, true)) != HM_OK) return st;
-    use_tuning(c);
+    if ((st = use_tuning(c)) != HM_OK) return st;
     if (c.res_rb == RB_OWN && own_applies(h, c.m) && (st = ensure_own(h, c.m)) != HM_OK) return st;
     void *bt = h->ws.vec32[0], *xt = h->ws.vec32[1], *rt = h->ws.vec32[3];
     launch_permute_in(b, ldb, bt, h->pN, h->d_pperm, nrhs, false, s);

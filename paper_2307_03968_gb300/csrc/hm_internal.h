@@ -57,7 +57,7 @@ struct Item {
 static_assert(sizeof(Item) == 32, "Item layout");
 
 // One directed product of a small stored block into an output cluster (the
-// tensor-core product, k_mrhs_tc.cu): Z_out += B X_in with B the block (dense,
+// owner-computes residual, k_resid_own.cu): Z_out += B X_in with B the block (dense,
 // read row-major or transposed) or, for a low-rank block, Y (W X_in) with the
 // input-side factor W read row-major (rank rows) and the output-side factor Y
 // read transposed.
@@ -76,6 +76,30 @@ struct TcProd {
 static_assert(sizeof(TcProd) == 48, "TcProd layout");
 // a work unit: products [p0, p1) into the output cluster at out0 (mlen = largest olen)
 struct TcUnit { int32_t out0, mlen, p0, p1; };
+
+// The tensor-core product (k_mrhs_tc.cu) in two launches.  The first runs stage 1 of
+// every low-rank directed product, T = W X_in, batched over the products that share
+// an input cluster (their W rows stacked along N); it stores T in chunks of 8 rank
+// rows (TC_T_CHUNK floats per chunk and RHS tile).  The second runs, per output
+// cluster, the dense products and the second stages Y T, which read T back.
+constexpr int TC_T_CHUNK = 2 * 128 * 8;   // floats of one T chunk: Re and Im planes of 128 RHS x 8 rank rows
+// one operation of the second launch
+struct TcOp {
+    int64_t src;     // complex offset of the dense block, or of Y (low-rank second stage)
+    int64_t t0;      // low-rank: first T chunk of the product (per RHS tile)
+    int32_t kind;    // 0 dense (element (out i, in j) = block[i][j]), 1 dense mirror (= block[j][i]), 2 Y T
+    int32_t klen;    // K length: the input length (dense) or the rank
+    int32_t ld;      // row stride of the block or of Y as stored (rank rows)
+    int32_t olen;    // output length
+    int32_t xg0;     // dense: first split-x chunk of the input cluster
+    int32_t pad;
+};
+static_assert(sizeof(TcOp) == 40, "TcOp layout");
+// a batch of the first launch: stacked rows [row0, row0 + nrows) (nrows a multiple of
+// 8, at most 64) of the row table, all over one input cluster (split-x chunks from xg0,
+// K length klen); each row's W offset (-1: a zero row) is in the row table, each group
+// of 8 rows' T chunk in the chunk table (index row / 8)
+struct TcBatch { int32_t xg0, klen, row0, nrows; };
 
 __host__ __device__ inline int64_t even(int64_t v) { return (v + 1) & ~int64_t(1); }
 
@@ -103,9 +127,13 @@ struct LevelList {
     int small_dim = 0, small_rank = 0;   // largest (even) side and rank among the small items
     // the small items as directed products grouped into work units by output
     // cluster, for the tensor-core product (both mirrored halves of every block)
-    TcProd *d_tcp = nullptr;
-    TcUnit *d_tcu = nullptr;
-    int64_t n_tcp = 0, n_tcu = 0;
+    TcOp *d_tco = nullptr;
+    TcUnit *d_tcu = nullptr;          // units over d_tco
+    int64_t n_tco = 0, n_tcu = 0;
+    TcBatch *d_tcb = nullptr;         // stage-1 batches over the row table
+    int64_t *d_tcr = nullptr;         // row table: W row offsets (-1 = zero row)
+    int32_t *d_tcc = nullptr;         // chunk table: T chunk of each 8-row group
+    int64_t n_tcb = 0, n_tcr = 0, n_tchunk = 0;   // batches, rows, T chunks per RHS tile
     // the same directed products with one unit per output cluster (the owner-computes
     // FP64-class residual: each output row summed by one CTA in a fixed order)
     TcProd *d_rcp = nullptr;
@@ -216,6 +244,8 @@ struct Workspace {
     int64_t dev_bytes = 0;        // device bytes held by the vectors, norms and partial slots
     float *d_xpl = nullptr;       // split x chunks of the tensor-core product (16 KB per chunk and RHS tile)
     size_t xpl_bytes = 0;
+    float *d_tct = nullptr;       // stage-1 results T of the tensor-core product (TC_T_CHUNK floats per chunk and tile)
+    size_t tct_bytes = 0;
     double2 *d_own = nullptr;     // FP64 owner sums of the residual, [level][RHS][pN]
     size_t own_bytes = 0;
 };
@@ -266,6 +296,7 @@ struct hm_matrix_s {
     int64_t device_bytes = 0;
     int num_sms = 0;
     int64_t tc_max_xch = 0;           // largest split-x chunk count over the levels
+    int64_t tc_max_tchunk = 0;        // largest T chunk count over the levels
     int64_t tc_wait_limit = -1;       // polls of each pipeline wait of the tensor-core product (-1 = default)
 
     // mesh geometry kept for excitation (operators made by hm_build):
@@ -436,8 +467,10 @@ hm_status launch_serve_loop(LoopEntry *ring, int ring_size, LoopCtl *ctl, LoopDe
 hm_status launch_persist(hm_matrix h, const Phase *d_phases, int n_phases, int units, cudaStream_t s);
 // bytes of the split-x workspace of the tensor-core product for n_xch chunks and nrhs (k_mrhs_tc.cu)
 size_t tc_xplane_bytes(int64_t n_xch, int nrhs);
+// bytes of its stage-1 workspace for n_tchunk T chunks and nrhs (k_mrhs_tc.cu)
+size_t tc_t_bytes(int64_t n_tchunk, int nrhs);
 // tensor-core products of a level's small items for all right-hand sides (k_mrhs_tc.cu);
-// z accumulates (vector atomics); needs the split-x workspace for nrhs
+// z accumulates (vector atomics); needs the split-x and stage-1 workspaces for nrhs
 void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s);
 // the FP64-class partial-slot products of the small items for many right-hand sides (k_mrhs.cu)
 void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part,

@@ -7,10 +7,7 @@
 //
 // Orientation.  The right-hand sides are the M dimension: a tile of 128 of them
 // gives the 128 rows of the accumulator (tensor-memory lane r = right-hand side
-// r of the tile).  Every stored block yields two directed products (output
-// cluster O, input cluster J); the host groups them by output cluster into work
-// units, so one CTA keeps the sum for (O, tile) in tensor memory while it streams
-// that unit's blocks, and adds it into z once.
+// r of the tile).
 //
 // Complex arithmetic.  With X = Xr + i Xi (tile rows x input) and B = Br + i Bi
 // (output x input), the accumulator [Re Z | Im Z] (128 x 2*m8) is
@@ -19,16 +16,27 @@
 // three planes -Bi, Br, Bi one after another, so both products are windows of
 // the same shared-memory rows (start at -Bi or at Br, N = 2*m8).
 //
-// Low-rank blocks (B = U V, rank k).  Stage 1 puts T = X W^T (128 x k; W = V for
-// the forward product, U^T for the mirror) into a second tensor-memory
-// accumulator with the same plane trick; stage 2 reads T back (tcgen05.ld),
-// splits it and multiplies it into the output accumulator with the output-side
-// factor read transposed (U for the forward product, V^T for the mirror).
+// Two launches per product.
+//  - k_tc_stage1: stage 1 of every low-rank directed product (B = Y W, rank k;
+//    W = V and Y = U forward, W = U^T and Y = V^T mirrored), T = X W^T, batched over
+//    the products that share an input cluster: their W rows are stacked along N
+//    (roundup8(k) rows each, at most 64 in all), so one K chunk of split x feeds
+//    MMAs of N up to 128 instead of one product's 2*roundup8(k).  Each batch's
+//    accumulator (two alternate in tensor memory) is stored in HBM as T chunks of 8
+//    rank rows: for the 128 RHS of the tile, a plane of Re T and a plane of Im T in
+//    the layout of an A operand plane (poff).
+//  - k_apply_tc: per output cluster, work units of its dense products and second
+//    stages Z += T Y^T.  A second stage's A operand is a T chunk copied in raw and
+//    split by the converters in place: thread r reads row r's 16 values and writes
+//    the four split planes at row r's own positions, so no thread reads what another
+//    writes.  One CTA keeps the sum for (cluster, RHS tile) in tensor memory while it
+//    streams the unit, and adds it into z once.
 //
 // Precision (3xTF32): every FP32 operand a is split as a = hi + lo, hi = a
 // rounded to TF32 (|a - hi| <= 2^-11 |a|), lo = a - hi rounded to TF32 too; each
 // K step accumulates hi*hi + hi*lo + lo*hi in FP32 (the dropped lo*lo and the
-// rounding of lo are <= 2^-22 |a b| each).  The larger error is the tensor core's
+// rounding of lo are <= 2^-22 |a b| each).  T is held in FP32 between the stages,
+// as it was when it stayed in tensor memory.  The larger error is the tensor core's
 // FP32 accumulation, which loses a little on every MMA added into a large running
 // sum: measured against the oracle, the product erred 7.4e-6 (relative, 60-unknown
 // leaves) when a work unit summed 256 K chunks in tensor memory, and a refined
@@ -38,21 +46,21 @@
 // the oracle (16-chunk units: 5.4e-7 and 7e-6, at 31 % more time per launch).
 // Adding the lo*lo products changed neither (same errors to four digits).
 //
-// Pipeline (warp-specialised, mbarrier hand-offs, no CTA-wide barrier per chunk).
-// K goes in chunks of 8 (one MMA K step) through a ring of shared-memory slots.
-// Before the launch, x is split once into hi/lo planes per (input-cluster K
-// chunk, RHS tile), already in the operand layout (k_split_x).  Warp 0 (producer)
-// copies a chunk's A planes with one 16 KB cp.async.bulk and the raw complex64
-// rows of the block or factor with cp.async.  Warps 1-4 (converters) split the
-// block rows into the B planes (and, for stage 2, read T from tensor memory into
-// the A planes), and add finished accumulators into z.  Warp 5 issues the six
-// MMAs of a chunk and commits them to the slot's "empty" mbarrier.  Two CTAs
-// share an SM.  Every pipeline wait is bounded by a number of polls given at
-// launch (hm_set_wait_limit; default 2^24): on timeout the kernel records
-// HM_ERR_TIMEOUT in the status word and all roles leave their loops.  Before the
-// CTA ends, the producer waits for its bulk copies in flight and the MMA issuer
-// for its MMAs in flight, both at the full bound (2^24 polls) whatever the
-// pipeline limit, and only then is the tensor memory freed.
+// Pipeline (both kernels; warp-specialised, mbarrier hand-offs, no CTA-wide barrier
+// per chunk).  K goes in chunks of 8 (one MMA K step) through a ring of shared-memory
+// slots.  Before the launches, x is split once into hi/lo planes per (input-cluster
+// K chunk, RHS tile), already in the operand layout (k_split_x).  Warp 0 (producer)
+// copies a chunk's A planes (split x, or a raw T chunk) with one cp.async.bulk and
+// the raw complex64 rows of the block or factor with cp.async.  Warps 1-4
+// (converters) split the block rows into the B planes (and a raw T chunk into the A
+// planes), and store finished accumulators (into z, or as T chunks).  Warp 5 issues
+// the six MMAs of a chunk and commits them to the slot's "empty" mbarrier.  Two CTAs
+// share an SM.  Every pipeline wait is bounded by a number of polls given at launch
+// (hm_set_wait_limit; default 2^24): on timeout the kernel records HM_ERR_TIMEOUT in
+// the status word and all roles leave their loops.  Before the CTA ends, the
+// producer waits for its bulk copies in flight and the MMA issuer for its MMAs in
+// flight, both at the full bound (2^24 polls) whatever the pipeline limit, and only
+// then is the tensor memory freed.
 #include "k_common.cuh"
 
 namespace hm {
@@ -73,11 +81,15 @@ constexpr int B_RAW = 64 * KCH * 8;              // raw complex64 block / factor
 constexpr int SLOT = A_BYTES + 2 * B_PLANE + B_RAW;   // 32 KB
 constexpr int OFF_B = A_BYTES, OFF_RAW = A_BYTES + 2 * B_PLANE;
 constexpr int SMEM = NSLOT * SLOT;
-constexpr uint32_t TMEM_COLS = 256;              // output accumulator at column 0 (<= 128), T at column 128 (<= 64)
-constexpr uint32_t T_COL = 128;
+constexpr uint32_t TMEM_COLS = 128;              // k_apply_tc: the output accumulator (N = 2*m8 <= 128)
+constexpr uint32_t S1_TMEM_COLS = 256;           // k_tc_stage1: two alternate accumulators at columns 0 and 128
+constexpr int S1_ROWS = 64;                      // stacked W rows of a stage-1 batch, at most
+constexpr int T_PLANE = TM * KCH;                // floats of one plane (Re or Im) of a T chunk
 constexpr uint32_t GROUP_BYTES = 2 * 128;        // one 8-row group: two K-adjacent core matrices
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 static_assert(TC_MAX_DIM <= 64 && TC_MAX_RANK <= 32, "operand planes and tensor-memory columns");
+static_assert(2 * T_PLANE == TC_T_CHUNK && 2 * T_PLANE * 4 <= A_BYTES, "a raw T chunk fits the A planes it becomes");
+static_assert(3 * S1_ROWS <= B_ROWS && S1_ROWS <= 64, "stacked rows fit the B planes and the raw rows");
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -241,14 +253,35 @@ __device__ __forceinline__ void fetch_b_tr(uint32_t raw, int lane, const float2 
     }
 }
 
-// converter: A planes from the T accumulator (columns k0 .. k0+7 of Re T and of Im T), row r
-__device__ __forceinline__ void conv_a_t(float *slot, uint32_t tmem, int quad, int r, int k8, int k0)
+// producer lane: the stacked W rows of a stage-1 batch, natural orientation: element
+// (row, q) = pool[rs + q] for q = k0 + j < klen, with rs the row's W offset (-1: a zero
+// row).  The lane's rows are (lane >> 2) + 8 i (offsets in rs[i]), its 16-byte piece
+// lane & 3: the same pieces fetch_b_nat gives it.
+__device__ __forceinline__ void fetch_b_rows(uint32_t raw, int lane, const float2 *__restrict__ pool,
+                                             const int64_t (&rs)[8], int R8, int k0, int klen, uint64_t pol)
 {
-    float re[8], im[8];
-    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-    tld8(tmem + lane_base + T_COL + (uint32_t)k0, re);
-    tld8(tmem + lane_base + T_COL + (uint32_t)(k8 + k0), im);
-    tld_wait();
+    const int pc = lane & 3, q = k0 + 2 * pc;
+    const int bytes_k = clamp16((klen - q) * 8);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int row = (lane >> 2) + 8 * i;
+        if (row >= R8) break;
+        const int bytes = rs[i] >= 0 ? bytes_k : 0;
+        cp16(raw + swz_n(row, pc), bytes > 0 ? (const void *)(pool + rs[i] + q) : (const void *)pool, bytes, pol);
+    }
+}
+
+// converter thread r (0..127): the A planes of row r from a raw T chunk in the same
+// slot (Re T in plane 0, Im T in plane 1, both at the positions poff(r, k)).  Row r's
+// 16 values are read before any is written, and put_a_row writes only row r's
+// positions, so the split runs in place without a barrier between threads.
+__device__ __forceinline__ void conv_a_raw(float *slot, int r)
+{
+    const float4 *p = reinterpret_cast<const float4 *>(slot);
+    const int o0 = poff(r, 0) >> 2, o1 = poff(r, 4) >> 2;
+    const float4 a = p[o0], b = p[o1], c = p[T_PLANE / 4 + o0], d = p[T_PLANE / 4 + o1];
+    const float re[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const float im[8] = {c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
     put_a_row(reinterpret_cast<float4 *>(slot), r, re, im);
 }
 
@@ -349,35 +382,233 @@ __device__ __forceinline__ void drain(uint32_t tmem, int quad, int lane, int m8,
     }
 }
 
-// Position in a CTA's chunk sequence: unit-tile u (units taken in turn with
-// stride gridDim.x, tile-major so that one RHS tile's split x stays in L2),
-// product p of the unit (the next one's record loaded ahead), stage (0: the dense
-// product or stage 1 of a low-rank one, 1: stage 2), chunk c of nch.  Every role
-// walks the same sequence.
+// converter: store a stage-1 accumulator (tensor-memory column acc, rows of lane
+// quadrant quad, R8 stacked rows) as T chunks: group g of 8 rows -> chunk tch[g] of the
+// tile's T (tbase), Re and Im planes at row r's positions poff(r, k)
+__device__ __forceinline__ void store_t(uint32_t tmem, uint32_t acc, int quad, int lane, int R8,
+                                        const int32_t *__restrict__ tch, float *__restrict__ tbase)
+{
+    const int r = 32 * quad + lane;
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    const int o0 = poff(r, 0) >> 2, o1 = poff(r, 4) >> 2;
+    for (int g = 0; g < R8 / 8; ++g) {
+        float re[8], im[8];
+        tld8(tmem + lane_base + acc + (uint32_t)(8 * g), re);
+        tld8(tmem + lane_base + acc + (uint32_t)(R8 + 8 * g), im);
+        const int64_t chunk = tch[g];
+        tld_wait();
+        float4 *d = reinterpret_cast<float4 *>(tbase + chunk * TC_T_CHUNK);
+        d[o0] = make_float4(re[0], re[1], re[2], re[3]);
+        d[o1] = make_float4(re[4], re[5], re[6], re[7]);
+        d[T_PLANE / 4 + o0] = make_float4(im[0], im[1], im[2], im[3]);
+        d[T_PLANE / 4 + o1] = make_float4(im[4], im[5], im[6], im[7]);
+    }
+}
+
+// the mbarriers and tensor-memory allocation of a CTA of either kernel
+__device__ __forceinline__ void init_pipeline(uint64_t *full, uint64_t *ready, uint64_t *empty, uint64_t *acc_full,
+                                              uint64_t *acc_empty, int n_acc, uint64_t *fin, volatile int *abort_flag)
+{
+    for (int s = 0; s < NSLOT; ++s) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[s])), "r"(33));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ready[s])), "r"(NCV));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])));
+    }
+    for (int b = 0; b < n_acc; ++b) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&acc_full[b])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acc_empty[b])), "r"(NCV));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(fin)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    *abort_flag = 0;
+}
+
+// producer lane 0: one bulk copy of `bytes` into the slot, completing on full
+__device__ __forceinline__ void bulk_in(uint32_t slot, const float *src, uint32_t bytes, uint64_t *full, uint64_t pol)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(full)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                 " [%0], [%1], %2, [%3], %4;"
+                 ::"r"(slot), "l"(src), "r"(bytes), "r"(su32(full)), "l"(pol) : "memory");
+}
+
+// producer, after its loop: its cp.async copies, and the slot fills still in flight,
+// land before the CTA may end (their full phases complete on the copies alone)
+__device__ __forceinline__ void producer_drain(uint64_t *full, uint32_t n, int lane, volatile int *abort_flag)
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (lane == 0)
+        for (uint32_t f = n > (uint32_t)NSLOT ? n - NSLOT : 0; f < n; ++f)
+            mbar_drain(su32(&full[f % NSLOT]), (f / NSLOT) & 1, abort_flag);
+    __syncwarp();
+}
+
+// ---- k_tc_stage1: T = X W^T for batches of stacked W rows --------------------------
+
+// Position in a CTA's chunk sequence: batch-tile u (taken in turn with stride
+// gridDim.x, tile-major), chunk c of nch.  Every role walks the same sequence.
+struct S1Pos {
+    int64_t u;
+    int c, nch, tile;
+    bool valid;
+    TcBatch B;
+};
+
+struct S1Seq {
+    const TcBatch *batches;
+    int n_batches;
+    int64_t total;
+    __device__ void unit(S1Pos &q) const
+    {
+        q.valid = q.u < total;
+        if (!q.valid) return;
+        q.B = batches[q.u % n_batches];
+        q.tile = (int)(q.u / n_batches);
+        q.c = 0;
+        q.nch = (q.B.klen + KCH - 1) / KCH;
+    }
+    __device__ void next(S1Pos &q) const
+    {
+        if (++q.c < q.nch) return;
+        q.u += gridDim.x;
+        unit(q);
+    }
+};
+
+__global__ void __launch_bounds__(TT, 2)
+k_tc_stage1(const TcBatch *__restrict__ batches, int n_batches, const int64_t *__restrict__ rows,
+            const int32_t *__restrict__ tchunks, int64_t n_xch, const float *__restrict__ xpl,
+            const float2 *__restrict__ pool, float *__restrict__ tct, int64_t n_tchunk, int n_tiles, int *status,
+            uint32_t wait_limit)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t full[NSLOT], ready[NSLOT], empty[NSLOT];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    if (tid == 0) init_pipeline(full, ready, empty, acc_full, acc_empty, 2, &fin, &abort_flag);
+    if (w == NWARP - 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "n"(S1_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t sm0 = su32(smraw);
+    const S1Seq seq{batches, n_batches, (int64_t)n_batches * n_tiles};
+    S1Pos q;
+    q.u = blockIdx.x;
+    seq.unit(q);
+    uint32_t n = 0;
+
+    if (w == 0) {
+        // ---- producer: split x (one bulk copy) and the stacked W rows into slot n % NSLOT
+        uint64_t keep, stream;
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
+        int64_t rs[8];
+        while (q.valid && !abort_flag) {
+            const int s = (int)(n % NSLOT);
+            if (n >= NSLOT && !mbar_wait(su32(&empty[s]), ((n / NSLOT) + 1) & 1, &abort_flag, wait_limit)) break;
+            if (q.c == 0) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int row = (lane >> 2) + 8 * i;
+                    rs[i] = row < q.B.nrows ? rows[q.B.row0 + row] : -1;
+                }
+            }
+            const uint32_t slot = sm0 + (uint32_t)(s * SLOT);
+            if (lane == 0)
+                bulk_in(slot, xpl + ((int64_t)q.tile * n_xch + q.B.xg0 + q.c) * (A_BYTES / 4), A_BYTES, &full[s], keep);
+            fetch_b_rows(slot + OFF_RAW, lane, pool, rs, q.B.nrows, q.c * KCH, q.B.klen, stream);
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&full[s])) : "memory");
+            ++n;
+            seq.next(q);
+        }
+        producer_drain(full, n, lane, &abort_flag);
+    } else if (w <= 4) {
+        // ---- converters: B planes, then each finished batch's T chunks
+        const int t = tid - 32, quad = w & 3;
+        uint32_t nb = 0;
+        while (q.valid && !abort_flag) {
+            const int s = (int)(n % NSLOT);
+            if (!mbar_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
+            float *bh = reinterpret_cast<float *>(smraw + s * SLOT + OFF_B), *bl = bh + B_PLANE / 4;
+            conv_b_nat(bh, bl, smraw + s * SLOT + OFF_RAW, q.B.nrows, t);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            arrive(su32(&ready[s]));
+            if (q.c == q.nch - 1) {
+                const int b = (int)(nb & 1);
+                if (!mbar_wait(su32(&acc_full[b]), (nb >> 1) & 1, &abort_flag, wait_limit)) break;
+                fence_after();
+                store_t(tmem, (uint32_t)(128 * b), quad, lane, q.B.nrows, tchunks + q.B.row0 / 8,
+                        tct + (int64_t)q.tile * n_tchunk * TC_T_CHUNK);
+                fence_before();
+                arrive(su32(&acc_empty[b]));
+                ++nb;
+            }
+            ++n;
+            seq.next(q);
+        }
+    } else if (lane == 0) {
+        // ---- MMA issuer: batch j into accumulator j % 2, once its previous contents are stored
+        uint32_t nb = 0;
+        while (q.valid && !abort_flag) {
+            const int s = (int)(n % NSLOT);
+            const int b = (int)(nb & 1);
+            if (q.c == 0 && nb >= 2 && !mbar_wait(su32(&acc_empty[b]), ((nb >> 1) - 1) & 1, &abort_flag, wait_limit))
+                break;
+            if (!mbar_wait(su32(&ready[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
+            fence_after();
+            issue_chunk(sm0 + (uint32_t)(s * SLOT), tmem + (uint32_t)(128 * b), q.B.nrows, q.c > 0);
+            commit(su32(&empty[s]));
+            if (q.c == q.nch - 1) {
+                commit(su32(&acc_full[b]));
+                ++nb;
+            }
+            ++n;
+            seq.next(q);
+        }
+        commit(su32(&fin));                         // every MMA issued, then a bounded wait before freeing
+        mbar_drain(su32(&fin), 0, &abort_flag);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (abort_flag && status && tid == 0) atomicCAS(status, 0, (int)HM_ERR_TIMEOUT);
+    if (w == NWARP - 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(S1_TMEM_COLS));
+}
+
+// ---- k_apply_tc: dense products and second stages, by output cluster ---------------
+
+// Position in a CTA's chunk sequence: unit-tile u (units taken in turn with stride
+// gridDim.x, tile-major so that one RHS tile's split x stays in L2), operation p of
+// the unit (the next one's record loaded ahead), chunk c of nch.  Every role walks
+// the same sequence.
 struct Pos {
     int64_t u;
-    int p, stage, c, nch;
-    int tile, r0, nr, m8, k8;
+    int p, c, nch;
+    int tile, r0, nr, m8;
     bool valid;
     TcUnit U;
-    TcProd P, Pn;
-    __device__ bool lr1() const { return P.rank > 0 && stage == 0; }
-    __device__ bool lr2() const { return P.rank > 0 && stage == 1; }
-    __device__ bool last_of_unit() const { return c == nch - 1 && (P.rank == 0 || stage == 1) && p == U.p1 - 1; }
+    TcOp P, Pn;
+    __device__ bool last_of_unit() const { return c == nch - 1 && p == U.p1 - 1; }
 };
 
 struct Seq {
     const TcUnit *units;
-    const TcProd *prods;
+    const TcOp *ops;
     int n_units, nrhs;
     int64_t total;
     __device__ void start(Pos &q) const
     {
-        if (q.p + 1 < q.U.p1) q.Pn = prods[q.p + 1];
-        q.stage = 0;
+        if (q.p + 1 < q.U.p1) q.Pn = ops[q.p + 1];
         q.c = 0;
         q.nch = (q.P.klen + KCH - 1) / KCH;
-        q.k8 = (q.P.rank + 7) & ~7;
     }
     __device__ void unit(Pos &q) const
     {
@@ -389,18 +620,12 @@ struct Seq {
         q.nr = min(TM, nrhs - q.r0);
         q.m8 = (q.U.mlen + 7) & ~7;
         q.p = q.U.p0;
-        q.P = prods[q.p];
+        q.P = ops[q.p];
         start(q);
     }
     __device__ void next(Pos &q) const
     {
         if (++q.c < q.nch) return;
-        if (q.P.rank > 0 && q.stage == 0) {
-            q.stage = 1;
-            q.c = 0;
-            q.nch = q.k8 / KCH;
-            return;
-        }
         if (++q.p < q.U.p1) {
             q.P = q.Pn;
             start(q);
@@ -412,30 +637,18 @@ struct Seq {
 };
 
 __global__ void __launch_bounds__(TT, 2)
-k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restrict__ prods, int64_t n_xch,
-           const float *__restrict__ xpl, const float2 *__restrict__ pool, float2 *__restrict__ z, int64_t ldz,
-           int nrhs, int *status, uint32_t wait_limit)
+k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcOp *__restrict__ ops, int64_t n_xch,
+           const float *__restrict__ xpl, const float *__restrict__ tct, int64_t n_tchunk,
+           const float2 *__restrict__ pool, float2 *__restrict__ z, int64_t ldz, int nrhs, int *status,
+           uint32_t wait_limit)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t full[NSLOT], ready[NSLOT], empty[NSLOT];
-    __shared__ __align__(8) uint64_t t_ready, t_empty, acc_full, acc_empty, fin;
+    __shared__ __align__(8) uint64_t acc_full, acc_empty, fin;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    if (tid == 0) {
-        for (int s = 0; s < NSLOT; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[s])), "r"(33));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ready[s])), "r"(NCV));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])));
-        }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&t_ready)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&t_empty)), "r"(NCV));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&acc_full)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acc_empty)), "r"(NCV));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&fin)));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-        abort_flag = 0;
-    }
+    if (tid == 0) init_pipeline(full, ready, empty, &acc_full, &acc_empty, 1, &fin, &abort_flag);
     if (w == NWARP - 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
                      "n"(TMEM_COLS));
@@ -446,15 +659,16 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
     fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t sm0 = su32(smraw);
-    const Seq seq{units, prods, n_units, nrhs, (int64_t)n_units * ((nrhs + TM - 1) / TM)};
+    const Seq seq{units, ops, n_units, nrhs, (int64_t)n_units * ((nrhs + TM - 1) / TM)};
     Pos q;
     q.u = blockIdx.x;
     seq.unit(q);
     uint32_t n = 0;
 
     if (w == 0) {
-        // ---- producer: A planes (one bulk copy) and raw B rows into slot n % NSLOT;
-        // the split x is kept in L2 (evict last), the block stream is not (evict first)
+        // ---- producer: the A planes (split x, or a raw T chunk; one bulk copy) and the raw
+        // B rows into slot n % NSLOT; the split x is kept in L2 (evict last), T and the
+        // block stream are not (evict first)
         uint64_t keep, stream;
         asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
         asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
@@ -464,62 +678,35 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
             const uint32_t slot = sm0 + (uint32_t)(s * SLOT);
             const int k0 = q.c * KCH;
             if (lane == 0) {
-                if (!q.lr2()) {
-                    const float *src = xpl + ((int64_t)q.tile * n_xch + q.P.xg0 + q.c) * (A_BYTES / 4);
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[s])),
-                                 "r"(A_BYTES) : "memory");
-                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-                                 " [%0], [%1], %2, [%3], %4;"
-                                 ::"r"(slot), "l"(src), "r"(A_BYTES), "r"(su32(&full[s])), "l"(keep) : "memory");
-                } else {
-                    arrive(su32(&full[s]));
-                }
+                if (q.P.kind == 2)
+                    bulk_in(slot, tct + ((int64_t)q.tile * n_tchunk + q.P.t0 + q.c) * TC_T_CHUNK, TC_T_CHUNK * 4,
+                            &full[s], stream);
+                else
+                    bulk_in(slot, xpl + ((int64_t)q.tile * n_xch + q.P.xg0 + q.c) * (A_BYTES / 4), A_BYTES, &full[s],
+                            keep);
             }
             const uint32_t raw = slot + OFF_RAW;
-            if (q.P.rank == 0) {
-                if (q.P.trans) fetch_b_tr(raw, lane, pool + q.P.b_off, q.P.b_ld, q.m8, q.P.olen, k0, q.P.klen, stream);
-                else fetch_b_nat(raw, lane, pool + q.P.b_off, q.P.b_ld, q.m8, q.P.olen, k0, q.P.klen, stream);
-            } else if (q.stage == 0) {
-                fetch_b_nat(raw, lane, pool + q.P.b_off, q.P.b_ld, q.k8, q.P.rank, k0, q.P.klen, stream);
-            } else {
-                fetch_b_tr(raw, lane, pool + q.P.y_off, q.P.y_ld, q.m8, q.P.olen, k0, q.P.rank, stream);
-            }
+            if (q.P.kind == 0) fetch_b_nat(raw, lane, pool + q.P.src, q.P.ld, q.m8, q.P.olen, k0, q.P.klen, stream);
+            else fetch_b_tr(raw, lane, pool + q.P.src, q.P.ld, q.m8, q.P.olen, k0, q.P.klen, stream);
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&full[s])) : "memory");
             ++n;
             seq.next(q);
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        // the slot fills still in flight land before the CTA may end (their full phases
-        // complete on the copies alone)
-        if (lane == 0)
-            for (uint32_t f = n > (uint32_t)NSLOT ? n - NSLOT : 0; f < n; ++f)
-                mbar_drain(su32(&full[f % NSLOT]), (f / NSLOT) & 1, &abort_flag);
-        __syncwarp();
+        producer_drain(full, n, lane, &abort_flag);
     } else if (w <= 4) {
-        // ---- converters: B planes (and A planes from T), accumulators into z
-        const int t = tid - 32, quad = w & 3, r = 32 * quad + lane;
-        uint32_t n_t = 0, n_u = 0;
+        // ---- converters: B planes (and A planes from a raw T chunk), accumulators into z
+        const int t = tid - 32, quad = w & 3;
+        uint32_t n_u = 0;
         while (q.valid && !abort_flag) {
             const int s = (int)(n % NSLOT);
             if (!mbar_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
             float *slot = reinterpret_cast<float *>(smraw + s * SLOT);
             const unsigned char *raw = smraw + s * SLOT + OFF_RAW;
             float *bh = reinterpret_cast<float *>(smraw + s * SLOT + OFF_B), *bl = bh + B_PLANE / 4;
-            const bool lr1 = q.lr1(), lr2 = q.lr2();
-            if (lr2) {
-                if (q.c == 0 && !mbar_wait(su32(&t_ready), n_t & 1, &abort_flag, wait_limit)) break;
-                fence_after();
-                conv_a_t(slot, tmem, quad, r, q.k8, q.c * KCH);
-            }
-            const int R8 = lr1 ? q.k8 : q.m8;
-            if (q.P.rank == 0 ? q.P.trans != 0 : lr2) conv_b_tr(bh, bl, raw, R8, t);
-            else conv_b_nat(bh, bl, raw, R8, t);
+            if (q.P.kind == 2) conv_a_raw(slot, t);
+            if (q.P.kind == 0) conv_b_nat(bh, bl, raw, q.m8, t);
+            else conv_b_tr(bh, bl, raw, q.m8, t);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (lr2 && q.c == q.nch - 1) {
-                fence_before();
-                arrive(su32(&t_empty));
-                ++n_t;
-            }
             arrive(su32(&ready[s]));
             if (q.last_of_unit()) {
                 if (!mbar_wait(su32(&acc_full), n_u & 1, &abort_flag, wait_limit)) break;
@@ -534,23 +721,16 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcProd *__restri
         }
     } else if (lane == 0) {
         // ---- MMA issuer
-        uint32_t n_lr = 0, n_u = 0;
+        uint32_t n_u = 0;
         bool started = false;
         while (q.valid && !abort_flag) {
             const int s = (int)(n % NSLOT);
-            const bool lr1 = q.lr1();
-            if (lr1 && q.c == 0 && n_lr > 0 && !mbar_wait(su32(&t_empty), (n_lr - 1) & 1, &abort_flag, wait_limit)) break;
-            if (!lr1 && !started && n_u > 0 && !mbar_wait(su32(&acc_empty), (n_u - 1) & 1, &abort_flag, wait_limit)) break;
+            if (!started && n_u > 0 && !mbar_wait(su32(&acc_empty), (n_u - 1) & 1, &abort_flag, wait_limit)) break;
             if (!mbar_wait(su32(&ready[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
             fence_after();
-            issue_chunk(sm0 + (uint32_t)(s * SLOT), lr1 ? tmem + T_COL : tmem, lr1 ? q.k8 : q.m8,
-                        lr1 ? q.c > 0 : started);
+            issue_chunk(sm0 + (uint32_t)(s * SLOT), tmem, q.m8, started);
             commit(su32(&empty[s]));
-            if (lr1 && q.c == q.nch - 1) {
-                commit(su32(&t_ready));
-                ++n_lr;
-            }
-            if (!lr1) started = true;
+            started = true;
             if (q.last_of_unit()) {
                 commit(su32(&acc_full));
                 ++n_u;
@@ -579,36 +759,48 @@ __global__ void k_set_status(int *status, int code)
 
 size_t tc_xplane_bytes(int64_t n_xch, int nrhs) { return (size_t)A_BYTES * (size_t)n_xch * (size_t)((nrhs + TM - 1) / TM); }
 
+size_t tc_t_bytes(int64_t n_tchunk, int nrhs)
+{
+    return sizeof(float) * (size_t)TC_T_CHUNK * (size_t)n_tchunk * (size_t)((nrhs + TM - 1) / TM);
+}
+
 // tensor-core products of the level's small items (dense and low-rank) for all
-// right-hand sides, in tiles of 128: split x, then the products
+// right-hand sides, in tiles of 128: split x, stage 1 of the low-rank products, then
+// the dense products and second stages
 void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
 {
     if (L.n_tcu == 0 || nrhs <= 0) return;
-    if (!h->ws.d_xpl || h->ws.xpl_bytes < tc_xplane_bytes(L.n_xch, nrhs)) {
-        // not reached through the API (the workspace is sized before every product); the call
+    const bool have_x = h->ws.d_xpl && h->ws.xpl_bytes >= tc_xplane_bytes(L.n_xch, nrhs);
+    const bool have_t = L.n_tcb == 0 || (h->ws.d_tct && h->ws.tct_bytes >= tc_t_bytes(L.n_tchunk, nrhs));
+    if (!have_x || !have_t) {
+        // not reached through the API (the workspaces are sized before every product); the call
         // reports HM_ERR_STATE through the status word instead of returning an incomplete product
-        fail(HM_ERR_STATE, "tensor-core product without its split-x workspace");
+        fail(HM_ERR_STATE, "tensor-core product without its split-x or stage-1 workspace");
         k_set_status<<<1, 32, 0, s>>>(h->d_status, (int)HM_ERR_STATE);
         return;
     }
     static bool attr = false;
     if (!attr) {   // two CTAs of ~98 KB per SM need the largest shared-memory carveout
-        cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+        for (const void *k : {(const void *)k_apply_tc, (const void *)k_tc_stage1}) {
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        }
         attr = true;
     }
     const int n_tiles = (nrhs + TM - 1) / TM;
+    const uint32_t limit = h->tc_wait_limit < 0 ? WAIT_LIMIT : (uint32_t)h->tc_wait_limit;
     k_split_x<<<dim3((unsigned)L.n_xch, (unsigned)n_tiles), TM, 0, s>>>(L.d_xch, L.n_xch, x, h->pN, nrhs, h->ws.d_xpl);
-    // two CTAs per SM: tensor memory holds 2 x 256 columns of 512, shared memory 2 x ~98 KB
-    // of 228 KB; the persistent loop is correct for any grid
-    const int per_sm = 2;
-    const int64_t units = L.n_tcu * (int64_t)n_tiles;
-    int64_t g = (int64_t)per_sm * (h->num_sms > 0 ? h->num_sms : 1);
-    if (g > units) g = units;
-    k_apply_tc<<<(unsigned)g, TT, SMEM, s>>>(L.d_tcu, (int)L.n_tcu, L.d_tcp, L.n_xch, h->ws.d_xpl, h->d_pool32, z,
-                                           h->pN, nrhs, h->d_status,
-                                           h->tc_wait_limit < 0 ? WAIT_LIMIT : (uint32_t)h->tc_wait_limit);
+    // two CTAs per SM in both launches: shared memory 2 x ~98 KB of 228 KB, tensor memory
+    // 2 x 256 (stage 1) or 2 x 128 columns of 512; the persistent loops are correct for any grid
+    const int64_t per_sm = 2 * (int64_t)(h->num_sms > 0 ? h->num_sms : 1);
+    if (L.n_tcb > 0) {
+        const int64_t g1 = std::min<int64_t>(per_sm, L.n_tcb * (int64_t)n_tiles);
+        k_tc_stage1<<<(unsigned)g1, TT, SMEM, s>>>(L.d_tcb, (int)L.n_tcb, L.d_tcr, L.d_tcc, L.n_xch, h->ws.d_xpl,
+                                                 h->d_pool32, h->ws.d_tct, L.n_tchunk, n_tiles, h->d_status, limit);
+    }
+    const int64_t g = std::min<int64_t>(per_sm, L.n_tcu * (int64_t)n_tiles);
+    k_apply_tc<<<(unsigned)g, TT, SMEM, s>>>(L.d_tcu, (int)L.n_tcu, L.d_tco, L.n_xch, h->ws.d_xpl, h->ws.d_tct,
+                                           L.n_tchunk, h->d_pool32, z, h->pN, nrhs, h->d_status, limit);
 }
 
 } // namespace hm
