@@ -647,10 +647,11 @@ def extra_configs(A2, local, barrier):
     A.close()
     del b, x
     torch.cuda.synchronize()
-    # config 5: a short serving stream (cold start, saturation, Poisson arrivals at 0.8 of it)
-    out["serving"] = serving_run(WORKLOADS["serving"], n_requests=300, loads=(0.8,), sat_requests=200, local=local)
-    out["serving_device_loop"] = serving_run(WORKLOADS["serving"], n_requests=300, loads=(0.8,), sat_requests=200,
-                                             local=local, device_loop=True)
+    # config 5: a short serving stream (cold start, saturation, Poisson arrivals at 0.5, 0.8 and 1.0 of it)
+    out["serving"] = serving_run(WORKLOADS["serving"], n_requests=300, loads=(0.5, 0.8, 1.0), sat_requests=200,
+                                 local=local)
+    out["serving_device_loop"] = serving_run(WORKLOADS["serving"], n_requests=300, loads=(0.5, 0.8, 1.0),
+                                             sat_requests=200, local=local, device_loop=True)
     return out
 
 

@@ -70,6 +70,7 @@ using namespace kc;
 constexpr int NWARP = 6;                         // 0 producer, 1-4 converters (tensor-memory lanes 32(w%4)..), 5 MMA
 constexpr int TT = NWARP * 32;
 constexpr int NCV = 128;                         // converter threads
+constexpr int NCW = NCV / 32;                    // converter warps: the arrivals on ready and acc_empty
 constexpr int TM = 128;                          // MMA M: right-hand sides per tile
 constexpr int KCH = 8;                           // K per chunk (complex unknowns; one MMA K step)
 constexpr int NSLOT = 3;
@@ -136,6 +137,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volati
     return false;
 }
 
+// converter warp: the bounded wait taken by the whole warp, so that its lanes leave
+// together (they go on to warp-collective steps: tcgen05.ld, one arrival per warp)
+__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, volatile int *abort, uint32_t limit)
+{
+    const bool ok = mbar_wait(mbar, parity, abort, limit);
+    return __all_sync(0xffffffffu, ok);
+}
+__device__ __forceinline__ bool warp_aborted(volatile int *abort) { return __any_sync(0xffffffffu, *abort != 0); }
+
 // wait for asynchronous work this thread issued (bulk copies, MMAs) before the CTA
 // frees what that work writes: the full bound, not cut short by an abort
 __device__ __forceinline__ void mbar_drain(uint32_t mbar, uint32_t parity, volatile int *abort)
@@ -148,6 +158,14 @@ __device__ __forceinline__ void mbar_drain(uint32_t mbar, uint32_t parity, volat
 __device__ __forceinline__ void arrive(uint32_t mbar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+// converter warp: one arrival for the warp once every lane is past its writes (each lane
+// has fenced its own shared-memory writes to the async proxy, or its tensor-memory loads,
+// before the warp synchronises; the arrival releases them all)
+__device__ __forceinline__ void warp_arrive(uint32_t mbar, int lane)
+{
+    __syncwarp();
+    if (lane == 0) arrive(mbar);
 }
 __device__ __forceinline__ void commit(uint32_t mbar)
 {
@@ -386,12 +404,14 @@ __device__ __forceinline__ void drain(uint32_t tmem, int quad, int lane, int m8,
 // quadrant quad, R8 stacked rows) as T chunks: group g of 8 rows -> chunk tch[g] of the
 // tile's T (tbase), Re and Im planes at row r's positions poff(r, k)
 __device__ __forceinline__ void store_t(uint32_t tmem, uint32_t acc, int quad, int lane, int R8,
-                                        const int32_t *__restrict__ tch, float *__restrict__ tbase)
+                                        const int32_t (&tch)[S1_ROWS / 8], float *__restrict__ tbase)
 {
     const int r = 32 * quad + lane;
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
     const int o0 = poff(r, 0) >> 2, o1 = poff(r, 4) >> 2;
-    for (int g = 0; g < R8 / 8; ++g) {
+#pragma unroll
+    for (int g = 0; g < S1_ROWS / 8; ++g) {
+        if (8 * g >= R8) break;
         float re[8], im[8];
         tld8(tmem + lane_base + acc + (uint32_t)(8 * g), re);
         tld8(tmem + lane_base + acc + (uint32_t)(R8 + 8 * g), im);
@@ -411,12 +431,12 @@ __device__ __forceinline__ void init_pipeline(uint64_t *full, uint64_t *ready, u
 {
     for (int s = 0; s < NSLOT; ++s) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[s])), "r"(33));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ready[s])), "r"(NCV));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ready[s])), "r"(NCW));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])));
     }
     for (int b = 0; b < n_acc; ++b) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&acc_full[b])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acc_empty[b])), "r"(NCV));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acc_empty[b])), "r"(NCW));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(fin)));
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -446,34 +466,55 @@ __device__ __forceinline__ void producer_drain(uint64_t *full, uint32_t n, int l
 // ---- k_tc_stage1: T = X W^T for batches of stacked W rows --------------------------
 
 // Position in a CTA's chunk sequence: batch-tile u (taken in turn with stride
-// gridDim.x, tile-major), chunk c of nch.  Every role walks the same sequence.
+// gridDim.x, tile-major), chunk c of nch; the next batch's record is loaded when a
+// batch begins.  Every role walks the same sequence.
 struct S1Pos {
     int64_t u;
     int c, nch, tile;
-    bool valid;
-    TcBatch B;
+    bool valid, has_next;
+    TcBatch B, Bn;
 };
 
 struct S1Seq {
     const TcBatch *batches;
     int n_batches;
     int64_t total;
-    __device__ void unit(S1Pos &q) const
+    __device__ void enter(S1Pos &q) const
+    {
+        q.tile = (int)(q.u / n_batches);
+        q.c = 0;
+        q.nch = (q.B.klen + KCH - 1) / KCH;
+        const int64_t un = q.u + gridDim.x;
+        q.has_next = un < total;
+        if (q.has_next) q.Bn = batches[un % n_batches];
+    }
+    __device__ void first(S1Pos &q) const
     {
         q.valid = q.u < total;
         if (!q.valid) return;
         q.B = batches[q.u % n_batches];
-        q.tile = (int)(q.u / n_batches);
-        q.c = 0;
-        q.nch = (q.B.klen + KCH - 1) / KCH;
+        enter(q);
     }
     __device__ void next(S1Pos &q) const
     {
         if (++q.c < q.nch) return;
         q.u += gridDim.x;
-        unit(q);
+        q.valid = q.has_next;
+        if (!q.valid) return;
+        q.B = q.Bn;
+        enter(q);
     }
 };
+
+// producer lane: the W offsets of its stacked rows (lane >> 2) + 8 i of batch B
+__device__ __forceinline__ void load_rows(int64_t (&rs)[8], const int64_t *__restrict__ rows, const TcBatch &B, int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int row = (lane >> 2) + 8 * i;
+        rs[i] = row < B.nrows ? rows[B.row0 + row] : -1;
+    }
+}
 
 __global__ void __launch_bounds__(TT, 2)
 k_tc_stage1(const TcBatch *__restrict__ batches, int n_batches, const int64_t *__restrict__ rows,
@@ -501,7 +542,7 @@ k_tc_stage1(const TcBatch *__restrict__ batches, int n_batches, const int64_t *_
     const S1Seq seq{batches, n_batches, (int64_t)n_batches * n_tiles};
     S1Pos q;
     q.u = blockIdx.x;
-    seq.unit(q);
+    seq.first(q);
     uint32_t n = 0;
 
     if (w == 0) {
@@ -509,22 +550,23 @@ k_tc_stage1(const TcBatch *__restrict__ batches, int n_batches, const int64_t *_
         uint64_t keep, stream;
         asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
         asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
-        int64_t rs[8];
+        // the row offsets of the current batch (rs) and, loaded while its first chunk goes
+        // out, of the next one (rsn)
+        int64_t rs[8], rsn[8];
+        if (q.valid) load_rows(rsn, rows, q.B, lane);
         while (q.valid && !abort_flag) {
             const int s = (int)(n % NSLOT);
             if (n >= NSLOT && !mbar_wait(su32(&empty[s]), ((n / NSLOT) + 1) & 1, &abort_flag, wait_limit)) break;
             if (q.c == 0) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int row = (lane >> 2) + 8 * i;
-                    rs[i] = row < q.B.nrows ? rows[q.B.row0 + row] : -1;
-                }
+                for (int i = 0; i < 8; ++i) rs[i] = rsn[i];
             }
             const uint32_t slot = sm0 + (uint32_t)(s * SLOT);
             if (lane == 0)
                 bulk_in(slot, xpl + ((int64_t)q.tile * n_xch + q.B.xg0 + q.c) * (A_BYTES / 4), A_BYTES, &full[s], keep);
             fetch_b_rows(slot + OFF_RAW, lane, pool, rs, q.B.nrows, q.c * KCH, q.B.klen, stream);
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&full[s])) : "memory");
+            if (q.c == 0 && q.has_next) load_rows(rsn, rows, q.Bn, lane);
             ++n;
             seq.next(q);
         }
@@ -533,21 +575,25 @@ k_tc_stage1(const TcBatch *__restrict__ batches, int n_batches, const int64_t *_
         // ---- converters: B planes, then each finished batch's T chunks
         const int t = tid - 32, quad = w & 3;
         uint32_t nb = 0;
-        while (q.valid && !abort_flag) {
+        int32_t tch[S1_ROWS / 8];   // the batch's T chunks, loaded at its first chunk, stored at its last
+        while (q.valid && !warp_aborted(&abort_flag)) {
             const int s = (int)(n % NSLOT);
-            if (!mbar_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
+            if (q.c == 0) {
+#pragma unroll
+                for (int g = 0; g < S1_ROWS / 8; ++g) tch[g] = 8 * g < q.B.nrows ? tchunks[q.B.row0 / 8 + g] : 0;
+            }
+            if (!warp_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
             float *bh = reinterpret_cast<float *>(smraw + s * SLOT + OFF_B), *bl = bh + B_PLANE / 4;
             conv_b_nat(bh, bl, smraw + s * SLOT + OFF_RAW, q.B.nrows, t);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            arrive(su32(&ready[s]));
+            warp_arrive(su32(&ready[s]), lane);
             if (q.c == q.nch - 1) {
                 const int b = (int)(nb & 1);
-                if (!mbar_wait(su32(&acc_full[b]), (nb >> 1) & 1, &abort_flag, wait_limit)) break;
+                if (!warp_wait(su32(&acc_full[b]), (nb >> 1) & 1, &abort_flag, wait_limit)) break;
                 fence_after();
-                store_t(tmem, (uint32_t)(128 * b), quad, lane, q.B.nrows, tchunks + q.B.row0 / 8,
-                        tct + (int64_t)q.tile * n_tchunk * TC_T_CHUNK);
+                store_t(tmem, (uint32_t)(128 * b), quad, lane, q.B.nrows, tch, tct + (int64_t)q.tile * n_tchunk * TC_T_CHUNK);
                 fence_before();
-                arrive(su32(&acc_empty[b]));
+                warp_arrive(su32(&acc_empty[b]), lane);
                 ++nb;
             }
             ++n;
@@ -587,14 +633,15 @@ k_tc_stage1(const TcBatch *__restrict__ batches, int n_batches, const int64_t *_
 
 // Position in a CTA's chunk sequence: unit-tile u (units taken in turn with stride
 // gridDim.x, tile-major so that one RHS tile's split x stays in L2), operation p of
-// the unit (the next one's record loaded ahead), chunk c of nch.  Every role walks
-// the same sequence.
+// the unit, chunk c of nch.  The next unit's record is loaded when a unit begins, the
+// next operation's (of this unit or the next) when an operation begins.  Every role
+// walks the same sequence.
 struct Pos {
     int64_t u;
     int p, c, nch;
     int tile, r0, nr, m8;
-    bool valid;
-    TcUnit U;
+    bool valid, has_next;
+    TcUnit U, Un;
     TcOp P, Pn;
     __device__ bool last_of_unit() const { return c == nch - 1 && p == U.p1 - 1; }
 };
@@ -607,19 +654,27 @@ struct Seq {
     __device__ void start(Pos &q) const
     {
         if (q.p + 1 < q.U.p1) q.Pn = ops[q.p + 1];
+        else if (q.has_next) q.Pn = ops[q.Un.p0];
         q.c = 0;
         q.nch = (q.P.klen + KCH - 1) / KCH;
     }
-    __device__ void unit(Pos &q) const
+    __device__ void enter(Pos &q) const
     {
-        q.valid = q.u < total;
-        if (!q.valid) return;
-        q.U = units[q.u % n_units];
         q.tile = (int)(q.u / n_units);
         q.r0 = q.tile * TM;
         q.nr = min(TM, nrhs - q.r0);
         q.m8 = (q.U.mlen + 7) & ~7;
         q.p = q.U.p0;
+        const int64_t un = q.u + gridDim.x;
+        q.has_next = un < total;
+        if (q.has_next) q.Un = units[un % n_units];
+    }
+    __device__ void first(Pos &q) const
+    {
+        q.valid = q.u < total;
+        if (!q.valid) return;
+        q.U = units[q.u % n_units];
+        enter(q);
         q.P = ops[q.p];
         start(q);
     }
@@ -632,7 +687,12 @@ struct Seq {
             return;
         }
         q.u += gridDim.x;
-        unit(q);
+        q.valid = q.has_next;
+        if (!q.valid) return;
+        q.U = q.Un;
+        enter(q);
+        q.P = q.Pn;
+        start(q);
     }
 };
 
@@ -662,7 +722,7 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcOp *__restrict
     const Seq seq{units, ops, n_units, nrhs, (int64_t)n_units * ((nrhs + TM - 1) / TM)};
     Pos q;
     q.u = blockIdx.x;
-    seq.unit(q);
+    seq.first(q);
     uint32_t n = 0;
 
     if (w == 0) {
@@ -697,9 +757,9 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcOp *__restrict
         // ---- converters: B planes (and A planes from a raw T chunk), accumulators into z
         const int t = tid - 32, quad = w & 3;
         uint32_t n_u = 0;
-        while (q.valid && !abort_flag) {
+        while (q.valid && !warp_aborted(&abort_flag)) {
             const int s = (int)(n % NSLOT);
-            if (!mbar_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
+            if (!warp_wait(su32(&full[s]), (n / NSLOT) & 1, &abort_flag, wait_limit)) break;
             float *slot = reinterpret_cast<float *>(smraw + s * SLOT);
             const unsigned char *raw = smraw + s * SLOT + OFF_RAW;
             float *bh = reinterpret_cast<float *>(smraw + s * SLOT + OFF_B), *bl = bh + B_PLANE / 4;
@@ -707,13 +767,13 @@ k_apply_tc(const TcUnit *__restrict__ units, int n_units, const TcOp *__restrict
             if (q.P.kind == 0) conv_b_nat(bh, bl, raw, q.m8, t);
             else conv_b_tr(bh, bl, raw, q.m8, t);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            arrive(su32(&ready[s]));
+            warp_arrive(su32(&ready[s]), lane);
             if (q.last_of_unit()) {
-                if (!mbar_wait(su32(&acc_full), n_u & 1, &abort_flag, wait_limit)) break;
+                if (!warp_wait(su32(&acc_full), n_u & 1, &abort_flag, wait_limit)) break;
                 fence_after();
                 drain(tmem, quad, lane, q.m8, q.U.mlen, z, ldz, q.r0, q.nr, q.U.out0);
                 fence_before();
-                arrive(su32(&acc_empty));
+                warp_arrive(su32(&acc_empty), lane);
                 ++n_u;
             }
             ++n;
