@@ -450,7 +450,10 @@ hm_status hm_get_tuning(hm_matrix h, int nrhs, int *prod_rb, int *res_rb, double
  * letting the autotuner time it (e.g. for reproducible benchmarks or to test a
  * kernel): prod_rb 0 (one right-hand side at a time), 8 / 16 / 32 (shared-memory
  * SIMT chunks) or 1016 (tensor-core products of the blocks of at most 64 x 64 and
- * rank <= 32, dense and low-rank, tiles of 128 right-hand sides, tcgen05 3xTF32);
+ * rank <= 32, dense and low-rank, tiles of 128 right-hand sides, tcgen05 3xTF32;
+ * the first call that runs it allocates its stage-1 workspace: the low-rank
+ * intermediates, 8 KB per 8 rank rows of every low-rank block side and per tile,
+ * counted in hm_info.device_bytes);
  * res_rb 0, 8, 16 or 1017 (owner-computes; calls whose levels hold larger blocks
  * fall back to the partial-slot kernel of one right-hand side at a time).  Drops captured solve graphs.  HM_ERR_ARG for nrhs < 4 or
  * another value.

@@ -43,7 +43,9 @@
 // solve 1.2e-4, above the 1e-4 bar; with units of at most 64 chunks
 // (TC_UNIT_CHUNKS: each unit's sum is drained into z in FP32) the product errs
 // 1.9e-6, and the 181-RHS sweep of the 30,720-unknown sphere stays within 2.3e-5 of
-// the oracle (16-chunk units: 5.4e-7 and 7e-6, at 31 % more time per launch).
+// the oracle (16-chunk units: 5.4e-7 and 7e-6, at 31 % more time per launch); in two
+// launches, whose units gather about five times as many low-rank products (only their
+// second-stage chunks count), the sweep stays within 2.9e-5.
 // Adding the lo*lo products changed neither (same errors to four digits).
 //
 // Pipeline (both kernels; warp-specialised, mbarrier hand-offs, no CTA-wide barrier
@@ -417,11 +419,12 @@ __device__ __forceinline__ void store_t(uint32_t tmem, uint32_t acc, int quad, i
         tld8(tmem + lane_base + acc + (uint32_t)(R8 + 8 * g), im);
         const int64_t chunk = tch[g];
         tld_wait();
+        // streaming stores (evict first): T passes through L2 once, the split x stays
         float4 *d = reinterpret_cast<float4 *>(tbase + chunk * TC_T_CHUNK);
-        d[o0] = make_float4(re[0], re[1], re[2], re[3]);
-        d[o1] = make_float4(re[4], re[5], re[6], re[7]);
-        d[T_PLANE / 4 + o0] = make_float4(im[0], im[1], im[2], im[3]);
-        d[T_PLANE / 4 + o1] = make_float4(im[4], im[5], im[6], im[7]);
+        __stcs(d + o0, make_float4(re[0], re[1], re[2], re[3]));
+        __stcs(d + o1, make_float4(re[4], re[5], re[6], re[7]));
+        __stcs(d + T_PLANE / 4 + o0, make_float4(im[0], im[1], im[2], im[3]));
+        __stcs(d + T_PLANE / 4 + o1, make_float4(im[4], im[5], im[6], im[7]));
     }
 }
 
