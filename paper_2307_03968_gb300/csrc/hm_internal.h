@@ -23,18 +23,14 @@
 #include <tuple>
 
 #include "../../include/hmps.h"
+#include "hm_lists.h"
 
 namespace hm {
 
-constexpr int MRHS_MAX_DIM = 64;    // largest block side of the multi-RHS product kernel
-constexpr int MRHS_MAX_RANK = 32;   // largest rank of a low-rank block it takes
 constexpr int MRHS_MIN_RHS = 4;     // from this many right-hand sides on, the multi-RHS kernels take the small blocks
 constexpr int RESID_CHUNK = 16;     // right-hand sides per chunk of the FP64-class residual (partial slots held)
 constexpr int RB_TC = 1016;         // product choice: tensor-core products of the small items, RHS tiles of 128
-constexpr int TC_MAX_DIM = MRHS_MAX_DIM;    // the tensor-core product takes the same small items
-constexpr int TC_MAX_RANK = MRHS_MAX_RANK;
 constexpr int TC_MIN_RHS = 32;      // the autotuner times the tensor-core product from this many RHS on
-constexpr int TC_UNIT_CHUNKS = 64;  // K chunks (of 8) a tensor-core work unit sums in tensor memory
 constexpr int RB_OWN = 1017;        // residual choice: owner-computes FP64-class products (levels of small items)
 
 // Double-float numbers of the FP64-class residual (hi + lo, |lo| a few ulps of hi at
@@ -45,69 +41,6 @@ struct df { float hi, lo; };
 struct alignas(16) cdf { df re, im; };
 } // namespace dot2
 
-// One stored block = one work item of the product kernels (32 bytes).
-struct Item {
-    int64_t off;    // complex-element offset into the pool
-    int32_t row0;   // padded-tree offset of the row cluster
-    int32_t col0;   // padded-tree offset of the column cluster
-    int32_t m, n;   // padded cluster lengths (dense: m = true rows, n = true cols)
-    int32_t k;      // rank; 0 = dense block
-    int32_t pad;    // offset of the block's partial slots (row side, then column side)
-};
-static_assert(sizeof(Item) == 32, "Item layout");
-
-// One directed product of a small stored block into an output cluster (the
-// owner-computes residual, k_resid_own.cu): Z_out += B X_in with B the block (dense,
-// read row-major or transposed) or, for a low-rank block, Y (W X_in) with the
-// input-side factor W read row-major (rank rows) and the output-side factor Y
-// read transposed.
-struct TcProd {
-    int64_t b_off;   // complex offset of the block (dense) or of W (low-rank)
-    int64_t y_off;   // complex offset of Y (low-rank)
-    int32_t in0;     // padded-tree offset of the input cluster
-    int32_t klen;    // input length (K of the dense product and of stage 1)
-    int32_t rank;    // 0 = dense
-    int32_t b_ld;    // row stride of the block / of W
-    int32_t y_ld;    // row stride of Y as stored (rank rows)
-    int32_t trans;   // dense: 1 = element (out i, in j) is block[j][i] (the mirror product)
-    int32_t olen;    // output length of this product
-    int32_t xg0;     // first K chunk of the input cluster in the level's split-x chunk list
-};
-static_assert(sizeof(TcProd) == 48, "TcProd layout");
-// a work unit: products [p0, p1) into the output cluster at out0 (mlen = largest olen)
-struct TcUnit { int32_t out0, mlen, p0, p1; };
-
-// The tensor-core product (k_mrhs_tc.cu) in two launches.  The first runs stage 1 of
-// every low-rank directed product, T = W X_in, batched over the products that share
-// an input cluster (their W rows stacked along N); it stores T in chunks of 8 rank
-// rows (TC_T_CHUNK floats per chunk and RHS tile).  The second runs, per output
-// cluster, the dense products and the second stages Y T, which read T back.
-constexpr int TC_T_CHUNK = 2 * 128 * 8;   // floats of one T chunk: Re and Im planes of 128 RHS x 8 rank rows
-// one operation of the second launch
-struct TcOp {
-    int64_t src;     // complex offset of the dense block, or of Y (low-rank second stage)
-    int64_t t0;      // low-rank: first T chunk of the product (per RHS tile)
-    int32_t kind;    // 0 dense (element (out i, in j) = block[i][j]), 1 dense mirror (= block[j][i]), 2 Y T
-    int32_t klen;    // K length: the input length (dense) or the rank
-    int32_t ld;      // row stride of the block or of Y as stored (rank rows)
-    int32_t olen;    // output length
-    int32_t xg0;     // dense: first split-x chunk of the input cluster
-    int32_t pad;
-};
-static_assert(sizeof(TcOp) == 40, "TcOp layout");
-// a batch of the first launch: stacked rows [row0, row0 + nrows) (nrows a multiple of
-// 8, at most 64) of the row table, all over one input cluster (split-x chunks from xg0,
-// K length klen); each row's W offset (-1: a zero row) is in the row table, each group
-// of 8 rows' T chunk in the chunk table (index row / 8)
-struct TcBatch { int32_t xg0, klen, row0, nrows; };
-
-__host__ __device__ inline int64_t even(int64_t v) { return (v + 1) & ~int64_t(1); }
-
-__host__ __device__ inline int64_t item_elems(const Item &it)
-{
-    if (it.k == 0) return int64_t(it.m) * even(it.n);
-    return int64_t(it.k) * (even(it.m) + even(it.n));
-}
 
 struct LevelList {
     int64_t alg_elems = 0;        // complex elements at unpadded sizes (algorithmic bytes / 8)
@@ -142,7 +75,7 @@ struct LevelList {
     float2 *d_rcb = nullptr;      // per product of d_rcp: its common-grid bounds (k_prod_bounds)
     // the input clusters' K chunks of 8 unknowns (padded-tree offset, valid length):
     // the tensor-core product splits x once per launch into these chunks
-    int2 *d_xch = nullptr;
+    XChunk *d_xch = nullptr;
     int64_t n_xch = 0;
     int64_t n_dense = 0, n_lowrank = 0;
     int64_t elems = 0;            // stored complex elements

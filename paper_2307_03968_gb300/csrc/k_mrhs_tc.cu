@@ -219,20 +219,20 @@ __device__ __forceinline__ void put_a_row(float4 *p, int r, const float (&re)[8]
 // split x once per launch: chunk g of the input clusters (unknowns off .. off+valid-1)
 // for RHS tile t (rows r0 .. r0+127) -> xpl[(t * n_xch + g)], A_BYTES each
 __global__ void __launch_bounds__(TM)
-k_split_x(const int2 *__restrict__ xch, int64_t n_xch, const float2 *__restrict__ x, int64_t ldx, int nrhs,
+k_split_x(const XChunk *__restrict__ xch, int64_t n_xch, const float2 *__restrict__ x, int64_t ldx, int nrhs,
           float *__restrict__ xpl)
 {
     const int64_t g = blockIdx.x;
     const int t = blockIdx.y, r = threadIdx.x, r0 = t * TM;
-    const int2 ch = xch[g];
+    const XChunk ch = xch[g];
     float re[8], im[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) { re[j] = 0.f; im[j] = 0.f; }
     if (r0 + r < nrhs) {
-        const float2 *src = x + (int64_t)(r0 + r) * ldx + ch.x;
+        const float2 *src = x + (int64_t)(r0 + r) * ldx + ch.off;
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (j < ch.y) { const float2 v = __ldg(src + j); re[j] = v.x; im[j] = v.y; }
+            if (j < ch.len) { const float2 v = __ldg(src + j); re[j] = v.x; im[j] = v.y; }
     }
     put_a_row(reinterpret_cast<float4 *>(xpl + ((int64_t)t * n_xch + g) * (A_BYTES / 4)), r, re, im);
 }
