@@ -517,9 +517,9 @@ def product_roofline(A, b, x, opts, nrhs, Kp, sm_max):
         bound, unit, rpeak = "tensor", "TFLOP/s", tf32 / 3.0
         rkind = ("measured sustained bf16 %.1f TFLOP/s x 1.1/2.25 (TF32) / 3 (3xTF32 products)" % bf16_s
                  if bf16_s else "fallback 1.7 PFLOP/s bf16 sustained x 1.1/2.25 / 3")
-        kernel = ("k_split_x + k_apply_tc (tcgen05 kind::tf32, 3xTF32; units of <= 64 K chunks; blocks <= 64 x 64, "
-                  "rank <= 32) "
-                  "+ k_apply_items for larger blocks (k_mrhs_tc.cu, k_product.cu)")
+        kernel = ("k_split_x + k_tc_stage1 (low-rank stage 1 batched over shared input clusters) + k_apply_tc "
+                  "(dense products and second stages; tcgen05 kind::tf32, 3xTF32; units of <= 64 K chunks; blocks "
+                  "<= 64 x 64, rank <= 32) + k_apply_items for larger blocks (k_mrhs_tc.cu, k_product.cu)")
     elif flops_per_launch / (alu_peak * 1e12) > per_launch_bytes / (peak * 1e9):
         bound, unit, rpeak = "alu", "TFLOP/s", alu_peak
         rkind = "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
