@@ -18,6 +18,9 @@ Modules
 
 Parity status
   Every function above is pinned by tests under ``tests/test_oracle_*.py``.
-  The nested multi-level series at finite K has no printed values in the
-  paper; beyond the brute-force dense recursion it is "parity unpinned".
+  The paper prints no values of the nested multi-level series at finite K; it
+  is pinned by brute force instead: on an operator with far blocks on three
+  levels, at 1, 2 and 3 levels and K = 1, 2 (plain and refined), it equals the
+  same operators formed as dense matrix products with explicit matrix powers,
+  and it reaches the closed form A_m^{-1} b as K grows.
 """

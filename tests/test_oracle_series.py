@@ -9,7 +9,11 @@
 - special cases: a single leaf gives the exact solve, zero coupling gives
   D^{-1} b, a random diagonal alpha (eqs. 9-12) changes nothing;
 - reciprocity: every form is a symmetric operator applied to b;
-- one refinement step squares the truncation factor.
+- one refinement step squares the truncation factor;
+- at finite K on an operator with far blocks on three levels: the nested form
+  (eq. 19) at m = 1, 2, 3 levels, plain and refined, and the flat form equal the
+  same operators written as dense matrix products (P_0 = D^{-1},
+  P_m = sum_{k<=K} (-P_{m-1} M_m)^k P_{m-1}), with explicit matrix powers.
 """
 
 import copy
@@ -162,3 +166,76 @@ def test_refinement_squares_truncation(hm2, rhs2):
     x = H.to_tree(series.solve(H, rhs2, K=K, levels=1, refine=True))
     pred = np.linalg.matrix_power(-U, 2 * (K + 1)) @ xs
     assert np.linalg.norm((xs - x) - pred) < 1e-9 * np.linalg.norm(pred)
+
+
+@pytest.fixture(scope="module")
+def hm3(sphere_small):
+    """The 1,920-unknown sphere on a binary tree with leaves of 16: far blocks on three
+    levels (about 2,300, 640 and 4 of them)."""
+    H = HMatrix(sphere_small, leaf_size=16, arity=2, adm=1.0, aca_tol=1e-4)
+    assert H.n_levels == 3 and all(len(H.far.get(lev, [])) > 0 for lev in (1, 2, 3))
+    return H
+
+
+@pytest.fixture(scope="module")
+def dense3(hm3):
+    """D, M_1..M_3 and, for K = 1 and 2, the dense P_1 and P_2 of eq. 19."""
+    D, M = dense_parts(hm3)
+    Dinv = np.linalg.inv(D)
+    P = {}
+    for K in (1, 2):
+        Pm = Dinv
+        for lev in (1, 2):
+            T = Pm @ M[lev]
+            S = sum(np.linalg.matrix_power(-T, k) for k in range(K + 1))
+            Pm = S @ Pm
+            P[K, lev] = Pm
+        P[K, 0] = Dinv
+    return D, M, P
+
+
+def dense_apply_P(dense, K, m, v):
+    """P_m v from the dense matrices: P_1, P_2 as formed above; P_3 v = S_K(T_3)(P_2 v)
+    with T_3 = P_2 M_3, as the explicit sum of matrix powers applied to P_2 v."""
+    D, M, P = dense
+    if m <= 2:
+        return P[K, m] @ v
+    T = P[K, 2] @ M[3]
+    y = P[K, 2] @ v
+    return sum(np.linalg.matrix_power(-T, k) @ y for k in range(K + 1))
+
+
+@pytest.mark.parametrize("K", [1, 2])
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_nested_series_equals_dense_products_on_three_levels(hm3, dense3, rhs2, K, m):
+    bt = hm3.to_tree(rhs2)
+    ref = dense_apply_P(dense3, K, m, bt)
+    got = hm3.to_tree(series.solve(hm3, rhs2, K=K, levels=m))
+    assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref)
+
+
+def test_refined_nested_series_equals_dense_products_on_three_levels(hm3, dense3, rhs2):
+    D, M, _ = dense3
+    A = D + M[1] + M[2] + M[3]
+    bt = hm3.to_tree(rhs2)
+    x1 = dense_apply_P(dense3, 2, 3, bt)
+    ref = x1 + dense_apply_P(dense3, 2, 3, bt - A @ x1)
+    got = hm3.to_tree(series.solve(hm3, rhs2, K=2, levels=-1, refine=True))
+    assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref)
+
+
+def test_flat_series_equals_dense_powers_on_three_levels(hm3, dense3, rhs2):
+    D, M, P = dense3
+    U = P[1, 0] @ (M[1] + M[2] + M[3])
+    y = P[1, 0] @ hm3.to_tree(rhs2)
+    ref = sum(np.linalg.matrix_power(-U, k) @ y for k in range(3))
+    got = hm3.to_tree(series.solve(hm3, rhs2, K=2, levels=3, nested_form=False))
+    assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref)
+
+
+def test_nested_and_flat_differ_beyond_the_leaf_level(hm3, rhs2):
+    """The two forms agree at m = 1 and differ at finite K for m > 1 (the nested form
+    re-applies the inner series inside every outer term), so the pins above tell them apart."""
+    a = series.solve(hm3, rhs2, K=2, levels=3, nested_form=True)
+    b = series.solve(hm3, rhs2, K=2, levels=3, nested_form=False)
+    assert np.linalg.norm(a - b) > 1e-6 * np.linalg.norm(a)
