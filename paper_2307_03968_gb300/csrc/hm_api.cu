@@ -503,7 +503,7 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
         }
         if (h->prof_used + 2 <= h->prof_ev.size()) cudaEventRecord(h->prof_ev[h->prof_used], c.s);
     }
-    launch_apply_items(c.h, it->second, x, z, c.nrhs, c.fp64, c.s, c.prod_rb);
+    const int launched = launch_apply_items(c.h, it->second, x, z, c.nrhs, c.fp64, c.s, c.prod_rb);
     if (timed && h->prof_used + 2 <= h->prof_ev.size()) {
         cudaEventRecord(h->prof_ev[h->prof_used + 1], c.s);
         h->prof_used += 2;
@@ -511,7 +511,7 @@ static void apply_level(SolveCtx &c, int lev, const void *x, void *z)
         // algorithmic bytes: every stored block once, x read and z written once per right-hand side
         h->prof_bytes += it->second.alg_elems * 8 + 2 * 8 * h->N * (int64_t)c.nrhs;
     }
-    c.launches++;
+    c.launches += launched;
     c.bytes += level_bytes(c.h, lev, c.fp64) * c.nrhs;
 }
 
@@ -763,8 +763,8 @@ static void residual64(SolveCtx &c, const float2 *xt, const float2 *bt, float2 *
         for (int lev = 1; lev <= c.m; ++lev) {
             auto it = h->levels.find(lev);
             if (it == h->levels.end() || it->second.items.empty()) continue;
-            launch_apply_items_partials(h, it->second, x, h->ws.d_part, h->partial_elems, nr, c.s, c.res_rb);
-            c.launches++;
+            c.launches += launch_apply_items_partials(h, it->second, x, h->ws.d_part, h->partial_elems, nr, c.s,
+                                                      c.res_rb);
         }
         if (y_next && nr == c.nrhs) {
             launch_gather_leaf_update(h, x, c.m, h->ws.d_part, h->partial_elems, bt, out, norms, y_next, nr, c.s);

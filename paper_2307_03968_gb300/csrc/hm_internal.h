@@ -300,8 +300,9 @@ void launch_permute_out(const void *xt, int64_t pN, void *x, int64_t ldx, const 
 void launch_zero(void *p, size_t bytes, cudaStream_t s);
 // z (+)= M_level x  for one item list; z must be pre-zeroed by the caller
 // rb: -1 = default choice by nrhs, 0 = one right-hand side at a time for every block,
-// 8 / 16 / 32 = shared-memory multi-RHS kernel with that chunk for the blocks it takes
-void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
+// 8 / 16 / 32 = shared-memory multi-RHS kernel with that chunk for the blocks it takes.
+// Returns the number of kernels it enqueued.
+int launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
                         cudaStream_t s, int rb = -1);
 // FP64-class (Dot2) products of every block of a level into its partial slots (no atomics)
 // warps of the FP32 product kernel's persistent grid (k_product.cu) and of the
@@ -310,8 +311,8 @@ int64_t product_warps(hm_matrix h);
 int64_t residual_warps(hm_matrix h);
 // the residual products' block bounds of items[0 .. n) (k_residual.cu)
 void launch_item_bounds(const Item *items, int64_t n, const float2 *pool, float4 *bnd, cudaStream_t s);
-void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part, int64_t pstride,
-                                 int nrhs, cudaStream_t s, int rb = -1);
+int launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part, int64_t pstride,
+                                int nrhs, cudaStream_t s, int rb = -1);   // returns the kernels enqueued
 // per leaf: acc = D x + sum of the leaf's partial slots of levels 1..m (double-float, fixed order);
 // out = b - acc (+ norms) when b is given, else out = acc (rounded to complex64)
 void launch_gather_acc64(hm_matrix h, const float2 *x, int m, const dot2::cdf *part, int64_t pstride,
@@ -404,7 +405,7 @@ size_t tc_xplane_bytes(int64_t n_xch, int nrhs);
 size_t tc_t_bytes(int64_t n_tchunk, int nrhs);
 // tensor-core products of a level's small items for all right-hand sides (k_mrhs_tc.cu);
 // z accumulates (vector atomics); needs the split-x and stage-1 workspaces for nrhs
-void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s);
+int launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s);
 // the FP64-class partial-slot products of the small items for many right-hand sides (k_mrhs.cu)
 void launch_apply_items_partials_mrhs(hm_matrix h, const LevelList &L, const float2 *x, dot2::cdf *part,
                                       int64_t pstride, int nrhs, cudaStream_t s, int rb = -1);

@@ -830,9 +830,9 @@ size_t tc_t_bytes(int64_t n_tchunk, int nrhs)
 // tensor-core products of the level's small items (dense and low-rank) for all
 // right-hand sides, in tiles of 128: split x, stage 1 of the low-rank products, then
 // the dense products and second stages
-void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
+int launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z, int nrhs, cudaStream_t s)
 {
-    if (L.n_tcu == 0 || nrhs <= 0) return;
+    if (L.n_tcu == 0 || nrhs <= 0) return 0;
     const bool have_x = h->ws.d_xpl && h->ws.xpl_bytes >= tc_xplane_bytes(L.n_xch, nrhs);
     const bool have_t = L.n_tcb == 0 || (h->ws.d_tct && h->ws.tct_bytes >= tc_t_bytes(L.n_tchunk, nrhs));
     if (!have_x || !have_t) {
@@ -840,7 +840,7 @@ void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z
         // reports HM_ERR_STATE through the status word instead of returning an incomplete product
         fail(HM_ERR_STATE, "tensor-core product without its split-x or stage-1 workspace");
         k_set_status<<<1, 32, 0, s>>>(h->d_status, (int)HM_ERR_STATE);
-        return;
+        return 1;
     }
     static bool attr = false;
     if (!attr) {   // two CTAs of ~98 KB per SM need the largest shared-memory carveout
@@ -864,6 +864,7 @@ void launch_apply_tc(hm_matrix h, const LevelList &L, const float2 *x, float2 *z
     const int64_t g = std::min<int64_t>(per_sm, L.n_tcu * (int64_t)n_tiles);
     k_apply_tc<<<(unsigned)g, TT, SMEM, s>>>(L.d_tcu, (int)L.n_tcu, L.d_tco, L.n_xch, h->ws.d_xpl, h->ws.d_tct,
                                            L.n_tchunk, h->d_pool32, z, h->pN, nrhs, h->d_status, limit);
+    return L.n_tcb > 0 ? 3 : 2;
 }
 
 } // namespace hm

@@ -68,38 +68,42 @@ int64_t product_warps(hm_matrix h)
     return (int64_t)apply_grid<float, float, 3>(h) * APPLY_WARPS;
 }
 
-void launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
-                        cudaStream_t s, int rb)
+int launch_apply_items(hm_matrix h, const LevelList &L, const void *x, void *z, int nrhs, bool fp64,
+                       cudaStream_t s, int rb)
 {
     const int64_t n = (int64_t)L.items.size();
-    if (n == 0) return;
+    if (n == 0) return 0;
     if (fp64) {
         int g = apply_grid<double, double, 1>(h);
         if ((int64_t)g * APPLY_WARPS > n) g = (int)((n + APPLY_WARPS - 1) / APPLY_WARPS);
         k_apply_items<double, double, 1><<<g, APPLY_WARPS * 32, 0, s>>>(
             L.d_items, n, h->d_pool64, (const double2 *)x, h->pN, (double2 *)z, h->pN, nrhs);
+        return 1;
     } else {
+        int launched = 0;
         // tall dense blocks go as row panels (LevelList::d_prod), one warp each
         const Item *list = L.d_prod ? L.d_prod : L.d_items;
         int64_t cnt = L.d_prod ? L.n_prod : n;
         if (rb < 0) rb = nrhs < MRHS_MIN_RHS ? 0 : nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : 32;
         if (rb == RB_TC && nrhs > 1) {
             // the small blocks (dense and low-rank) on the tensor cores
-            launch_apply_tc(h, L, (const float2 *)x, (float2 *)z, nrhs, s);
+            launched += launch_apply_tc(h, L, (const float2 *)x, (float2 *)z, nrhs, s);
             list = L.d_prod ? L.d_prod_big : L.d_big;
             cnt = L.d_prod ? L.n_prod_big : L.n_big;
-            if (cnt == 0) return;
+            if (cnt == 0) return launched;
         } else if (rb > 0 && nrhs > 1 && L.n_small > 0) {
             // many right-hand sides: blocks that fit shared memory are read once per RHS chunk
             launch_apply_items_mrhs(h, L, (const float2 *)x, (float2 *)z, nrhs, rb, s);
+            launched += 1;
             list = L.d_prod ? L.d_prod_big : L.d_big;
             cnt = L.d_prod ? L.n_prod_big : L.n_big;
-            if (cnt == 0) return;
+            if (cnt == 0) return launched;
         }
         int g = apply_grid<float, float, 3>(h);
         if ((int64_t)g * APPLY_WARPS > cnt) g = (int)((cnt + APPLY_WARPS - 1) / APPLY_WARPS);
         k_apply_items<float, float, 3><<<g, APPLY_WARPS * 32, 0, s>>>(
             list, cnt, h->d_pool32, (const float2 *)x, h->pN, (float2 *)z, h->pN, nrhs);
+        return launched + 1;
     }
 }
 

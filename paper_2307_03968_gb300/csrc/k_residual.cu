@@ -106,9 +106,10 @@ void launch_gather_leaf_update(hm_matrix h, const float2 *x, int m, const cdf *p
         h->d_csr_idx, part, pstride, b, out, norms, y);
 }
 
-void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, cdf *part, int64_t pstride,
-                                 int nrhs, cudaStream_t s, int rb)
+int launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *x, cdf *part, int64_t pstride,
+                                int nrhs, cudaStream_t s, int rb)
 {
+    int launched = 0;
     const Item *list = L.d_res;
     const float4 *bnd = L.d_bnd;
     int64_t n = (int64_t)L.items.size();
@@ -116,14 +117,16 @@ void launch_apply_items_partials(hm_matrix h, const LevelList &L, const float2 *
     if (rb > 0 && nrhs > 1 && L.n_small > 0) {
         // many right-hand sides: blocks that fit shared memory are read once per chunk
         launch_apply_items_partials_mrhs(h, L, x, part, pstride, nrhs, s, rb);
+        launched = 1;
         list = L.d_big;
         bnd = L.d_bnd_big;
         n = L.n_big;
     }
-    if (n == 0) return;
+    if (n == 0) return launched;
     int g = (int)(residual_warps(h) / APPLY_WARPS);
     if ((int64_t)g * APPLY_WARPS > n) g = (int)((n + APPLY_WARPS - 1) / APPLY_WARPS);
     k_residual_items<<<g, APPLY_WARPS * 32, 0, s>>>(list, bnd, n, h->d_pool32, x, h->pN, part, pstride, nrhs);
+    return launched + 1;
 }
 
 int64_t residual_warps(hm_matrix h)
