@@ -45,28 +45,6 @@ template <class T> static hm_status upload(hm_matrix h, T **dst, const std::vect
     return HM_OK;
 }
 
-// items reordered for a persistent kernel whose nw warps take items t, t + nw, ...:
-// sorted by cost, largest first, and every odd round of nw reversed (a snake), so that
-// the warps' sums match.  Cost of the product: stored bytes plus a fixed 2 KB for the
-// per-block latencies; of the FP64-class residual (instruction-bound): about 39 lane
-// instructions per stored element of a dense block, 52 of a low-rank one, plus 3,000.
-static int64_t product_cost(const Item &it) { return item_elems(it) * 8 + 2048; }
-static int64_t residual_cost(const Item &it) { return item_elems(it) * (it.k == 0 ? 39 : 52) + 3000; }
-template <class Cost>
-static std::vector<Item> balanced_order(const std::vector<Item> &in, int64_t nw, Cost cost)
-{
-    std::vector<Item> v = in;
-    std::stable_sort(v.begin(), v.end(), [&](const Item &a, const Item &b) { return cost(a) > cost(b); });
-    const int64_t n = (int64_t)v.size();
-    nw = std::min<int64_t>(std::max<int64_t>(nw, 1), std::max<int64_t>(n, 1));
-    std::vector<Item> out(v.size());
-    for (int64_t t = 0; t < n; ++t) {
-        const int64_t q = t / nw, p = t % nw, rem = std::min<int64_t>(nw, n - q * nw);
-        out[t] = v[q * nw + ((q & 1) ? rem - 1 - p : p)];
-    }
-    return out;
-}
-
 hm_status upload_item_lists(hm_matrix h, cudaStream_t s)
 {
     hm_status st;

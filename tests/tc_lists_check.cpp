@@ -1,7 +1,9 @@
 // Host-side check of the block products' work lists (csrc/hm_lists.h): builds the
 // directed products, the owner-computes residual's units and the tensor-core
 // product's two-launch lists for a random set of small blocks, and checks every
-// property the kernels rely on.  Prints "ok ..." and exits 0, or prints the first
+// property the kernels rely on; also the snake order the persistent product and
+// residual kernels take their blocks in (each block once, warp sums within the
+// largest cost of one another).  Prints "ok ..." and exits 0, or prints the first
 // violation and exits 1.
 //
 // usage: tc_lists_check <seed> <mode>
@@ -12,6 +14,8 @@
 //   mode 4: one dense block on the diagonal cluster pair (both directed products into one cluster)
 //   mode 5: mode 0 with two entries of the chunk table swapped after the build (must FAIL)
 //   mode 6: mode 0 with one batch moved by a group of 8 rows after the build (must FAIL)
+//   mode 7: mode 0 with the blocks handed out in build order, unsorted (must FAIL the
+//           balance check)
 #include "hm_lists.h"
 
 #include <cstdio>
@@ -55,7 +59,7 @@ int main(int argc, char **argv)
         for (int i = 0; i < ncl; ++i)
             for (int j = i; j < ncl; ++j) {
                 if (uni(0, 2) != 0) continue;
-                const int k = mode == 1 ? 32 : mode == 2 ? 1 : (uni(0, 1) ? uni(1, 32) : 0);   // modes 0, 5, 6
+                const int k = mode == 1 ? 32 : mode == 2 ? 1 : (uni(0, 1) ? uni(1, 32) : 0);   // modes 0, 5-7
                 add(i, j, k);
             }
     }
@@ -180,6 +184,29 @@ int main(int argc, char **argv)
                         found = found || T.xch[o.xg0].off == p.in0;
                 if (!found) return fail("dense operation's split x");
             }
+
+    // snake order for nw round-robin warps: a permutation of the blocks, and no two warps'
+    // cost sums more than the largest cost apart
+    for (int pass = 0; pass < 2; ++pass)
+        for (int64_t nw : {1, 7, 64, 1000}) {
+            auto cost = [&](const Item &it) { return pass == 0 ? product_cost(it) : residual_cost(it); };
+            std::vector<Item> ord = balanced_order(items, nw, cost);
+            if (mode == 7) ord = items;
+            if (ord.size() != items.size()) return fail("snake order size");
+            std::multiset<int64_t> a, b;
+            for (const Item &it : items) a.insert(it.off);
+            for (const Item &it : ord) b.insert(it.off);
+            if (a != b) return fail("snake order is not a permutation");
+            const int64_t w = std::min<int64_t>(nw, std::max<int64_t>((int64_t)ord.size(), 1));
+            std::vector<int64_t> sum(w, 0);
+            int64_t cmax = 0;
+            for (size_t t = 0; t < ord.size(); ++t) {
+                sum[t % w] += cost(ord[t]);
+                cmax = std::max(cmax, cost(ord[t]));
+            }
+            if (!ord.empty() && *std::max_element(sum.begin(), sum.end()) - *std::min_element(sum.begin(), sum.end()) > cmax)
+                return fail("snake order unbalanced");
+        }
 
     std::printf("ok blocks=%zu ops=%zu units=%zu batches=%zu rows=%zu tchunks=%lld\n", items.size(), T.ops.size(),
                 T.units.size(), T.batches.size(), T.rows.size(), (long long)T.n_tchunk);

@@ -4,8 +4,10 @@ directed products (eq. 6 and eq. 8 with the half storage of §III); the owner-co
 residual takes each once, by output cluster; the tensor-core product's stage-1 batches
 stack each low-rank product's W rows in order, over its own input cluster, into T
 chunks that are each written once, and its second launch holds exactly the directed
-products, in units of at most TC_UNIT_CHUNKS K chunks.  Two damaged list sets must
-fail the same checks."""
+products, in units of at most TC_UNIT_CHUNKS K chunks.  The snake order in which the
+persistent product and residual kernels take their blocks holds each block once, with
+the round-robin warps' cost sums within the largest cost of one another.  Three damaged
+list sets must fail the same checks."""
 import os
 import shutil
 import subprocess
@@ -39,7 +41,7 @@ def test_lists_hold_the_kernels_invariants(checker, seed, mode):
     assert rc == 0 and out.startswith("ok"), out
 
 
-@pytest.mark.parametrize("mode", [5, 6])
+@pytest.mark.parametrize("mode", [5, 6, 7])
 def test_damaged_lists_fail(checker, mode):
     rc, out = run(checker, 1, mode)
     assert rc == 1 and out.startswith("FAIL"), out
